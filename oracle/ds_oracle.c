@@ -1,0 +1,432 @@
+/*
+ * FP64 CPU oracle for the third-order directionally split exponential
+ * Runge-Kutta integrator EXPRK3DS_REAL (Cassini, "Efficient third order
+ * tensor-oriented directional splitting for exponential integrators",
+ * arXiv 2310.07551).
+ *
+ * TEST INFRASTRUCTURE: this file is the plain, slow, independent reference
+ * that the CUDA library is checked against.  Only the test-suite, the smoke
+ * check and the CPU-baseline leg of the benchmark load it; the library
+ * never does, and it shares no code, header or table with the CUDA sources.
+ *
+ * Conventions
+ *   - Tensors are stored with mode 1 fastest (the paper's column-stacking
+ *     vec, Section 2): element (i_1, ..., i_d) at i_1 + n_1 (i_2 + n_2 (...)).
+ *   - Matrices are column-major: L[i + n j] is row i, column j.
+ *   - Dimension arrays list n_1 first.  Everything is IEEE double, built
+ *     without floating-point contraction so x86 and Arm hosts agree.
+ *
+ * Parity status: every function below is pinned by a test in tests/ against
+ * an independent fact (order conditions, explicit Kronecker matrices, dense
+ * expm of the assembled K, scalar closed forms, eigendecomposition,
+ * observed order 3, steady-state invariance); none is "parity unpinned".
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_MAXD 4
+
+/* ------------------------------------------------------------------------ */
+/* Split coefficients.                                                       */
+/* d == 2: Table 1, real columns, "+" sign (Section 2.1 and 2.4).            */
+/* d >= 3: Table 3, "+" sign in alpha_{1,mu}, eta_{2,d} scaled by 2^(d-3)    */
+/*         (Section 2.3).                                                    */
+/* Term i uses phi_{l_i}: l = (1, 2) for d == 2, (1, 2, 1) for d >= 3.       */
+/* alpha is laid out alpha[i * 4 + mu] (mu 0-based).                        */
+/* Returns the number of terms k, or -1 on bad input.                        */
+/* ------------------------------------------------------------------------ */
+int orc_coeffs(int d, int ell, int *ell_i, double *eta, double *alpha)
+{
+    if (d < 2 || d > ORC_MAXD || (ell != 1 && ell != 2)) return -1;
+    memset(alpha, 0, sizeof(double) * 12);
+    if (d == 2) {
+        ell_i[0] = 1; ell_i[1] = 2;
+        if (ell == 1) {
+            double s = sqrt(10.0);
+            eta[0] = -5.0 / 4.0;
+            eta[1] = 9.0;
+            alpha[0 * 4 + 0] = 4.0 * s / 15.0 + 4.0 / 3.0;
+            alpha[0 * 4 + 1] = -4.0 * s / 15.0 + 4.0 / 3.0;
+            alpha[1 * 4 + 0] = 2.0 * s / 9.0 + 16.0 / 9.0;
+            alpha[1 * 4 + 1] = -2.0 * s / 9.0 + 16.0 / 9.0;
+        } else {
+            double s = sqrt(33.0);
+            eta[0] = -4.0 / 3.0;
+            eta[1] = 22.0 / 3.0;
+            alpha[0 * 4 + 0] = s / 8.0 + 9.0 / 8.0;
+            alpha[0 * 4 + 1] = -s / 8.0 + 9.0 / 8.0;
+            alpha[1 * 4 + 0] = 3.0 * s / 22.0 + 3.0 / 2.0;
+            alpha[1 * 4 + 1] = -3.0 * s / 22.0 + 3.0 / 2.0;
+        }
+        return 2;
+    }
+    ell_i[0] = 1; ell_i[1] = 2; ell_i[2] = 1;
+    double scale = ldexp(1.0, d - 3);
+    double a1, a2, a3;
+    if (ell == 1) {
+        double r = sqrt(2991111.0);
+        eta[0] = 2243.0 / 1350.0 + 440521.0 / (675.0 * r);
+        eta[1] = -12544.0 / 675.0 * scale;
+        eta[2] = 2243.0 / 1350.0 - 440521.0 / (675.0 * r);
+        a1 = 3.0 * (5161.0 + r) / 15869.0;
+        a2 = 45.0 / 28.0;
+        a3 = 3.0 * (5161.0 - r) / 15869.0;
+    } else {
+        double r = sqrt(2391.0);
+        eta[0] = 19.0 / 27.0 + 151.0 / (27.0 * r);
+        eta[1] = -196.0 / 27.0 * scale;
+        eta[2] = 19.0 / 27.0 - 151.0 / (27.0 * r);
+        a1 = 3.0 * (121.0 + r) / 490.0;
+        a2 = 9.0 / 7.0;
+        a3 = 3.0 * (121.0 - r) / 490.0;
+    }
+    for (int mu = 0; mu < d; ++mu) {
+        alpha[0 * 4 + mu] = a1;
+        alpha[1 * 4 + mu] = a2;
+        alpha[2 * 4 + mu] = a3;
+    }
+    return 3;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Dense n x n helpers (column-major).                                       */
+/* ------------------------------------------------------------------------ */
+static void mat_mul(int n, const double *A, const double *B, double *C)
+{
+    #pragma omp parallel for schedule(static)
+    for (int j = 0; j < n; ++j) {
+        for (int i = 0; i < n; ++i) {
+            double s = 0.0;
+            for (int q = 0; q < n; ++q) s += A[i + (int64_t)n * q] * B[q + (int64_t)n * j];
+            C[i + (int64_t)n * j] = s;
+        }
+    }
+}
+
+static double norm1(int n, const double *A)
+{
+    double best = 0.0;
+    for (int j = 0; j < n; ++j) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) s += fabs(A[i + (int64_t)n * j]);
+        if (s > best) best = s;
+    }
+    return best;
+}
+
+/* ------------------------------------------------------------------------ */
+/* phi_0 .. phi_lmax of a small dense matrix X (Section 1: the phi-functions */
+/* are the power series sum_k X^k / (k + l)!).  Evaluated by scaling,        */
+/* truncated Taylor series and the modified squaring of Skaflestad & Wright  */
+/* (the paper's [SW09], Section 2.4):                                        */
+/*   choose s >= 0 with ||2^-s X||_1 <= 1/2, Y = 2^-s X,                     */
+/*   phi_k(Y) = sum_{j=0}^{q} Y^j / (j + k)!,  q = 16,                       */
+/*   then s times: phi_0(2Y) = phi_0(Y)^2,                                   */
+/*   phi_k(2Y) = 2^-k [phi_0(Y) phi_k(Y) + sum_{j=1}^{k} phi_j(Y)/(k-j)!].    */
+/* out holds (lmax + 1) column-major n x n matrices.  Returns s, or -1.      */
+/* ------------------------------------------------------------------------ */
+int orc_phi(int n, const double *X, int lmax, double *out)
+{
+    if (n < 1 || lmax < 0 || lmax > 8) return -1;
+    const int q = 16;
+    int64_t nn = (int64_t)n * n;
+    double nrm = norm1(n, X);
+    int s = 0;
+    while (ldexp(nrm, -s) > 0.5) ++s;
+    double *Y = malloc(sizeof(double) * nn);
+    double *Pw = malloc(sizeof(double) * nn);
+    double *T = malloc(sizeof(double) * nn);
+    double *old = malloc(sizeof(double) * nn * (lmax + 1));
+    if (!Y || !Pw || !T || !old) { free(Y); free(Pw); free(T); free(old); return -1; }
+    for (int64_t e = 0; e < nn; ++e) Y[e] = ldexp(X[e], -s);
+
+    /* factorials 0! .. (q + lmax)! */
+    double fact[32];
+    fact[0] = 1.0;
+    for (int j = 1; j < 32; ++j) fact[j] = fact[j - 1] * j;
+
+    memset(out, 0, sizeof(double) * nn * (lmax + 1));
+    /* Pw = Y^0 = I */
+    memset(Pw, 0, sizeof(double) * nn);
+    for (int i = 0; i < n; ++i) Pw[i + (int64_t)n * i] = 1.0;
+    for (int j = 0; j <= q; ++j) {
+        for (int k = 0; k <= lmax; ++k) {
+            double c = 1.0 / fact[j + k];
+            double *o = out + nn * k;
+            for (int64_t e = 0; e < nn; ++e) o[e] += c * Pw[e];
+        }
+        if (j < q) {
+            mat_mul(n, Pw, Y, T);
+            memcpy(Pw, T, sizeof(double) * nn);
+        }
+    }
+    for (int it = 0; it < s; ++it) {
+        memcpy(old, out, sizeof(double) * nn * (lmax + 1));
+        const double *p0 = old;
+        /* phi_0(2Y) = phi_0(Y)^2 */
+        mat_mul(n, p0, p0, out);
+        for (int k = 1; k <= lmax; ++k) {
+            double *o = out + nn * k;
+            mat_mul(n, p0, old + nn * k, o);
+            for (int j = 1; j <= k; ++j) {
+                double c = 1.0 / fact[k - j];
+                const double *pj = old + nn * j;
+                for (int64_t e = 0; e < nn; ++e) o[e] += c * pj[e];
+            }
+            double w = ldexp(1.0, -k);
+            for (int64_t e = 0; e < nn; ++e) o[e] *= w;
+        }
+    }
+    free(Y); free(Pw); free(T); free(old);
+    return s;
+}
+
+/* ------------------------------------------------------------------------ */
+/* mu-mode product S = T x_mu L (Section 2):                                 */
+/*   s_{i_1..i_d} = sum_j t_{i_1..j..i_d} l_{i_mu j}.                        */
+/* mu is 0-based here (mode mu + 1 in the paper).  Plain loops, FP64         */
+/* accumulator, natural j order.                                             */
+/* ------------------------------------------------------------------------ */
+void orc_mode_product(int d, const int64_t *n, const double *X, int mu,
+                      const double *L, double *Y)
+{
+    int64_t I = 1, O = 1, m = n[mu];
+    for (int q = 0; q < mu; ++q) I *= n[q];
+    for (int q = mu + 1; q < d; ++q) O *= n[q];
+    #pragma omp parallel for collapse(2) schedule(static)
+    for (int64_t o = 0; o < O; ++o) {
+        for (int64_t i = 0; i < m; ++i) {
+            for (int64_t x = 0; x < I; ++x) {
+                double s = 0.0;
+                for (int64_t j = 0; j < m; ++j)
+                    s += L[i + m * j] * X[x + I * (j + m * o)];
+                Y[x + I * (i + m * o)] = s;
+            }
+        }
+    }
+}
+
+static int64_t numel(int d, const int64_t *n)
+{
+    int64_t N = 1;
+    for (int q = 0; q < d; ++q) N *= n[q];
+    return N;
+}
+
+/* Tucker operator Y = X x_1 L_1 x_2 ... x_d L_d (Section 2, eq. krontomu). */
+/* L[mu] points to the column-major n_mu x n_mu matrix of mode mu + 1.       */
+int orc_tucker(int d, const int64_t *n, const double *X, const double *const *L, double *Y)
+{
+    int64_t N = numel(d, n);
+    double *a = malloc(sizeof(double) * N), *b = malloc(sizeof(double) * N);
+    if (!a || !b) { free(a); free(b); return -1; }
+    memcpy(a, X, sizeof(double) * N);
+    for (int mu = 0; mu < d; ++mu) {
+        orc_mode_product(d, n, a, mu, L[mu], b);
+        double *t = a; a = b; b = t;
+    }
+    memcpy(Y, a, sizeof(double) * N);
+    free(a); free(b);
+    return 0;
+}
+
+/* Action of the Kronecker sum in tensor form (Section 2.4, eq. kronsumv):   */
+/* Y = sum_mu X x_mu A_mu.  Dense mode products, no stencil.                 */
+int orc_kronsum(int d, const int64_t *n, const double *X, const double *const *A, double *Y)
+{
+    int64_t N = numel(d, n);
+    double *t = malloc(sizeof(double) * N);
+    if (!t) return -1;
+    memset(Y, 0, sizeof(double) * N);
+    for (int mu = 0; mu < d; ++mu) {
+        orc_mode_product(d, n, X, mu, A[mu], t);
+        for (int64_t e = 0; e < N; ++e) Y[e] += t[e];
+    }
+    free(t);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Reaction terms (Section 3 models; parameters as the workloads fix them).  */
+/*   model 0, Schnakenberg, p = (gamma, a, b):                               */
+/*     g_u = gamma (a - u + u^2 v),  g_v = gamma (b - u^2 v)                 */
+/*   model 1, FitzHugh-Nagumo, p = (eps, alpha1, alpha0):                    */
+/*     g_u = u - u^3 - v,            g_v = eps (u - alpha1 v - alpha0)       */
+/*   model 2, linear test problem: g_u = g_v = 0 (pure diffusion).           */
+/* U and G hold the two components back to back, N points each.             */
+/* ------------------------------------------------------------------------ */
+int orc_g(int model, const double *p, int64_t N, const double *U, double *G)
+{
+    if (model < 0 || model > 2) return -1;
+    #pragma omp parallel for schedule(static)
+    for (int64_t e = 0; e < N; ++e) {
+        double u = U[e], v = U[N + e];
+        if (model == 0) {
+            double u2v = u * u * v;
+            G[e] = p[0] * (p[1] - u + u2v);
+            G[N + e] = p[0] * (p[2] - u2v);
+        } else if (model == 1) {
+            G[e] = u - u * u * u - v;
+            G[N + e] = p[0] * (u - p[1] * v - p[2]);
+        } else {
+            G[e] = 0.0;
+            G[N + e] = 0.0;
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* phi-matrix set of Algorithms 1 and 2 ("Needed phi-functions").            */
+/* For component c, slot q, term i and direction mu:                         */
+/*   slot 0: P_{i,2}^{(1)} = phi_{l_i}(tau/3   alpha_{i,mu}^{(1)} A_{c,mu})   */
+/*   slot 1: P_{i,3}^{(1)} = phi_{l_i}(2tau/3  alpha_{i,mu}^{(1)} A_{c,mu})   */
+/*   slot 2: P_{i,3}^{(2)} = phi_{l_i}(2tau/3  alpha_{i,mu}^{(2)} A_{c,mu})   */
+/*   slot 3: P_{i,f}^{(1)} = phi_{l_i}(tau     alpha_{i,mu}^{(1)} A_{c,mu})   */
+/*   slot 4: P_{i,f}^{(2)} = phi_{l_i}(tau     alpha_{i,mu}^{(2)} A_{c,mu})   */
+/* A holds, for c = 0, 1 and mu = 0..d-1 in that order, the column-major     */
+/* n_mu x n_mu matrices A_{c,mu}.  P is written in the order                 */
+/* [c][slot][i][mu], each block n_mu x n_mu, i over k terms.                 */
+/* ------------------------------------------------------------------------ */
+static const double kSlotC[5] = {1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0, 1.0, 1.0};
+static const int kSlotEll[5] = {1, 1, 2, 1, 2};
+
+int64_t orc_phi_set_size(int d, const int64_t *n)
+{
+    int k = (d == 2) ? 2 : 3;
+    int64_t per = 0;
+    for (int mu = 0; mu < d; ++mu) per += n[mu] * n[mu];
+    return 2 * 5 * k * per;
+}
+
+int orc_phi_set(int d, const int64_t *n, const double *A, double tau, double *P)
+{
+    if (d < 2 || d > ORC_MAXD || !(tau > 0.0)) return -1;
+    int ell_i[3]; double eta[3], alpha[2][12];
+    int k = orc_coeffs(d, 1, ell_i, eta, alpha[0]);
+    orc_coeffs(d, 2, ell_i, eta, alpha[1]);
+    int64_t nmax = 0;
+    for (int mu = 0; mu < d; ++mu) if (n[mu] > nmax) nmax = n[mu];
+    double *X = malloc(sizeof(double) * nmax * nmax);
+    double *tmp = malloc(sizeof(double) * nmax * nmax * 3);
+    if (!X || !tmp) { free(X); free(tmp); return -1; }
+    const double *Acur = A;
+    const double *Ac[2][ORC_MAXD];
+    for (int c = 0; c < 2; ++c)
+        for (int mu = 0; mu < d; ++mu) { Ac[c][mu] = Acur; Acur += n[mu] * n[mu]; }
+    double *out = P;
+    for (int c = 0; c < 2; ++c) {
+        for (int q = 0; q < 5; ++q) {
+            for (int i = 0; i < k; ++i) {
+                for (int mu = 0; mu < d; ++mu) {
+                    int64_t m = n[mu], mm = m * m;
+                    double z = kSlotC[q] * tau * alpha[kSlotEll[q] - 1][i * 4 + mu];
+                    for (int64_t e = 0; e < mm; ++e) X[e] = z * Ac[c][mu][e];
+                    if (orc_phi((int)m, X, ell_i[i], tmp) < 0) { free(X); free(tmp); return -1; }
+                    memcpy(out, tmp + mm * ell_i[i], sizeof(double) * mm);
+                    out += mm;
+                }
+            }
+        }
+    }
+    free(X); free(tmp);
+    return 0;
+}
+
+/* Pointer into the phi-set for (c, slot, term i, mu). */
+static const double *pset_at(int d, const int64_t *n, int k, const double *P,
+                             int c, int q, int i, int mu)
+{
+    int64_t per = 0;
+    for (int v = 0; v < d; ++v) per += n[v] * n[v];
+    const double *b = P + ((int64_t)c * 5 + q) * k * per + (int64_t)i * per;
+    for (int v = 0; v < mu; ++v) b += n[v] * n[v];
+    return b;
+}
+
+/* acc += w * sum_i eta_i T(X, {P_{c,q,i,mu}}_mu) */
+static int split_action(int d, const int64_t *n, int k, const double *P, int c, int q,
+                        const double *eta, double w, const double *X, double *acc, double *tmp)
+{
+    int64_t N = numel(d, n);
+    double *s = malloc(sizeof(double) * N);
+    if (!s) return -1;
+    memset(s, 0, sizeof(double) * N);
+    for (int i = 0; i < k; ++i) {
+        const double *L[ORC_MAXD];
+        for (int mu = 0; mu < d; ++mu) L[mu] = pset_at(d, n, k, P, c, q, i, mu);
+        if (orc_tucker(d, n, X, L, tmp) < 0) { free(s); return -1; }
+        for (int64_t e = 0; e < N; ++e) s[e] += eta[i] * tmp[e];
+    }
+    for (int64_t e = 0; e < N; ++e) acc[e] += w * s[e];
+    free(s);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* nsteps steps of EXPRK3DS_REAL (Algorithm 1 for d == 2 with the real       */
+/* Table 1 coefficients, Algorithm 2 for d >= 3 with Table 3), applied to    */
+/* the two-component block system of Section 3 (eq. twocompdisc):            */
+/*   G = g(U), F = K(U) + G                                                  */
+/*   U2 = U + tau/3  S_2^{(1)}(F)                                            */
+/*   D2 = g(U2) - G                                                          */
+/*   U3 = U + 2tau/3 S_3^{(1)}(F) + 4tau/3 S_3^{(2)}(D2)                     */
+/*   D3 = g(U3) - G                                                          */
+/*   U <- U + tau S_f^{(1)}(F) + 3tau/2 S_f^{(2)}(D3)                        */
+/* with S_s^{(l)}(X) = sum_i eta_i^{(l)} T(X, P_{i,s}^{(l)}).  The time      */
+/* argument of g is dropped: both models are autonomous.                     */
+/* A as in orc_phi_set; P from orc_phi_set; U is [2][N] in/out.              */
+/* ------------------------------------------------------------------------ */
+int orc_step(int d, const int64_t *n, const double *A, const double *P,
+             int model, const double *p, double tau, double *U, int nsteps)
+{
+    if (d < 2 || d > ORC_MAXD || nsteps < 0) return -1;
+    int ell_i[3]; double eta1[3], eta2[3], alpha[12];
+    int k = orc_coeffs(d, 1, ell_i, eta1, alpha);
+    orc_coeffs(d, 2, ell_i, eta2, alpha);
+    int64_t N = numel(d, n);
+    const double *Ac[2][ORC_MAXD];
+    const double *Acur = A;
+    for (int c = 0; c < 2; ++c)
+        for (int mu = 0; mu < d; ++mu) { Ac[c][mu] = Acur; Acur += n[mu] * n[mu]; }
+    double *G = malloc(sizeof(double) * 2 * N), *F = malloc(sizeof(double) * 2 * N);
+    double *U2 = malloc(sizeof(double) * 2 * N), *U3 = malloc(sizeof(double) * 2 * N);
+    double *Dt = malloc(sizeof(double) * 2 * N), *Un = malloc(sizeof(double) * 2 * N);
+    double *tmp = malloc(sizeof(double) * N);
+    int rc = -1;
+    if (!G || !F || !U2 || !U3 || !Dt || !Un || !tmp) goto done;
+    for (int step = 0; step < nsteps; ++step) {
+        orc_g(model, p, N, U, G);
+        for (int c = 0; c < 2; ++c) {
+            if (orc_kronsum(d, n, U + c * N, Ac[c], F + c * N) < 0) goto done;
+            for (int64_t e = 0; e < N; ++e) F[c * N + e] += G[c * N + e];
+        }
+        /* stage U_{n2} */
+        memcpy(U2, U, sizeof(double) * 2 * N);
+        for (int c = 0; c < 2; ++c)
+            if (split_action(d, n, k, P, c, 0, eta1, tau / 3.0, F + c * N, U2 + c * N, tmp) < 0) goto done;
+        orc_g(model, p, N, U2, Dt);
+        for (int64_t e = 0; e < 2 * N; ++e) Dt[e] -= G[e];
+        /* stage U_{n3} */
+        memcpy(U3, U, sizeof(double) * 2 * N);
+        for (int c = 0; c < 2; ++c) {
+            if (split_action(d, n, k, P, c, 1, eta1, 2.0 * tau / 3.0, F + c * N, U3 + c * N, tmp) < 0) goto done;
+            if (split_action(d, n, k, P, c, 2, eta2, 4.0 * tau / 3.0, Dt + c * N, U3 + c * N, tmp) < 0) goto done;
+        }
+        orc_g(model, p, N, U3, Dt);
+        for (int64_t e = 0; e < 2 * N; ++e) Dt[e] -= G[e];
+        /* final approximation U_{n+1} */
+        memcpy(Un, U, sizeof(double) * 2 * N);
+        for (int c = 0; c < 2; ++c) {
+            if (split_action(d, n, k, P, c, 3, eta1, tau, F + c * N, Un + c * N, tmp) < 0) goto done;
+            if (split_action(d, n, k, P, c, 4, eta2, 1.5 * tau, Dt + c * N, Un + c * N, tmp) < 0) goto done;
+        }
+        memcpy(U, Un, sizeof(double) * 2 * N);
+    }
+    rc = 0;
+done:
+    free(G); free(F); free(U2); free(U3); free(Dt); free(Un); free(tmp);
+    return rc;
+}

