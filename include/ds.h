@@ -1,0 +1,183 @@
+/*
+ * ds.h -- C ABI of the GB300 (sm_103a) library for third-order directionally
+ * split exponential integrators on Kronecker-sum matrices
+ * (Cassini, "Efficient third order tensor-oriented directional splitting for
+ * exponential integrators", arXiv 2310.07551).
+ *
+ * What the library computes
+ *   The stiff linear part is K = A_d (+) ... (+) A_1 (Section 1, eq. kronsum).
+ *   phi_l(tau K) v is replaced by the directional splits of Section 2
+ *   (Table 1 real coefficients for d = 2, Table 3 for d = 3), each realised
+ *   as Tucker operators, i.e. chained mu-mode products (Section 2,
+ *   eq. krontomu).  These drive the exponential Runge-Kutta scheme EXPRK3
+ *   (Section 2.4, eq. exprk3), i.e. EXPRK3DS_REAL of Algorithms 1 and 2, on
+ *   the two-component block system of Section 3 (eq. twocompdisc).
+ *
+ * Conventions shared by every entry point
+ *   - Tensors: FP64, mode 1 fastest (column-stacking vec of Section 2):
+ *     element (i_1, ..., i_d) sits at i_1 + n_1 (i_2 + n_2 (...)).
+ *     A two-component state is the u tensor followed by the v tensor.
+ *   - Matrices: FP64, column-major, n_mu x n_mu.
+ *   - Device pointers are CUDA device (or managed) addresses on the current
+ *     device; host pointers are ordinary host addresses.
+ *   - Ownership: the caller owns every tensor and matrix it passes; the
+ *     library owns the objects it creates (phi-sets, plans) and their device
+ *     workspaces, and frees them only in the matching *_destroy call.
+ *   - Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *     default stream).  Calls enqueue work and return without waiting,
+ *     except where stated.
+ *   - Errors: every call returns a ds_status; on failure nothing is
+ *     launched, and ds_last_error() gives a message (thread-local).  No C++
+ *     exception crosses the ABI.  There is no CPU fallback: a missing or
+ *     non-sm_103 GPU gives DS_ERR_UNSUPPORTED or DS_ERR_CUDA.
+ *   - Device-side failures (a bounded wait that gave up) are recorded in the
+ *     plan and reported by ds_plan_sync as DS_ERR_TIMEOUT.
+ */
+#ifndef DS3_DS_H
+#define DS3_DS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DS_OK = 0,
+    DS_ERR_INVALID_ARG = 1,   /* bad pointer, size, tau, model, ... */
+    DS_ERR_UNSUPPORTED = 2,   /* valid request this build cannot serve */
+    DS_ERR_OOM = 3,           /* device allocation failed */
+    DS_ERR_CUDA = 4,          /* a CUDA runtime call failed */
+    DS_ERR_NONFINITE = 5,     /* NaN/Inf found in the state */
+    DS_ERR_TIMEOUT = 6        /* a bounded device-side wait gave up */
+} ds_status;
+
+/* Arithmetic of the mu-mode contractions.
+ *   DS_PREC_F64    : FP64 everywhere (FP64 FMA pipe).
+ *   DS_PREC_BF16X6 : each FP32-class operand x is split into three BF16
+ *                    parts x = x0 + x1 + x2; the six partial products of
+ *                    weight >= 2^-16 run on the tcgen05 tensor cores with FP32
+ *                    accumulation in tensor memory.  The state u_{n+1}, the
+ *                    stage sums and the phi-matrices stay FP64. */
+typedef enum { DS_PREC_F64 = 0, DS_PREC_BF16X6 = 1 } ds_precision;
+
+/* Reaction term g of the two-component systems (Section 3).
+ *   DS_SCHNAKENBERG, p = (gamma, a, b):
+ *       g_u = gamma (a - u + u^2 v),  g_v = gamma (b - u^2 v)   (Sect. 3.1)
+ *   DS_FHN (FitzHugh-Nagumo), p = (eps, alpha1, alpha0):
+ *       g_u = u - u^3 - v,            g_v = eps (u - alpha1 v - alpha0)
+ *       (the Section 3.2 model with the reaction written in this form)
+ *   DS_LINEAR: g = 0 (pure linear problem; used to check against exp(tau K)). */
+typedef enum { DS_SCHNAKENBERG = 0, DS_FHN = 1, DS_LINEAR = 2 } ds_model;
+
+/* Grid: d in {2, 3}; n[0] = n_1 (fastest) ... n[d-1] = n_d; n_mu >= 2. */
+typedef struct {
+    int32_t d;
+    int64_t n[4];
+} ds_grid;
+
+typedef struct {
+    int32_t model;   /* ds_model */
+    double p[8];     /* model parameters, see ds_model */
+} ds_params;
+
+typedef struct ds_phi_set ds_phi_set;
+typedef struct ds_plan ds_plan;
+
+/* ds_phi_setup -- the "Needed phi-functions" block of Algorithms 1 and 2.
+ *   For component c in {0, 1}, direction mu, term i (k = 2 terms for d = 2,
+ *   3 for d = 3) it forms, in FP64 on the GPU,
+ *     P_{i,2}^{(1)}{mu} = phi_{l_i}(tau/3  alpha_{i,mu}^{(1)} A_{c,mu})
+ *     P_{i,3}^{(l)}{mu} = phi_{l_i}(2tau/3 alpha_{i,mu}^{(l)} A_{c,mu}), l = 1, 2
+ *     P_{i,f}^{(l)}{mu} = phi_{l_i}(tau    alpha_{i,mu}^{(l)} A_{c,mu}), l = 1, 2
+ *   with the coefficients of Table 1 (real, "+" sign, d = 2) or Table 3
+ *   (d = 3) (Section 2.4 fixes the "+" choice), by scaling, a degree-16
+ *   Taylor series and the modified squaring of Skaflestad & Wright
+ *   (the paper's [SW09]; Section 2.4 uses it with a Pade core).
+ *   A: for c = 0, 1 and mu = 0..d-1, in that order, the column-major
+ *      n_mu x n_mu matrix A_{c,mu}, concatenated (2 sum_mu n_mu^2 doubles).
+ *      a_on_device = 0: host memory; 1: device memory.
+ *   tau: time step, > 0.
+ *   *out: receives a library-owned phi-set (device FP64 matrices plus a copy
+ *      of A).  Synchronous: returns after the set is complete.
+ *   Errors: DS_ERR_INVALID_ARG (d, n, tau, NULL), DS_ERR_NONFINITE (A has
+ *   NaN/Inf), DS_ERR_OOM, DS_ERR_CUDA. */
+ds_status ds_phi_setup(const ds_grid *grid, const double *A, int a_on_device,
+                       double tau, ds_phi_set **out, void *stream);
+
+/* Release a phi-set (NULL is accepted).  Plans created from it must be
+ * destroyed first. */
+ds_status ds_phi_set_destroy(ds_phi_set *set);
+
+/* Copy one phi-matrix to host memory (column-major n_mu x n_mu), for
+ * inspection and tests.  slot: 0 = P_{i,2}^{(1)}, 1 = P_{i,3}^{(1)},
+ * 2 = P_{i,3}^{(2)}, 3 = P_{i,f}^{(1)}, 4 = P_{i,f}^{(2)}.  Synchronous. */
+ds_status ds_phi_get(const ds_phi_set *set, int c, int slot, int term, int mu,
+                     double *host_out);
+
+/* ds_tucker -- Tucker operator Y = X x_1 L_1 x_2 ... x_d L_d (Section 2,
+ * eq. krontomu: equals (L_d (x) ... (x) L_1) vec(X)).
+ *   X, Y: device FP64 tensors of grid's sizes; may not overlap.
+ *   L: host array of d device pointers to column-major n_mu x n_mu FP64
+ *      matrices (L[0] is L_1).
+ *   transpose = 1 uses L_mu^T instead of L_mu (the adjoint operator).
+ *   precision: DS_PREC_F64 or DS_PREC_BF16X6 (the latter needs n_1 % 8 == 0;
+ *      intermediates are FP32, Y is written in FP64).
+ *   Temporary device memory is allocated per call and released before the
+ *   call returns (stream-ordered).
+ *   Errors: DS_ERR_INVALID_ARG, DS_ERR_UNSUPPORTED (precision/shape),
+ *   DS_ERR_OOM, DS_ERR_CUDA. */
+ds_status ds_tucker(const ds_grid *grid, const double *X, double *Y,
+                    const double *const *L, int transpose, int precision, void *stream);
+
+/* ds_kronsum -- Y = K x = vec(sum_mu X x_mu A_mu) (Section 2.4,
+ * eq. kronsumv), FP64, for component c of a phi-set's A.  Tridiagonal A
+ * run as a (2d+1)-point stencil, others as dense mode products. */
+ds_status ds_kronsum(const ds_phi_set *set, int c, const double *X, double *Y, void *stream);
+
+/* ds_plan_create -- bind a phi-set, the reaction model and a precision into
+ * a stepping plan with its device workspace.  Synchronous.
+ *   Errors: DS_ERR_INVALID_ARG (grid does not match the set, unknown model),
+ *   DS_ERR_UNSUPPORTED (precision for this grid: BF16X6 needs n_1 % 8 == 0
+ *   and n_mu >= 16), DS_ERR_OOM. */
+ds_status ds_plan_create(const ds_grid *grid, const ds_params *params,
+                         const ds_phi_set *set, int precision, ds_plan **out);
+
+/* ds_step -- one EXPRK3DS_REAL step (Algorithm 1 for d = 2, Algorithm 2
+ * for d = 3):
+ *   G = g(U), F = K(U) + G
+ *   U2 = U + tau/3 S_2^{(1)}(F),  D2 = g(U2) - G
+ *   U3 = U + 2tau/3 S_3^{(1)}(F) + 4tau/3 S_3^{(2)}(D2),  D3 = g(U3) - G
+ *   U <- U + tau S_f^{(1)}(F) + 3tau/2 S_f^{(2)}(D3)
+ * with S_s^{(l)}(X) = sum_i eta_i^{(l)} T(X, {P_{i,s}^{(l)}{mu}}).
+ *   U: device FP64 two-component state (2 N doubles), updated in place.
+ *   The time argument of g is not used (autonomous models). */
+ds_status ds_step(ds_plan *plan, double *U, void *stream);
+
+/* ds_integrate -- nsteps >= 0 steps of ds_step.  The step is captured once
+ * into a CUDA graph (per U pointer) and replayed, so the loop makes no host
+ * round trips.  Asynchronous. */
+ds_status ds_integrate(ds_plan *plan, double *U, int64_t nsteps, void *stream);
+
+/* ds_plan_sync -- wait for the plan's work and report device-side errors:
+ * DS_ERR_TIMEOUT if a bounded wait gave up, DS_ERR_NONFINITE if check_state
+ * is non-zero and U (may be NULL) holds NaN/Inf. */
+ds_status ds_plan_sync(ds_plan *plan, const double *U, int check_state);
+
+/* Number of the library's own kernel launches enqueued by the last ds_step
+ * (graph replays count the kernels inside the graph). */
+int64_t ds_plan_kernels_per_step(const ds_plan *plan);
+
+ds_status ds_plan_destroy(ds_plan *plan);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *ds_last_error(void);
+
+/* Library version string. */
+const char *ds_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DS3_DS_H */

@@ -1,0 +1,544 @@
+// C ABI entry points: validation, object lifetimes, step orchestration and
+// CUDA-graph replay.  The arithmetic lives in f64.cu and tc.cu.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "ds_internal.h"
+#include "tc.h"
+
+namespace ds {
+
+static thread_local std::string g_err;
+void set_error(const std::string &msg) { g_err = msg; }
+ds_status fail(ds_status st, const std::string &msg)
+{
+    set_error(msg);
+    return st;
+}
+
+// ---------------------------------------------------------------------------
+// Split coefficients from the closed forms of the paper's tables.
+//   d = 2: Table 1, real columns, upper ("+") sign; terms use phi_1, phi_2.
+//   d = 3: Table 3, upper sign in alpha_{1,mu}; terms use phi_1, phi_2,
+//          phi_1; eta_{2,d} carries 2^(d-3); alpha is the same in every mu.
+// ---------------------------------------------------------------------------
+SplitCoeffs split_coeffs(int d, int ell)
+{
+    SplitCoeffs c{};
+    if (d == 2) {
+        c.k = 2;
+        c.ell_i[0] = 1;
+        c.ell_i[1] = 2;
+        if (ell == 1) {
+            const double r10 = sqrt(10.0);
+            c.eta[0] = -1.25;
+            c.eta[1] = 9.0;
+            c.alpha[0][0] = 4.0 / 3.0 + 4.0 * r10 / 15.0;
+            c.alpha[0][1] = 4.0 / 3.0 - 4.0 * r10 / 15.0;
+            c.alpha[1][0] = 16.0 / 9.0 + 2.0 * r10 / 9.0;
+            c.alpha[1][1] = 16.0 / 9.0 - 2.0 * r10 / 9.0;
+        } else {
+            const double r33 = sqrt(33.0);
+            c.eta[0] = -4.0 / 3.0;
+            c.eta[1] = 22.0 / 3.0;
+            c.alpha[0][0] = 9.0 / 8.0 + r33 / 8.0;
+            c.alpha[0][1] = 9.0 / 8.0 - r33 / 8.0;
+            c.alpha[1][0] = 1.5 + 3.0 * r33 / 22.0;
+            c.alpha[1][1] = 1.5 - 3.0 * r33 / 22.0;
+        }
+        return c;
+    }
+    c.k = 3;
+    c.ell_i[0] = 1;
+    c.ell_i[1] = 2;
+    c.ell_i[2] = 1;
+    const double pow2 = ldexp(1.0, d - 3);
+    double e_mid, e_off, a_mid, a_off, eta2, alpha2;
+    if (ell == 1) {
+        const double r = sqrt(2991111.0);
+        e_mid = 2243.0 / 1350.0;
+        e_off = 440521.0 / 675.0 / r;
+        a_mid = 3.0 * 5161.0 / 15869.0;
+        a_off = 3.0 * r / 15869.0;
+        eta2 = -(12544.0 / 675.0) * pow2;
+        alpha2 = 45.0 / 28.0;
+    } else {
+        const double r = sqrt(2391.0);
+        e_mid = 19.0 / 27.0;
+        e_off = 151.0 / 27.0 / r;
+        a_mid = 3.0 * 121.0 / 490.0;
+        a_off = 3.0 * r / 490.0;
+        eta2 = -(196.0 / 27.0) * pow2;
+        alpha2 = 9.0 / 7.0;
+    }
+    c.eta[0] = e_mid + e_off;
+    c.eta[1] = eta2;
+    c.eta[2] = e_mid - e_off;
+    for (int mu = 0; mu < d; ++mu) {
+        c.alpha[0][mu] = a_mid + a_off;
+        c.alpha[1][mu] = alpha2;
+        c.alpha[2][mu] = a_mid - a_off;
+    }
+    return c;
+}
+
+const double kSlotC[kSlots] = {1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0, 1.0, 1.0};
+const int kSlotEll[kSlots] = {1, 1, 2, 1, 2};
+const double kSlotW[kSlots] = {1.0 / 3.0, 2.0 / 3.0, 4.0 / 3.0, 1.0, 1.5};
+
+}  // namespace ds
+
+using namespace ds;
+
+namespace {
+
+int64_t numel(const ds_grid *g)
+{
+    int64_t N = 1;
+    for (int q = 0; q < g->d; ++q) N *= g->n[q];
+    return N;
+}
+
+ds_status check_grid(const ds_grid *g)
+{
+    if (!g) return fail(DS_ERR_INVALID_ARG, "grid is NULL");
+    if (g->d < 2 || g->d > kMaxD) return fail(DS_ERR_INVALID_ARG, "d must be 2 or 3");
+    for (int q = 0; q < g->d; ++q)
+        if (g->n[q] < 2 || g->n[q] > (1 << 20))
+            return fail(DS_ERR_INVALID_ARG, "n_mu must be in [2, 2^20]");
+    if (numel(g) > (int64_t)1 << 34) return fail(DS_ERR_INVALID_ARG, "grid too large");
+    return DS_OK;
+}
+
+ds_status check_device()
+{
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(DS_ERR_CUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+    int major = 0, minor = 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    if (major != 10 || minor != 3)
+        return fail(DS_ERR_UNSUPPORTED, "this library is built for sm_103a (GB300) only");
+    return DS_OK;
+}
+
+bool is_tridiagonal(const double *A, int64_t n)
+{
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t i = 0; i < n; ++i)
+            if ((i > j + 1 || j > i + 1) && A[i + n * j] != 0.0) return false;
+    return true;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Plans.
+// ---------------------------------------------------------------------------
+struct ds_plan {
+    ds_grid grid;
+    int64_t N;
+    int prec;
+    Model model;
+    const ds_phi_set *set;
+    cudaStream_t st = nullptr;            // internal non-blocking stream
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    double *ws = nullptr;                 // FP64 workspace
+    int64_t ws_count = 0;
+    DevStatus *status = nullptr;          // device error word
+    Stencil sten[2];
+    std::map<double *, cudaGraphExec_t> graphs;
+    int64_t launches = 0;
+    tc::MixedPlan *mixed = nullptr;       // tensor-core path state
+};
+
+namespace {
+
+// Enqueue sum_i eta_i T(X_c, {P[c][slot][i][mu]}) into acc (FP64 path).
+int tucker_sum_f64(const ds_plan *p, int c, int slot, const double *X, double *acc, double *t1,
+                   double *t2, cudaStream_t st)
+{
+    const ds_phi_set *s = p->set;
+    const int d = s->d;
+    const SplitCoeffs &co = s->co[kSlotEll[slot] - 1];
+    int launches = 0;
+    for (int i = 0; i < co.k; ++i) {
+        const double *in = X;
+        for (int mu = 0; mu < d; ++mu) {
+            const double *L = s->P_dev + s->P_off[c][slot][i][mu];
+            const bool last = (mu == d - 1);
+            double *out = last ? acc : ((mu % 2 == 0) ? t1 : t2);
+            launch_mode_product_f64(d, s->n, in, mu, L, 0, out, last ? co.eta[i] : 1.0,
+                                    (last && i > 0) ? 1.0 : 0.0, st);
+            ++launches;
+            in = out;
+        }
+    }
+    return launches;
+}
+
+// F = K U + g(U) with dense mode products (A not tridiagonal)
+int rhs_dense_f64(const ds_plan *p, const double *U, double *F, cudaStream_t st)
+{
+    const ds_phi_set *s = p->set;
+    int launches = 0;
+    for (int c = 0; c < 2; ++c)
+        for (int mu = 0; mu < s->d; ++mu) {
+            launch_mode_product_f64(s->d, s->n, U + c * p->N, mu, s->A_dev + s->A_off[c][mu], 0,
+                                    F + c * p->N, 1.0, mu > 0 ? 1.0 : 0.0, st);
+            ++launches;
+        }
+    launch_add_g_f64(p->model, p->N, U, F, st);
+    return launches + 1;
+}
+
+int enqueue_step_f64(ds_plan *p, double *U, cudaStream_t st)
+{
+    const int64_t N = p->N;
+    const double tau = p->set->tau;
+    double *F = p->ws, *a = p->ws + 2 * N, *b = p->ws + 4 * N, *D = p->ws + 6 * N;
+    double *t1 = p->ws + 8 * N, *t2 = p->ws + 9 * N;
+    int L = 0;
+    if (p->set->tridiag[0] && p->set->tridiag[1])
+        L += launch_rhs_f64(p->sten, p->model, N, U, F, st);
+    else
+        L += rhs_dense_f64(p, U, F, st);
+    // stage U_{n2}
+    for (int c = 0; c < 2; ++c) L += tucker_sum_f64(p, c, 0, F + c * N, a + c * N, t1, t2, st);
+    launch_stage_diff_f64(p->model, N, U, a, kSlotW[0] * tau, nullptr, 0.0, D, st);
+    ++L;
+    // stage U_{n3}
+    for (int c = 0; c < 2; ++c) {
+        L += tucker_sum_f64(p, c, 1, F + c * N, a + c * N, t1, t2, st);
+        L += tucker_sum_f64(p, c, 2, D + c * N, b + c * N, t1, t2, st);
+    }
+    launch_stage_diff_f64(p->model, N, U, a, kSlotW[1] * tau, b, kSlotW[2] * tau, D, st);
+    ++L;
+    // final approximation
+    for (int c = 0; c < 2; ++c) {
+        L += tucker_sum_f64(p, c, 3, F + c * N, a + c * N, t1, t2, st);
+        L += tucker_sum_f64(p, c, 4, D + c * N, b + c * N, t1, t2, st);
+    }
+    launch_final_f64(N, U, a, kSlotW[3] * tau, b, kSlotW[4] * tau, st);
+    ++L;
+    return L;
+}
+
+int enqueue_step(ds_plan *p, double *U, cudaStream_t st)
+{
+    if (p->prec == DS_PREC_F64) return enqueue_step_f64(p, U, st);
+    return tc::enqueue_step_mixed(p->mixed, p->set, p->model, p->sten, U, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ds_last_error(void) { return g_err.c_str(); }
+
+const char *ds_version(void) { return "ds3 0.1 (sm_103a)"; }
+
+ds_status ds_phi_setup(const ds_grid *grid, const double *A, int a_on_device, double tau,
+                       ds_phi_set **out, void *stream)
+{
+    try {
+        ds_status r = check_grid(grid);
+        if (r != DS_OK) return r;
+        if (!A || !out) return fail(DS_ERR_INVALID_ARG, "A or out is NULL");
+        if (!(tau > 0.0) || !isfinite(tau)) return fail(DS_ERR_INVALID_ARG, "tau must be finite and > 0");
+        if ((r = check_device()) != DS_OK) return r;
+        cudaStream_t st = (cudaStream_t)stream;
+        const int d = grid->d;
+        int64_t Acount = 0;
+        for (int c = 0; c < 2; ++c)
+            for (int mu = 0; mu < d; ++mu) Acount += grid->n[mu] * grid->n[mu];
+        std::vector<double> hA(Acount);
+        if (a_on_device) {
+            DS_CUDA_TRY(cudaMemcpyAsync(hA.data(), A, sizeof(double) * Acount, cudaMemcpyDeviceToHost, st));
+            DS_CUDA_TRY(cudaStreamSynchronize(st));
+        } else {
+            memcpy(hA.data(), A, sizeof(double) * Acount);
+        }
+        for (int64_t e = 0; e < Acount; ++e)
+            if (!isfinite(hA[e])) return fail(DS_ERR_NONFINITE, "A has a non-finite entry");
+
+        ds_phi_set *s = new (std::nothrow) ds_phi_set();
+        if (!s) return fail(DS_ERR_OOM, "host allocation");
+        s->d = d;
+        for (int q = 0; q < kMaxD; ++q) s->n[q] = q < d ? grid->n[q] : 1;
+        s->tau = tau;
+        s->co[0] = split_coeffs(d, 1);
+        s->co[1] = split_coeffs(d, 2);
+        s->k = s->co[0].k;
+        // A copy + tridiagonal bands
+        int64_t off = 0, toff = 0;
+        for (int c = 0; c < 2; ++c) {
+            s->tridiag[c] = true;
+            for (int mu = 0; mu < d; ++mu) {
+                s->A_off[c][mu] = off;
+                s->tri_off[c][mu] = toff;
+                if (!is_tridiagonal(hA.data() + off, grid->n[mu])) s->tridiag[c] = false;
+                off += grid->n[mu] * grid->n[mu];
+                toff += 3 * grid->n[mu];
+            }
+        }
+        std::vector<double> htri(toff, 0.0);
+        for (int c = 0; c < 2; ++c)
+            for (int mu = 0; mu < d; ++mu) {
+                const int64_t n = grid->n[mu];
+                const double *Am = hA.data() + s->A_off[c][mu];
+                double *lo = htri.data() + s->tri_off[c][mu], *di = lo + n, *up = lo + 2 * n;
+                for (int64_t i = 0; i < n; ++i) {
+                    lo[i] = i > 0 ? Am[i + n * (i - 1)] : 0.0;
+                    di[i] = Am[i + n * i];
+                    up[i] = i + 1 < n ? Am[i + n * (i + 1)] : 0.0;
+                }
+            }
+        // phi-matrix layout [c][slot][i][mu]
+        int64_t poff = 0;
+        for (int c = 0; c < 2; ++c)
+            for (int q = 0; q < kSlots; ++q)
+                for (int i = 0; i < s->k; ++i)
+                    for (int mu = 0; mu < d; ++mu) {
+                        s->P_off[c][q][i][mu] = poff;
+                        poff += grid->n[mu] * grid->n[mu];
+                    }
+        s->P_count = poff;
+        cudaError_t e1 = cudaMalloc(&s->A_dev, sizeof(double) * Acount);
+        cudaError_t e2 = cudaMalloc(&s->tri_dev, sizeof(double) * toff);
+        cudaError_t e3 = cudaMalloc(&s->P_dev, sizeof(double) * poff);
+        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+            cudaGetLastError();
+            ds_phi_set_destroy(s);
+            return fail(DS_ERR_OOM, "phi-set device allocation");
+        }
+        cudaMemcpyAsync(s->A_dev, hA.data(), sizeof(double) * Acount, cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(s->tri_dev, htri.data(), sizeof(double) * toff, cudaMemcpyHostToDevice, st);
+        // group the phi jobs by size
+        std::map<int64_t, std::vector<PhiJob>> groups;
+        for (int c = 0; c < 2; ++c)
+            for (int q = 0; q < kSlots; ++q) {
+                const SplitCoeffs &co = s->co[kSlotEll[q] - 1];
+                for (int i = 0; i < s->k; ++i)
+                    for (int mu = 0; mu < d; ++mu) {
+                        PhiJob j;
+                        j.A = s->A_dev + s->A_off[c][mu];
+                        j.z = kSlotC[q] * tau * co.alpha[i][mu];
+                        j.ell = co.ell_i[i];
+                        j.out = s->P_dev + s->P_off[c][q][i][mu];
+                        groups[grid->n[mu]].push_back(j);
+                    }
+            }
+        for (auto &kv : groups) {
+            r = phi_batch_f64((int)kv.first, kv.second, st);
+            if (r != DS_OK) { ds_phi_set_destroy(s); return r; }
+        }
+        *out = s;
+        return DS_OK;
+    } catch (const std::exception &ex) {
+        return fail(DS_ERR_CUDA, std::string("exception: ") + ex.what());
+    }
+}
+
+ds_status ds_phi_set_destroy(ds_phi_set *s)
+{
+    if (!s) return DS_OK;
+    cudaFree(s->A_dev);
+    cudaFree(s->tri_dev);
+    cudaFree(s->P_dev);
+    delete s;
+    return DS_OK;
+}
+
+ds_status ds_phi_get(const ds_phi_set *s, int c, int slot, int term, int mu, double *host_out)
+{
+    if (!s || !host_out) return fail(DS_ERR_INVALID_ARG, "NULL argument");
+    if (c < 0 || c > 1 || slot < 0 || slot >= kSlots || term < 0 || term >= s->k || mu < 0 || mu >= s->d)
+        return fail(DS_ERR_INVALID_ARG, "index out of range");
+    const int64_t n = s->n[mu];
+    DS_CUDA_TRY(cudaMemcpy(host_out, s->P_dev + s->P_off[c][slot][term][mu], sizeof(double) * n * n,
+                           cudaMemcpyDeviceToHost));
+    return DS_OK;
+}
+
+ds_status ds_tucker(const ds_grid *grid, const double *X, double *Y, const double *const *L,
+                    int transpose, int precision, void *stream)
+{
+    ds_status r = check_grid(grid);
+    if (r != DS_OK) return r;
+    if (!X || !Y || !L) return fail(DS_ERR_INVALID_ARG, "NULL argument");
+    for (int mu = 0; mu < grid->d; ++mu)
+        if (!L[mu]) return fail(DS_ERR_INVALID_ARG, "L[mu] is NULL");
+    if ((r = check_device()) != DS_OK) return r;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t N = numel(grid);
+    const int d = grid->d;
+    if (precision == DS_PREC_BF16X6) return tc::tucker_mixed(grid, X, Y, L, transpose, st);
+    if (precision != DS_PREC_F64) return fail(DS_ERR_UNSUPPORTED, "unknown precision");
+    double *tmp = nullptr;
+    DS_CUDA_TRY(cudaMallocAsync(&tmp, sizeof(double) * N * 2, st));
+    const double *in = X;
+    for (int mu = 0; mu < d; ++mu) {
+        double *out = (mu == d - 1) ? Y : tmp + (mu % 2) * N;
+        launch_mode_product_f64(d, grid->n, in, mu, L[mu], transpose, out, 1.0, 0.0, st);
+        in = out;
+    }
+    cudaFreeAsync(tmp, st);
+    DS_CUDA_TRY(cudaGetLastError());
+    return DS_OK;
+}
+
+ds_status ds_kronsum(const ds_phi_set *s, int c, const double *X, double *Y, void *stream)
+{
+    if (!s || !X || !Y || c < 0 || c > 1) return fail(DS_ERR_INVALID_ARG, "bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int mu = 0; mu < s->d; ++mu)
+        launch_mode_product_f64(s->d, s->n, X, mu, s->A_dev + s->A_off[c][mu], 0, Y, 1.0,
+                                mu > 0 ? 1.0 : 0.0, st);
+    DS_CUDA_TRY(cudaGetLastError());
+    return DS_OK;
+}
+
+ds_status ds_plan_create(const ds_grid *grid, const ds_params *params, const ds_phi_set *set,
+                         int precision, ds_plan **out)
+{
+    try {
+        ds_status r = check_grid(grid);
+        if (r != DS_OK) return r;
+        if (!params || !set || !out) return fail(DS_ERR_INVALID_ARG, "NULL argument");
+        if (grid->d != set->d) return fail(DS_ERR_INVALID_ARG, "grid does not match the phi-set");
+        for (int q = 0; q < grid->d; ++q)
+            if (grid->n[q] != set->n[q]) return fail(DS_ERR_INVALID_ARG, "grid does not match the phi-set");
+        if (params->model < 0 || params->model > 2) return fail(DS_ERR_INVALID_ARG, "unknown model");
+        for (int q = 0; q < 8; ++q)
+            if (!isfinite(params->p[q])) return fail(DS_ERR_INVALID_ARG, "non-finite model parameter");
+        if (precision != DS_PREC_F64 && precision != DS_PREC_BF16X6)
+            return fail(DS_ERR_UNSUPPORTED, "unknown precision");
+        if ((r = check_device()) != DS_OK) return r;
+        ds_plan *p = new (std::nothrow) ds_plan();
+        if (!p) return fail(DS_ERR_OOM, "host allocation");
+        p->grid = *grid;
+        p->N = numel(grid);
+        p->prec = precision;
+        p->model.model = params->model;
+        for (int q = 0; q < 8; ++q) p->model.p[q] = params->p[q];
+        p->set = set;
+        for (int c = 0; c < 2; ++c) {
+            p->sten[c].d = set->d;
+            for (int mu = 0; mu < kMaxD; ++mu) {
+                p->sten[c].n[mu] = mu < set->d ? set->n[mu] : 1;
+                const double *base = set->tri_dev + (mu < set->d ? set->tri_off[c][mu] : 0);
+                p->sten[c].lo[mu] = base;
+                p->sten[c].di[mu] = base + p->sten[c].n[mu];
+                p->sten[c].up[mu] = base + 2 * p->sten[c].n[mu];
+            }
+        }
+        auto cleanup = [&](ds_status st, const char *m) { ds_plan_destroy(p); return fail(st, m); };
+        if (cudaStreamCreateWithFlags(&p->st, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&p->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&p->ev_out, cudaEventDisableTiming) != cudaSuccess)
+            return cleanup(DS_ERR_CUDA, "stream/event creation");
+        if (cudaMalloc(&p->status, sizeof(DevStatus)) != cudaSuccess)
+            return cleanup(DS_ERR_OOM, "status word");
+        cudaMemset(p->status, 0, sizeof(DevStatus));
+        if (precision == DS_PREC_F64) {
+            p->ws_count = 10 * p->N;
+            if (cudaMalloc(&p->ws, sizeof(double) * p->ws_count) != cudaSuccess) {
+                cudaGetLastError();
+                return cleanup(DS_ERR_OOM, "FP64 workspace");
+            }
+        } else {
+            r = tc::mixed_plan_create(grid, set, p->status, &p->mixed);
+            if (r != DS_OK) { ds_plan_destroy(p); return r; }
+        }
+        cudaDeviceSynchronize();
+        *out = p;
+        return DS_OK;
+    } catch (const std::exception &ex) {
+        return fail(DS_ERR_CUDA, std::string("exception: ") + ex.what());
+    }
+}
+
+ds_status ds_step(ds_plan *p, double *U, void *stream)
+{
+    if (!p || !U) return fail(DS_ERR_INVALID_ARG, "NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    p->launches = enqueue_step(p, U, st);
+    if (p->launches < 0) return fail(DS_ERR_CUDA, "step enqueue failed");
+    DS_CUDA_TRY(cudaGetLastError());
+    return DS_OK;
+}
+
+ds_status ds_integrate(ds_plan *p, double *U, int64_t nsteps, void *stream)
+{
+    if (!p || !U || nsteps < 0) return fail(DS_ERR_INVALID_ARG, "bad argument");
+    if (nsteps == 0) return DS_OK;
+    cudaStream_t user = (cudaStream_t)stream;
+    auto it = p->graphs.find(U);
+    if (it == p->graphs.end()) {
+        cudaGraph_t g;
+        DS_CUDA_TRY(cudaStreamBeginCapture(p->st, cudaStreamCaptureModeThreadLocal));
+        int L = enqueue_step(p, U, p->st);
+        cudaError_t e = cudaStreamEndCapture(p->st, &g);
+        if (e != cudaSuccess || L < 0)
+            return fail(DS_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        p->launches = L;
+        cudaGraphExec_t ex;
+        e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail(DS_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+        it = p->graphs.emplace(U, ex).first;
+    }
+    DS_CUDA_TRY(cudaEventRecord(p->ev_in, user));
+    DS_CUDA_TRY(cudaStreamWaitEvent(p->st, p->ev_in, 0));
+    for (int64_t s = 0; s < nsteps; ++s) DS_CUDA_TRY(cudaGraphLaunch(it->second, p->st));
+    DS_CUDA_TRY(cudaEventRecord(p->ev_out, p->st));
+    DS_CUDA_TRY(cudaStreamWaitEvent(user, p->ev_out, 0));
+    return DS_OK;
+}
+
+ds_status ds_plan_sync(ds_plan *p, const double *U, int check_state)
+{
+    if (!p) return fail(DS_ERR_INVALID_ARG, "NULL plan");
+    DS_CUDA_TRY(cudaStreamSynchronize(p->st));
+    DS_CUDA_TRY(cudaDeviceSynchronize());
+    if (check_state && U) {
+        launch_nonfinite_scan(U, 2 * p->N, &p->status->nonfinite, p->st);
+        DS_CUDA_TRY(cudaStreamSynchronize(p->st));
+    }
+    DevStatus h{};
+    DS_CUDA_TRY(cudaMemcpy(&h, p->status, sizeof(h), cudaMemcpyDeviceToHost));
+    if (h.timeout)
+        return fail(DS_ERR_TIMEOUT, "a tensor-core pipeline wait gave up (site " + std::to_string(h.where) + ")");
+    if (h.nonfinite) {
+        cudaMemset(&p->status->nonfinite, 0, sizeof(int));
+        return fail(DS_ERR_NONFINITE, "state holds NaN/Inf");
+    }
+    return DS_OK;
+}
+
+int64_t ds_plan_kernels_per_step(const ds_plan *p) { return p ? p->launches : -1; }
+
+ds_status ds_plan_destroy(ds_plan *p)
+{
+    if (!p) return DS_OK;
+    if (p->st) cudaStreamSynchronize(p->st);
+    for (auto &kv : p->graphs) cudaGraphExecDestroy(kv.second);
+    if (p->mixed) tc::mixed_plan_destroy(p->mixed);
+    cudaFree(p->ws);
+    cudaFree(p->status);
+    if (p->ev_in) cudaEventDestroy(p->ev_in);
+    if (p->ev_out) cudaEventDestroy(p->ev_out);
+    if (p->st) cudaStreamDestroy(p->st);
+    delete p;
+    return DS_OK;
+}
+
+}  // extern "C"

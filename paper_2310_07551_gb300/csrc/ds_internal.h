@@ -1,0 +1,120 @@
+// Internal declarations of the ds3 CUDA library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ds.h"
+
+namespace ds {
+
+constexpr int kMaxD = 3;      // d in {2, 3}
+constexpr int kSlots = 5;     // (s2,l1) (s3,l1) (s3,l2) (sf,l1) (sf,l2)
+constexpr int kMaxTerms = 3;
+
+// Split coefficients of one target function phi_l (Section 2 tables).
+struct SplitCoeffs {
+    int k;                    // number of terms
+    int ell_i[kMaxTerms];     // phi index of each term
+    double eta[kMaxTerms];
+    double alpha[kMaxTerms][kMaxD];
+};
+SplitCoeffs split_coeffs(int d, int ell);
+
+// Stage scalar c_s of each slot and target l of each slot.
+extern const double kSlotC[kSlots];
+extern const int kSlotEll[kSlots];
+// Weight multiplying S_s^{(l)} in the step: tau/3, 2tau/3, 4tau/3, tau, 3tau/2 (x tau).
+extern const double kSlotW[kSlots];
+
+// Error helpers ----------------------------------------------------------
+void set_error(const std::string &msg);
+ds_status fail(ds_status st, const std::string &msg);
+#define DS_CUDA_TRY(expr)                                                             \
+    do {                                                                              \
+        cudaError_t _e = (expr);                                                      \
+        if (_e != cudaSuccess)                                                        \
+            return ::ds::fail(_e == cudaErrorMemoryAllocation ? DS_ERR_OOM : DS_ERR_CUDA, \
+                              std::string(#expr) + ": " + cudaGetErrorString(_e));   \
+    } while (0)
+
+// Strided batched FP64 GEMM: C[b] = alpha * A[b] B[b] + beta * C[b] ------
+struct DGemm {
+    int M, N, K, batch;
+    const double *A; int64_t sAm, sAk, sAb;
+    const double *B; int64_t sBk, sBn, sBb;
+    double *C; int64_t sCm, sCn, sCb;
+    double alpha, beta;
+};
+void launch_dgemm(const DGemm &g, cudaStream_t st);
+
+// One FP64 mu-mode product Y = X x_mu L (+ beta Y), any mode, as a GEMM.
+// L column-major n_mu x n_mu; transpose uses L^T.
+void launch_mode_product_f64(int d, const int64_t *n, const double *X, int mu, const double *L,
+                             int transpose, double *Y, double alpha, double beta, cudaStream_t st);
+
+// Reaction model ---------------------------------------------------------
+struct Model {
+    int model;
+    double p[8];
+};
+
+// Stencil description of K for one component (tridiagonal A_mu only).
+struct Stencil {
+    int d;
+    int64_t n[kMaxD];
+    const double *lo[kMaxD], *di[kMaxD], *up[kMaxD];   // device arrays of length n_mu
+};
+
+// F = K U + g(U) for both components (FP64, stencil).  Returns #launches.
+int launch_rhs_f64(const Stencil *st2, const Model &m, int64_t N, const double *U, double *F,
+                   cudaStream_t st);
+// D = g(U + w1 a (+ w2 b)) - g(U); b may be null.
+void launch_stage_diff_f64(const Model &m, int64_t N, const double *U, const double *a, double w1,
+                           const double *b, double w2, double *D, cudaStream_t st);
+// U <- (U + w1 a) + w2 b
+void launch_final_f64(int64_t N, double *U, const double *a, double w1, const double *b,
+                      double w2, cudaStream_t st);
+void launch_add_g_f64(const Model &m, int64_t N, const double *U, double *F, cudaStream_t st);
+
+// phi-function evaluation (batched) -------------------------------------
+struct PhiJob {
+    const double *A;   // device, column-major n x n
+    double z;          // scalar multiplying A
+    int ell;           // phi index wanted
+    double *out;       // device destination n x n column-major
+};
+ds_status phi_batch_f64(int n, const std::vector<PhiJob> &jobs, cudaStream_t st);
+
+// Non-finite scan: sets *flag (device int) to 1 if any entry is NaN/Inf.
+void launch_nonfinite_scan(const double *x, int64_t count, int *flag, cudaStream_t st);
+
+// Device-side error word shared by the bounded waits of the tensor-core kernels.
+struct DevStatus {
+    int timeout;       // set to 1 by a wait that gave up
+    int where;         // which wait
+    int nonfinite;
+    int pad;
+};
+
+}  // namespace ds
+
+// Library-owned objects ---------------------------------------------------
+struct ds_phi_set {
+    int d;
+    int64_t n[ds::kMaxD];
+    int k;
+    double tau;
+    ds::SplitCoeffs co[2];                  // [l-1]
+    double *A_dev = nullptr;                // copy of A, column-major blocks
+    int64_t A_off[2][ds::kMaxD];
+    bool tridiag[2];                        // every A_{c,mu} tridiagonal
+    double *tri_dev = nullptr;              // [c][mu][3][n_mu]
+    int64_t tri_off[2][ds::kMaxD];
+    double *P_dev = nullptr;                // FP64 phi-matrices, column-major blocks
+    int64_t P_off[2][ds::kSlots][ds::kMaxTerms][ds::kMaxD];
+    int64_t P_count = 0;
+};

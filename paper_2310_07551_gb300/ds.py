@@ -1,0 +1,195 @@
+"""Thin Python binding of the ds3 C ABI (include/ds.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  PyTorch supplies device memory and streams.  If the compiled
+library is missing this module raises at import of `lib()`: there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libds3.so")
+
+DS_OK, DS_ERR_INVALID_ARG, DS_ERR_UNSUPPORTED, DS_ERR_OOM, DS_ERR_CUDA, DS_ERR_NONFINITE, DS_ERR_TIMEOUT = range(7)
+STATUS_NAMES = ["DS_OK", "DS_ERR_INVALID_ARG", "DS_ERR_UNSUPPORTED", "DS_ERR_OOM", "DS_ERR_CUDA",
+                "DS_ERR_NONFINITE", "DS_ERR_TIMEOUT"]
+PREC = {"f64": 0, "bf16x6": 1}
+MODELS = {"schnakenberg": 0, "fhn": 1, "linear": 2}
+
+
+class DsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 7 else status}: {msg}")
+        self.status = status
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int32), ("n", ctypes.c_int64 * 4)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int32), ("p", ctypes.c_double * 8)]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"CUDA library not built: {LIB_PATH} (run __graft_entry__.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        gp, pp = ctypes.POINTER(Grid), ctypes.POINTER(Params)
+        sig = {
+            "ds_phi_setup": ([gp, _vp, ctypes.c_int, ctypes.c_double, ctypes.POINTER(_vp), _vp], ctypes.c_int),
+            "ds_phi_set_destroy": ([_vp], ctypes.c_int),
+            "ds_phi_get": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp], ctypes.c_int),
+            "ds_tucker": ([gp, _vp, _vp, ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, _vp], ctypes.c_int),
+            "ds_kronsum": ([_vp, ctypes.c_int, _vp, _vp, _vp], ctypes.c_int),
+            "ds_plan_create": ([gp, pp, _vp, ctypes.c_int, ctypes.POINTER(_vp)], ctypes.c_int),
+            "ds_step": ([_vp, _vp, _vp], ctypes.c_int),
+            "ds_integrate": ([_vp, _vp, ctypes.c_int64, _vp], ctypes.c_int),
+            "ds_plan_sync": ([_vp, _vp, ctypes.c_int], ctypes.c_int),
+            "ds_plan_kernels_per_step": ([_vp], ctypes.c_int64),
+            "ds_plan_destroy": ([_vp], ctypes.c_int),
+            "ds_last_error": ([], ctypes.c_char_p),
+            "ds_version": ([], ctypes.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def check(status: int):
+    if status != DS_OK:
+        raise DsError(status, lib().ds_last_error().decode())
+
+
+def make_grid(dims) -> Grid:
+    g = Grid()
+    g.d = len(dims)
+    for q, n in enumerate(dims):
+        g.n[q] = int(n)
+    return g
+
+
+def _stream_ptr(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dptr(t) -> ctypes.c_void_p:
+    import torch
+    assert isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def pack_A(As) -> np.ndarray:
+    """As[c][mu] as (n, n) arrays -> concatenated column-major blocks (the
+    ds_phi_setup layout)."""
+    return np.concatenate([np.ascontiguousarray(np.asarray(As[c][mu], dtype=np.float64).T).ravel()
+                           for c in range(2) for mu in range(len(As[c]))])
+
+
+class PhiSet:
+    """ds_phi_set: FP64 phi-matrices of Algorithms 1/2 for both components."""
+
+    def __init__(self, dims, As, tau: float, stream=None):
+        self.dims = tuple(int(n) for n in dims)
+        self.grid = make_grid(self.dims)
+        self.tau = float(tau)
+        host = pack_A(As)
+        self._h = _vp()
+        check(lib().ds_phi_setup(ctypes.byref(self.grid), host.ctypes.data_as(_vp), 0, self.tau,
+                                 ctypes.byref(self._h), _stream_ptr(stream)))
+
+    def get(self, c: int, slot: int, term: int, mu: int) -> np.ndarray:
+        n = self.dims[mu]
+        out = np.empty(n * n)
+        check(lib().ds_phi_get(self._h, c, slot, term, mu, out.ctypes.data_as(_dp)))
+        return out.reshape(n, n).T.copy()
+
+    def kronsum(self, c: int, X, stream=None):
+        import torch
+        Y = torch.empty_like(X)
+        check(lib().ds_kronsum(self._h, c, _dptr(X), _dptr(Y), _stream_ptr(stream)))
+        return Y
+
+    def close(self):
+        if self._h:
+            lib().ds_phi_set_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Plan:
+    """ds_plan: an EXPRK3DS_REAL stepper bound to a phi-set and a model."""
+
+    def __init__(self, phiset: PhiSet, model: str, p, precision: str = "f64"):
+        self.phiset = phiset
+        self.dims = phiset.dims
+        self.precision = precision
+        prm = Params()
+        prm.model = MODELS[model]
+        for q, v in enumerate(p):
+            prm.p[q] = float(v)
+        self._h = _vp()
+        check(lib().ds_plan_create(ctypes.byref(phiset.grid), ctypes.byref(prm), phiset._h,
+                                   PREC[precision], ctypes.byref(self._h)))
+
+    def step(self, U, stream=None):
+        check(lib().ds_step(self._h, _dptr(U), _stream_ptr(stream)))
+        return U
+
+    def integrate(self, U, nsteps: int, stream=None):
+        check(lib().ds_integrate(self._h, _dptr(U), int(nsteps), _stream_ptr(stream)))
+        return U
+
+    def sync(self, U=None, check_state: bool = False):
+        check(lib().ds_plan_sync(self._h, _dptr(U) if U is not None else None, int(check_state)))
+
+    @property
+    def kernels_per_step(self) -> int:
+        return int(lib().ds_plan_kernels_per_step(self._h))
+
+    def close(self):
+        if self._h:
+            lib().ds_plan_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tucker(X, Ls, transpose: bool = False, precision: str = "f64", stream=None):
+    """Y = X x_1 L_1 ... x_d L_d on the GPU; X shape (n_d, ..., n_1) float64
+    CUDA tensor; Ls[mu] (n_mu, n_mu) float64 CUDA tensors (row/col as usual)."""
+    import torch
+    dims = tuple(reversed(X.shape))
+    g = make_grid(dims)
+    cm = [L.t().contiguous() for L in Ls]   # column-major storage
+    arr = (_vp * len(cm))(*[c.data_ptr() for c in cm])
+    Y = torch.empty_like(X)
+    check(lib().ds_tucker(ctypes.byref(g), _dptr(X), _dptr(Y), arr, int(transpose), PREC[precision],
+                          _stream_ptr(stream)))
+    return Y
