@@ -168,6 +168,20 @@ ds_status ds_plan_sync(ds_plan *plan, const double *U, int check_state);
  * (graph replays count the kernels inside the graph). */
 int64_t ds_plan_kernels_per_step(const ds_plan *plan);
 
+/* ds_plan_profile -- when enable != 0, every later ds_step (not the graph
+ * replay of ds_integrate) records a CUDA event pair around each of the
+ * library's kernel launches, on the stream the kernel is launched on.  The
+ * events add a few microseconds per launch. */
+ds_status ds_plan_profile(ds_plan *plan, int enable);
+
+/* ds_plan_profile_read -- wait for the recorded events and return, per
+ * launch kind k (0 = tensor-core mode products, 1 = FP64 mode products,
+ * 2 = pointwise kernels), the summed device time ms[k] (milliseconds), the
+ * launch count launches[k] and the useful floating-point operations
+ * flops[k] (2 N n_mu per mode product, FP32-class or FP64 as the kind
+ * says).  Arrays have 3 entries each.  Clears the records. */
+ds_status ds_plan_profile_read(ds_plan *plan, double *ms, int64_t *launches, double *flops);
+
 ds_status ds_plan_destroy(ds_plan *plan);
 
 /* Message of the last failed call on this thread ("" if none). */

@@ -157,12 +157,14 @@ struct ds_plan {
     std::map<double *, cudaGraphExec_t> graphs;
     int64_t launches = 0;
     tc::MixedPlan *mixed = nullptr;       // tensor-core path state
+    Prof prof;                            // optional per-launch event timing
+    bool profiling = false;               // ds_step records events when set
 };
 
 namespace {
 
 // Enqueue sum_i eta_i T(X_c, {P[c][slot][i][mu]}) into acc (FP64 path).
-int tucker_sum_f64(const ds_plan *p, int c, int slot, const double *X, double *acc, double *t1,
+int tucker_sum_f64(ds_plan *p, int c, int slot, const double *X, double *acc, double *t1,
                    double *t2, cudaStream_t st)
 {
     const ds_phi_set *s = p->set;
@@ -175,8 +177,10 @@ int tucker_sum_f64(const ds_plan *p, int c, int slot, const double *X, double *a
             const double *L = s->P_dev + s->P_off[c][slot][i][mu];
             const bool last = (mu == d - 1);
             double *out = last ? acc : ((mu % 2 == 0) ? t1 : t2);
+            p->prof.begin(st, 1, 2.0 * (double)p->N * (double)s->n[mu]);
             launch_mode_product_f64(d, s->n, in, mu, L, 0, out, last ? co.eta[i] : 1.0,
                                     (last && i > 0) ? 1.0 : 0.0, st);
+            p->prof.end(st);
             ++launches;
             in = out;
         }
@@ -231,10 +235,16 @@ int enqueue_step_f64(ds_plan *p, double *U, cudaStream_t st)
     return L;
 }
 
-int enqueue_step(ds_plan *p, double *U, cudaStream_t st)
+int enqueue_step(ds_plan *p, double *U, cudaStream_t st, bool profile)
 {
-    if (p->prec == DS_PREC_F64) return enqueue_step_f64(p, U, st);
-    return tc::enqueue_step_mixed(p->mixed, p->set, p->model, p->sten, U, st);
+    p->prof.on = profile;
+    int L;
+    if (p->prec == DS_PREC_F64)
+        L = enqueue_step_f64(p, U, st);
+    else
+        L = tc::enqueue_step_mixed(p->mixed, p->set, p->model, p->sten, U, st, &p->prof);
+    p->prof.on = false;
+    return L;
 }
 
 }  // namespace
@@ -470,7 +480,7 @@ ds_status ds_step(ds_plan *p, double *U, void *stream)
 {
     if (!p || !U) return fail(DS_ERR_INVALID_ARG, "NULL argument");
     cudaStream_t st = (cudaStream_t)stream;
-    p->launches = enqueue_step(p, U, st);
+    p->launches = enqueue_step(p, U, st, p->profiling);
     if (p->launches < 0) return fail(DS_ERR_CUDA, "step enqueue failed");
     DS_CUDA_TRY(cudaGetLastError());
     return DS_OK;
@@ -485,7 +495,7 @@ ds_status ds_integrate(ds_plan *p, double *U, int64_t nsteps, void *stream)
     if (it == p->graphs.end()) {
         cudaGraph_t g;
         DS_CUDA_TRY(cudaStreamBeginCapture(p->st, cudaStreamCaptureModeThreadLocal));
-        int L = enqueue_step(p, U, p->st);
+        int L = enqueue_step(p, U, p->st, false);
         cudaError_t e = cudaStreamEndCapture(p->st, &g);
         if (e != cudaSuccess || L < 0)
             return fail(DS_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
@@ -525,6 +535,31 @@ ds_status ds_plan_sync(ds_plan *p, const double *U, int check_state)
 }
 
 int64_t ds_plan_kernels_per_step(const ds_plan *p) { return p ? p->launches : -1; }
+
+ds_status ds_plan_profile(ds_plan *p, int enable)
+{
+    if (!p) return fail(DS_ERR_INVALID_ARG, "NULL plan");
+    p->profiling = enable != 0;
+    return DS_OK;
+}
+
+ds_status ds_plan_profile_read(ds_plan *p, double *ms, int64_t *launches, double *flops)
+{
+    if (!p || !ms || !launches || !flops) return fail(DS_ERR_INVALID_ARG, "NULL argument");
+    for (int k = 0; k < 3; ++k) { ms[k] = 0.0; launches[k] = 0; flops[k] = 0.0; }
+    for (auto &r : p->prof.recs) {
+        DS_CUDA_TRY(cudaEventSynchronize(r.b));
+        float t = 0.f;
+        DS_CUDA_TRY(cudaEventElapsedTime(&t, r.a, r.b));
+        ms[r.kind] += t;
+        launches[r.kind] += 1;
+        flops[r.kind] += r.flops;
+        p->prof.pool.push_back(r.a);
+        p->prof.pool.push_back(r.b);
+    }
+    p->prof.recs.clear();
+    return DS_OK;
+}
 
 ds_status ds_plan_destroy(ds_plan *p)
 {

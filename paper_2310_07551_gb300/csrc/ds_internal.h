@@ -92,6 +92,47 @@ ds_status phi_batch_f64(int n, const std::vector<PhiJob> &jobs, cudaStream_t st)
 // Non-finite scan: sets *flag (device int) to 1 if any entry is NaN/Inf.
 void launch_nonfinite_scan(const double *x, int64_t count, int *flag, cudaStream_t st);
 
+// Optional per-launch timing with CUDA events on the launching stream.
+// kind: 0 = tensor-core mode product, 1 = FP64 mode product, 2 = pointwise.
+struct Prof {
+    struct Rec {
+        cudaEvent_t a, b;
+        int kind;
+        double flops;
+    };
+    bool on = false;
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
+    cudaEvent_t take()
+    {
+        if (pool.empty()) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            return e;
+        }
+        cudaEvent_t e = pool.back();
+        pool.pop_back();
+        return e;
+    }
+    void begin(cudaStream_t st, int kind, double flops)
+    {
+        if (!on) return;
+        Rec r{take(), take(), kind, flops};
+        cudaEventRecord(r.a, st);
+        recs.push_back(r);
+    }
+    void end(cudaStream_t st)
+    {
+        if (!on || recs.empty()) return;
+        cudaEventRecord(recs.back().b, st);
+    }
+    ~Prof()
+    {
+        for (auto &r : recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
+
 // Device-side error word shared by the bounded waits of the tensor-core kernels.
 struct DevStatus {
     int timeout;       // set to 1 by a wait that gave up

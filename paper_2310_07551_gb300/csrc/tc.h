@@ -14,7 +14,7 @@ void mixed_plan_destroy(MixedPlan *mp);
 // Enqueue one EXPRK3DS_REAL step on the split-BF16 path; returns the number
 // of kernel launches, or -1 on failure.
 int enqueue_step_mixed(MixedPlan *mp, const ds_phi_set *set, const Model &model,
-                       const Stencil *sten, double *U, cudaStream_t st);
+                       const Stencil *sten, double *U, cudaStream_t st, Prof *prof);
 ds_status tucker_mixed(const ds_grid *grid, const double *X, double *Y, const double *const *L,
                        int transpose, cudaStream_t st);
 

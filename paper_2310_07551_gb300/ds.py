@@ -59,6 +59,8 @@ def lib() -> ctypes.CDLL:
             "ds_integrate": ([_vp, _vp, ctypes.c_int64, _vp], ctypes.c_int),
             "ds_plan_sync": ([_vp, _vp, ctypes.c_int], ctypes.c_int),
             "ds_plan_kernels_per_step": ([_vp], ctypes.c_int64),
+            "ds_plan_profile": ([_vp, ctypes.c_int], ctypes.c_int),
+            "ds_plan_profile_read": ([_vp, _dp, ctypes.POINTER(ctypes.c_int64), _dp], ctypes.c_int),
             "ds_plan_destroy": ([_vp], ctypes.c_int),
             "ds_last_error": ([], ctypes.c_char_p),
             "ds_version": ([], ctypes.c_char_p),
@@ -164,6 +166,17 @@ class Plan:
 
     def sync(self, U=None, check_state: bool = False):
         check(lib().ds_plan_sync(self._h, _dptr(U) if U is not None else None, int(check_state)))
+
+    def profile(self, enable: bool = True):
+        check(lib().ds_plan_profile(self._h, int(enable)))
+
+    def profile_read(self):
+        """{kind: (ms, launches, useful_flops)} for kinds 'tc', 'f64', 'pointwise'."""
+        ms = (ctypes.c_double * 3)()
+        n = (ctypes.c_int64 * 3)()
+        fl = (ctypes.c_double * 3)()
+        check(lib().ds_plan_profile_read(self._h, ms, n, fl))
+        return {k: (ms[i], n[i], fl[i]) for i, k in enumerate(("tc", "f64", "pointwise"))}
 
     @property
     def kernels_per_step(self) -> int:

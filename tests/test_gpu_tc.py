@@ -1,0 +1,89 @@
+"""GPU parity of the split-BF16 tensor-core path (tcgen05) against the FP64
+oracle, through the C ABI.
+
+Error model: each operand is held as three BF16 parts (representation error
+<= 2^-24 relative), the three dropped partial products have weight <= 2^-24,
+and the contraction accumulates in FP32.  So a mode product errs by a few
+2^-24 * sum |a||b| per element; tolerances are stated against the Tucker
+operator of the absolute values, the natural scale of that error."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O
+from paper_2310_07551_gb300 import configs, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ds():
+    from paper_2310_07551_gb300 import ds as _ds
+    _ds.lib()
+    return _ds
+
+
+def problem(dims, lo, hi, delta):
+    Ds = [inputs.fd_neumann(n, lo, hi) for n in dims]
+    return [[delta[c] * D for D in Ds] for c in range(2)]
+
+
+# shapes: several 128x256 tiles, ragged tails in every mode, mode-1 n not a
+# multiple of the 32-wide K chunk, inner sizes below the 64-wide TMA box
+SHAPES = [(64, 64), (136, 40), (32, 24, 16), (64, 48, 40), (40, 33, 70), (256, 256), (96, 72, 20)]
+
+
+@pytest.mark.parametrize("dims", SHAPES)
+@pytest.mark.parametrize("transpose", [0, 1])
+def test_tucker_bf16x6_matches_oracle(ds, dims, transpose):
+    X = inputs.random_tensor(dims, seed=11)
+    Ls = [inputs.random_matrix(n, seed=12, stream=q) for q, n in enumerate(dims)]
+    Lu = [L.T if transpose else L for L in Ls]
+    ref = O.tucker(X, Lu)
+    scale = O.tucker(np.abs(X), [np.abs(L) for L in Lu])
+    got = ds.tucker(torch.from_numpy(X).cuda(), [torch.from_numpy(L).cuda() for L in Ls],
+                    transpose=bool(transpose), precision="bf16x6").cpu().numpy()
+    err = np.max(np.abs(got - ref) / scale)
+    assert err < 1e-5, err
+
+
+def test_tucker_bf16x6_rejects_unaligned_n1(ds):
+    X = torch.zeros((4, 5, 12), dtype=torch.float64, device="cuda")
+    Ls = [torch.eye(n, dtype=torch.float64, device="cuda") for n in (12, 5, 4)]
+    with pytest.raises(ds.DsError) as e:
+        ds.tucker(X, Ls, precision="bf16x6")
+    assert e.value.status == ds.DS_ERR_UNSUPPORTED
+
+
+def run_mixed(ds, dims, lo, hi, delta, model, p, tau, U0, m):
+    As = problem(dims, lo, hi, delta)
+    ref = O.step(dims, As, O.phi_set(dims, As, tau), model, p, tau, U0, m)
+    ps = ds.PhiSet(dims, As, tau)
+    plan = ds.Plan(ps, model, p, "bf16x6")
+    U = torch.from_numpy(U0.copy()).cuda()
+    plan.integrate(U, m)
+    plan.sync(U, check_state=True)
+    return U.cpu().numpy(), ref
+
+
+def relmax(a, b):
+    return max(np.abs(a[c] - b[c]).max() / np.abs(b[c]).max() for c in range(2))
+
+
+@pytest.mark.parametrize("dims,m", [((32, 24, 16), 5), ((40, 33, 70), 3)])
+def test_fhn_3d_mixed_step(ds, dims, m):
+    U0 = inputs.initial_state("fhn", dims, seed=1)
+    got, ref = run_mixed(ds, dims, -1.0, 1.0, (1.0, 42.1887), "fhn", (0.1, 2.0, -0.1), 1e-3, U0, m)
+    err = relmax(got, ref)
+    print("fhn3d mixed rel err", dims, err)
+    assert err < 1e-6, err
+
+
+def test_schnakenberg_64_mixed_full_horizon(ds):
+    w = configs.WORKLOADS["schnak2d_64"]
+    U0 = inputs.initial_state("schnakenberg", w.dims, seed=w.seed)
+    got, ref = run_mixed(ds, w.dims, w.lo, w.hi, w.delta, "schnakenberg", w.params, w.tau, U0, w.steps)
+    err = relmax(got, ref)
+    print("schnak64 mixed rel err", err)
+    assert err < 1e-6, err
