@@ -54,12 +54,15 @@ typedef enum {
 
 /* Arithmetic of the mu-mode contractions.
  *   DS_PREC_F64    : FP64 everywhere (FP64 FMA pipe).
+ *   DS_PREC_F32    : FP32 mode products on the CUDA cores (FP32 FMA, FP32
+ *                    intermediates and stage sums), FP64 state -- the
+ *                    design of the paper's single-precision GPU runs.
  *   DS_PREC_BF16X6 : each FP32-class operand x is split into three BF16
  *                    parts x = x0 + x1 + x2; the six partial products of
  *                    weight >= 2^-16 run on the tcgen05 tensor cores with FP32
  *                    accumulation in tensor memory.  The state u_{n+1}, the
  *                    stage sums and the phi-matrices stay FP64. */
-typedef enum { DS_PREC_F64 = 0, DS_PREC_BF16X6 = 1 } ds_precision;
+typedef enum { DS_PREC_F64 = 0, DS_PREC_BF16X6 = 1, DS_PREC_F32 = 2 } ds_precision;
 
 /* Reaction term g of the two-component systems (Section 3).
  *   DS_SCHNAKENBERG, p = (gamma, a, b):
@@ -121,8 +124,9 @@ ds_status ds_phi_get(const ds_phi_set *set, int c, int slot, int term, int mu,
  *   L: host array of d device pointers to column-major n_mu x n_mu FP64
  *      matrices (L[0] is L_1).
  *   transpose = 1 uses L_mu^T instead of L_mu (the adjoint operator).
- *   precision: DS_PREC_F64 or DS_PREC_BF16X6 (the latter needs n_1 % 8 == 0;
- *      intermediates are FP32, Y is written in FP64).
+ *   precision: DS_PREC_F64, DS_PREC_F32 or DS_PREC_BF16X6 (the latter needs
+ *      n_1 % 8 == 0; for both reduced precisions intermediates are FP32 and
+ *      Y is written in FP64).
  *   Temporary device memory is allocated per call and released before the
  *   call returns (stream-ordered).
  *   Errors: DS_ERR_INVALID_ARG, DS_ERR_UNSUPPORTED (precision/shape),

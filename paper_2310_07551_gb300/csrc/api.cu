@@ -152,6 +152,8 @@ struct ds_plan {
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     double *ws = nullptr;                 // FP64 workspace
     int64_t ws_count = 0;
+    float *ws32 = nullptr;                // FP32 path workspace
+    float *P32 = nullptr;                 // FP32 copies of the phi-matrices
     DevStatus *status = nullptr;          // device error word
     Stencil sten[2];
     std::map<double *, cudaGraphExec_t> graphs;
@@ -235,12 +237,73 @@ int enqueue_step_f64(ds_plan *p, double *U, cudaStream_t st)
     return L;
 }
 
+// FP32 CUDA-core path: same sequence as the FP64 path with FP32 operands
+int tucker_sum_f32(ds_plan *p, int c, int slot, const float *X, float *acc, float *t1, float *t2,
+                   cudaStream_t st)
+{
+    const ds_phi_set *s = p->set;
+    const int d = s->d;
+    const SplitCoeffs &co = s->co[kSlotEll[slot] - 1];
+    int launches = 0;
+    for (int i = 0; i < co.k; ++i) {
+        const float *in = X;
+        for (int mu = 0; mu < d; ++mu) {
+            const float *L = p->P32 + s->P_off[c][slot][i][mu];
+            const bool last = (mu == d - 1);
+            float *out = last ? acc : ((mu % 2 == 0) ? t1 : t2);
+            p->prof.begin(st, 1, 2.0 * (double)p->N * (double)s->n[mu]);
+            launch_mode_product_f32(d, s->n, in, mu, L, 0, out, last ? co.eta[i] : 1.0,
+                                    (last && i > 0) ? 1.0 : 0.0, st);
+            p->prof.end(st);
+            ++launches;
+            in = out;
+        }
+    }
+    return launches;
+}
+
+int enqueue_step_f32(ds_plan *p, double *U, cudaStream_t st)
+{
+    const int64_t N = p->N;
+    const double tau = p->set->tau;
+    float *F = p->ws32, *a = F + 2 * N, *b = F + 4 * N, *D = F + 6 * N, *t1 = F + 8 * N, *t2 = F + 9 * N;
+    int L = 0;
+    p->prof.begin(st, 2, 0.0);
+    tc::launch_rhs_f32(p->sten, p->model, N, U, F, st);
+    p->prof.end(st);
+    ++L;
+    for (int c = 0; c < 2; ++c) L += tucker_sum_f32(p, c, 0, F + c * N, a + c * N, t1, t2, st);
+    p->prof.begin(st, 2, 0.0);
+    tc::launch_stage_f32(p->model, N, U, a, kSlotW[0] * tau, nullptr, 0.0, D, st);
+    p->prof.end(st);
+    ++L;
+    for (int c = 0; c < 2; ++c) {
+        L += tucker_sum_f32(p, c, 1, F + c * N, a + c * N, t1, t2, st);
+        L += tucker_sum_f32(p, c, 2, D + c * N, b + c * N, t1, t2, st);
+    }
+    p->prof.begin(st, 2, 0.0);
+    tc::launch_stage_f32(p->model, N, U, a, kSlotW[1] * tau, b, kSlotW[2] * tau, D, st);
+    p->prof.end(st);
+    ++L;
+    for (int c = 0; c < 2; ++c) {
+        L += tucker_sum_f32(p, c, 3, F + c * N, a + c * N, t1, t2, st);
+        L += tucker_sum_f32(p, c, 4, D + c * N, b + c * N, t1, t2, st);
+    }
+    p->prof.begin(st, 2, 0.0);
+    tc::launch_final_f32(N, U, a, kSlotW[3] * tau, b, kSlotW[4] * tau, st);
+    p->prof.end(st);
+    ++L;
+    return L;
+}
+
 int enqueue_step(ds_plan *p, double *U, cudaStream_t st, bool profile)
 {
     p->prof.on = profile;
     int L;
     if (p->prec == DS_PREC_F64)
         L = enqueue_step_f64(p, U, st);
+    else if (p->prec == DS_PREC_F32)
+        L = enqueue_step_f32(p, U, st);
     else
         L = tc::enqueue_step_mixed(p->mixed, p->set, p->model, p->sten, U, st, &p->prof);
     p->prof.on = false;
@@ -391,6 +454,27 @@ ds_status ds_tucker(const ds_grid *grid, const double *X, double *Y, const doubl
     const int64_t N = numel(grid);
     const int d = grid->d;
     if (precision == DS_PREC_BF16X6) return tc::tucker_mixed(grid, X, Y, L, transpose, st);
+    if (precision == DS_PREC_F32) {
+        int64_t pm = 0;
+        for (int mu = 0; mu < d; ++mu) pm += grid->n[mu] * grid->n[mu];
+        float *w = nullptr;
+        DS_CUDA_TRY(cudaMallocAsync(&w, sizeof(float) * (3 * N + pm), st));
+        float *x32 = w, *b0 = w + N, *b1 = w + 2 * N, *l32 = w + 3 * N;
+        tc::launch_convert_f64_f32(N, X, x32, st);
+        const float *in = x32;
+        float *pl = l32;
+        for (int mu = 0; mu < d; ++mu) {
+            tc::launch_convert_f64_f32(grid->n[mu] * grid->n[mu], L[mu], pl, st);
+            float *out = (mu % 2 == 0) ? b0 : b1;
+            launch_mode_product_f32(d, grid->n, in, mu, pl, transpose, out, 1.0, 0.0, st);
+            in = out;
+            pl += grid->n[mu] * grid->n[mu];
+        }
+        tc::launch_convert_f32_f64(N, in, Y, st);
+        cudaFreeAsync(w, st);
+        DS_CUDA_TRY(cudaGetLastError());
+        return DS_OK;
+    }
     if (precision != DS_PREC_F64) return fail(DS_ERR_UNSUPPORTED, "unknown precision");
     double *tmp = nullptr;
     DS_CUDA_TRY(cudaMallocAsync(&tmp, sizeof(double) * N * 2, st));
@@ -429,7 +513,7 @@ ds_status ds_plan_create(const ds_grid *grid, const ds_params *params, const ds_
         if (params->model < 0 || params->model > 2) return fail(DS_ERR_INVALID_ARG, "unknown model");
         for (int q = 0; q < 8; ++q)
             if (!isfinite(params->p[q])) return fail(DS_ERR_INVALID_ARG, "non-finite model parameter");
-        if (precision != DS_PREC_F64 && precision != DS_PREC_BF16X6)
+        if (precision != DS_PREC_F64 && precision != DS_PREC_BF16X6 && precision != DS_PREC_F32)
             return fail(DS_ERR_UNSUPPORTED, "unknown precision");
         if ((r = check_device()) != DS_OK) return r;
         ds_plan *p = new (std::nothrow) ds_plan();
@@ -464,6 +548,13 @@ ds_status ds_plan_create(const ds_grid *grid, const ds_params *params, const ds_
                 cudaGetLastError();
                 return cleanup(DS_ERR_OOM, "FP64 workspace");
             }
+        } else if (precision == DS_PREC_F32) {
+            if (cudaMalloc(&p->ws32, sizeof(float) * 10 * p->N) != cudaSuccess ||
+                cudaMalloc(&p->P32, sizeof(float) * set->P_count) != cudaSuccess) {
+                cudaGetLastError();
+                return cleanup(DS_ERR_OOM, "FP32 workspace");
+            }
+            tc::launch_convert_f64_f32(set->P_count, set->P_dev, p->P32, 0);
         } else {
             r = tc::mixed_plan_create(grid, set, p->status, &p->mixed);
             if (r != DS_OK) { ds_plan_destroy(p); return r; }
@@ -568,6 +659,8 @@ ds_status ds_plan_destroy(ds_plan *p)
     for (auto &kv : p->graphs) cudaGraphExecDestroy(kv.second);
     if (p->mixed) tc::mixed_plan_destroy(p->mixed);
     cudaFree(p->ws);
+    cudaFree(p->ws32);
+    cudaFree(p->P32);
     cudaFree(p->status);
     if (p->ev_in) cudaEventDestroy(p->ev_in);
     if (p->ev_out) cudaEventDestroy(p->ev_out);

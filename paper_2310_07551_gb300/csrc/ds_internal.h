@@ -50,6 +50,16 @@ struct DGemm {
     double alpha, beta;
 };
 void launch_dgemm(const DGemm &g, cudaStream_t st);
+struct SGemm {
+    int M, N, K, batch;
+    const float *A; int64_t sAm, sAk, sAb;
+    const float *B; int64_t sBk, sBn, sBb;
+    float *C; int64_t sCm, sCn, sCb;
+    double alpha, beta;
+};
+void launch_sgemm(const SGemm &g, cudaStream_t st);
+void launch_mode_product_f32(int d, const int64_t *n, const float *X, int mu, const float *L,
+                             int transpose, float *Y, double alpha, double beta, cudaStream_t st);
 
 // One FP64 mu-mode product Y = X x_mu L (+ beta Y), any mode, as a GEMM.
 // L column-major n_mu x n_mu; transpose uses L^T.

@@ -11,7 +11,8 @@
 namespace ds {
 
 // ---------------------------------------------------------------------------
-// Strided batched DGEMM.  64x64 output tile, K chunks of 16, 256 threads,
+// Strided batched GEMM (FP64, and FP32 for the CUDA-core FP32 path).
+// 64x64 output tile, K chunks of 16, 256 threads,
 // 4x4 outputs per thread.  GB300's FP64 pipe is narrow, so the kernel is
 // built to keep it fed rather than to save bandwidth: each operand tile is
 // staged once in shared memory with whichever index has unit stride mapped
@@ -20,25 +21,26 @@ namespace ds {
 namespace {
 constexpr int BM = 64, BN = 64, BK = 16;
 
-__global__ void __launch_bounds__(256) k_dgemm(DGemm g)
+template <typename T, typename G>
+__global__ void __launch_bounds__(256) k_gemm(G g)
 {
-    __shared__ double As[BK][BM + 1];
-    __shared__ double Bs[BK][BN + 1];
+    __shared__ T As[BK][BM + 1];
+    __shared__ T Bs[BK][BN + 1];
     const int t = threadIdx.x;
     const int tx = t % 16, ty = t / 16;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     const int b = blockIdx.z;
-    const double *A = g.A + (int64_t)b * g.sAb;
-    const double *B = g.B + (int64_t)b * g.sBb;
-    double *C = g.C + (int64_t)b * g.sCb;
+    const T *A = g.A + (int64_t)b * g.sAb;
+    const T *B = g.B + (int64_t)b * g.sBb;
+    T *C = g.C + (int64_t)b * g.sCb;
     const bool a_m_fast = (g.sAm == 1);
     const bool b_n_fast = (g.sBn == 1);
 
-    double acc[4][4];
+    T acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
 
     for (int k0 = 0; k0 < g.K; k0 += BK) {
 #pragma unroll
@@ -47,16 +49,16 @@ __global__ void __launch_bounds__(256) k_dgemm(DGemm g)
             int mm, kk;
             if (a_m_fast) { mm = e % BM; kk = e / BM; } else { kk = e % BK; mm = e / BK; }
             int gm = m0 + mm, gk = k0 + kk;
-            As[kk][mm] = (gm < g.M && gk < g.K) ? A[gm * g.sAm + gk * g.sAk] : 0.0;
+            As[kk][mm] = (gm < g.M && gk < g.K) ? A[gm * g.sAm + gk * g.sAk] : T(0);
             int nn, kb;
             if (b_n_fast) { nn = e % BN; kb = e / BN; } else { kb = e % BK; nn = e / BK; }
             int gn = n0 + nn, gkb = k0 + kb;
-            Bs[kb][nn] = (gn < g.N && gkb < g.K) ? B[gkb * g.sBk + gn * g.sBn] : 0.0;
+            Bs[kb][nn] = (gn < g.N && gkb < g.K) ? B[gkb * g.sBk + gn * g.sBn] : T(0);
         }
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
-            double a[4], bb[4];
+            T a[4], bb[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
@@ -76,9 +78,9 @@ __global__ void __launch_bounds__(256) k_dgemm(DGemm g)
         for (int j = 0; j < 4; ++j) {
             int gn = n0 + tx + 16 * j;
             if (gn >= g.N) continue;
-            double *c = C + gm * g.sCm + gn * g.sCn;
-            double v = g.alpha * acc[i][j];
-            if (g.beta != 0.0) v = __dadd_rn(v, g.beta * *c);
+            T *c = C + gm * g.sCm + gn * g.sCn;
+            T v = (T)g.alpha * acc[i][j];
+            if (g.beta != 0.0) v = v + (T)g.beta * *c;
             *c = v;
         }
     }
@@ -89,7 +91,38 @@ void launch_dgemm(const DGemm &g, cudaStream_t st)
 {
     if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return;
     dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, g.batch);
-    k_dgemm<<<grid, 256, 0, st>>>(g);
+    k_gemm<double, DGemm><<<grid, 256, 0, st>>>(g);
+}
+
+void launch_sgemm(const SGemm &g, cudaStream_t st)
+{
+    if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return;
+    dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, g.batch);
+    k_gemm<float, SGemm><<<grid, 256, 0, st>>>(g);
+}
+
+void launch_mode_product_f32(int d, const int64_t *n, const float *X, int mu, const float *L,
+                             int transpose, float *Y, double alpha, double beta, cudaStream_t st)
+{
+    int64_t I = 1, O = 1, m = n[mu];
+    for (int q = 0; q < mu; ++q) I *= n[q];
+    for (int q = mu + 1; q < d; ++q) O *= n[q];
+    const int64_t sLi = transpose ? m : 1, sLj = transpose ? 1 : m;
+    SGemm g{};
+    g.alpha = alpha;
+    g.beta = beta;
+    if (mu == 0) {
+        g.M = (int)O; g.N = (int)m; g.K = (int)m; g.batch = 1;
+        g.A = X; g.sAm = m; g.sAk = 1; g.sAb = 0;
+        g.B = L; g.sBk = sLj; g.sBn = sLi; g.sBb = 0;
+        g.C = Y; g.sCm = m; g.sCn = 1; g.sCb = 0;
+    } else {
+        g.M = (int)m; g.N = (int)I; g.K = (int)m; g.batch = (int)O;
+        g.A = L; g.sAm = sLi; g.sAk = sLj; g.sAb = 0;
+        g.B = X; g.sBk = I; g.sBn = 1; g.sBb = I * m;
+        g.C = Y; g.sCm = I; g.sCn = 1; g.sCb = I * m;
+    }
+    launch_sgemm(g, st);
 }
 
 void launch_mode_product_f64(int d, const int64_t *n, const double *X, int mu, const double *L,

@@ -599,6 +599,78 @@ static int pw_grid(int64_t n)
     return (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
 }
 
+// ---- FP32 CUDA-core path (plain FP32 mode products; FP64 state) ----------
+__global__ void k_rhs_f32(Stencil s0, Stencil s1, Model m, int64_t N, const double *__restrict__ U,
+                          float *__restrict__ F)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < N;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        double gu, gv;
+        react_d(m, U[p], U[N + p], gu, gv);
+        F[p] = (float)(stencil_k(s0, U, p) + gu);
+        F[N + p] = (float)(stencil_k(s1, U + N, p) + gv);
+    }
+}
+__global__ void k_stage_f32(Model m, int64_t N, const double *__restrict__ U, const float *__restrict__ a,
+                            float w1, const float *__restrict__ b, float w2, float *__restrict__ D)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < N;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const float u = (float)U[p], v = (float)U[N + p];
+        float du = w1 * a[p], dv = w1 * a[N + p];
+        if (b) {
+            du += w2 * b[p];
+            dv += w2 * b[N + p];
+        }
+        float Du, Dv;
+        react_diff(m, u, v, du, dv, Du, Dv);
+        D[p] = Du;
+        D[N + p] = Dv;
+    }
+}
+__global__ void k_final_f32(int64_t n2, double *__restrict__ U, const float *__restrict__ a, double w1,
+                            const float *__restrict__ b, double w2)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n2;
+         p += (int64_t)gridDim.x * blockDim.x)
+        U[p] = (U[p] + w1 * (double)a[p]) + w2 * (double)b[p];
+}
+__global__ void k_cvt_d2f(int64_t n, const double *__restrict__ x, float *__restrict__ y)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x)
+        y[p] = (float)x[p];
+}
+__global__ void k_cvt_f2d(int64_t n, const float *__restrict__ x, double *__restrict__ y)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x)
+        y[p] = (double)x[p];
+}
+void launch_rhs_f32(const Stencil *sten, const Model &m, int64_t N, const double *U, float *F,
+                    cudaStream_t st)
+{
+    k_rhs_f32<<<pw_grid(N), 256, 0, st>>>(sten[0], sten[1], m, N, U, F);
+}
+void launch_stage_f32(const Model &m, int64_t N, const double *U, const float *a, double w1,
+                      const float *b, double w2, float *D, cudaStream_t st)
+{
+    k_stage_f32<<<pw_grid(N), 256, 0, st>>>(m, N, U, a, (float)w1, b, (float)w2, D);
+}
+void launch_final_f32(int64_t N, double *U, const float *a, double w1, const float *b, double w2,
+                      cudaStream_t st)
+{
+    k_final_f32<<<pw_grid(2 * N), 256, 0, st>>>(2 * N, U, a, w1, b, w2);
+}
+void launch_convert_f64_f32(int64_t n, const double *x, float *y, cudaStream_t st)
+{
+    k_cvt_d2f<<<pw_grid(n), 256, 0, st>>>(n, x, y);
+}
+void launch_convert_f32_f64(int64_t n, const float *x, double *y, cudaStream_t st)
+{
+    k_cvt_f2d<<<pw_grid(n), 256, 0, st>>>(n, x, y);
+}
+
 // ---------------------------------------------------------------------------
 // Host side: tensor maps and launch descriptors.
 // ---------------------------------------------------------------------------

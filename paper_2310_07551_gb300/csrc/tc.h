@@ -15,6 +15,15 @@ void mixed_plan_destroy(MixedPlan *mp);
 // of kernel launches, or -1 on failure.
 int enqueue_step_mixed(MixedPlan *mp, const ds_phi_set *set, const Model &model,
                        const Stencil *sten, double *U, cudaStream_t st, Prof *prof);
+// FP32 CUDA-core path pointwise kernels (two components, N points each)
+void launch_rhs_f32(const Stencil *sten, const Model &m, int64_t N, const double *U, float *F,
+                    cudaStream_t st);
+void launch_stage_f32(const Model &m, int64_t N, const double *U, const float *a, double w1,
+                      const float *b, double w2, float *D, cudaStream_t st);
+void launch_final_f32(int64_t N, double *U, const float *a, double w1, const float *b, double w2,
+                      cudaStream_t st);
+void launch_convert_f64_f32(int64_t n, const double *x, float *y, cudaStream_t st);
+void launch_convert_f32_f64(int64_t n, const float *x, double *y, cudaStream_t st);
 ds_status tucker_mixed(const ds_grid *grid, const double *X, double *Y, const double *const *L,
                        int transpose, cudaStream_t st);
 
