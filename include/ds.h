@@ -134,6 +134,30 @@ ds_status ds_phi_get(const ds_phi_set *set, int c, int slot, int term, int mu,
 ds_status ds_tucker(const ds_grid *grid, const double *X, double *Y,
                     const double *const *L, int transpose, int precision, void *stream);
 
+/* ds_tucker_static -- the FP64 Tucker operator of ds_tucker (same result,
+ * same kernels) for callers that cannot allocate device memory when they
+ * need it: code running inside an allocator or memory-pool callback, hosts
+ * that forbid allocation after start-up, plugins whose framework owns the
+ * device heap.  The paper has no counterpart; this is a property of the
+ * library, not of the method.
+ *   It allocates nothing.  Its two intermediate tensors live in one fixed
+ *   device array inside the library (16 MiB: two FP64 tensors of up to
+ *   1,048,576 points), which every GPU that loads the library holds until
+ *   the process exits.  Grids with more than 1,048,576 points are rejected
+ *   with DS_ERR_INVALID_ARG; use ds_tucker for them.
+ *   The first call on each device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture on the device.
+ *   All calls on a device share the array and it keeps the last call's
+ *   contents; every intermediate is fully overwritten, so nothing needs
+ *   clearing.  Calls whose work overlaps on the GPU (different streams,
+ *   or host threads without ordering) race on the array and must be
+ *   serialised by the caller.
+ *   Arguments, layouts and the other errors are those of ds_tucker with
+ *   precision DS_PREC_F64.  Asynchronous on `stream`. */
+ds_status ds_tucker_static(const ds_grid *grid, const double *X, double *Y,
+                           const double *const *L, int transpose, void *stream);
+
 /* ds_kronsum -- Y = K x = vec(sum_mu X x_mu A_mu) (Section 2.4,
  * eq. kronsumv), FP64, for component c of a phi-set's A.  Tridiagonal A
  * run as a (2d+1)-point stencil, others as dense mode products. */

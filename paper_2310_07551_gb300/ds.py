@@ -54,6 +54,7 @@ def lib() -> ctypes.CDLL:
             "ds_phi_get": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp], ctypes.c_int),
             "ds_tucker": ([gp, _vp, _vp, ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, _vp], ctypes.c_int),
             "ds_kronsum": ([_vp, ctypes.c_int, _vp, _vp, _vp], ctypes.c_int),
+            "ds_tucker_static": ([gp, _vp, _vp, ctypes.POINTER(_vp), ctypes.c_int, _vp], ctypes.c_int),
             "ds_plan_create": ([gp, pp, _vp, ctypes.c_int, ctypes.POINTER(_vp)], ctypes.c_int),
             "ds_step": ([_vp, _vp, _vp], ctypes.c_int),
             "ds_integrate": ([_vp, _vp, ctypes.c_int64, _vp], ctypes.c_int),
@@ -205,4 +206,19 @@ def tucker(X, Ls, transpose: bool = False, precision: str = "f64", stream=None):
     Y = torch.empty_like(X)
     check(lib().ds_tucker(ctypes.byref(g), _dptr(X), _dptr(Y), arr, int(transpose), PREC[precision],
                           _stream_ptr(stream)))
+    return Y
+
+
+def tucker_static(X, Ls, transpose: bool = False, stream=None):
+    """FP64 Tucker operator through ds_tucker_static, the entry point that
+    allocates no device memory (its intermediates live in a fixed device
+    array of the library; grids of at most 1,048,576 points)."""
+    import torch
+    dims = tuple(reversed(X.shape))
+    g = make_grid(dims)
+    cm = [L.t().contiguous() for L in Ls]   # column-major storage
+    arr = (_vp * len(cm))(*[c.data_ptr() for c in cm])
+    Y = torch.empty_like(X)
+    check(lib().ds_tucker_static(ctypes.byref(g), _dptr(X), _dptr(Y), arr, int(transpose),
+                                 _stream_ptr(stream)))
     return Y
