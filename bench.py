@@ -1,13 +1,16 @@
 """Throughput benchmark of the EXPRK3DS_REAL step on one GB300 (or N replicas).
 
-Default workload: 3D FitzHugh-Nagumo on a 256^3 grid (tau = 1e-3), split-BF16
-tensor-core mode products with the FP64 state.  A "step" is one time step of
-the scheme (Kronecker-sum action + reaction, the three Tucker-operator groups
-and the stage updates); the phi-matrix setup runs once before timing and is
-reported separately.
+Default workload: 2D Schnakenberg on a 1024^2 grid (tau = 1e-4, 1000-step
+horizon), split-BF16 tensor-core mode products with the FP64 state; the error
+against the FP64 GPU path is measured over the full horizon.  --workload
+fhn3d_256 runs the 3D FitzHugh-Nagumo 256^3 case.  A "step" is one time step
+of the scheme (Kronecker-sum action + reaction, the three Tucker-operator
+groups and the stage updates); the phi-matrix setup runs once before timing
+and is reported separately.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload fhn3d_256] [--precision bf16x6|f64]
+                  [--workload schnak2d_1024|fhn3d_256|...] [--precision bf16x6|f32|f64]
+                  [--err-steps E]   (default: the workload's horizon; 0 skips)
 
 Under torchrun each rank runs an independent replica on its own GPU (the
 split step has no data-path exchange), timing is the max over ranks and the
@@ -78,9 +81,9 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
 
-    def stop(self):
+    def stop(self, t0: float | None = None, t1: float | None = None):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -92,7 +95,11 @@ class ClockSampler:
             self.thread.join(timeout=2)
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        lines = self.lines
+        if t0 is not None:
+            inside = [x for x in lines if t0 - 0.05 <= x[0] <= t1 + 0.15]
+            lines = inside if inside else lines[-2:]
+        for _, ln in lines:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -107,6 +114,21 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def job_rate(t_local: float, points_per_rank: int, steps: int, dist=None, device=None):
+    """Whole-job rate of N independent replicas: every rank times its own K
+    steps; the job time is the max over ranks, the work the sum over ranks.
+    Returns (value, t_max)."""
+    import torch
+    world = 1
+    t = t_local
+    if dist is not None and dist.is_initialized():
+        world = dist.get_world_size()
+        tt = torch.tensor([t_local], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    return world * points_per_rank * steps / t, t
 
 
 def _problem(w):
@@ -173,21 +195,116 @@ def run_reference(args, w, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args, rank, world):
+    """64 independent Schnakenberg instances with uneven grids, stepped
+    together by one CUDA graph per 10 steps (one captured stream per
+    instance).  value = sum of the instances' grid points x steps / time."""
+    import numpy as np
+    import torch
+
+    from paper_2310_07551_gb300 import configs, ds, inputs
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    insts = configs.batch_instances()
+    As = []
+    for inst in insts:
+        Ds = [inputs.fd_neumann(n, 0.0, 1.0) for n in inst.dims]
+        As.append([[dl * D for D in Ds] for dl in inst.delta])
+    t0 = time.perf_counter()
+    batch = ds.Batch([i.dims for i in insts], As, [i.tau for i in insts], "schnakenberg",
+                     [i.params for i in insts], args.precision)
+    setup_s = time.perf_counter() - t0
+    U0 = [inputs.initial_state("schnakenberg", i.dims, seed=7 + k, a=i.params[1], b=i.params[2])
+          for k, i in enumerate(insts)]
+    Us = [torch.from_numpy(u.copy()).cuda() for u in U0]
+    npts = sum(int(np.prod(i.dims)) for i in insts)
+    batch.integrate(Us, args.warmup)
+    batch.sync()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if args.steps <= 0:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        batch.integrate(Us, 10)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        per = e0.elapsed_time(e1) / 1e4
+        args.steps = max(30, int(1.5 / max(per, 1e-6)) // 10 * 10)
+    clocks = ClockSampler(local)
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    t_wall0 = time.time()
+    e0.record(stream)
+    batch.integrate(Us, args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_wall1 = time.time()
+    clk = clocks.stop(t_wall0, t_wall1)
+    batch.sync()
+    t = e0.elapsed_time(e1) / 1e3
+    value = npts * args.steps / t
+    useful = sum(40.0 * np.prod(i.dims) * sum(i.dims) for i in insts)   # flops per batch step
+    err = None
+    if args.precision != "f64" and args.err_steps != 0:
+        m = configs.BATCH_STEPS if args.err_steps < 0 else args.err_steps
+        b64 = ds.Batch([i.dims for i in insts], As, [i.tau for i in insts], "schnakenberg",
+                       [i.params for i in insts], "f64")
+        Ua = [torch.from_numpy(u.copy()).cuda() for u in U0]
+        Ub = [torch.from_numpy(u.copy()).cuda() for u in U0]
+        batch.integrate(Ua, m)
+        b64.integrate(Ub, m)
+        batch.sync()
+        b64.sync()
+        err = max(float((a[c] - b[c]).abs().max() / b[c].abs().max()) for a, b in zip(Ua, Ub) for c in range(2))
+        b64.close()
+        err = {"value": err, "steps": m, "reduction": "max over instances and components"}
+    peaks, peak_src = _peaks()
+    tensor_tf = 6.0 * useful * args.steps / t / 1e12 if args.precision == "bf16x6" else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+        "config": {"workload": "batch64", "instances": len(insts), "grid_points": npts,
+                   "precision": args.precision, "state": "fp64", "phi_setup_s": setup_s,
+                   "l2": "L2 not flushed (batch state 2.3 GB of FP64 > L2)"},
+        "rel_err_vs_fp64": err,
+        "roofline": {"bound": "tensor", "achieved": tensor_tf, "peak": peaks["bf16_tflops_sustained"],
+                     "unit": "TFLOP/s", "frac": tensor_tf / peaks["bf16_tflops_sustained"] if tensor_tf else None,
+                     "traffic": None, "kernel": "whole batch step (all instances' kernels)",
+                     "peak_source": f"{peak_src} bf16_tflops_sustained"},
+        "gpu_launches": batch.kernels_per_step * args.steps,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    batch.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=0,
+                    help="timed steps (default: enough for about 1.5 s of timed work)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="fhn3d_256")
-    ap.add_argument("--precision", default="bf16x6", choices=["bf16x6", "f64"])
-    ap.add_argument("--err-steps", type=int, default=2)
+    ap.add_argument("--workload", default="schnak2d_1024")
+    ap.add_argument("--precision", default="bf16x6", choices=["bf16x6", "f32", "f64"])
+    ap.add_argument("--err-steps", type=int, default=-1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
     from paper_2310_07551_gb300 import configs
+    if args.workload == "batch64":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "reference arm covers the single-instance workloads"}))
+            return
+        run_batch(args, int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")))
+        return
     w = configs.WORKLOADS[args.workload]
+    if args.err_steps < 0:
+        args.err_steps = w.steps
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -228,24 +345,30 @@ def main():
 
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if args.steps <= 0:
+        barrier()
+        e0.record(stream)
+        plan.integrate(U, 3)
+        e1.record(stream)
+        barrier()
+        per = e0.elapsed_time(e1) / 3e3
+        args.steps = max(30, int(1.5 / max(per, 1e-6)))
     clocks = ClockSampler(local)
     barrier()
     clocks.start()
     time.sleep(0.3)
     barrier()
+    t_wall0 = time.time()
     e0.record(stream)
     for _ in range(args.steps):
         plan.integrate(U, 1)
     e1.record(stream)
     barrier()
-    clk = clocks.stop()
+    t_wall1 = time.time()
+    clk = clocks.stop(t_wall0, t_wall1)
     plan.sync(U, check_state=True)
     t = e0.elapsed_time(e1) / 1e3
-    if dist is not None:
-        tt = torch.tensor([t], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
-    value = world * w.npoints * args.steps / t
+    value, t = job_rate(t, w.npoints, args.steps, dist, "cuda")
     launches_per_step = plan.kernels_per_step
 
     # per-kernel device times with CUDA events on the launching stream
@@ -297,7 +420,12 @@ def main():
     tc_ms, tc_n, tc_fl = prof["tc"]
     f64_ms, f64_n, f64_fl = prof["f64"]
     pw_ms, pw_n, _ = prof["pointwise"]
-    if args.precision == "bf16x6":
+    if args.precision == "f32":
+        achieved = f64_fl / (f64_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": None, "unit": "TFLOP/s", "frac": None,
+                "traffic": None, "kernel": "k_gemm<float> (FP32 CUDA-core mode product)",
+                "peak_source": "no measured FP32 peak"}
+    elif args.precision == "bf16x6":
         # tensor-instruction flops: six BF16 products per FP32-class product
         achieved = 6.0 * tc_fl / (tc_ms / 1e3) / 1e12
         peak = peaks["bf16_tflops_sustained"]
@@ -321,8 +449,9 @@ def main():
         "config": {"workload": w.name, "grid": list(w.dims), "tau": w.tau, "model": w.model,
                    "precision": args.precision, "state": "fp64",
                    "parallelism": f"replicas{world}" if world > 1 else "single",
-                   "l2": "inputs larger than L2 (FP64 state 268 MB; >10 GB moved per step)"
-                   if w.npoints >= 1 << 24 else "L2 not flushed (small workload)",
+                   "l2": (f"inputs larger than L2: FP64 state {16 * w.npoints / 1e6:.0f} MB, "
+                          f"split-BF16 intermediates {6 * 18 * w.npoints / 1e9:.1f} GB per step")
+                   if 16 * w.npoints > 129e6 else "L2 not flushed (small workload)",
                    "phi_setup_s": setup_s},
         "rel_err_vs_fp64": {"value": err, "steps": args.err_steps} if err is not None else None,
         "roofline": roof,

@@ -187,6 +187,35 @@ ds_status ds_step(ds_plan *plan, double *U, void *stream);
  * round trips.  Asynchronous. */
 ds_status ds_integrate(ds_plan *plan, double *U, int64_t nsteps, void *stream);
 
+/* ds_step_backward -- adjoint (reverse mode) of one ds_step, for FP64
+ * plans.  The paper has no adjoint; this is the exact transpose of the step
+ * of Algorithms 1/2.  From U = U_n it recomputes F, U2, D2, U3 and, with
+ * lam = dL/dU_{n+1}, forms
+ *   lam_F  = tau S_f^{(1)T}(lam),  lam_D3 = 3tau/2 S_f^{(2)T}(lam),
+ *   lam_U3 = J_g(U3)^T lam_D3,
+ *   lam_F += 2tau/3 S_3^{(1)T}(lam_U3),  lam_D2 = 4tau/3 S_3^{(2)T}(lam_U3),
+ *   lam_U2 = J_g(U2)^T lam_D2,  lam_F += tau/3 S_2^{(1)T}(lam_U2),
+ *   lam_n  = lam + lam_U3 + lam_U2 + K^T lam_F + J_g(U)^T (lam_F - lam_D2 - lam_D3),
+ * where S^T uses the transposed phi-matrices (T(X, P)^T = T(X, P^T)) and
+ * J_g is the 2x2 pointwise Jacobian of the reaction.
+ *   U, lam, lam_n: device FP64 two-component tensors (2 N doubles); lam_n
+ *     must not alias U or lam.
+ *   dparams: NULL, or a device array of 3 doubles to which dL/dp[0..2] of
+ *     the model parameters is added (atomically; zero it before the sweep):
+ *     (dg/dp)(U)^T (lam_F - lam_D2 - lam_D3) + (dg/dp)(U2)^T lam_D2
+ *     + (dg/dp)(U3)^T lam_D3, summed over the grid.
+ *   dscale: NULL, or a device array of 2 doubles to which dL/ds_c is added,
+ *     s_c a relative scaling of component c's matrices (A_{c,mu} -> s_c
+ *     A_{c,mu} at s_c = 1; for A = delta_c D, dL/d delta_c = dL/ds_c /
+ *     delta_c).  It flows through K (<lam_F, K U>) and through every
+ *     phi-matrix: d/ds phi_l(s Z) = phi_{l-1}(Z) - l phi_l(Z) (from the
+ *     power series), formed once by ds_phi_setup.  Costs d extra Tucker
+ *     operators per Tucker operator of the step.
+ *   Errors: DS_ERR_INVALID_ARG, DS_ERR_UNSUPPORTED (non-FP64 plan), DS_ERR_OOM
+ *   (first call allocates a 24 N-double workspace). */
+ds_status ds_step_backward(ds_plan *plan, const double *U, const double *lam, double *lam_n,
+                           double *dparams, double *dscale, void *stream);
+
 /* ds_plan_sync -- wait for the plan's work and report device-side errors:
  * DS_ERR_TIMEOUT if a bounded wait gave up, DS_ERR_NONFINITE if check_state
  * is non-zero and U (may be NULL) holds NaN/Inf. */
@@ -211,6 +240,27 @@ ds_status ds_plan_profile(ds_plan *plan, int enable);
 ds_status ds_plan_profile_read(ds_plan *plan, double *ms, int64_t *launches, double *flops);
 
 ds_status ds_plan_destroy(ds_plan *plan);
+
+/* Batches of independent instances (uneven grids, parameters, tau).
+ * ds_batch_create -- one phi-set and plan per instance (as ds_phi_setup
+ *   with host A and ds_plan_create).  grids, A, tau, params: arrays of
+ *   ninst entries; A[i] is the host pointer of instance i's packed matrices
+ *   (layout of ds_phi_setup).  Synchronous.
+ * ds_batch_integrate -- nsteps steps of every instance; U: host array of
+ *   ninst device pointers to the instances' FP64 states.  The steps of all
+ *   instances are captured into one CUDA graph with one captured stream per
+ *   instance (fork/join), so independent instances run concurrently; a graph
+ *   covers up to 10 steps and is cached per set of U pointers.  Asynchronous.
+ * ds_batch_sync -- wait and report the first instance's device-side error.
+ * ds_batch_kernels_per_step -- library kernel launches per batch step.
+ * The paper has no batching; the instances are independent problems. */
+typedef struct ds_batch ds_batch;
+ds_status ds_batch_create(int ninst, const ds_grid *grids, const double *const *A, const double *tau,
+                          const ds_params *params, int precision, ds_batch **out);
+ds_status ds_batch_integrate(ds_batch *batch, double *const *U, int64_t nsteps, void *stream);
+ds_status ds_batch_sync(ds_batch *batch);
+int64_t ds_batch_kernels_per_step(const ds_batch *batch);
+ds_status ds_batch_destroy(ds_batch *batch);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char *ds_last_error(void);

@@ -430,3 +430,253 @@ done:
     free(G); free(F); free(U2); free(U3); free(Dt); free(Un); free(tmp);
     return rc;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Adjoint of one EXPRK3DS_REAL step (reverse mode of orc_step; the paper    */
+/* has no adjoint, this is the exact transpose of the step above).           */
+/* Forward values are recomputed from U = U_n.  With lam = dL/dU_{n+1}:      */
+/*   lam_F  = tau S_f^{(1)T}(lam),  lam_D3 = 3tau/2 S_f^{(2)T}(lam)            */
+/*   lam_U3 = J_g(U3)^T lam_D3                                               */
+/*   lam_F += 2tau/3 S_3^{(1)T}(lam_U3),  lam_D2 = 4tau/3 S_3^{(2)T}(lam_U3)   */
+/*   lam_U2 = J_g(U2)^T lam_D2                                               */
+/*   lam_F += tau/3 S_2^{(1)T}(lam_U2)                                        */
+/*   lam_G  = lam_F - lam_D2 - lam_D3                                        */
+/*   lam_n  = lam + lam_U3 + lam_U2 + K^T lam_F + J_g(U)^T lam_G             */
+/* where S^T(X) = sum_i eta_i T(X, {P_{i,s}{mu}^T}).  dp[q] += dL/dp_q for   */
+/* the three model parameters:                                               */
+/*   (dg/dp)(U)^T lam_G + (dg/dp)(U2)^T lam_D2 + (dg/dp)(U3)^T lam_D3.        */
+/* ------------------------------------------------------------------------ */
+static void transpose_into(int64_t m, const double *L, double *T)
+{
+    for (int64_t j = 0; j < m; ++j)
+        for (int64_t i = 0; i < m; ++i) T[j + m * i] = L[i + m * j];
+}
+
+/* acc += w * sum_i eta_i T(X, {P_{c,q,i,mu}^T}) */
+static int split_action_T(int d, const int64_t *n, int k, const double *P, int c, int q,
+                          const double *eta, double w, const double *X, double *acc, double *tmp)
+{
+    int64_t N = numel(d, n);
+    double *s = malloc(sizeof(double) * N);
+    double *Ts[ORC_MAXD] = {0};
+    int rc = -1;
+    if (!s) return -1;
+    memset(s, 0, sizeof(double) * N);
+    for (int mu = 0; mu < d; ++mu) {
+        Ts[mu] = malloc(sizeof(double) * n[mu] * n[mu]);
+        if (!Ts[mu]) goto out;
+    }
+    for (int i = 0; i < k; ++i) {
+        const double *L[ORC_MAXD];
+        for (int mu = 0; mu < d; ++mu) {
+            transpose_into(n[mu], pset_at(d, n, k, P, c, q, i, mu), Ts[mu]);
+            L[mu] = Ts[mu];
+        }
+        if (orc_tucker(d, n, X, L, tmp) < 0) goto out;
+        for (int64_t e = 0; e < N; ++e) s[e] += eta[i] * tmp[e];
+    }
+    for (int64_t e = 0; e < N; ++e) acc[e] += w * s[e];
+    rc = 0;
+out:
+    for (int mu = 0; mu < d; ++mu) free(Ts[mu]);
+    free(s);
+    return rc;
+}
+
+/* J_g(U)^T lam added into out; model as in orc_g */
+static void jacT_add(int model, const double *p, int64_t N, const double *U, const double *lam,
+                     double *out)
+{
+    for (int64_t e = 0; e < N; ++e) {
+        double u = U[e], v = U[N + e], lu = lam[e], lv = lam[N + e];
+        double juu, juv, jvu, jvv;
+        if (model == 0) {
+            juu = p[0] * (-1.0 + 2.0 * u * v);
+            juv = p[0] * u * u;
+            jvu = -2.0 * p[0] * u * v;
+            jvv = -p[0] * u * u;
+        } else if (model == 1) {
+            juu = 1.0 - 3.0 * u * u;
+            juv = -1.0;
+            jvu = p[0];
+            jvv = -p[0] * p[1];
+        } else {
+            juu = juv = jvu = jvv = 0.0;
+        }
+        out[e] += juu * lu + jvu * lv;
+        out[N + e] += juv * lu + jvv * lv;
+    }
+}
+
+/* dp += (dg/dp)(U)^T lam, the three model parameters */
+static void dparam_add(int model, const double *p, int64_t N, const double *U, const double *lam,
+                       double *dp)
+{
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    for (int64_t e = 0; e < N; ++e) {
+        double u = U[e], v = U[N + e], lu = lam[e], lv = lam[N + e];
+        if (model == 0) {
+            a0 += (p[1] - u + u * u * v) * lu + (p[2] - u * u * v) * lv;
+            a1 += p[0] * lu;
+            a2 += p[0] * lv;
+        } else if (model == 1) {
+            a0 += (u - p[1] * v - p[2]) * lv;
+            a1 += -p[0] * v * lv;
+            a2 += -p[0] * lv;
+        }
+    }
+    dp[0] += a0;
+    dp[1] += a1;
+    dp[2] += a2;
+}
+
+/* dL/ds_c for A_{c,mu}(s) = s A_{c,mu} at s = 1, for one Tucker operator     */
+/* family: sum_i sum_mu < Ybar_i, T(X, {P_i{nu}}, P_i{mu} -> dP_i{mu}) > with */
+/* Ybar_i = w eta_i lam_s and dP = d/ds phi_l(s Z) = phi_{l-1}(Z) - l phi_l(Z), */
+/* Z = c_q tau alpha_{i,mu} A_{c,mu} (Z phi_l'(Z), from the power series).      */
+static int dscale_family(int d, const int64_t *n, int k, const double *P, const double *const *Ac,
+                         int c, int q, double tau, const double *eta, double w, const double *X,
+                         const double *lam_s, double *acc, double *tmp)
+{
+    int ell_i[3]; double e_[3], alpha[12];
+    orc_coeffs(d, kSlotEll[q], ell_i, e_, alpha);
+    int64_t N = numel(d, n), nmax = 0;
+    for (int mu = 0; mu < d; ++mu) if (n[mu] > nmax) nmax = n[mu];
+    double *Z = malloc(sizeof(double) * nmax * nmax), *ph = malloc(sizeof(double) * nmax * nmax * 3);
+    double *dP = malloc(sizeof(double) * nmax * nmax);
+    int rc = -1;
+    if (!Z || !ph || !dP) goto out;
+    for (int i = 0; i < k; ++i) {
+        for (int mu = 0; mu < d; ++mu) {
+            int64_t m = n[mu], mm = m * m;
+            double z = kSlotC[q] * tau * alpha[i * 4 + mu];
+            for (int64_t e = 0; e < mm; ++e) Z[e] = z * Ac[mu][e];
+            int l = ell_i[i];
+            if (orc_phi((int)m, Z, l, ph) < 0) goto out;
+            for (int64_t e = 0; e < mm; ++e) dP[e] = ph[mm * (l - 1) + e] - l * ph[mm * l + e];
+            const double *L[ORC_MAXD];
+            for (int nu = 0; nu < d; ++nu) L[nu] = (nu == mu) ? dP : pset_at(d, n, k, P, c, q, i, nu);
+            if (orc_tucker(d, n, X, L, tmp) < 0) goto out;
+            double dot = 0.0;
+            for (int64_t e = 0; e < N; ++e) dot += lam_s[e] * tmp[e];
+            *acc += w * eta[i] * dot;
+        }
+    }
+    rc = 0;
+out:
+    free(Z); free(ph); free(dP);
+    return rc;
+}
+
+int orc_step_adjoint(int d, const int64_t *n, const double *A, const double *P, int model,
+                     const double *p, double tau, const double *U, const double *lam,
+                     double *lam_out, double *dp, double *dscale)
+{
+    if (d < 2 || d > ORC_MAXD) return -1;
+    int ell_i[3]; double eta1[3], eta2[3], alpha[12];
+    int k = orc_coeffs(d, 1, ell_i, eta1, alpha);
+    orc_coeffs(d, 2, ell_i, eta2, alpha);
+    int64_t N = numel(d, n);
+    const double *Ac[2][ORC_MAXD];
+    const double *Acur = A;
+    for (int c = 0; c < 2; ++c)
+        for (int mu = 0; mu < d; ++mu) { Ac[c][mu] = Acur; Acur += n[mu] * n[mu]; }
+    int64_t nb = 2 * N;
+    double *G = malloc(sizeof(double) * nb), *F = malloc(sizeof(double) * nb);
+    double *U2 = malloc(sizeof(double) * nb), *U3 = malloc(sizeof(double) * nb);
+    double *D2 = malloc(sizeof(double) * nb), *lF = malloc(sizeof(double) * nb);
+    double *lD2 = malloc(sizeof(double) * nb), *lD3 = malloc(sizeof(double) * nb);
+    double *lU2 = malloc(sizeof(double) * nb), *lU3 = malloc(sizeof(double) * nb);
+    double *tmp = malloc(sizeof(double) * N), *At = NULL;
+    int rc = -1;
+    if (!G || !F || !U2 || !U3 || !D2 || !lF || !lD2 || !lD3 || !lU2 || !lU3 || !tmp) goto done;
+    /* forward recomputation */
+    orc_g(model, p, N, U, G);
+    for (int c = 0; c < 2; ++c) {
+        if (orc_kronsum(d, n, U + c * N, Ac[c], F + c * N) < 0) goto done;
+        for (int64_t e = 0; e < N; ++e) F[c * N + e] += G[c * N + e];
+    }
+    memcpy(U2, U, sizeof(double) * nb);
+    for (int c = 0; c < 2; ++c)
+        if (split_action(d, n, k, P, c, 0, eta1, tau / 3.0, F + c * N, U2 + c * N, tmp) < 0) goto done;
+    orc_g(model, p, N, U2, D2);
+    for (int64_t e = 0; e < nb; ++e) D2[e] -= G[e];
+    memcpy(U3, U, sizeof(double) * nb);
+    for (int c = 0; c < 2; ++c) {
+        if (split_action(d, n, k, P, c, 1, eta1, 2.0 * tau / 3.0, F + c * N, U3 + c * N, tmp) < 0) goto done;
+        if (split_action(d, n, k, P, c, 2, eta2, 4.0 * tau / 3.0, D2 + c * N, U3 + c * N, tmp) < 0) goto done;
+    }
+    /* reverse sweep */
+    memset(lF, 0, sizeof(double) * nb);
+    memset(lD3, 0, sizeof(double) * nb);
+    memset(lD2, 0, sizeof(double) * nb);
+    memset(lU2, 0, sizeof(double) * nb);
+    memset(lU3, 0, sizeof(double) * nb);
+    for (int c = 0; c < 2; ++c) {
+        if (split_action_T(d, n, k, P, c, 3, eta1, tau, lam + c * N, lF + c * N, tmp) < 0) goto done;
+        if (split_action_T(d, n, k, P, c, 4, eta2, 1.5 * tau, lam + c * N, lD3 + c * N, tmp) < 0) goto done;
+    }
+    jacT_add(model, p, N, U3, lD3, lU3);
+    for (int c = 0; c < 2; ++c) {
+        if (split_action_T(d, n, k, P, c, 1, eta1, 2.0 * tau / 3.0, lU3 + c * N, lF + c * N, tmp) < 0) goto done;
+        if (split_action_T(d, n, k, P, c, 2, eta2, 4.0 * tau / 3.0, lU3 + c * N, lD2 + c * N, tmp) < 0) goto done;
+    }
+    jacT_add(model, p, N, U2, lD2, lU2);
+    for (int c = 0; c < 2; ++c)
+        if (split_action_T(d, n, k, P, c, 0, eta1, tau / 3.0, lU2 + c * N, lF + c * N, tmp) < 0) goto done;
+    /* lam_n = lam + lam_U3 + lam_U2 + K^T lam_F + J_g(U)^T (lam_F - lam_D2 - lam_D3) */
+    for (int64_t e = 0; e < nb; ++e) lam_out[e] = lam[e] + lU3[e] + lU2[e];
+    {
+        int64_t nmax = 0;
+        for (int mu = 0; mu < d; ++mu) if (n[mu] > nmax) nmax = n[mu];
+        At = malloc(sizeof(double) * nmax * nmax * ORC_MAXD);
+        if (!At) goto done;
+        for (int c = 0; c < 2; ++c) {
+            const double *AT[ORC_MAXD];
+            for (int mu = 0; mu < d; ++mu) {
+                transpose_into(n[mu], Ac[c][mu], At + nmax * nmax * mu);
+                AT[mu] = At + nmax * nmax * mu;
+            }
+            if (orc_kronsum(d, n, lF + c * N, AT, tmp) < 0) goto done;
+            for (int64_t e = 0; e < N; ++e) lam_out[c * N + e] += tmp[e];
+        }
+    }
+    /* lG reuses lU2's storage after its last use: lG = lF - lD2 - lD3 */
+    for (int64_t e = 0; e < nb; ++e) lU2[e] = lF[e] - lD2[e] - lD3[e];
+    jacT_add(model, p, N, U, lU2, lam_out);
+    if (dp) {
+        /* D3's forward value is not needed: only U3 enters (dg/dp)(U3) */
+        dparam_add(model, p, N, U, lU2, dp);
+        dparam_add(model, p, N, U2, lD2, dp);
+        dparam_add(model, p, N, U3, lD3, dp);
+    }
+    if (dscale) {
+        /* lU2 now holds lam_G; recompute lam_U2 = J_g(U2)^T lam_D2 and D3 */
+        double *lU2b = malloc(sizeof(double) * nb), *D3 = malloc(sizeof(double) * nb);
+        if (!lU2b || !D3) { free(lU2b); free(D3); goto done; }
+        memset(lU2b, 0, sizeof(double) * nb);
+        jacT_add(model, p, N, U2, lD2, lU2b);
+        orc_g(model, p, N, U3, D3);
+        for (int64_t e = 0; e < nb; ++e) D3[e] -= G[e];
+        int bad = 0;
+        for (int c = 0; c < 2 && !bad; ++c) {
+            double acc = 0.0;
+            /* through K: F = s K U + G */
+            for (int64_t e = 0; e < N; ++e) acc += lF[c * N + e] * (F[c * N + e] - G[c * N + e]);
+            const double *Fc = F + c * N, *Dc2 = D2 + c * N, *Dc3 = D3 + c * N;
+            bad |= dscale_family(d, n, k, P, Ac[c], c, 0, tau, eta1, tau / 3.0, Fc, lU2b + c * N, &acc, tmp) < 0;
+            bad |= dscale_family(d, n, k, P, Ac[c], c, 1, tau, eta1, 2.0 * tau / 3.0, Fc, lU3 + c * N, &acc, tmp) < 0;
+            bad |= dscale_family(d, n, k, P, Ac[c], c, 2, tau, eta2, 4.0 * tau / 3.0, Dc2, lU3 + c * N, &acc, tmp) < 0;
+            bad |= dscale_family(d, n, k, P, Ac[c], c, 3, tau, eta1, tau, Fc, lam + c * N, &acc, tmp) < 0;
+            bad |= dscale_family(d, n, k, P, Ac[c], c, 4, tau, eta2, 1.5 * tau, Dc3, lam + c * N, &acc, tmp) < 0;
+            dscale[c] += acc;
+        }
+        free(lU2b); free(D3);
+        if (bad) goto done;
+    }
+    rc = 0;
+done:
+    free(G); free(F); free(U2); free(U3); free(D2); free(lF); free(lD2); free(lD3);
+    free(lU2); free(lU3); free(tmp); free(At);
+    return rc;
+}

@@ -62,10 +62,9 @@ def lib():
             L.orc_step.argtypes = [ctypes.c_int, _i64p, _dp, _dp, ctypes.c_int, _dp,
                                    ctypes.c_double, _dp, ctypes.c_int]
             L.orc_step.restype = ctypes.c_int
-            if hasattr(L, "orc_step_adjoint"):
-                L.orc_step_adjoint.argtypes = [ctypes.c_int, _i64p, _dp, _dp, _dp, ctypes.c_int,
-                                               _dp, ctypes.c_double, _dp, _dp, _dp, _dp]
-                L.orc_step_adjoint.restype = ctypes.c_int
+            L.orc_step_adjoint.argtypes = [ctypes.c_int, _i64p, _dp, _dp, ctypes.c_int, _dp,
+                                           ctypes.c_double, _dp, _dp, _dp, _dp, _dp]
+            L.orc_step_adjoint.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -201,3 +200,24 @@ def step(dims, As, P, model: str, p, tau: float, U: np.ndarray, nsteps: int = 1)
     if rc != 0:
         raise RuntimeError("orc_step failed")
     return Uo
+
+
+def step_adjoint(dims, As, P, model: str, p, tau: float, U: np.ndarray, lam: np.ndarray,
+                 with_scale: bool = False):
+    """Reverse-mode adjoint of one step at U = U_n: returns (dL/dU_n, dL/dp[3])
+    for lam = dL/dU_{n+1}; with_scale adds dL/ds[2], the derivative with
+    respect to a relative scaling s_c of component c's matrices A_{c,mu}."""
+    d = len(dims)
+    Uc = np.ascontiguousarray(U, dtype=np.float64)
+    lc = np.ascontiguousarray(lam, dtype=np.float64)
+    out = np.zeros_like(Uc)
+    dp = np.zeros(3)
+    dsc = np.zeros(2)
+    pp = np.asarray(list(p) + [0.0] * (8 - len(p)), dtype=np.float64)
+    Ap = _pack_A(As)
+    rc = lib().orc_step_adjoint(d, _dims(dims), _ptr(Ap), _ptr(np.ascontiguousarray(P)), MODELS[model],
+                                _ptr(pp), float(tau), _ptr(Uc), _ptr(lc), _ptr(out), _ptr(dp),
+                                _ptr(dsc) if with_scale else None)
+    if rc != 0:
+        raise RuntimeError("orc_step_adjoint failed")
+    return (out, dp, dsc) if with_scale else (out, dp)

@@ -50,3 +50,34 @@ WORKLOADS: dict[str, Workload] = {
     "fhn3d_96": Workload("fhn3d_96", "fhn", (96, 96, 96), -1.0, 1.0,
                          1e-3, 200, FHN, (1.0, 42.1887), seed=1),
 }
+
+
+@dataclass(frozen=True)
+class Instance:
+    dims: tuple[int, int]
+    params: tuple[float, float, float]   # (gamma, a, b)
+    delta: tuple[float, float]
+    tau: float
+
+
+def batch_instances(count: int = 64, seed: int = 7) -> list[Instance]:
+    """Independent Schnakenberg instances with uneven, non-square grids:
+    n_1, n_2 from {96, 128, 192, 256, 384, 512}, a in [0.05, 0.2],
+    b in [0.7, 1.0], delta_v in [8, 20], tau in [5e-5, 2e-4], gamma = 1000,
+    delta_u = 1, domain [0, 1]^2; all drawn from the counter-based generator."""
+    from .inputs import uniform01
+    sizes = (96, 128, 192, 256, 384, 512)
+    r = uniform01(seed, 0, 7 * count).reshape(count, 7)
+    out = []
+    for k in range(count):
+        n1 = sizes[min(int(r[k, 0] * 6), 5)]
+        n2 = sizes[min(int(r[k, 1] * 6), 5)]
+        a = 0.05 + 0.15 * r[k, 2]
+        b = 0.7 + 0.3 * r[k, 3]
+        dv = 8.0 + 12.0 * r[k, 4]
+        tau = 5e-5 + 1.5e-4 * r[k, 5]
+        out.append(Instance((n1, n2), (1000.0, a, b), (1.0, dv), tau))
+    return out
+
+
+BATCH_STEPS = 500

@@ -159,15 +159,17 @@ struct ds_plan {
     std::map<double *, cudaGraphExec_t> graphs;
     int64_t launches = 0;
     tc::MixedPlan *mixed = nullptr;       // tensor-core path state
+    double *bws = nullptr;                // adjoint workspace (24 N doubles), lazily allocated
     Prof prof;                            // optional per-launch event timing
     bool profiling = false;               // ds_step records events when set
 };
 
 namespace {
 
-// Enqueue sum_i eta_i T(X_c, {P[c][slot][i][mu]}) into acc (FP64 path).
-int tucker_sum_f64(ds_plan *p, int c, int slot, const double *X, double *acc, double *t1,
-                   double *t2, cudaStream_t st)
+// acc (+)= w sum_i eta_i T(X_c, {P[c][slot][i][mu]}) (FP64 path); with
+// transpose the matrices are P^T (the adjoint operator S^T).
+int tucker_sum_f64x(ds_plan *p, int c, int slot, const double *X, double *acc, double w, bool accumulate,
+                    int transpose, double *t1, double *t2, cudaStream_t st)
 {
     const ds_phi_set *s = p->set;
     const int d = s->d;
@@ -180,14 +182,21 @@ int tucker_sum_f64(ds_plan *p, int c, int slot, const double *X, double *acc, do
             const bool last = (mu == d - 1);
             double *out = last ? acc : ((mu % 2 == 0) ? t1 : t2);
             p->prof.begin(st, 1, 2.0 * (double)p->N * (double)s->n[mu]);
-            launch_mode_product_f64(d, s->n, in, mu, L, 0, out, last ? co.eta[i] : 1.0,
-                                    (last && i > 0) ? 1.0 : 0.0, st);
+            launch_mode_product_f64(d, s->n, in, mu, L, transpose, out, last ? w * co.eta[i] : 1.0,
+                                    (last && (i > 0 || accumulate)) ? 1.0 : 0.0, st);
             p->prof.end(st);
             ++launches;
             in = out;
         }
     }
     return launches;
+}
+
+// Enqueue sum_i eta_i T(X_c, {P[c][slot][i][mu]}) into acc (FP64 path).
+int tucker_sum_f64(ds_plan *p, int c, int slot, const double *X, double *acc, double *t1,
+                   double *t2, cudaStream_t st)
+{
+    return tucker_sum_f64x(p, c, slot, X, acc, 1.0, false, 0, t1, t2, st);
 }
 
 // F = K U + g(U) with dense mode products (A not tridiagonal)
@@ -387,7 +396,8 @@ ds_status ds_phi_setup(const ds_grid *grid, const double *A, int a_on_device, do
         cudaError_t e1 = cudaMalloc(&s->A_dev, sizeof(double) * Acount);
         cudaError_t e2 = cudaMalloc(&s->tri_dev, sizeof(double) * toff);
         cudaError_t e3 = cudaMalloc(&s->P_dev, sizeof(double) * poff);
-        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+        cudaError_t e4 = cudaMalloc(&s->dP_dev, sizeof(double) * poff);
+        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || e4 != cudaSuccess) {
             cudaGetLastError();
             ds_phi_set_destroy(s);
             return fail(DS_ERR_OOM, "phi-set device allocation");
@@ -406,6 +416,7 @@ ds_status ds_phi_setup(const ds_grid *grid, const double *A, int a_on_device, do
                         j.z = kSlotC[q] * tau * co.alpha[i][mu];
                         j.ell = co.ell_i[i];
                         j.out = s->P_dev + s->P_off[c][q][i][mu];
+                        j.dout = s->dP_dev + s->P_off[c][q][i][mu];
                         groups[grid->n[mu]].push_back(j);
                     }
             }
@@ -426,6 +437,7 @@ ds_status ds_phi_set_destroy(ds_phi_set *s)
     cudaFree(s->A_dev);
     cudaFree(s->tri_dev);
     cudaFree(s->P_dev);
+    cudaFree(s->dP_dev);
     delete s;
     return DS_OK;
 }
@@ -549,6 +561,8 @@ ds_status ds_plan_create(const ds_grid *grid, const ds_params *params, const ds_
                 return cleanup(DS_ERR_OOM, "FP64 workspace");
             }
         } else if (precision == DS_PREC_F32) {
+            if (!set->tridiag[0] || !set->tridiag[1])
+                return cleanup(DS_ERR_UNSUPPORTED, "reduced-precision paths need tridiagonal A_mu (use DS_PREC_F64)");
             if (cudaMalloc(&p->ws32, sizeof(float) * 10 * p->N) != cudaSuccess ||
                 cudaMalloc(&p->P32, sizeof(float) * set->P_count) != cudaSuccess) {
                 cudaGetLastError();
@@ -605,6 +619,104 @@ ds_status ds_integrate(ds_plan *p, double *U, int64_t nsteps, void *stream)
     return DS_OK;
 }
 
+// dscale[c] += w sum_i eta_i sum_mu < lam_s_c, T(X_c, P with P_mu -> dP_mu) >
+static void dscale_family(ds_plan *p, int c, int slot, const double *X, const double *lam_s, double w,
+                          double *out, double *t1, double *t2, double *dscale, cudaStream_t st)
+{
+    const ds_phi_set *s = p->set;
+    const int d = s->d;
+    const SplitCoeffs &co = s->co[kSlotEll[slot] - 1];
+    for (int i = 0; i < co.k; ++i)
+        for (int md = 0; md < d; ++md) {
+            const double *in = X;
+            for (int mu = 0; mu < d; ++mu) {
+                const double *L = (mu == md ? s->dP_dev : s->P_dev) + s->P_off[c][slot][i][mu];
+                double *o = (mu == d - 1) ? out : ((mu % 2 == 0) ? t1 : t2);
+                launch_mode_product_f64(d, s->n, in, mu, L, 0, o, 1.0, 0.0, st);
+                in = o;
+            }
+            launch_dot_accum_f64(p->N, lam_s, out, w * co.eta[i], dscale + c, st);
+        }
+}
+
+ds_status ds_step_backward(ds_plan *p, const double *U, const double *lam, double *lam_n, double *dparams,
+                           double *dscale, void *stream)
+{
+    if (!p || !U || !lam || !lam_n) return fail(DS_ERR_INVALID_ARG, "NULL argument");
+    if (lam_n == lam || lam_n == U) return fail(DS_ERR_INVALID_ARG, "lam_n must not alias U or lam");
+    if (p->prec != DS_PREC_F64) return fail(DS_ERR_UNSUPPORTED, "the adjoint step needs an FP64 plan");
+    const int64_t N = p->N;
+    if (!p->bws) {
+        cudaError_t e = cudaMalloc(&p->bws, sizeof(double) * 24 * N);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            p->bws = nullptr;
+            return fail(DS_ERR_OOM, "adjoint workspace");
+        }
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const double tau = p->set->tau;
+    double *F = p->bws, *a = F + 2 * N, *b = F + 4 * N, *D2 = F + 6 * N, *U2 = F + 8 * N, *U3 = F + 10 * N;
+    double *lF = F + 12 * N, *lD3 = F + 14 * N, *lD2 = F + 16 * N, *lU3 = F + 18 * N, *lU2 = F + 20 * N;
+    double *t1 = F + 22 * N, *t2 = F + 23 * N;
+    const Model &m = p->model;
+    const bool tri = p->set->tridiag[0] && p->set->tridiag[1];
+    // forward recomputation of F, U2, D2, U3
+    if (tri)
+        launch_rhs_f64(p->sten, m, N, U, F, st);
+    else
+        rhs_dense_f64(p, U, F, st);
+    for (int c = 0; c < 2; ++c) tucker_sum_f64(p, c, 0, F + c * N, a + c * N, t1, t2, st);
+    launch_axpy2_f64(N, U, a, kSlotW[0] * tau, nullptr, 0.0, U2, st);
+    launch_gdiff_f64(m, N, U, U2, D2, st);
+    for (int c = 0; c < 2; ++c) {
+        tucker_sum_f64(p, c, 1, F + c * N, a + c * N, t1, t2, st);
+        tucker_sum_f64(p, c, 2, D2 + c * N, b + c * N, t1, t2, st);
+    }
+    launch_axpy2_f64(N, U, a, kSlotW[1] * tau, b, kSlotW[2] * tau, U3, st);
+    // reverse sweep
+    for (int c = 0; c < 2; ++c) {
+        tucker_sum_f64x(p, c, 3, lam + c * N, lF + c * N, kSlotW[3] * tau, false, 1, t1, t2, st);
+        tucker_sum_f64x(p, c, 4, lam + c * N, lD3 + c * N, kSlotW[4] * tau, false, 1, t1, t2, st);
+    }
+    launch_jacT_f64(m, N, U3, lD3, lU3, st);
+    for (int c = 0; c < 2; ++c) {
+        tucker_sum_f64x(p, c, 1, lU3 + c * N, lF + c * N, kSlotW[1] * tau, true, 1, t1, t2, st);
+        tucker_sum_f64x(p, c, 2, lU3 + c * N, lD2 + c * N, kSlotW[2] * tau, false, 1, t1, t2, st);
+    }
+    launch_jacT_f64(m, N, U2, lD2, lU2, st);
+    for (int c = 0; c < 2; ++c)
+        tucker_sum_f64x(p, c, 0, lU2 + c * N, lF + c * N, kSlotW[0] * tau, true, 1, t1, t2, st);
+    if (dscale) {
+        // through K (F = s K U + G) and through every phi-matrix; a and b are
+        // free after U3: b <- D3 = g(U3) - g(U), a holds one Tucker output
+        launch_dot_kterm_f64(m, N, U, F, lF, dscale, st);
+        launch_gdiff_f64(m, N, U, U3, b, st);
+        for (int c = 0; c < 2; ++c) {
+            const double *Fc = F + c * N;
+            double *o = a + c * N;
+            dscale_family(p, c, 0, Fc, lU2 + c * N, kSlotW[0] * tau, o, t1, t2, dscale, st);
+            dscale_family(p, c, 1, Fc, lU3 + c * N, kSlotW[1] * tau, o, t1, t2, dscale, st);
+            dscale_family(p, c, 2, D2 + c * N, lU3 + c * N, kSlotW[2] * tau, o, t1, t2, dscale, st);
+            dscale_family(p, c, 3, Fc, lam + c * N, kSlotW[3] * tau, o, t1, t2, dscale, st);
+            dscale_family(p, c, 4, b + c * N, lam + c * N, kSlotW[4] * tau, o, t1, t2, dscale, st);
+        }
+    }
+    // K^T lam_F into F's storage
+    if (tri) {
+        launch_kronsumT_f64(p->sten, N, lF, F, st);
+    } else {
+        for (int c = 0; c < 2; ++c)
+            for (int mu = 0; mu < p->set->d; ++mu)
+                launch_mode_product_f64(p->set->d, p->set->n, lF + c * N, mu,
+                                        p->set->A_dev + p->set->A_off[c][mu], 1, F + c * N, 1.0,
+                                        mu > 0 ? 1.0 : 0.0, st);
+    }
+    launch_adjoint_final_f64(m, N, U, U2, U3, lam, lU3, lU2, F, lF, lD2, lD3, lam_n, dparams, st);
+    DS_CUDA_TRY(cudaGetLastError());
+    return DS_OK;
+}
+
 ds_status ds_plan_sync(ds_plan *p, const double *U, int check_state)
 {
     if (!p) return fail(DS_ERR_INVALID_ARG, "NULL plan");
@@ -626,6 +738,171 @@ ds_status ds_plan_sync(ds_plan *p, const double *U, int check_state)
 }
 
 int64_t ds_plan_kernels_per_step(const ds_plan *p) { return p ? p->launches : -1; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batches of independent instances: one CUDA graph forks every instance's
+// steps onto its own captured stream and joins them, so the kernels of
+// different instances run concurrently on the GPU's SMs and one graph launch
+// advances the whole batch.
+// ---------------------------------------------------------------------------
+struct ds_batch {
+    int ninst = 0;
+    std::vector<ds_phi_set *> sets;
+    std::vector<ds_plan *> plans;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> join;
+    cudaStream_t origin = nullptr;
+    cudaEvent_t fork = nullptr, ev_in = nullptr, ev_out = nullptr;
+    struct Graph {
+        std::vector<double *> U;
+        int steps;
+        cudaGraphExec_t exec;
+    };
+    std::vector<Graph> graphs;
+    int64_t launches_per_step = 0;
+};
+
+namespace {
+ds_status batch_graph(ds_batch *b, double *const *U, int steps, cudaGraphExec_t *out)
+{
+    for (auto &g : b->graphs) {
+        if (g.steps != steps) continue;
+        bool same = true;
+        for (int i = 0; i < b->ninst && same; ++i) same = (g.U[i] == U[i]);
+        if (same) { *out = g.exec; return DS_OK; }
+    }
+    cudaGraph_t graph;
+    DS_CUDA_TRY(cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal));
+    cudaEventRecord(b->fork, b->origin);
+    int64_t L = 0;
+    bool bad = false;
+    for (int i = 0; i < b->ninst; ++i) {
+        cudaStream_t s = b->streams[i];
+        cudaStreamWaitEvent(s, b->fork, 0);
+        for (int k = 0; k < steps; ++k) {
+            int l = enqueue_step(b->plans[i], U[i], s, false);
+            if (l < 0) bad = true;
+            L += l;
+        }
+        cudaEventRecord(b->join[i], s);
+        cudaStreamWaitEvent(b->origin, b->join[i], 0);
+    }
+    cudaError_t e = cudaStreamEndCapture(b->origin, &graph);
+    if (e != cudaSuccess || bad) return fail(DS_ERR_CUDA, std::string("batch capture: ") + cudaGetErrorString(e));
+    cudaGraphExec_t ex;
+    e = cudaGraphInstantiate(&ex, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(DS_ERR_CUDA, std::string("batch instantiate: ") + cudaGetErrorString(e));
+    b->launches_per_step = L / steps;
+    b->graphs.push_back({std::vector<double *>(U, U + b->ninst), steps, ex});
+    *out = ex;
+    return DS_OK;
+}
+}  // namespace
+
+extern "C" {
+
+ds_status ds_batch_destroy(ds_batch *b)
+{
+    if (!b) return DS_OK;
+    if (b->origin) cudaStreamSynchronize(b->origin);
+    for (auto &g : b->graphs) cudaGraphExecDestroy(g.exec);
+    for (auto p : b->plans) ds_plan_destroy(p);
+    for (auto s : b->sets) ds_phi_set_destroy(s);
+    for (auto s : b->streams) cudaStreamDestroy(s);
+    for (auto e : b->join) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->ev_in) cudaEventDestroy(b->ev_in);
+    if (b->ev_out) cudaEventDestroy(b->ev_out);
+    if (b->origin) cudaStreamDestroy(b->origin);
+    delete b;
+    return DS_OK;
+}
+
+ds_status ds_batch_create(int ninst, const ds_grid *grids, const double *const *A, const double *tau,
+                          const ds_params *params, int precision, ds_batch **out)
+{
+    if (ninst <= 0 || ninst > 4096 || !grids || !A || !tau || !params || !out)
+        return fail(DS_ERR_INVALID_ARG, "bad batch arguments");
+    ds_batch *b = new (std::nothrow) ds_batch();
+    if (!b) return fail(DS_ERR_OOM, "host allocation");
+    b->ninst = ninst;
+    for (int i = 0; i < ninst; ++i) {
+        ds_phi_set *s = nullptr;
+        ds_status r = ds_phi_setup(&grids[i], A[i], 0, tau[i], &s, nullptr);
+        if (r != DS_OK) {
+            std::string m = g_err;
+            ds_batch_destroy(b);
+            return fail(r, "instance " + std::to_string(i) + ": " + m);
+        }
+        b->sets.push_back(s);
+        ds_plan *p = nullptr;
+        r = ds_plan_create(&grids[i], &params[i], s, precision, &p);
+        if (r != DS_OK) {
+            std::string m = g_err;
+            ds_batch_destroy(b);
+            return fail(r, "instance " + std::to_string(i) + ": " + m);
+        }
+        b->plans.push_back(p);
+        cudaStream_t st;
+        cudaEvent_t ev;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            ds_batch_destroy(b);
+            return fail(DS_ERR_CUDA, "stream/event creation");
+        }
+        b->streams.push_back(st);
+        b->join.push_back(ev);
+    }
+    if (cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+        ds_batch_destroy(b);
+        return fail(DS_ERR_CUDA, "stream/event creation");
+    }
+    *out = b;
+    return DS_OK;
+}
+
+ds_status ds_batch_integrate(ds_batch *b, double *const *U, int64_t nsteps, void *stream)
+{
+    if (!b || !U || nsteps < 0) return fail(DS_ERR_INVALID_ARG, "bad argument");
+    for (int i = 0; i < b->ninst; ++i)
+        if (!U[i]) return fail(DS_ERR_INVALID_ARG, "U[i] is NULL");
+    if (nsteps == 0) return DS_OK;
+    const int chunk = (int)std::min<int64_t>(nsteps, 10);
+    cudaGraphExec_t g_chunk = nullptr, g_one = nullptr;
+    ds_status r = batch_graph(b, U, chunk, &g_chunk);
+    if (r != DS_OK) return r;
+    if (nsteps % chunk) {
+        r = batch_graph(b, U, 1, &g_one);
+        if (r != DS_OK) return r;
+    }
+    cudaStream_t user = (cudaStream_t)stream;
+    DS_CUDA_TRY(cudaEventRecord(b->ev_in, user));
+    DS_CUDA_TRY(cudaStreamWaitEvent(b->origin, b->ev_in, 0));
+    for (int64_t k = 0; k < nsteps / chunk; ++k) DS_CUDA_TRY(cudaGraphLaunch(g_chunk, b->origin));
+    for (int64_t k = 0; k < nsteps % chunk; ++k) DS_CUDA_TRY(cudaGraphLaunch(g_one, b->origin));
+    DS_CUDA_TRY(cudaEventRecord(b->ev_out, b->origin));
+    DS_CUDA_TRY(cudaStreamWaitEvent(user, b->ev_out, 0));
+    return DS_OK;
+}
+
+ds_status ds_batch_sync(ds_batch *b)
+{
+    if (!b) return fail(DS_ERR_INVALID_ARG, "NULL batch");
+    DS_CUDA_TRY(cudaStreamSynchronize(b->origin));
+    for (int i = 0; i < b->ninst; ++i) {
+        ds_status r = ds_plan_sync(b->plans[i], nullptr, 0);
+        if (r != DS_OK) return fail(r, "instance " + std::to_string(i) + ": " + g_err);
+    }
+    return DS_OK;
+}
+
+int64_t ds_batch_kernels_per_step(const ds_batch *b) { return b ? b->launches_per_step : -1; }
 
 ds_status ds_plan_profile(ds_plan *p, int enable)
 {
@@ -659,6 +936,7 @@ ds_status ds_plan_destroy(ds_plan *p)
     for (auto &kv : p->graphs) cudaGraphExecDestroy(kv.second);
     if (p->mixed) tc::mixed_plan_destroy(p->mixed);
     cudaFree(p->ws);
+    cudaFree(p->bws);
     cudaFree(p->ws32);
     cudaFree(p->P32);
     cudaFree(p->status);

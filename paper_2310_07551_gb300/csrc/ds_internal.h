@@ -89,13 +89,31 @@ void launch_stage_diff_f64(const Model &m, int64_t N, const double *U, const dou
 void launch_final_f64(int64_t N, double *U, const double *a, double w1, const double *b,
                       double w2, cudaStream_t st);
 void launch_add_g_f64(const Model &m, int64_t N, const double *U, double *F, cudaStream_t st);
+// adjoint helpers (FP64)
+void launch_axpy2_f64(int64_t N, const double *U, const double *a, double w1, const double *b, double w2,
+                      double *Y, cudaStream_t st);
+void launch_gdiff_f64(const Model &m, int64_t N, const double *U, const double *Us, double *D, cudaStream_t st);
+void launch_jacT_f64(const Model &m, int64_t N, const double *Us, const double *lam, double *out,
+                     cudaStream_t st);
+void launch_kronsumT_f64(const Stencil *s2, int64_t N, const double *X, double *Y, cudaStream_t st);
+// out[0] += w * sum a.b over n values (block reduction + one atomic per block)
+void launch_dot_accum_f64(int64_t n, const double *a, const double *b, double w, double *out,
+                          cudaStream_t st);
+// out[c] += sum over points of lF_c (F_c - g_c(U)) for c = 0, 1
+void launch_dot_kterm_f64(const Model &m, int64_t N, const double *U, const double *F, const double *lF,
+                          double *out, cudaStream_t st);
+void launch_adjoint_final_f64(const Model &m, int64_t N, const double *U, const double *U2,
+                              const double *U3, const double *lam, const double *lU3, const double *lU2,
+                              const double *KT, const double *lF, const double *lD2, const double *lD3,
+                              double *lam_n, double *dp, cudaStream_t st);
 
 // phi-function evaluation (batched) -------------------------------------
 struct PhiJob {
     const double *A;   // device, column-major n x n
     double z;          // scalar multiplying A
-    int ell;           // phi index wanted
+    int ell;           // phi index wanted (1 or 2)
     double *out;       // device destination n x n column-major
+    double *dout;      // optional: d/ds phi_ell(s zA) at s = 1 = phi_{ell-1} - ell phi_ell
 };
 ds_status phi_batch_f64(int n, const std::vector<PhiJob> &jobs, cudaStream_t st);
 
@@ -166,6 +184,7 @@ struct ds_phi_set {
     double *tri_dev = nullptr;              // [c][mu][3][n_mu]
     int64_t tri_off[2][ds::kMaxD];
     double *P_dev = nullptr;                // FP64 phi-matrices, column-major blocks
+    double *dP_dev = nullptr;               // their derivatives w.r.t. a scaling of A (same offsets)
     int64_t P_off[2][ds::kSlots][ds::kMaxTerms][ds::kMaxD];
     int64_t P_count = 0;
 };

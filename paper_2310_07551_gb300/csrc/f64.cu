@@ -252,6 +252,208 @@ __global__ void k_nonfinite(const double *x, int64_t count, int *flag)
         if (!isfinite(x[p])) atomicExch(flag, 1);
 }
 
+// J_g(U)^T lam for one point; model as in react()
+__device__ __forceinline__ void jacT(const Model &m, double u, double v, double lu, double lv, double &ou,
+                                     double &ov)
+{
+    double juu, juv, jvu, jvv;
+    if (m.model == DS_SCHNAKENBERG) {
+        juu = m.p[0] * (-1.0 + 2.0 * u * v);
+        juv = m.p[0] * u * u;
+        jvu = -2.0 * m.p[0] * u * v;
+        jvv = -m.p[0] * u * u;
+    } else if (m.model == DS_FHN) {
+        juu = 1.0 - 3.0 * u * u;
+        juv = -1.0;
+        jvu = m.p[0];
+        jvv = -m.p[0] * m.p[1];
+    } else {
+        juu = juv = jvu = jvv = 0.0;
+    }
+    ou = juu * lu + jvu * lv;
+    ov = juv * lu + jvv * lv;
+}
+
+// (dg/dp)(U)^T lam for one point: contributions to the three model parameters
+__device__ __forceinline__ void dparam_point(const Model &m, double u, double v, double lu, double lv,
+                                             double &d0, double &d1, double &d2)
+{
+    if (m.model == DS_SCHNAKENBERG) {
+        d0 = (m.p[1] - u + u * u * v) * lu + (m.p[2] - u * u * v) * lv;
+        d1 = m.p[0] * lu;
+        d2 = m.p[0] * lv;
+    } else if (m.model == DS_FHN) {
+        d0 = (u - m.p[1] * v - m.p[2]) * lv;
+        d1 = -m.p[0] * v * lv;
+        d2 = -m.p[0] * lv;
+    } else {
+        d0 = d1 = d2 = 0.0;
+    }
+}
+
+// Y = U + w1 a (+ w2 b), 2 N values
+__global__ void k_axpy2(int64_t n2, const double *__restrict__ U, const double *__restrict__ a, double w1,
+                        const double *__restrict__ b, double w2, double *__restrict__ Y)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n2;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        double y = __dadd_rn(U[p], __dmul_rn(w1, a[p]));
+        if (b) y = __dadd_rn(y, __dmul_rn(w2, b[p]));
+        Y[p] = y;
+    }
+}
+
+// D = g(Us) - g(U)
+__global__ void k_gdiff(Model m, int64_t N, const double *__restrict__ U, const double *__restrict__ Us,
+                        double *__restrict__ D)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < N;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        double g0u, g0v, gu, gv;
+        react(m, U[p], U[N + p], g0u, g0v);
+        react(m, Us[p], Us[N + p], gu, gv);
+        D[p] = __dsub_rn(gu, g0u);
+        D[N + p] = __dsub_rn(gv, g0v);
+    }
+}
+
+// out = J_g(Us)^T lam
+__global__ void k_jacT(Model m, int64_t N, const double *__restrict__ Us, const double *__restrict__ lam,
+                       double *__restrict__ out)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < N;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        double ou, ov;
+        jacT(m, Us[p], Us[N + p], lam[p], lam[N + p], ou, ov);
+        out[p] = ou;
+        out[N + p] = ov;
+    }
+}
+
+// K^T x for one point of one component (transposed tridiagonal rows)
+__device__ __forceinline__ double stencil_point_T(const Stencil &s, const double *X, int64_t p)
+{
+    double acc = 0.0;
+    int64_t stride = 1, rest = p;
+#pragma unroll
+    for (int mu = 0; mu < kMaxD; ++mu) {
+        if (mu < s.d) {
+            const int64_t nm = s.n[mu];
+            const int64_t i = rest % nm;
+            rest /= nm;
+            double r = s.di[mu][i] * X[p];
+            if (i > 0) r += s.up[mu][i - 1] * X[p - stride];
+            if (i + 1 < nm) r += s.lo[mu][i + 1] * X[p + stride];
+            acc += r;
+            stride *= nm;
+        }
+    }
+    return acc;
+}
+
+__global__ void k_kronsumT(Stencil s0, Stencil s1, int64_t N, const double *__restrict__ X,
+                           double *__restrict__ Y)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < N;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        Y[p] = stencil_point_T(s0, X, p);
+        Y[N + p] = stencil_point_T(s1, X + N, p);
+    }
+}
+
+// lam_n = lam + lU3 + lU2 + KT + J_g(U)^T (lF - lD2 - lD3); dp += the three
+// parameter gradients (block reduction, one atomic per block and parameter)
+__global__ void __launch_bounds__(256) k_adjoint_final(Model m, int64_t N, const double *__restrict__ U,
+                                                       const double *__restrict__ U2,
+                                                       const double *__restrict__ U3,
+                                                       const double *__restrict__ lam,
+                                                       const double *__restrict__ lU3,
+                                                       const double *__restrict__ lU2,
+                                                       const double *__restrict__ KT,
+                                                       const double *__restrict__ lF,
+                                                       const double *__restrict__ lD2,
+                                                       const double *__restrict__ lD3,
+                                                       double *__restrict__ lam_n, double *dp)
+{
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < N;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const double gu = lF[p] - lD2[p] - lD3[p], gv = lF[N + p] - lD2[N + p] - lD3[N + p];
+        double ou, ov;
+        jacT(m, U[p], U[N + p], gu, gv, ou, ov);
+        lam_n[p] = lam[p] + lU3[p] + lU2[p] + KT[p] + ou;
+        lam_n[N + p] = lam[N + p] + lU3[N + p] + lU2[N + p] + KT[N + p] + ov;
+        if (dp) {
+            double a0, a1, a2;
+            dparam_point(m, U[p], U[N + p], gu, gv, a0, a1, a2);
+            s0 += a0; s1 += a1; s2 += a2;
+            dparam_point(m, U2[p], U2[N + p], lD2[p], lD2[N + p], a0, a1, a2);
+            s0 += a0; s1 += a1; s2 += a2;
+            dparam_point(m, U3[p], U3[N + p], lD3[p], lD3[N + p], a0, a1, a2);
+            s0 += a0; s1 += a1; s2 += a2;
+        }
+    }
+    if (!dp) return;
+    __shared__ double red[3][256];
+    red[0][threadIdx.x] = s0;
+    red[1][threadIdx.x] = s1;
+    red[2][threadIdx.x] = s2;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int q = 0; q < 3; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int q = 0; q < 3; ++q) atomicAdd(dp + q, red[q][0]);
+}
+
+__global__ void __launch_bounds__(256) k_dot_accum(int64_t n, const double *__restrict__ a,
+                                                   const double *__restrict__ b, double w, double *out)
+{
+    double s = 0.0;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x)
+        s += a[p] * b[p];
+    __shared__ double red[256];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = 128; k > 0; k >>= 1) {
+        if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(out, w * red[0]);
+}
+
+__global__ void __launch_bounds__(256) k_dot_kterm(Model m, int64_t N, const double *__restrict__ U,
+                                                   const double *__restrict__ F,
+                                                   const double *__restrict__ lF, double *out)
+{
+    double s0 = 0.0, s1 = 0.0;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < N;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        double gu, gv;
+        react(m, U[p], U[N + p], gu, gv);
+        s0 += lF[p] * (F[p] - gu);
+        s1 += lF[N + p] * (F[N + p] - gv);
+    }
+    __shared__ double red[2][256];
+    red[0][threadIdx.x] = s0;
+    red[1][threadIdx.x] = s1;
+    __syncthreads();
+    for (int k = 128; k > 0; k >>= 1) {
+        if (threadIdx.x < k) {
+            red[0][threadIdx.x] += red[0][threadIdx.x + k];
+            red[1][threadIdx.x] += red[1][threadIdx.x + k];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        atomicAdd(out, red[0][0]);
+        atomicAdd(out + 1, red[1][0]);
+    }
+}
+
 int grid_for(int64_t n)
 {
     int64_t b = (n + 255) / 256;
@@ -281,6 +483,43 @@ void launch_final_f64(int64_t N, double *U, const double *a, double w1, const do
 void launch_add_g_f64(const Model &m, int64_t N, const double *U, double *F, cudaStream_t st)
 {
     k_add_g_f64<<<grid_for(N), 256, 0, st>>>(m, N, U, F);
+}
+
+void launch_axpy2_f64(int64_t N, const double *U, const double *a, double w1, const double *b, double w2,
+                      double *Y, cudaStream_t st)
+{
+    k_axpy2<<<grid_for(2 * N), 256, 0, st>>>(2 * N, U, a, w1, b, w2, Y);
+}
+void launch_gdiff_f64(const Model &m, int64_t N, const double *U, const double *Us, double *D, cudaStream_t st)
+{
+    k_gdiff<<<grid_for(N), 256, 0, st>>>(m, N, U, Us, D);
+}
+void launch_jacT_f64(const Model &m, int64_t N, const double *Us, const double *lam, double *out,
+                     cudaStream_t st)
+{
+    k_jacT<<<grid_for(N), 256, 0, st>>>(m, N, Us, lam, out);
+}
+void launch_kronsumT_f64(const Stencil *s2, int64_t N, const double *X, double *Y, cudaStream_t st)
+{
+    k_kronsumT<<<grid_for(N), 256, 0, st>>>(s2[0], s2[1], N, X, Y);
+}
+void launch_adjoint_final_f64(const Model &m, int64_t N, const double *U, const double *U2,
+                              const double *U3, const double *lam, const double *lU3, const double *lU2,
+                              const double *KT, const double *lF, const double *lD2, const double *lD3,
+                              double *lam_n, double *dp, cudaStream_t st)
+{
+    k_adjoint_final<<<grid_for(N), 256, 0, st>>>(m, N, U, U2, U3, lam, lU3, lU2, KT, lF, lD2, lD3, lam_n, dp);
+}
+
+void launch_dot_accum_f64(int64_t n, const double *a, const double *b, double w, double *out,
+                          cudaStream_t st)
+{
+    k_dot_accum<<<grid_for(n), 256, 0, st>>>(n, a, b, w, out);
+}
+void launch_dot_kterm_f64(const Model &m, int64_t N, const double *U, const double *F, const double *lF,
+                          double *out, cudaStream_t st)
+{
+    k_dot_kterm<<<grid_for(N), 256, 0, st>>>(m, N, U, F, lF, out);
 }
 
 void launch_nonfinite_scan(const double *x, int64_t count, int *flag, cudaStream_t st)
@@ -388,6 +627,17 @@ __global__ void k_extract(int64_t nn, const double *const *src, double *const *d
         dst[b][e] = src[b][e];
 }
 
+// dst_b = lo_b - ell_b hi_b  (phi_{ell-1} - ell phi_ell)
+__global__ void k_extract_deriv(int64_t nn, const double *const *lo, const double *const *hi,
+                                const int *ell, double *const *dst)
+{
+    const int b = blockIdx.y;
+    if (!dst[b]) return;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nn;
+         e += (int64_t)gridDim.x * blockDim.x)
+        dst[b][e] = lo[b][e] - (double)ell[b] * hi[b][e];
+}
+
 void batched_square_gemm(int n, int nb, const double *A, const double *B, double *C,
                          cudaStream_t st)
 {
@@ -481,6 +731,26 @@ ds_status phi_batch_f64(int n, const std::vector<PhiJob> &jobs, cudaStream_t st)
     cudaMemcpyAsync(dSrc, hsrc.data(), sizeof(void *) * nb, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(dDst, hdst.data(), sizeof(void *) * nb, cudaMemcpyHostToDevice, st);
     k_extract<<<g2, 256, 0, st>>>(nn, (const double *const *)dSrc, (double *const *)dDst);
+    bool any_d = false;
+    for (int b = 0; b < nb; ++b) any_d |= (jobs[b].dout != nullptr);
+    if (any_d) {
+        std::vector<double *> hlo(nb), hdd(nb);
+        std::vector<int> hell(nb);
+        for (int b = 0; b < nb; ++b) {
+            const int l = jobs[b].ell;
+            hlo[b] = (l == 1 ? p0 : p1) + b * nn;
+            hsrc[b] = (l == 1 ? p1 : p2) + b * nn;
+            hdd[b] = jobs[b].dout;
+            hell[b] = l;
+        }
+        // the tables are reused: dA <- lo, dSrc <- hi, dDst <- dout, ds_ <- ell
+        cudaMemcpyAsync(dA, hlo.data(), sizeof(void *) * nb, cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(dSrc, hsrc.data(), sizeof(void *) * nb, cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(dDst, hdd.data(), sizeof(void *) * nb, cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(ds_, hell.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st);
+        k_extract_deriv<<<g2, 256, 0, st>>>(nn, (const double *const *)dA, (const double *const *)dSrc, ds_,
+                                            (double *const *)dDst);
+    }
     cudaFreeAsync(ws, st);
     cudaFreeAsync(tab, st);
     DS_CUDA_TRY(cudaStreamSynchronize(st));

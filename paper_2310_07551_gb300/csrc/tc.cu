@@ -30,7 +30,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "tc.h"
@@ -41,7 +43,8 @@ namespace tc {
 using bf16 = __nv_bfloat16;
 
 constexpr int BM = 128, BN = 256, BK = 32, STAGES = 3;
-constexpr int kThreads = 192;
+constexpr int kThreads = 320;            // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
+constexpr int kEpiThreads = 256;
 constexpr uint32_t A_PLANE = BM * BK * 2;          // 8 KiB
 constexpr uint32_t B_PLANE = BN * BK * 2;          // 16 KiB
 constexpr uint32_t STAGE_A = 3 * A_PLANE;
@@ -58,13 +61,18 @@ constexpr uint32_t kSw128 = 2, kSw64 = 4;
 struct alignas(128) TcArgs {
     CUtensorMap tmA;
     CUtensorMap tmB;
-    int S, T, xs_stride, n;
+    int S, T, xs_stride, xs_div, n;
     int mtiles, ntiles, kchunks, out_kind;
     int64_t I, O, num_tiles;
     int64_t out_cs, out_ps;
     void *out;
     float alpha;
     DevStatus *status;
+    // split-K: tile t covers K part (t % ksplit) of base tile (t / ksplit);
+    // with ksplit > 1 every part writes FP32 partials to part_ws[part][s][N]
+    int ksplit, kpi;
+    int64_t part_stride;
+    float *part_ws;
 };
 
 // ---------------------------------------------------------------------------
@@ -260,7 +268,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mode_tc(const __grid_constant__
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(TFULL(b), 1);
-            mbar_init(TEMPTY(b), 128);
+            mbar_init(TEMPTY(b), kEpiThreads);
         }
         mbar_init(DRAIN, 1);
         *abort_flag = 0;
@@ -289,13 +297,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_mode_tc(const __grid_constant__
             for (int s = 0; s < STAGES; ++s) issued_phase[s] = -1;
             bool ok = true;
             for (int64_t tile = blockIdx.x; ok && tile < a.num_tiles; tile += gridDim.x) {
-                const TileCoord tc = decode<MODE1>(a, tile);
-                for (int it = 0; it < kiters; ++it) {
+                const int part = (int)(tile % a.ksplit);
+                const TileCoord tc = decode<MODE1>(a, tile / a.ksplit);
+                const int it0 = part * a.kpi, it1 = min(it0 + a.kpi, kiters);
+                for (int it = it0; it < it1; ++it) {
                     const int tt = it / a.kchunks, kc = it % a.kchunks;
                     if (!wait_bar(EMPTY(stage), phase ^ 1u, abort_flag, a.status, 1)) { ok = false; break; }
                     mbar_expect_tx(FULL(stage), STAGE_BYTES);
                     const uint32_t sA = base + stage * STAGE_BYTES, sB = sA + STAGE_A;
-                    const int xc = tc.s * a.xs_stride + tt, pc = tc.s * a.T + tt;
+                    const int xc = (tc.s / a.xs_div) * a.xs_stride + tt, pc = tc.s * a.T + tt;
                     if (MODE1) {
 #pragma unroll
                         for (int p = 0; p < 3; ++p)
@@ -338,7 +348,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_mode_tc(const __grid_constant__
                 if (!wait_bar(TEMPTY(acc), acc_phase ^ 1u, abort_flag, a.status, 2)) break;
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)acc * BN;
-                for (int it = 0; it < kiters; ++it) {
+                const int part = (int)(tile % a.ksplit);
+                const int it0 = part * a.kpi, it1 = min(it0 + a.kpi, kiters);
+                for (int it = it0; it < it1; ++it) {
                     if (!wait_bar(FULL(stage), phase, abort_flag, a.status, 3)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t sA = base + stage * STAGE_BYTES, sB = sA + STAGE_A;
@@ -355,7 +367,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mode_tc(const __grid_constant__
                                 ad = sdesc(sA + pa * A_PLANE + ks * 2048, A_PLANE / 2, 1024, kSw128);
                             }
                             bd = sdesc(sB + pb * B_PLANE + ks * 32, 16, 512, kSw64);
-                            mma_bf16(d, ad, bd, idesc, (it > 0 || ks > 0 || q > 0) ? 1u : 0u);
+                            mma_bf16(d, ad, bd, idesc, (it > it0 || ks > 0 || q > 0) ? 1u : 0u);
                         }
                     }
                     mma_commit(EMPTY(stage));
@@ -371,54 +383,80 @@ __global__ void __launch_bounds__(kThreads, 1) k_mode_tc(const __grid_constant__
             wait_bar(DRAIN, 0, &never, nullptr, 0);
         }
     } else {
-        // ---------------- epilogue (warps 2..5) ----------------
+        // ---------------- epilogue (warps 2..9) ----------------
+        // TMEM lane quarter = warp % 4; the two warps of a quarter split the
+        // 256 accumulator columns into halves.
         const int quarter = warp % 4;
+        const int half = (warp - 2) / 4;
         const int m = quarter * 32 + lane;
         int acc = 0;
         uint32_t acc_phase = 0;
         for (int64_t tile = blockIdx.x; tile < a.num_tiles; tile += gridDim.x) {
-            const TileCoord tc = decode<MODE1>(a, tile);
-            if (!wait_bar(TFULL(acc), acc_phase, abort_flag, a.status, 4)) break;
+            const int part = (int)(tile % a.ksplit);
+            const TileCoord tc = decode<MODE1>(a, tile / a.ksplit);
+            // split-K parts write FP32 partials; the reduction writes the output
+            const int out_kind = a.ksplit > 1 ? 1 : a.out_kind;
+            void *const out_ptr = a.ksplit > 1 ? (void *)(a.part_ws + part * a.part_stride) : a.out;
+            const int64_t out_cs = a.ksplit > 1 ? a.out_ps : a.out_cs;
+            // every lane waits, and the warp leaves together: tcgen05.ld below is
+            // .sync.aligned, so no lane may skip one that its warp executes
+            const bool ready = wait_bar(TFULL(acc), acc_phase, abort_flag, a.status, 4);
+            if (!__all_sync(0xffffffffu, ready)) break;
             tc_fence_after();
-            // row of the accumulator this thread owns
+            // row of the accumulator this thread owns, and the output stride
+            // between consecutive accumulator columns
             int64_t row_index;
             bool row_ok;
-            int64_t col_stride;
+            uint32_t col_stride;
             if (MODE1) {
                 const int i = tc.mt * BM + m;
                 row_ok = i < a.n;
                 row_index = i;
-                col_stride = a.n;               // consecutive fibres r
+                col_stride = (uint32_t)a.n;       // consecutive fibres r
             } else {
                 const int64_t x = (int64_t)tc.mt * BM + m;
                 row_ok = x < a.I;
                 row_index = x + a.I * ((int64_t)a.n * tc.o);
-                col_stride = a.I;               // consecutive output indices i
+                col_stride = (uint32_t)a.I;       // consecutive output indices i
             }
-            const int64_t col0 = (int64_t)tc.nt * BN;
             const int64_t col_lim = MODE1 ? a.O : (int64_t)a.n;
-            const int64_t obase = (int64_t)tc.s * a.out_cs;
+            const int64_t cbase = (int64_t)tc.nt * BN + half * (BN / 2);
+            // element offset of column cbase in this row
+            const int64_t rbase = (int64_t)tc.s * out_cs + row_index + cbase * (int64_t)col_stride;
 #pragma unroll 1
-            for (int c = 0; c < BN / 32; ++c) {
+            for (int c = 0; c < BN / 64; ++c) {
+                // warp-uniform exit (depends on the tile and c only), taken before
+                // the collective load so that every lane issues the same loads
+                const int64_t col0 = cbase + c * 32;
+                if (col0 >= col_lim) break;
                 uint32_t v[32];
-                tmem_ld32(tmem + (uint32_t)acc * BN + (uint32_t)(c * 32) + ((uint32_t)(quarter * 32) << 16), v);
+                tmem_ld32(tmem + (uint32_t)acc * BN + (uint32_t)(half * (BN / 2) + c * 32) +
+                              ((uint32_t)(quarter * 32) << 16),
+                          v);
                 if (!row_ok) continue;
+                const int jmax = (col_lim - col0 >= 32) ? 32 : (int)(col_lim - col0);
+                // offsets from here are below 32 * col_stride < 2^32
+                const int64_t e0 = rbase + (int64_t)(c * 32) * col_stride;
+                if (out_kind == 0) {
+                    bf16 *o0 = (bf16 *)out_ptr + e0;
+                    bf16 *o1 = o0 + a.out_ps;
+                    bf16 *o2 = o1 + a.out_ps;
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int64_t col = col0 + c * 32 + j;
-                    if (col >= col_lim) break;
-                    const int64_t idx = obase + row_index + col * col_stride;
-                    const float val = __uint_as_float(v[j]) * a.alpha;
-                    if (a.out_kind == 0) {
-                        bf16 p0, p1, p2;
-                        split3f(val, p0, p1, p2);
-                        bf16 *o = (bf16 *)a.out;
-                        o[idx] = p0;
-                        o[idx + a.out_ps] = p1;
-                        o[idx + 2 * a.out_ps] = p2;
-                    } else {
-                        ((float *)a.out)[idx] = val;
+                    for (int j = 0; j < 32; ++j) {
+                        if (j < jmax) {
+                            bf16 p0, p1, p2;
+                            split3f(__uint_as_float(v[j]) * a.alpha, p0, p1, p2);
+                            const uint32_t off = (uint32_t)j * col_stride;
+                            o0[off] = p0;
+                            o1[off] = p1;
+                            o2[off] = p2;
+                        }
                     }
+                } else {
+                    float *o = (float *)out_ptr + e0;
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if (j < jmax) o[(uint32_t)j * col_stride] = __uint_as_float(v[j]) * a.alpha;
                 }
             }
             tc_fence_before();
@@ -518,17 +556,140 @@ __device__ __forceinline__ double stencil_k(const Stencil &s, const double *U, i
     return acc;
 }
 
-// F = K U + g(U) (FP64) for both components, stored as BF16 planes
-// Fp[c][plane][N].
-__global__ void k_rhs_planes(Stencil s0, Stencil s1, Model m, int64_t N, const double *__restrict__ U,
+// Exact split of an FP64 value into FP32 hi + lo with integer operations only
+// (GB300's FP64 pipe is ~1/64 of its FP32 rate, so the reduced-precision step
+// keeps FP64 arithmetic for the state update alone).  hi takes the leading
+// 24 significant bits, lo the next 29 rounded to 24: u = hi + lo to 2^-48
+// relative.  |u| outside [2^-74, 2^127] falls back to hi = (float)u, lo = 0.
+__device__ __forceinline__ void split_hilo(double u, float &hi, float &lo)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(u);
+    const unsigned h32 = (unsigned)(b >> 32), l32 = (unsigned)b;
+    const int e = (int)((h32 >> 20) & 0x7FF);
+    if (e < 949 || e > 1150) {
+        hi = (float)u;
+        lo = 0.0f;
+        return;
+    }
+    const unsigned sign = h32 & 0x80000000u;
+    const unsigned top23 = ((h32 & 0xFFFFFu) << 3) | (l32 >> 29);
+    hi = __uint_as_float(sign | ((unsigned)(e - 1023 + 127) << 23) | top23);
+    const float rest = __uint2float_rn(l32 & 0x1FFFFFFFu);            // < 2^29
+    const float scale = __uint_as_float((unsigned)(e - 1075 + 127) << 23);  // 2^(e-1075)
+    lo = __uint_as_float(sign | __float_as_uint(rest * scale));
+}
+
+// FP32 copy of the tridiagonal bands of one component.
+struct StencilF {
+    int d;
+    int64_t n[kMaxD];
+    const float *lo[kMaxD], *up[kMaxD], *rsum[kMaxD];   // rsum = lo + di + up
+    int has_rsum[kMaxD];
+};
+
+// K u for one point of one component from hi/lo parts: each tridiagonal row
+// is written as lo (u_{i-1} - u_i) + up (u_{i+1} - u_i) + (lo + di + up) u_i,
+// with the differences formed as (h_a - h_b) + (l_a - l_b) in FP32, so the
+// cancellation of a smooth field costs no more than 2^-24 of the difference.
+__device__ __forceinline__ float stencil_hilo(const StencilF &s, const double *U, int64_t p, float hc,
+                                              float lc)
+{
+    float acc = 0.0f;
+    int64_t stride = 1, rest = p;
+#pragma unroll
+    for (int mu = 0; mu < kMaxD; ++mu) {
+        if (mu < s.d) {
+            const int64_t nm = s.n[mu];
+            const int64_t i = rest % nm;
+            rest /= nm;
+            float r = 0.0f;
+            if (i > 0) {
+                float h, l;
+                split_hilo(U[p - stride], h, l);
+                r = fmaf(s.lo[mu][i], (h - hc) + (l - lc), r);
+            }
+            if (i + 1 < nm) {
+                float h, l;
+                split_hilo(U[p + stride], h, l);
+                r = fmaf(s.up[mu][i], (h - hc) + (l - lc), r);
+            }
+            if (s.has_rsum[mu]) r = fmaf(s.rsum[mu][i], hc + lc, r);
+            acc += r;
+            stride *= nm;
+        }
+    }
+    return acc;
+}
+
+// Double-float arithmetic (a value is an unevaluated sum hi + lo of two
+// floats): Knuth's two-sum and the FMA two-product (Dekker 1971) give the
+// rounding error of a float sum or product exactly, so g can be evaluated to
+// ~2^-44 with FP32 instructions only.  Needed because the reaction terms
+// cancel near a steady state (Schnakenberg: a - u + u^2 v ~ 0 while each term
+// is O(1), then multiplied by gamma = 1000).
+struct dfl {
+    float hi, lo;
+};
+// (explicitly rounded intrinsics: the transformations must not be contracted)
+__device__ __forceinline__ dfl df_two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ dfl df_add(dfl a, dfl b)
+{
+    dfl s = df_two_sum(a.hi, b.hi);
+    const float t = __fadd_rn(__fadd_rn(s.lo, a.lo), b.lo);
+    const float h = __fadd_rn(s.hi, t);
+    return {h, __fsub_rn(t, __fsub_rn(h, s.hi))};
+}
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+    const float h = __fadd_rn(p, e);
+    return {h, __fsub_rn(e, __fsub_rn(h, p))};
+}
+__device__ __forceinline__ dfl df_neg(dfl a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ float df_val(dfl a) { return a.hi + a.lo; }
+
+// g(u, v) in double-float from the hi/lo parts of the FP64 state.  The
+// parameters come pre-split on the host (pp[k] = hi/lo of p[k]).
+struct ModelDF {
+    int model;
+    dfl p[3];
+};
+__device__ __forceinline__ void react_df(const ModelDF &m, dfl u, dfl v, float &gu, float &gv)
+{
+    if (m.model == DS_SCHNAKENBERG) {
+        const dfl u2v = df_mul(df_mul(u, u), v);
+        gu = df_val(df_mul(m.p[0], df_add(df_add(m.p[1], df_neg(u)), u2v)));
+        gv = df_val(df_mul(m.p[0], df_add(m.p[2], df_neg(u2v))));
+    } else if (m.model == DS_FHN) {
+        const dfl u3 = df_mul(df_mul(u, u), u);
+        gu = df_val(df_add(df_add(u, df_neg(u3)), df_neg(v)));
+        gv = df_val(df_mul(m.p[0], df_add(df_add(u, df_neg(df_mul(m.p[1], v))), df_neg(m.p[2]))));
+    } else {
+        gu = 0.0f;
+        gv = 0.0f;
+    }
+}
+
+// F = K U + g(U) for both components, stored as BF16 planes Fp[c][plane][N].
+__global__ void k_rhs_planes(StencilF s0, StencilF s1, ModelDF m, int64_t N, const double *__restrict__ U,
                              bf16 *__restrict__ Fp)
 {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < N;
          p += (int64_t)gridDim.x * blockDim.x) {
-        double gu, gv;
-        react_d(m, U[p], U[N + p], gu, gv);
-        store_planes_f(Fp, N, p, (float)(stencil_k(s0, U, p) + gu));
-        store_planes_f(Fp + 3 * N, N, p, (float)(stencil_k(s1, U + N, p) + gv));
+        float hu, lu, hv, lv;
+        split_hilo(U[p], hu, lu);
+        split_hilo(U[N + p], hv, lv);
+        float gu, gv;
+        react_df(m, dfl{hu, lu}, dfl{hv, lv}, gu, gv);
+        store_planes_f(Fp, N, p, stencil_hilo(s0, U, p, hu, lu) + gu);
+        store_planes_f(Fp + 3 * N, N, p, stencil_hilo(s1, U + N, p, hv, lv) + gv);
     }
 }
 
@@ -541,27 +702,30 @@ __global__ void k_stage_planes(Model m, int64_t N, const double *__restrict__ U,
 {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < N;
          p += (int64_t)gridDim.x * blockDim.x) {
-        const float u = (float)U[p], v = (float)U[N + p];
+        float hu, lu, hv, lv;
+        split_hilo(U[p], hu, lu);
+        split_hilo(U[N + p], hv, lv);
         float du = a[p], dv = a[cs_a + p];
         if (b) {
             du += b[p];
             dv += b[cs_b + p];
         }
         float Du, Dv;
-        react_diff(m, u, v, du, dv, Du, Dv);
+        react_diff(m, hu + lu, hv + lv, du, dv, Du, Dv);
         store_planes_f(Dp, N, p, Du);
         store_planes_f(Dp + 3 * N, N, p, Dv);
     }
 }
 
-// U <- (U + a) + b in FP64 (both components).
+// U <- U + (a + b) in FP64 (both components); the two FP32 increments are
+// summed in FP32 first, so each value costs one conversion and one FP64 add.
 __global__ void k_final_mixed(int64_t N, double *__restrict__ U, const float *__restrict__ a, int64_t cs_a,
                               const float *__restrict__ b, int64_t cs_b)
 {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < N;
          p += (int64_t)gridDim.x * blockDim.x) {
-        U[p] = (U[p] + (double)a[p]) + (double)b[p];
-        U[N + p] = (U[N + p] + (double)a[cs_a + p]) + (double)b[cs_b + p];
+        U[p] += (double)(a[p] + b[p]);
+        U[N + p] += (double)(a[cs_a + p] + b[cs_b + p]);
     }
 }
 
@@ -709,6 +873,8 @@ struct ModeLaunch {
     TcArgs args;
     bool mode1 = false;
     int grid = 0;
+    int64_t base_tiles = 0;    // output tiles before the split-K factor
+    int64_t N = 0;             // points per output combo
 };
 
 static int num_sms()
@@ -725,12 +891,12 @@ static int num_sms()
 
 static int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
-// Describe Y_s = sum_t X_{s xs + t} x_mu P_{s T + t} for s < S, t < T.
+// Describe Y_s = sum_t X_{(s / xs_div) xs + t} x_mu P_{s T + t} for s < S, t < T.
 //   X: BF16 planes [xcombos][3][N];  P: BF16 planes [pcombos][3][n_mu][ldp]
 //   out: planes [S][3][N] (out_kind 0) or FP32 [S][N] (out_kind 1)
 static ds_status describe(ModeLaunch &L, int d, const int64_t *n, int mu, const bf16 *X, int xcombos,
-                          const bf16 *P, int pcombos, int ldp, int S, int T, int xs_stride, void *out,
-                          int out_kind, float alpha, DevStatus *status)
+                          const bf16 *P, int pcombos, int ldp, int S, int T, int xs_stride, int xs_div,
+                          void *out, int out_kind, float alpha, DevStatus *status)
 {
     int64_t N = 1;
     for (int q = 0; q < d; ++q) N *= n[q];
@@ -778,6 +944,7 @@ static ds_status describe(ModeLaunch &L, int d, const int64_t *n, int mu, const 
     a.S = S;
     a.T = T;
     a.xs_stride = xs_stride;
+    a.xs_div = xs_div;
     a.n = (int)nm;
     a.kchunks = (int)cdiv(nm, BK);
     a.out_kind = out_kind;
@@ -786,8 +953,49 @@ static ds_status describe(ModeLaunch &L, int d, const int64_t *n, int mu, const 
     a.out_cs = out_kind == 0 ? 3 * N : N;
     a.alpha = alpha;
     a.status = status;
+    a.ksplit = 1;
+    a.kpi = a.T * a.kchunks;
+    a.part_stride = (int64_t)S * N;
+    a.part_ws = nullptr;
+    L.base_tiles = a.num_tiles;
+    L.N = N;
     L.grid = (int)std::min<int64_t>(a.num_tiles, num_sms());
     return DS_OK;
+}
+
+// Split the K loop of every output tile into ksplit parts.
+static void set_split(ModeLaunch &L, int ksplit, float *ws)
+{
+    TcArgs &a = L.args;
+    const int kiters = a.T * a.kchunks;
+    a.ksplit = ksplit;
+    a.kpi = (kiters + ksplit - 1) / ksplit;
+    a.part_ws = ws;
+    a.num_tiles = L.base_tiles * ksplit;
+    L.grid = (int)std::min<int64_t>(a.num_tiles, num_sms());
+}
+
+// Sum the split-K partials in part order (deterministic) and write the
+// launch's real output: BF16 planes [S][3][N] or FP32 [S][N].
+__global__ void k_split_reduce(int64_t total, int64_t N, int ksplit, const float *__restrict__ ws, int out_kind,
+                               void *out)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        float v = ws[e];
+        for (int p = 1; p < ksplit; ++p) v += ws[p * total + e];
+        if (out_kind == 0) {
+            const int64_t s = e / N, i = e - s * N;
+            bf16 p0, p1, p2;
+            split3f(v, p0, p1, p2);
+            bf16 *o = (bf16 *)out + s * 3 * N + i;
+            o[0] = p0;
+            o[N] = p1;
+            o[2 * N] = p2;
+        } else {
+            ((float *)out)[e] = v;
+        }
+    }
 }
 
 static void launch(const ModeLaunch &L, cudaStream_t st)
@@ -802,6 +1010,70 @@ static void launch(const ModeLaunch &L, cudaStream_t st)
         k_mode_tc<true><<<L.grid, kThreads, SMEM_BYTES, st>>>(L.args);
     else
         k_mode_tc<false><<<L.grid, kThreads, SMEM_BYTES, st>>>(L.args);
+    if (L.args.ksplit > 1) {
+        const int64_t total = L.args.part_stride;
+        k_split_reduce<<<(int)std::min<int64_t>((total + 255) / 256, 152 * 8), 256, 0, st>>>(
+            total, L.N, L.args.ksplit, L.args.part_ws, L.args.out_kind, L.args.out);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner: for launches with fewer than two waves of output tiles, time
+// split-K factors 1..4 (each part keeping >= 4 K chunks) on the launch's own
+// buffers and keep the fastest.  Choices are cached per launch shape for the
+// process, so equal shapes in different plans run identical arithmetic.
+// ---------------------------------------------------------------------------
+struct ShapeKey {
+    bool mode1;
+    int n, S, T;
+    int64_t I, O;
+    bool operator<(const ShapeKey &o) const
+    {
+        return std::tie(mode1, n, S, T, I, O) < std::tie(o.mode1, o.n, o.S, o.T, o.I, o.O);
+    }
+};
+static std::mutex g_tune_mu;
+static std::map<ShapeKey, int> g_tuned;
+
+static int max_split(const ModeLaunch &L)
+{
+    const int kiters = L.args.T * L.args.kchunks;
+    if (L.base_tiles >= 2 * (int64_t)num_sms()) return 1;
+    return std::max(1, std::min(4, kiters / 4));
+}
+
+static int autotune_split(ModeLaunch &L, float *ws, cudaStream_t st)
+{
+    const ShapeKey key{L.mode1, L.args.n, L.args.S, L.args.T, L.args.I, L.args.O};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) return it->second;
+    }
+    const int kmax = max_split(L);
+    int best = 1;
+    if (kmax > 1) {
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        float best_ms = 1e30f;
+        for (int k = 1; k <= kmax; ++k) {
+            set_split(L, k, ws);
+            launch(L, st);
+            cudaEventRecord(e0, st);
+            for (int r = 0; r < 2; ++r) launch(L, st);
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_ms * 0.97f) { best_ms = ms; best = k; }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[key] = best;
+    return best;
 }
 
 static int round8(int64_t n) { return (int)((n + 7) / 8 * 8); }
@@ -833,8 +1105,12 @@ struct MixedPlan {
     bf16 *Z2 = nullptr;        // [3k][3][N] (d = 3)
     float *incF = nullptr;     // [2][3][N]
     float *incD = nullptr;     // [2][N]
-    // launches[c][group][mode]; group 0 = F, 1 = D2 (slot 2), 2 = D3 (slot 4)
-    ModeLaunch L[2][3][kMaxD];
+    float *bands = nullptr;    // FP32 bands [c][mu][lo, up, rowsum][n_mu]
+    float *part_ws = nullptr;  // split-K partials
+    StencilF stf[2];
+    // launches[group][mode], both components in one launch;
+    // group 0 = F, 1 = D2 (slot 2), 2 = D3 (slot 4)
+    ModeLaunch L[3][kMaxD];
 };
 
 ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatus *status, MixedPlan **out)
@@ -852,22 +1128,71 @@ ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatu
     }
     mp->status = status;
     const int d = mp->d, k = mp->k;
+    if (!set->tridiag[0] || !set->tridiag[1]) {
+        delete mp;
+        return fail(DS_ERR_UNSUPPORTED, "reduced-precision paths need tridiagonal A_mu (use DS_PREC_F64)");
+    }
+    // FP32 bands: lower, upper and row sum (lo + di + up; zero for the Neumann Laplacian)
+    {
+        int64_t tot = 0;
+        for (int mu = 0; mu < d; ++mu) tot += 2 * 3 * mp->n[mu];
+        std::vector<float> hb(tot);
+        int64_t off = 0;
+        for (int c = 0; c < 2; ++c) {
+            mp->stf[c].d = d;
+            for (int mu = 0; mu < kMaxD; ++mu) {
+                mp->stf[c].n[mu] = mp->n[mu];
+                mp->stf[c].has_rsum[mu] = 0;
+            }
+            for (int mu = 0; mu < d; ++mu) {
+                const int64_t nm = mp->n[mu];
+                std::vector<double> band(3 * nm);
+                cudaMemcpy(band.data(), set->tri_dev + set->tri_off[c][mu], sizeof(double) * 3 * nm,
+                           cudaMemcpyDeviceToHost);
+                for (int64_t i = 0; i < nm; ++i) {
+                    hb[off + i] = (float)band[i];
+                    hb[off + nm + i] = (float)band[2 * nm + i];
+                    const double rsum = band[i] + band[nm + i] + band[2 * nm + i];
+                    hb[off + 2 * nm + i] = (float)rsum;
+                    if (rsum != 0.0) mp->stf[c].has_rsum[mu] = 1;
+                }
+                mp->stf[c].lo[mu] = (const float *)(intptr_t)off;   // fixed up below
+                off += 3 * nm;
+            }
+        }
+        if (cudaMalloc(&mp->bands, sizeof(float) * tot) != cudaSuccess) {
+            cudaGetLastError();
+            delete mp;
+            return fail(DS_ERR_OOM, "band copy");
+        }
+        cudaMemcpy(mp->bands, hb.data(), sizeof(float) * tot, cudaMemcpyHostToDevice);
+        for (int c = 0; c < 2; ++c)
+            for (int mu = 0; mu < d; ++mu) {
+                const int64_t o = (int64_t)(intptr_t)mp->stf[c].lo[mu];
+                const int64_t nm = mp->n[mu];
+                mp->stf[c].lo[mu] = mp->bands + o;
+                mp->stf[c].up[mu] = mp->bands + o + nm;
+                mp->stf[c].rsum[mu] = mp->bands + o + 2 * nm;
+            }
+    }
     const int64_t N = mp->N;
     // phi planes: per component, per group, per mode, combos
     //   group F: mode 0 and middle: 3k combos (stage q' in {slot 0, 1, 3}, term i)
     //            last mode: 3k combos with w_q tau eta^{(1)}_i folded in
     //   group D2 (slot 2), D3 (slot 4): k combos per mode; last mode folds w eta^{(2)}
     const int Fslots[3] = {0, 1, 3};
+    // phi planes, per (group, mode): [c][combo][plane][n_mu][ldp]
+    //   group F: 3k combos (stage q' in {slot 0, 1, 3}, term i); the last mode's
+    //            matrices carry w_q tau eta^{(1)}_i
+    //   group D2 (slot 2), D3 (slot 4): k combos; last mode carries w eta^{(2)}
     int64_t total = 0;
-    std::vector<int64_t> goff(2 * 3 * kMaxD);
-    auto gidx = [&](int c, int g, int mu) { return (c * 3 + g) * kMaxD + mu; };
-    for (int c = 0; c < 2; ++c)
-        for (int g = 0; g < 3; ++g)
-            for (int mu = 0; mu < d; ++mu) {
-                goff[gidx(c, g, mu)] = total;
-                const int combos = g == 0 ? 3 * k : k;
-                total += (int64_t)combos * 3 * mp->n[mu] * round8(mp->n[mu]);
-            }
+    int64_t goff[3][kMaxD];
+    for (int g = 0; g < 3; ++g)
+        for (int mu = 0; mu < d; ++mu) {
+            goff[g][mu] = total;
+            const int combos = g == 0 ? 3 * k : k;
+            total += (int64_t)2 * combos * 3 * mp->n[mu] * round8(mp->n[mu]);
+        }
     auto cleanup = [&](ds_status s, const char *msg) {
         mixed_plan_destroy(mp);
         return fail(s, msg);
@@ -875,23 +1200,22 @@ ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatu
     if (cudaMalloc(&mp->Pp, sizeof(bf16) * total) != cudaSuccess ||
         cudaMalloc(&mp->Fp, sizeof(bf16) * 6 * N) != cudaSuccess ||
         cudaMalloc(&mp->Dp, sizeof(bf16) * 6 * N) != cudaSuccess ||
-        cudaMalloc(&mp->Z1, sizeof(bf16) * 9 * k * N) != cudaSuccess ||
-        (d == 3 && cudaMalloc(&mp->Z2, sizeof(bf16) * 9 * k * N) != cudaSuccess) ||
+        cudaMalloc(&mp->Z1, sizeof(bf16) * 18 * k * N) != cudaSuccess ||
+        (d == 3 && cudaMalloc(&mp->Z2, sizeof(bf16) * 18 * k * N) != cudaSuccess) ||
         cudaMalloc(&mp->incF, sizeof(float) * 6 * N) != cudaSuccess ||
         cudaMalloc(&mp->incD, sizeof(float) * 2 * N) != cudaSuccess) {
         cudaGetLastError();
         return cleanup(DS_ERR_OOM, "split-BF16 workspace");
     }
     const double tau = set->tau;
-    for (int c = 0; c < 2; ++c)
-        for (int g = 0; g < 3; ++g)
-            for (int mu = 0; mu < d; ++mu) {
-                const int64_t nm = mp->n[mu];
-                const int ldp = round8(nm);
-                const int64_t psz = 3 * nm * ldp;
-                bf16 *dst = mp->Pp + goff[gidx(c, g, mu)];
-                const bool last = (mu == d - 1);
-                const int combos = g == 0 ? 3 * k : k;
+    for (int g = 0; g < 3; ++g)
+        for (int mu = 0; mu < d; ++mu) {
+            const int64_t nm = mp->n[mu];
+            const int ldp = round8(nm);
+            const int64_t psz = 3 * nm * ldp;
+            const bool last = (mu == d - 1);
+            const int combos = g == 0 ? 3 * k : k;
+            for (int c = 0; c < 2; ++c)
                 for (int cb = 0; cb < combos; ++cb) {
                     int slot, i;
                     if (g == 0) { slot = Fslots[cb / k]; i = cb % k; }
@@ -899,37 +1223,67 @@ ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatu
                     const SplitCoeffs &co = set->co[kSlotEll[slot] - 1];
                     const double scale = last ? kSlotW[slot] * tau * co.eta[i] : 1.0;
                     const double *src = set->P_dev + set->P_off[c][slot][i][mu];
-                    k_split_matrix<<<pw_grid(nm * ldp), 256>>>((int)nm, ldp, src, 0, scale, dst + cb * psz);
+                    bf16 *dst = mp->Pp + goff[g][mu] + (int64_t)(c * combos + cb) * psz;
+                    k_split_matrix<<<pw_grid(nm * ldp), 256>>>((int)nm, ldp, src, 0, scale, dst);
                 }
-            }
-    // launch descriptors
-    for (int c = 0; c < 2; ++c)
-        for (int g = 0; g < 3; ++g) {
-            const int S0 = g == 0 ? 3 * k : k;       // stacked P on the shared input
-            const bf16 *Xin = g == 0 ? mp->Fp + c * 3 * N : mp->Dp + c * 3 * N;
-            bf16 *Zs[2] = {mp->Z1, mp->Z2};
-            for (int mu = 0; mu < d; ++mu) {
-                const bf16 *P = mp->Pp + goff[gidx(c, g, mu)];
-                const int ldp = round8(mp->n[mu]);
-                const bool last = (mu == d - 1);
-                const bf16 *X = mu == 0 ? Xin : Zs[(mu - 1) % 2];
-                const int xcombos = mu == 0 ? 1 : S0;
-                void *out;
-                int S, T, xs, kind;
-                if (!last) {
-                    S = S0; T = 1; xs = mu == 0 ? 0 : 1; kind = 0;
-                    out = Zs[mu % 2];
-                } else {
-                    S = g == 0 ? 3 : 1; T = k; xs = k; kind = 1;
-                    out = g == 0 ? (void *)(mp->incF + c * 3 * N) : (void *)(mp->incD + c * N);
-                    if (mu == 0) xs = 0;
-                }
-                r = describe(mp->L[c][g][mu], d, mp->n, mu, X, xcombos, P, S0, ldp, S, T, xs, out, kind, 1.0f,
-                             status);
-                if (r != DS_OK) { mixed_plan_destroy(mp); return r; }
-            }
         }
+    // launch descriptors: stack index s = c * S0 + combo
+    for (int g = 0; g < 3; ++g) {
+        const int S0 = g == 0 ? 3 * k : k;            // stacked P per component
+        const bf16 *Xin = g == 0 ? mp->Fp : mp->Dp;   // [c][plane][N]
+        bf16 *Zs[2] = {mp->Z1, mp->Z2};
+        for (int mu = 0; mu < d; ++mu) {
+            const bf16 *P = mp->Pp + goff[g][mu];
+            const int ldp = round8(mp->n[mu]);
+            const bool last = (mu == d - 1);
+            const bf16 *X = mu == 0 ? Xin : Zs[(mu - 1) % 2];
+            const int xcombos = mu == 0 ? 2 : 2 * S0;
+            void *out;
+            int S, T, xs, xdiv, kind;
+            if (!last) {
+                // Z_{c, combo} = X_c (or Z_{c, combo}) x_mu P_{c, combo}
+                S = 2 * S0; T = 1; kind = 0;
+                xs = 1; xdiv = mu == 0 ? S0 : 1;
+                out = Zs[mu % 2];
+            } else {
+                // increment of (c, stage): sum over terms t of Z_{c, stage k + t} x_d P~
+                S = g == 0 ? 6 : 2; T = k; kind = 1;
+                xs = k; xdiv = 1;
+                if (mu == 0) { xs = 1; xdiv = S / 2; T = 1; }   // not reached for d >= 2
+                out = g == 0 ? (void *)mp->incF : (void *)mp->incD;
+            }
+            r = describe(mp->L[g][mu], d, mp->n, mu, X, xcombos, P, 2 * S0, ldp, S, T, xs, xdiv, out, kind,
+                         1.0f, status);
+            if (r != DS_OK) { mixed_plan_destroy(mp); return r; }
+        }
+    }
     if (cudaDeviceSynchronize() != cudaSuccess) return cleanup(DS_ERR_CUDA, "phi plane split");
+    // split-K autotuning for launches with too few output tiles
+    {
+        int64_t ws_elems = 0;
+        for (int g = 0; g < 3; ++g)
+            for (int mu = 0; mu < d; ++mu) {
+                const ModeLaunch &L = mp->L[g][mu];
+                if (max_split(L) > 1) ws_elems = std::max<int64_t>(ws_elems, max_split(L) * L.args.part_stride);
+            }
+        if (ws_elems > 0) {
+            if (cudaMalloc(&mp->part_ws, sizeof(float) * ws_elems) != cudaSuccess) {
+                cudaGetLastError();
+                return cleanup(DS_ERR_OOM, "split-K workspace");
+            }
+            cudaStream_t ts;
+            cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking);
+            for (int g = 0; g < 3; ++g)
+                for (int mu = 0; mu < d; ++mu) {
+                    ModeLaunch &L = mp->L[g][mu];
+                    const int k = autotune_split(L, mp->part_ws, ts);
+                    set_split(L, k, k > 1 ? mp->part_ws : nullptr);
+                }
+            cudaStreamSynchronize(ts);
+            cudaStreamDestroy(ts);
+            if (cudaGetLastError() != cudaSuccess) return cleanup(DS_ERR_CUDA, "split-K autotuning");
+        }
+    }
     *out = mp;
     return DS_OK;
 }
@@ -944,7 +1298,21 @@ void mixed_plan_destroy(MixedPlan *mp)
     cudaFree(mp->Z2);
     cudaFree(mp->incF);
     cudaFree(mp->incD);
+    cudaFree(mp->bands);
+    cudaFree(mp->part_ws);
     delete mp;
+}
+
+// host split of the model parameters into double-float pairs
+static ModelDF model_df(const Model &m)
+{
+    ModelDF r;
+    r.model = m.model;
+    for (int k = 0; k < 3; ++k) {
+        const float h = (float)m.p[k];
+        r.p[k] = {h, (float)(m.p[k] - (double)h)};
+    }
+    return r;
 }
 
 // useful (FP32-equivalent) flops of one mode-product launch
@@ -963,16 +1331,15 @@ int enqueue_step_mixed(MixedPlan *mp, const ds_phi_set *set, const Model &model,
     Prof dummy;
     Prof &P = prof ? *prof : dummy;
     auto group = [&](int g) {
-        for (int c = 0; c < 2; ++c)
-            for (int mu = 0; mu < d; ++mu) {
-                P.begin(st, 0, launch_flops(mp->L[c][g][mu], N));
-                launch(mp->L[c][g][mu], st);
-                P.end(st);
-                ++L;
-            }
+        for (int mu = 0; mu < d; ++mu) {
+            P.begin(st, 0, launch_flops(mp->L[g][mu], N));
+            launch(mp->L[g][mu], st);
+            P.end(st);
+            ++L;
+        }
     };
     P.begin(st, 2, 0.0);
-    k_rhs_planes<<<pw_grid(N), 256, 0, st>>>(sten[0], sten[1], model, N, U, mp->Fp);
+    k_rhs_planes<<<pw_grid(N), 256, 0, st>>>(mp->stf[0], mp->stf[1], model_df(model), N, U, mp->Fp);
     P.end(st);
     ++L;
     group(0);
@@ -1039,7 +1406,7 @@ ds_status tucker_mixed(const ds_grid *grid, const double *X, double *Y, const do
         const bool last = (mu == d - 1);
         void *out = last ? (void *)outf : (void *)bufs[mu % 2];
         ModeLaunch ml;
-        r = describe(ml, d, grid->n, mu, in, 1, pcur, 1, ldp, 1, 1, 0, out, last ? 1 : 0, 1.0f, status);
+        r = describe(ml, d, grid->n, mu, in, 1, pcur, 1, ldp, 1, 1, 0, 1, out, last ? 1 : 0, 1.0f, status);
         if (r != DS_OK) { cudaFreeAsync(ws, st); return r; }
         launch(ml, st);
         in = bufs[mu % 2];

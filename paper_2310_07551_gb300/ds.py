@@ -58,11 +58,18 @@ def lib() -> ctypes.CDLL:
             "ds_plan_create": ([gp, pp, _vp, ctypes.c_int, ctypes.POINTER(_vp)], ctypes.c_int),
             "ds_step": ([_vp, _vp, _vp], ctypes.c_int),
             "ds_integrate": ([_vp, _vp, ctypes.c_int64, _vp], ctypes.c_int),
+            "ds_step_backward": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
             "ds_plan_sync": ([_vp, _vp, ctypes.c_int], ctypes.c_int),
             "ds_plan_kernels_per_step": ([_vp], ctypes.c_int64),
             "ds_plan_profile": ([_vp, ctypes.c_int], ctypes.c_int),
             "ds_plan_profile_read": ([_vp, _dp, ctypes.POINTER(ctypes.c_int64), _dp], ctypes.c_int),
             "ds_plan_destroy": ([_vp], ctypes.c_int),
+            "ds_batch_create": ([ctypes.c_int, gp, ctypes.POINTER(_vp), _dp, pp, ctypes.c_int,
+                                 ctypes.POINTER(_vp)], ctypes.c_int),
+            "ds_batch_integrate": ([_vp, ctypes.POINTER(_vp), ctypes.c_int64, _vp], ctypes.c_int),
+            "ds_batch_sync": ([_vp], ctypes.c_int),
+            "ds_batch_kernels_per_step": ([_vp], ctypes.c_int64),
+            "ds_batch_destroy": ([_vp], ctypes.c_int),
             "ds_last_error": ([], ctypes.c_char_p),
             "ds_version": ([], ctypes.c_char_p),
         }
@@ -161,6 +168,18 @@ class Plan:
         check(lib().ds_step(self._h, _dptr(U), _stream_ptr(stream)))
         return U
 
+    def step_backward(self, U, lam, dparams=None, dscale=None, stream=None):
+        """dL/dU_n for lam = dL/dU_{n+1} at the step that started from U;
+        adds dL/dp (3 model parameters) into dparams and dL/ds (relative
+        scaling of each component's A) into dscale if given."""
+        import torch
+        out = torch.empty_like(lam)
+        check(lib().ds_step_backward(self._h, _dptr(U), _dptr(lam), _dptr(out),
+                                     _dptr(dparams) if dparams is not None else None,
+                                     _dptr(dscale) if dscale is not None else None,
+                                     _stream_ptr(stream)))
+        return out
+
     def integrate(self, U, nsteps: int, stream=None):
         check(lib().ds_integrate(self._h, _dptr(U), int(nsteps), _stream_ptr(stream)))
         return U
@@ -222,3 +241,45 @@ def tucker_static(X, Ls, transpose: bool = False, stream=None):
     check(lib().ds_tucker_static(ctypes.byref(g), _dptr(X), _dptr(Y), arr, int(transpose),
                                  _stream_ptr(stream)))
     return Y
+
+
+class Batch:
+    """ds_batch: independent instances stepped together (one CUDA graph with
+    a captured stream per instance)."""
+
+    def __init__(self, dims_list, As_list, taus, model: str, params_list, precision: str = "bf16x6"):
+        n = len(dims_list)
+        grids = (Grid * n)(*[make_grid(dm) for dm in dims_list])
+        self._packed = [pack_A(As) for As in As_list]
+        Aptr = (_vp * n)(*[a.ctypes.data for a in self._packed])
+        tau = (ctypes.c_double * n)(*[float(t) for t in taus])
+        prms = (Params * n)()
+        for i, pr in enumerate(params_list):
+            prms[i].model = MODELS[model]
+            for q, v in enumerate(pr):
+                prms[i].p[q] = float(v)
+        self.n = n
+        self._h = _vp()
+        check(lib().ds_batch_create(n, grids, Aptr, tau, prms, PREC[precision], ctypes.byref(self._h)))
+
+    def integrate(self, Us, nsteps: int, stream=None):
+        arr = (_vp * self.n)(*[_dptr(U).value for U in Us])
+        check(lib().ds_batch_integrate(self._h, arr, int(nsteps), _stream_ptr(stream)))
+
+    def sync(self):
+        check(lib().ds_batch_sync(self._h))
+
+    @property
+    def kernels_per_step(self) -> int:
+        return int(lib().ds_batch_kernels_per_step(self._h))
+
+    def close(self):
+        if self._h:
+            lib().ds_batch_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

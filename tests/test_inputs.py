@@ -4,7 +4,7 @@ counter-based generator (determinism, range, uniformity)."""
 import numpy as np
 import pytest
 
-from paper_2310_07551_gb300 import inputs
+from paper_2310_07551_gb300 import configs, inputs
 
 
 @pytest.mark.parametrize("n,lo,hi", [(5, 0.0, 1.0), (64, -1.0, 1.0), (257, 0.0, 1.0)])
@@ -45,3 +45,14 @@ def test_initial_states():
     assert np.all((U[1] >= ve) & (U[1] < ve + 1e-3))
     V = inputs.initial_state("fhn", (4, 3, 2), seed=1)
     assert V.shape == (2, 2, 3, 4) and V.min() >= -1 and V.max() < 1
+
+
+def test_batch_recipe():
+    insts = configs.batch_instances()
+    assert len(insts) == 64
+    sizes = {96, 128, 192, 256, 384, 512}
+    for i in insts:
+        assert i.dims[0] in sizes and i.dims[1] in sizes
+        assert 0.05 <= i.params[1] <= 0.2 and 0.7 <= i.params[2] <= 1.0
+        assert 8 <= i.delta[1] <= 20 and 5e-5 <= i.tau <= 2e-4
+    assert len({i.dims for i in insts}) > 10
