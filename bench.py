@@ -35,15 +35,23 @@ sys.path.insert(0, ROOT)
 METRIC = "grid-point*steps/s"
 UNIT = "grid-point*steps/s"
 
-# DRAM traffic per launch of the tensor-core mode-product kernel, from one ncu
-# capture (dram__bytes_read.sum + dram__bytes_write.sum), keyed by the hash of
-# the kernel source it was measured on; a changed kernel reports null.
-NCU_TRAFFIC = {}
+# DRAM traffic per launch of the tensor-core mode-product kernel (mean over one
+# step's launches), from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum), keyed by "<hash of the kernel source>:<workload>";
+# a changed kernel reports null.
+NCU_TRAFFIC = {
+    # launches14_fhn: 9 k_mode_tc launches of one step, mean of read + write
+    "dfad67c0e1aba76c:fhn3d_256": 1.444e9,
+}
 
 
 def _source_hash() -> str:
+    """Hash of the tensor-core kernel's source: tc.cu up to its pointwise
+    section (PTX wrappers, descriptors, k_mode_tc)."""
     with open(os.path.join(ROOT, "paper_2310_07551_gb300", "csrc", "tc.cu"), "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()[:16]
+        src = fh.read()
+    cut = src.find(b"// Pointwise kernels of the split-BF16 step.")
+    return hashlib.sha256(src[:cut] if cut > 0 else src).hexdigest()[:16]
 
 
 def _peaks():
@@ -291,6 +299,8 @@ def main():
     ap.add_argument("--workload", default="schnak2d_1024")
     ap.add_argument("--precision", default="bf16x6", choices=["bf16x6", "f32", "f64"])
     ap.add_argument("--err-steps", type=int, default=-1)
+    ap.add_argument("--scheme", default="exprk3ds_real", choices=["exprk3ds_real", "etd2rkds"],
+                    help="etd2rkds: the second-order split ETD2RK (FP64 plans)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -331,8 +341,10 @@ def main():
         torch.cuda.synchronize()
 
     As = _problem(w)
+    if args.scheme != "exprk3ds_real":
+        args.precision = "f64"
     t0 = time.perf_counter()
-    ps = ds.PhiSet(w.dims, As, w.tau)
+    ps = ds.PhiSet(w.dims, As, w.tau, scheme=args.scheme)
     setup_s = time.perf_counter() - t0
     plan = ds.Plan(ps, w.model, w.params, args.precision)
     U0 = inputs.initial_state(w.model, w.dims, seed=w.seed)
@@ -353,21 +365,28 @@ def main():
         barrier()
         per = e0.elapsed_time(e1) / 3e3
         args.steps = max(30, int(1.5 / max(per, 1e-6)))
+    # L2 is flushed between timed steps: a 256 MB buffer (twice L2) is
+    # written outside each step's event pair, so no step starts with its
+    # inputs resident in L2.
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
     clocks = ClockSampler(local)
     barrier()
     clocks.start()
     time.sleep(0.3)
     barrier()
     t_wall0 = time.time()
-    e0.record(stream)
-    for _ in range(args.steps):
+    for a, b in evs:
+        flush.zero_()
+        a.record(stream)
         plan.integrate(U, 1)
-    e1.record(stream)
+        b.record(stream)
     barrier()
     t_wall1 = time.time()
     clk = clocks.stop(t_wall0, t_wall1)
     plan.sync(U, check_state=True)
-    t = e0.elapsed_time(e1) / 1e3
+    t = sum(a.elapsed_time(b) for a, b in evs) / 1e3
     value, t = job_rate(t, w.npoints, args.steps, dist, "cuda")
     launches_per_step = plan.kernels_per_step
 
@@ -375,8 +394,9 @@ def main():
     kprof = max(3, min(args.steps, 10))
     plan.profile(True)
     for _ in range(kprof):
+        flush.zero_()
         plan.step(U)
-    prof = plan.profile_read()
+    prof = plan.profile_read(with_bytes=True)
     plan.profile(False)
     plan.sync(U, check_state=True)
 
@@ -417,9 +437,9 @@ def main():
         p64.close()
 
     peaks, peak_src = _peaks()
-    tc_ms, tc_n, tc_fl = prof["tc"]
-    f64_ms, f64_n, f64_fl = prof["f64"]
-    pw_ms, pw_n, _ = prof["pointwise"]
+    tc_ms, tc_n, tc_fl, tc_by = prof["tc"]
+    f64_ms, f64_n, f64_fl, _ = prof["f64"]
+    pw_ms, pw_n, _, pw_by = prof["pointwise"]
     if args.precision == "f32":
         achieved = f64_fl / (f64_ms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": None, "unit": "TFLOP/s", "frac": None,
@@ -431,11 +451,19 @@ def main():
         peak = peaks["bf16_tflops_sustained"]
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak,
-                "traffic": NCU_TRAFFIC.get(_source_hash()),
+                "traffic": NCU_TRAFFIC.get(f"{_source_hash()}:{w.name}"),
+                "alg_bytes_per_launch": tc_by / tc_n if tc_n else None,
+                "launches_per_step": tc_n // kprof,
                 "kernel": "k_mode_tc (tcgen05 split-BF16 mode product)",
                 "peak_source": f"{peak_src} bf16_tflops_sustained",
                 "useful_fp32_tflops": tc_fl / (tc_ms / 1e3) / 1e12,
-                "kernel_share_of_step": tc_ms / (tc_ms + pw_ms) if tc_ms + pw_ms > 0 else None}
+                "kernel_share_of_step": tc_ms / (tc_ms + pw_ms) if tc_ms + pw_ms > 0 else None,
+                "pointwise": {"bound": "hbm", "achieved": pw_by / (pw_ms / 1e3) / 1e9 if pw_ms else None,
+                              "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                              "frac": pw_by / (pw_ms / 1e3) / 1e9 / peaks["hbm_gbs"] if pw_ms else None,
+                              "alg_bytes_per_step": pw_by / kprof,
+                              "kernels": "k_rhs_planes, k_stage_planes x2, k_final_mixed",
+                              "peak_source": f"{peak_src} hbm_gbs"}}
     else:
         achieved = f64_fl / (f64_ms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s",
@@ -447,11 +475,10 @@ def main():
         "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
         "config": {"workload": w.name, "grid": list(w.dims), "tau": w.tau, "model": w.model,
-                   "precision": args.precision, "state": "fp64",
+                   "scheme": args.scheme, "precision": args.precision, "state": "fp64",
                    "parallelism": f"replicas{world}" if world > 1 else "single",
-                   "l2": (f"inputs larger than L2: FP64 state {16 * w.npoints / 1e6:.0f} MB, "
-                          f"split-BF16 intermediates {6 * 18 * w.npoints / 1e9:.1f} GB per step")
-                   if 16 * w.npoints > 129e6 else "L2 not flushed (small workload)",
+                   "l2": (f"L2 flushed between timed steps (256 MB buffer written outside each step's "
+                          f"events); FP64 state {16 * w.npoints / 1e6:.0f} MB"),
                    "phi_setup_s": setup_s},
         "rel_err_vs_fp64": {"value": err, "steps": args.err_steps} if err is not None else None,
         "roofline": roof,
@@ -462,6 +489,9 @@ def main():
                                "pointwise": pw_ms / kprof},
         "clocks": clk,
     }
+    if args.precision == "bf16x6":
+        line["autotuner"] = [{"group": ["F", "D2", "D3"][g], "mode": mu, "split_k": k, "tiles": t,
+                              "candidates_ms": c} for g, mu, k, t, c in plan.tuning()]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, secs, desc = oracle_sample(w, 1)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",

@@ -7,7 +7,8 @@
  * What the library computes
  *   The stiff linear part is K = A_d (+) ... (+) A_1 (Section 1, eq. kronsum).
  *   phi_l(tau K) v is replaced by the directional splits of Section 2
- *   (Table 1 real coefficients for d = 2, Table 3 for d = 3), each realised
+ *   (Table 1 real coefficients for d = 2, Table 3 for d = 3 and 4, the
+ *   second eta scaled by 2^(d-3) as Section 2.3 prescribes), each realised
  *   as Tucker operators, i.e. chained mu-mode products (Section 2,
  *   eq. krontomu).  These drive the exponential Runge-Kutta scheme EXPRK3
  *   (Section 2.4, eq. exprk3), i.e. EXPRK3DS_REAL of Algorithms 1 and 2, on
@@ -73,7 +74,7 @@ typedef enum { DS_PREC_F64 = 0, DS_PREC_BF16X6 = 1, DS_PREC_F32 = 2 } ds_precisi
  *   DS_LINEAR: g = 0 (pure linear problem; used to check against exp(tau K)). */
 typedef enum { DS_SCHNAKENBERG = 0, DS_FHN = 1, DS_LINEAR = 2 } ds_model;
 
-/* Grid: d in {2, 3}; n[0] = n_1 (fastest) ... n[d-1] = n_d; n_mu >= 2. */
+/* Grid: d in {2, 3, 4}; n[0] = n_1 (fastest) ... n[d-1] = n_d; n_mu >= 2. */
 typedef struct {
     int32_t d;
     int64_t n[4];
@@ -84,17 +85,30 @@ typedef struct {
     double p[8];     /* model parameters, see ds_model */
 } ds_params;
 
+/* Time-stepping scheme of a phi-set (and of the plans built on it).
+ *   DS_EXPRK3DS_REAL: third-order EXPRK3 (Section 2.4, eq. exprk3) with the
+ *     Table 1 (d = 2) / Table 3 (d = 3, 4) splits -- Algorithms 1 and 2.
+ *   DS_ETD2RKDS: second-order ETD2RK (Section 1, eq. ETD2RK) with the
+ *     second-order split phi_l(tau K) ~ l!^(d-1) (x)_mu phi_l(tau A_mu)
+ *     (Section 2, eq. secondord); FP64 plans only.
+ *   DS_EXPRK3DS_CPLX: EXPRK3 with the complex two-term split of Table 2
+ *     (Section 2.2, Algorithm 1); each split action is complex and its real
+ *     part is the increment; phi of complex multiples of A via the real
+ *     2n x 2n embedding [[Re, -Im], [Im, Re]]; FP64 plans only. */
+typedef enum { DS_EXPRK3DS_REAL = 0, DS_ETD2RKDS = 1, DS_EXPRK3DS_CPLX = 2 } ds_scheme;
+
 typedef struct ds_phi_set ds_phi_set;
 typedef struct ds_plan ds_plan;
 
 /* ds_phi_setup -- the "Needed phi-functions" block of Algorithms 1 and 2.
  *   For component c in {0, 1}, direction mu, term i (k = 2 terms for d = 2,
- *   3 for d = 3) it forms, in FP64 on the GPU,
+ *   3 for d >= 3) it forms, in FP64 on the GPU (scheme DS_EXPRK3DS_REAL; see
+ *   ds_phi_setup_ex for the others),
  *     P_{i,2}^{(1)}{mu} = phi_{l_i}(tau/3  alpha_{i,mu}^{(1)} A_{c,mu})
  *     P_{i,3}^{(l)}{mu} = phi_{l_i}(2tau/3 alpha_{i,mu}^{(l)} A_{c,mu}), l = 1, 2
  *     P_{i,f}^{(l)}{mu} = phi_{l_i}(tau    alpha_{i,mu}^{(l)} A_{c,mu}), l = 1, 2
  *   with the coefficients of Table 1 (real, "+" sign, d = 2) or Table 3
- *   (d = 3) (Section 2.4 fixes the "+" choice), by scaling, a degree-16
+ *   (d >= 3, eta_2 times 2^(d-3)) (Section 2.4 fixes the "+" choice), by scaling, a degree-16
  *   Taylor series and the modified squaring of Skaflestad & Wright
  *   (the paper's [SW09]; Section 2.4 uses it with a Pade core).
  *   A: for c = 0, 1 and mu = 0..d-1, in that order, the column-major
@@ -108,6 +122,14 @@ typedef struct ds_plan ds_plan;
 ds_status ds_phi_setup(const ds_grid *grid, const double *A, int a_on_device,
                        double tau, ds_phi_set **out, void *stream);
 
+/* ds_phi_setup_ex -- ds_phi_setup for a given ds_scheme.  For
+ * DS_ETD2RKDS the set holds, per component and direction, slot 0 =
+ * phi_1(tau A_{c,mu}) and slot 1 = phi_2(tau A_{c,mu}) (one "term" each);
+ * a plan on it performs
+ *   U2 = U + tau T(F, {phi_1}),  U <- U2 + tau 2^(d-1) T(g(U2) - g(U), {phi_2}). */
+ds_status ds_phi_setup_ex(const ds_grid *grid, const double *A, int a_on_device, double tau,
+                          int scheme, ds_phi_set **out, void *stream);
+
 /* Release a phi-set (NULL is accepted).  Plans created from it must be
  * destroyed first. */
 ds_status ds_phi_set_destroy(ds_phi_set *set);
@@ -117,6 +139,12 @@ ds_status ds_phi_set_destroy(ds_phi_set *set);
  * 2 = P_{i,3}^{(2)}, 3 = P_{i,f}^{(1)}, 4 = P_{i,f}^{(2)}.  Synchronous. */
 ds_status ds_phi_get(const ds_phi_set *set, int c, int slot, int term, int mu,
                      double *host_out);
+
+/* ds_phi_get_ex -- as ds_phi_get, choosing the part: 0 = the phi-matrix
+ * (real part for DS_EXPRK3DS_CPLX), 1 = imaginary part (complex scheme only),
+ * 2 = its derivative d/ds phi_l(s Z) at s = 1 (real schemes).  Synchronous. */
+ds_status ds_phi_get_ex(const ds_phi_set *set, int c, int slot, int term, int mu, int part,
+                        double *host_out);
 
 /* ds_tucker -- Tucker operator Y = X x_1 L_1 x_2 ... x_d L_d (Section 2,
  * eq. krontomu: equals (L_d (x) ... (x) L_1) vec(X)).
@@ -172,7 +200,7 @@ ds_status ds_plan_create(const ds_grid *grid, const ds_params *params,
                          const ds_phi_set *set, int precision, ds_plan **out);
 
 /* ds_step -- one EXPRK3DS_REAL step (Algorithm 1 for d = 2, Algorithm 2
- * for d = 3):
+ * for d = 3 and its d = 4 extension):
  *   G = g(U), F = K(U) + G
  *   U2 = U + tau/3 S_2^{(1)}(F),  D2 = g(U2) - G
  *   U3 = U + 2tau/3 S_3^{(1)}(F) + 4tau/3 S_3^{(2)}(D2),  D3 = g(U3) - G
@@ -186,6 +214,16 @@ ds_status ds_step(ds_plan *plan, double *U, void *stream);
  * into a CUDA graph (per U pointer) and replayed, so the loop makes no host
  * round trips.  Asynchronous. */
 ds_status ds_integrate(ds_plan *plan, double *U, int64_t nsteps, void *stream);
+
+/* ds_integrate_ckpt -- ds_integrate with checkpoints for reverse mode: after
+ * every ckpt_every steps the state is copied (device to device, on stream)
+ * into ckpt + j * 2 N, j = 0, 1, ..., i.e. checkpoint j is the state after
+ * (j + 1) ckpt_every steps, for every such count <= nsteps.  ckpt: caller-
+ * owned device buffer of floor(nsteps / ckpt_every) * 2 N doubles (may be
+ * NULL when nsteps < ckpt_every).  ckpt_every <= 0 gives
+ * DS_ERR_INVALID_ARG.  Asynchronous. */
+ds_status ds_integrate_ckpt(ds_plan *plan, double *U, int64_t nsteps, int64_t ckpt_every, double *ckpt,
+                            void *stream);
 
 /* ds_step_backward -- adjoint (reverse mode) of one ds_step, for FP64
  * plans.  The paper has no adjoint; this is the exact transpose of the step
@@ -238,6 +276,24 @@ ds_status ds_plan_profile(ds_plan *plan, int enable);
  * flops[k] (2 N n_mu per mode product, FP32-class or FP64 as the kind
  * says).  Arrays have 3 entries each.  Clears the records. */
 ds_status ds_plan_profile_read(ds_plan *plan, double *ms, int64_t *launches, double *flops);
+
+/* ds_plan_profile_read_ex -- ds_plan_profile_read plus bytes[k], the summed
+ * algorithmic DRAM bytes of kind k: every distinct input read once, every
+ * output written once (for a split-BF16 mode product: its distinct input
+ * planes, its phi-matrix planes, its output; for a pointwise kernel: the
+ * state, increments and planes it touches).  Split-K partials and re-reads
+ * are not counted, so measured traffic above bytes[k] is waste.  bytes may be
+ * NULL; kinds without a byte model report 0. */
+ds_status ds_plan_profile_read_ex(ds_plan *plan, double *ms, int64_t *launches, double *flops,
+                                  double *bytes);
+
+/* ds_plan_tuning -- what the split-K autotuner chose for the split-BF16
+ * plan's mode-product launch of group (0 = the F group, 1 = D2, 2 = D3) and
+ * mode mu: the split factor, the number of output tiles, and the measured
+ * time (ms, fastest of five) of each candidate factor 1..8 (0 = not tried).
+ * Synchronous; DS_ERR_UNSUPPORTED for other precisions. */
+ds_status ds_plan_tuning(const ds_plan *plan, int group, int mu, int *ksplit, int64_t *tiles,
+                         float *times_ms);
 
 ds_status ds_plan_destroy(ds_plan *plan);
 

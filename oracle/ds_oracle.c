@@ -680,3 +680,319 @@ done:
     free(lU2); free(lU3); free(tmp); free(At);
     return rc;
 }
+
+/* ------------------------------------------------------------------------ */
+/* ETD2RKDS: the exponential Runge-Kutta scheme ETD2RK (Section 1,          */
+/* eq. ETD2RK) with the second-order directional split of the phi-actions   */
+/* (Section 2, eq. secondord):                                               */
+/*   phi_l(tau K) v ~ l!^(d-1) T(V, {phi_l(tau A_mu)}).                      */
+/* phi-set layout: [c][l - 1][mu], column-major n_mu x n_mu blocks.          */
+/*   G = g(U), F = K U + G                                                   */
+/*   U2 = U + tau T(F, {phi_1(tau A_{c,mu})})                                */
+/*   U <- U2 + tau 2^(d-1) T(g(U2) - G, {phi_2(tau A_{c,mu})})               */
+/* ------------------------------------------------------------------------ */
+int64_t orc_phi_set2_size(int d, const int64_t *n)
+{
+    int64_t per = 0;
+    for (int mu = 0; mu < d; ++mu) per += n[mu] * n[mu];
+    return 2 * 2 * per;
+}
+
+int orc_phi_set2(int d, const int64_t *n, const double *A, double tau, double *P)
+{
+    if (d < 2 || d > ORC_MAXD || !(tau > 0.0)) return -1;
+    int64_t nmax = 0;
+    for (int mu = 0; mu < d; ++mu) if (n[mu] > nmax) nmax = n[mu];
+    double *X = malloc(sizeof(double) * nmax * nmax), *ph = malloc(sizeof(double) * nmax * nmax * 3);
+    if (!X || !ph) { free(X); free(ph); return -1; }
+    const double *Acur = A;
+    const double *Ac[2][ORC_MAXD];
+    for (int c = 0; c < 2; ++c)
+        for (int mu = 0; mu < d; ++mu) { Ac[c][mu] = Acur; Acur += n[mu] * n[mu]; }
+    double *out = P;
+    for (int c = 0; c < 2; ++c)
+        for (int l = 1; l <= 2; ++l)
+            for (int mu = 0; mu < d; ++mu) {
+                int64_t mm = n[mu] * n[mu];
+                for (int64_t e = 0; e < mm; ++e) X[e] = tau * Ac[c][mu][e];
+                if (orc_phi((int)n[mu], X, l, ph) < 0) { free(X); free(ph); return -1; }
+                memcpy(out, ph + mm * l, sizeof(double) * mm);
+                out += mm;
+            }
+    free(X); free(ph);
+    return 0;
+}
+
+int orc_step2(int d, const int64_t *n, const double *A, const double *P, int model, const double *p,
+              double tau, double *U, int nsteps)
+{
+    if (d < 2 || d > ORC_MAXD || nsteps < 0) return -1;
+    int64_t N = numel(d, n), per = 0;
+    for (int mu = 0; mu < d; ++mu) per += n[mu] * n[mu];
+    const double *Ac[2][ORC_MAXD];
+    const double *Acur = A;
+    for (int c = 0; c < 2; ++c)
+        for (int mu = 0; mu < d; ++mu) { Ac[c][mu] = Acur; Acur += n[mu] * n[mu]; }
+    double *G = malloc(sizeof(double) * 2 * N), *F = malloc(sizeof(double) * 2 * N);
+    double *U2 = malloc(sizeof(double) * 2 * N), *D = malloc(sizeof(double) * 2 * N);
+    double *T = malloc(sizeof(double) * N);
+    int rc = -1;
+    if (!G || !F || !U2 || !D || !T) goto done;
+    const double w2 = ldexp(1.0, d - 1);   /* 2!^(d-1) */
+    for (int step = 0; step < nsteps; ++step) {
+        orc_g(model, p, N, U, G);
+        for (int c = 0; c < 2; ++c) {
+            if (orc_kronsum(d, n, U + c * N, Ac[c], F + c * N) < 0) goto done;
+            for (int64_t e = 0; e < N; ++e) F[c * N + e] += G[c * N + e];
+        }
+        for (int c = 0; c < 2; ++c) {
+            const double *L[ORC_MAXD];
+            const double *b = P + ((int64_t)c * 2 + 0) * per;
+            for (int mu = 0; mu < d; ++mu) { L[mu] = b; b += n[mu] * n[mu]; }
+            if (orc_tucker(d, n, F + c * N, L, T) < 0) goto done;
+            for (int64_t e = 0; e < N; ++e) U2[c * N + e] = U[c * N + e] + tau * T[e];
+        }
+        orc_g(model, p, N, U2, D);
+        for (int64_t e = 0; e < 2 * N; ++e) D[e] -= G[e];
+        for (int c = 0; c < 2; ++c) {
+            const double *L[ORC_MAXD];
+            const double *b = P + ((int64_t)c * 2 + 1) * per;
+            for (int mu = 0; mu < d; ++mu) { L[mu] = b; b += n[mu] * n[mu]; }
+            if (orc_tucker(d, n, D + c * N, L, T) < 0) goto done;
+            for (int64_t e = 0; e < N; ++e) U[c * N + e] = U2[c * N + e] + tau * w2 * T[e];
+        }
+    }
+    rc = 0;
+done:
+    free(G); free(F); free(U2); free(D); free(T);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* EXPRK3DS_CPLX: Algorithm 1 with the complex two-term coefficients of     */
+/* Table 2 (Section 2.2, eq. splitnd; l_1 = 1, l_2 = 2, upper signs,         */
+/* eta_{2,d} with 2^(d-2)).  Each split action is complex; the increment is  */
+/* its real part (the state is real).  Complex values are C99 double        */
+/* complex, laid out as (re, im) pairs.                                      */
+/* ------------------------------------------------------------------------ */
+#include <complex.h>
+typedef double complex cplx;
+
+int orc_coeffs_cplx(int d, int ell, double *eta, double *alpha)
+{
+    /* eta[2*i], eta[2*i+1] = re, im of eta_i; alpha likewise (same for every mu) */
+    if (d < 2 || d > ORC_MAXD || (ell != 1 && ell != 2)) return -1;
+    double s = ldexp(1.0, d - 2);
+    cplx e1, a1, e2, a2;
+    if (ell == 1) {
+        e1 = 7.0 / 4.0 + 3.0 * sqrt(2.0) / 2.0 * I;
+        a1 = 12.0 / 11.0 - 4.0 * sqrt(2.0) / 11.0 * I;
+        e2 = s * (-3.0 - 6.0 * sqrt(2.0) * I);
+        a2 = 4.0 / 3.0 - 2.0 * sqrt(2.0) / 3.0 * I;
+    } else {
+        e1 = 2.0 / 3.0 + 2.0 * sqrt(3.0) / 3.0 * I;
+        a1 = 3.0 / 4.0 - sqrt(3.0) / 4.0 * I;
+        e2 = s * (-2.0 / 3.0 - 8.0 * sqrt(3.0) / 3.0 * I);
+        a2 = 6.0 / 7.0 - 3.0 * sqrt(3.0) / 7.0 * I;
+    }
+    eta[0] = creal(e1); eta[1] = cimag(e1); eta[2] = creal(e2); eta[3] = cimag(e2);
+    alpha[0] = creal(a1); alpha[1] = cimag(a1); alpha[2] = creal(a2); alpha[3] = cimag(a2);
+    return 2;
+}
+
+static void cmat_mul(int n, const cplx *A, const cplx *B, cplx *C)
+{
+    #pragma omp parallel for schedule(static)
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) {
+            cplx s = 0.0;
+            for (int q = 0; q < n; ++q) s += A[i + (int64_t)n * q] * B[q + (int64_t)n * j];
+            C[i + (int64_t)n * j] = s;
+        }
+}
+
+/* phi_0..phi_lmax of a complex matrix: the scaling / Taylor / modified      */
+/* squaring of orc_phi, in complex arithmetic.                               */
+int orc_phi_cplx(int n, const double *Xd, int lmax, double *outd)
+{
+    const cplx *X = (const cplx *)Xd;
+    cplx *out = (cplx *)outd;
+    if (n < 1 || lmax < 0 || lmax > 8) return -1;
+    const int q = 16;
+    int64_t nn = (int64_t)n * n;
+    double nrm = 0.0;
+    for (int j = 0; j < n; ++j) {
+        double sc = 0.0;
+        for (int i = 0; i < n; ++i) sc += cabs(X[i + (int64_t)n * j]);
+        if (sc > nrm) nrm = sc;
+    }
+    int s = 0;
+    while (ldexp(nrm, -s) > 0.5) ++s;
+    cplx *Y = malloc(sizeof(cplx) * nn), *Pw = malloc(sizeof(cplx) * nn), *T = malloc(sizeof(cplx) * nn);
+    cplx *old = malloc(sizeof(cplx) * nn * (lmax + 1));
+    if (!Y || !Pw || !T || !old) { free(Y); free(Pw); free(T); free(old); return -1; }
+    for (int64_t e = 0; e < nn; ++e) Y[e] = ldexp(1.0, -s) * X[e];
+    double fact[32];
+    fact[0] = 1.0;
+    for (int j = 1; j < 32; ++j) fact[j] = fact[j - 1] * j;
+    for (int64_t e = 0; e < nn * (lmax + 1); ++e) out[e] = 0.0;
+    for (int64_t e = 0; e < nn; ++e) Pw[e] = 0.0;
+    for (int i = 0; i < n; ++i) Pw[i + (int64_t)n * i] = 1.0;
+    for (int j = 0; j <= q; ++j) {
+        for (int k = 0; k <= lmax; ++k) {
+            double c = 1.0 / fact[j + k];
+            cplx *o = out + nn * k;
+            for (int64_t e = 0; e < nn; ++e) o[e] += c * Pw[e];
+        }
+        if (j < q) {
+            cmat_mul(n, Pw, Y, T);
+            memcpy(Pw, T, sizeof(cplx) * nn);
+        }
+    }
+    for (int it = 0; it < s; ++it) {
+        memcpy(old, out, sizeof(cplx) * nn * (lmax + 1));
+        cmat_mul(n, old, old, out);
+        for (int k = 1; k <= lmax; ++k) {
+            cplx *o = out + nn * k;
+            cmat_mul(n, old, old + nn * k, o);
+            for (int j = 1; j <= k; ++j) {
+                double c = 1.0 / fact[k - j];
+                const cplx *pj = old + nn * j;
+                for (int64_t e = 0; e < nn; ++e) o[e] += c * pj[e];
+            }
+            double w = ldexp(1.0, -k);
+            for (int64_t e = 0; e < nn; ++e) o[e] *= w;
+        }
+    }
+    free(Y); free(Pw); free(T); free(old);
+    return s;
+}
+
+static void cmode_product(int d, const int64_t *n, const cplx *X, int mu, const cplx *L, cplx *Y)
+{
+    int64_t In = 1, On = 1, m = n[mu];
+    for (int q = 0; q < mu; ++q) In *= n[q];
+    for (int q = mu + 1; q < d; ++q) On *= n[q];
+    #pragma omp parallel for collapse(2) schedule(static)
+    for (int64_t o = 0; o < On; ++o)
+        for (int64_t i = 0; i < m; ++i)
+            for (int64_t x = 0; x < In; ++x) {
+                cplx s = 0.0;
+                for (int64_t j = 0; j < m; ++j) s += L[i + m * j] * X[x + In * (j + m * o)];
+                Y[x + In * (i + m * o)] = s;
+            }
+}
+
+/* phi-set of the complex scheme: [c][slot][i][mu] complex blocks, k = 2 */
+int64_t orc_phi_set_cplx_size(int d, const int64_t *n)
+{
+    int64_t per = 0;
+    for (int mu = 0; mu < d; ++mu) per += n[mu] * n[mu];
+    return 2 * 2 * 5 * 2 * per;   /* doubles: 2 comps, 5 slots, 2 terms, (re, im) */
+}
+
+int orc_phi_set_cplx(int d, const int64_t *n, const double *A, double tau, double *Pd)
+{
+    cplx *P = (cplx *)Pd;
+    if (d < 2 || d > ORC_MAXD || !(tau > 0.0)) return -1;
+    double eta[2][4], alpha[2][4];
+    orc_coeffs_cplx(d, 1, eta[0], alpha[0]);
+    orc_coeffs_cplx(d, 2, eta[1], alpha[1]);
+    int64_t nmax = 0;
+    for (int mu = 0; mu < d; ++mu) if (n[mu] > nmax) nmax = n[mu];
+    cplx *X = malloc(sizeof(cplx) * nmax * nmax), *ph = malloc(sizeof(cplx) * nmax * nmax * 3);
+    if (!X || !ph) { free(X); free(ph); return -1; }
+    const double *Ac[2][ORC_MAXD];
+    const double *Acur = A;
+    for (int c = 0; c < 2; ++c)
+        for (int mu = 0; mu < d; ++mu) { Ac[c][mu] = Acur; Acur += n[mu] * n[mu]; }
+    cplx *out = P;
+    for (int c = 0; c < 2; ++c)
+        for (int q = 0; q < 5; ++q) {
+            const double *al = alpha[kSlotEll[q] - 1];
+            for (int i = 0; i < 2; ++i)
+                for (int mu = 0; mu < d; ++mu) {
+                    int64_t mm = n[mu] * n[mu];
+                    cplx z = kSlotC[q] * tau * (al[2 * i] + al[2 * i + 1] * I);
+                    for (int64_t e = 0; e < mm; ++e) X[e] = z * Ac[c][mu][e];
+                    int l = i + 1;   /* l_1 = 1, l_2 = 2 */
+                    if (orc_phi_cplx((int)n[mu], (const double *)X, l, (double *)ph) < 0) { free(X); free(ph); return -1; }
+                    memcpy(out, ph + mm * l, sizeof(cplx) * mm);
+                    out += mm;
+                }
+        }
+    free(X); free(ph);
+    return 0;
+}
+
+/* acc += w Re(sum_i eta_i T(X, {P_{c,q,i,mu}})), X real */
+static int split_action_cplx(int d, const int64_t *n, const cplx *P, int c, int q, const double *eta,
+                             double w, const double *X, double *acc)
+{
+    int64_t N = numel(d, n), per = 0;
+    for (int mu = 0; mu < d; ++mu) per += n[mu] * n[mu];
+    cplx *a = malloc(sizeof(cplx) * N), *b = malloc(sizeof(cplx) * N);
+    if (!a || !b) { free(a); free(b); return -1; }
+    for (int i = 0; i < 2; ++i) {
+        for (int64_t e = 0; e < N; ++e) a[e] = X[e];
+        const cplx *blk = P + (((int64_t)c * 5 + q) * 2 + i) * per;
+        for (int mu = 0; mu < d; ++mu) {
+            cmode_product(d, n, a, mu, blk, b);
+            cplx *t = a; a = b; b = t;
+            blk += n[mu] * n[mu];
+        }
+        cplx et = eta[2 * i] + eta[2 * i + 1] * I;
+        for (int64_t e = 0; e < N; ++e) acc[e] += w * creal(et * a[e]);
+    }
+    free(a); free(b);
+    return 0;
+}
+
+int orc_step_cplx(int d, const int64_t *n, const double *A, const double *Pd, int model,
+                  const double *p, double tau, double *U, int nsteps)
+{
+    const cplx *P = (const cplx *)Pd;
+    if (d < 2 || d > ORC_MAXD || nsteps < 0) return -1;
+    double eta1[4], eta2[4], al[4];
+    orc_coeffs_cplx(d, 1, eta1, al);
+    orc_coeffs_cplx(d, 2, eta2, al);
+    int64_t N = numel(d, n);
+    const double *Ac[2][ORC_MAXD];
+    const double *Acur = A;
+    for (int c = 0; c < 2; ++c)
+        for (int mu = 0; mu < d; ++mu) { Ac[c][mu] = Acur; Acur += n[mu] * n[mu]; }
+    double *G = malloc(sizeof(double) * 2 * N), *F = malloc(sizeof(double) * 2 * N);
+    double *U2 = malloc(sizeof(double) * 2 * N), *U3 = malloc(sizeof(double) * 2 * N);
+    double *Dt = malloc(sizeof(double) * 2 * N), *Un = malloc(sizeof(double) * 2 * N);
+    int rc = -1;
+    if (!G || !F || !U2 || !U3 || !Dt || !Un) goto done;
+    for (int step = 0; step < nsteps; ++step) {
+        orc_g(model, p, N, U, G);
+        for (int c = 0; c < 2; ++c) {
+            if (orc_kronsum(d, n, U + c * N, Ac[c], F + c * N) < 0) goto done;
+            for (int64_t e = 0; e < N; ++e) F[c * N + e] += G[c * N + e];
+        }
+        memcpy(U2, U, sizeof(double) * 2 * N);
+        for (int c = 0; c < 2; ++c)
+            if (split_action_cplx(d, n, P, c, 0, eta1, tau / 3.0, F + c * N, U2 + c * N) < 0) goto done;
+        orc_g(model, p, N, U2, Dt);
+        for (int64_t e = 0; e < 2 * N; ++e) Dt[e] -= G[e];
+        memcpy(U3, U, sizeof(double) * 2 * N);
+        for (int c = 0; c < 2; ++c) {
+            if (split_action_cplx(d, n, P, c, 1, eta1, 2.0 * tau / 3.0, F + c * N, U3 + c * N) < 0) goto done;
+            if (split_action_cplx(d, n, P, c, 2, eta2, 4.0 * tau / 3.0, Dt + c * N, U3 + c * N) < 0) goto done;
+        }
+        orc_g(model, p, N, U3, Dt);
+        for (int64_t e = 0; e < 2 * N; ++e) Dt[e] -= G[e];
+        memcpy(Un, U, sizeof(double) * 2 * N);
+        for (int c = 0; c < 2; ++c) {
+            if (split_action_cplx(d, n, P, c, 3, eta1, tau, F + c * N, Un + c * N) < 0) goto done;
+            if (split_action_cplx(d, n, P, c, 4, eta2, 1.5 * tau, Dt + c * N, Un + c * N) < 0) goto done;
+        }
+        memcpy(U, Un, sizeof(double) * 2 * N);
+    }
+    rc = 0;
+done:
+    free(G); free(F); free(U2); free(U3); free(Dt); free(Un);
+    return rc;
+}

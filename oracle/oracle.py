@@ -62,6 +62,24 @@ def lib():
             L.orc_step.argtypes = [ctypes.c_int, _i64p, _dp, _dp, ctypes.c_int, _dp,
                                    ctypes.c_double, _dp, ctypes.c_int]
             L.orc_step.restype = ctypes.c_int
+            L.orc_coeffs_cplx.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp]
+            L.orc_coeffs_cplx.restype = ctypes.c_int
+            L.orc_phi_cplx.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _dp]
+            L.orc_phi_cplx.restype = ctypes.c_int
+            L.orc_phi_set_cplx_size.argtypes = [ctypes.c_int, _i64p]
+            L.orc_phi_set_cplx_size.restype = ctypes.c_int64
+            L.orc_phi_set_cplx.argtypes = [ctypes.c_int, _i64p, _dp, ctypes.c_double, _dp]
+            L.orc_phi_set_cplx.restype = ctypes.c_int
+            L.orc_step_cplx.argtypes = [ctypes.c_int, _i64p, _dp, _dp, ctypes.c_int, _dp, ctypes.c_double,
+                                        _dp, ctypes.c_int]
+            L.orc_step_cplx.restype = ctypes.c_int
+            L.orc_phi_set2_size.argtypes = [ctypes.c_int, _i64p]
+            L.orc_phi_set2_size.restype = ctypes.c_int64
+            L.orc_phi_set2.argtypes = [ctypes.c_int, _i64p, _dp, ctypes.c_double, _dp]
+            L.orc_phi_set2.restype = ctypes.c_int
+            L.orc_step2.argtypes = [ctypes.c_int, _i64p, _dp, _dp, ctypes.c_int, _dp, ctypes.c_double,
+                                    _dp, ctypes.c_int]
+            L.orc_step2.restype = ctypes.c_int
             L.orc_step_adjoint.argtypes = [ctypes.c_int, _i64p, _dp, _dp, ctypes.c_int, _dp,
                                            ctypes.c_double, _dp, _dp, _dp, _dp, _dp]
             L.orc_step_adjoint.restype = ctypes.c_int
@@ -221,3 +239,64 @@ def step_adjoint(dims, As, P, model: str, p, tau: float, U: np.ndarray, lam: np.
     if rc != 0:
         raise RuntimeError("orc_step_adjoint failed")
     return (out, dp, dsc) if with_scale else (out, dp)
+
+
+def phi_set2(dims, As, tau: float) -> np.ndarray:
+    """ETD2RKDS phi-set: [c][l - 1][mu] blocks of phi_l(tau A_{c,mu})."""
+    d = len(dims)
+    P = np.zeros(lib().orc_phi_set2_size(d, _dims(dims)))
+    if lib().orc_phi_set2(d, _dims(dims), _ptr(_pack_A(As)), float(tau), _ptr(P)) != 0:
+        raise RuntimeError("orc_phi_set2 failed")
+    return P
+
+
+def step2(dims, As, P, model: str, p, tau: float, U: np.ndarray, nsteps: int = 1) -> np.ndarray:
+    """nsteps ETD2RKDS steps; returns the new state."""
+    d = len(dims)
+    Uo = np.array(U, dtype=np.float64, order="C", copy=True)
+    pp = np.asarray(list(p) + [0.0] * (8 - len(p)), dtype=np.float64)
+    rc = lib().orc_step2(d, _dims(dims), _ptr(_pack_A(As)), _ptr(np.ascontiguousarray(P)), MODELS[model],
+                         _ptr(pp), float(tau), _ptr(Uo), int(nsteps))
+    if rc != 0:
+        raise RuntimeError("orc_step2 failed")
+    return Uo
+
+
+def coeffs_cplx(d: int, ell: int):
+    """(eta[2], alpha[2]) complex coefficients of Table 2 (same alpha in every mu)."""
+    eta = np.zeros(4)
+    alpha = np.zeros(4)
+    if lib().orc_coeffs_cplx(d, ell, _ptr(eta), _ptr(alpha)) < 0:
+        raise ValueError("bad (d, ell)")
+    return eta[0::2] + 1j * eta[1::2], alpha[0::2] + 1j * alpha[1::2]
+
+
+def phi_cplx(X: np.ndarray, lmax: int):
+    n = X.shape[0]
+    Xc = np.ascontiguousarray(np.asarray(X, dtype=np.complex128).T)
+    out = np.zeros((lmax + 1) * n * n, dtype=np.complex128)
+    if lib().orc_phi_cplx(n, Xc.view(np.float64).ctypes.data_as(_dp), lmax,
+                          out.view(np.float64).ctypes.data_as(_dp)) < 0:
+        raise RuntimeError("orc_phi_cplx failed")
+    return [out[k * n * n:(k + 1) * n * n].reshape(n, n).T.copy() for k in range(lmax + 1)]
+
+
+def phi_set_cplx(dims, As, tau: float) -> np.ndarray:
+    """Complex phi-set [c][slot][i][mu] (complex128, flat)."""
+    d = len(dims)
+    P = np.zeros(lib().orc_phi_set_cplx_size(d, _dims(dims)))
+    if lib().orc_phi_set_cplx(d, _dims(dims), _ptr(_pack_A(As)), float(tau), _ptr(P)) != 0:
+        raise RuntimeError("orc_phi_set_cplx failed")
+    return P.view(np.complex128)
+
+
+def step_cplx(dims, As, P, model: str, p, tau: float, U: np.ndarray, nsteps: int = 1) -> np.ndarray:
+    d = len(dims)
+    Uo = np.array(U, dtype=np.float64, order="C", copy=True)
+    pp = np.asarray(list(p) + [0.0] * (8 - len(p)), dtype=np.float64)
+    Pf = np.ascontiguousarray(P).view(np.float64)
+    rc = lib().orc_step_cplx(d, _dims(dims), _ptr(_pack_A(As)), _ptr(Pf), MODELS[model], _ptr(pp),
+                             float(tau), _ptr(Uo), int(nsteps))
+    if rc != 0:
+        raise RuntimeError("orc_step_cplx failed")
+    return Uo

@@ -1,7 +1,8 @@
 """Differentiation of a horizon of EXPRK3DS_REAL steps through the library's
 hand-written adjoint step (ds_step_backward), with step-level checkpointing.
 
-Forward: m steps from U0, keeping the state every `ckpt` steps.
+Forward: m graph-replayed steps from U0 (ds_integrate_ckpt), keeping the
+state every `ckpt` steps.
 Backward: for each segment, last first, recompute the segment's states from
 its checkpoint (ds_step) and sweep ds_step_backward over them in reverse,
 accumulating dL/dU and dL/dp for the reaction parameters.  Memory: m/ckpt
@@ -34,10 +35,8 @@ class Integrate(torch.autograd.Function):
             raise ValueError("the adjoint needs an FP64 plan")
         U = U0.detach().contiguous().clone()
         ckpts = [U.clone()]
-        for n in range(nsteps):
-            plan.step(U)
-            if (n + 1) % ckpt == 0 and n + 1 < nsteps:
-                ckpts.append(U.clone())
+        ck = plan.integrate_ckpt(U, nsteps, ckpt)
+        ckpts += [ck[j] for j in range(ck.shape[0]) if (j + 1) * ckpt < nsteps]
         ctx.plan, ctx.nsteps, ctx.ckpt, ctx.ckpts = plan, nsteps, ckpt, ckpts
         ctx.p_device = p.device
         ctx.want_s = bool(ctx.needs_input_grad[2])

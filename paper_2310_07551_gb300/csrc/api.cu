@@ -25,7 +25,7 @@ ds_status fail(ds_status st, const std::string &msg)
 // ---------------------------------------------------------------------------
 // Split coefficients from the closed forms of the paper's tables.
 //   d = 2: Table 1, real columns, upper ("+") sign; terms use phi_1, phi_2.
-//   d = 3: Table 3, upper sign in alpha_{1,mu}; terms use phi_1, phi_2,
+//   d >= 3: Table 3, upper sign in alpha_{1,mu}; terms use phi_1, phi_2,
 //          phi_1; eta_{2,d} carries 2^(d-3); alpha is the same in every mu.
 // ---------------------------------------------------------------------------
 SplitCoeffs split_coeffs(int d, int ell)
@@ -88,6 +88,38 @@ SplitCoeffs split_coeffs(int d, int ell)
     return c;
 }
 
+// Table 2 (complex two-term split, any d), upper signs; l_1 = 1, l_2 = 2;
+// eta_{2,d} carries 2^(d-2); alpha is the same in every direction.
+SplitCoeffs split_coeffs_cplx(int d, int ell)
+{
+    SplitCoeffs c{};
+    c.k = 2;
+    c.ell_i[0] = 1;
+    c.ell_i[1] = 2;
+    const double sc = ldexp(1.0, d - 2);
+    double e1r, e1i, a1r, a1i, e2r, e2i, a2r, a2i;
+    if (ell == 1) {
+        const double r2 = sqrt(2.0);
+        e1r = 1.75; e1i = 1.5 * r2;
+        a1r = 12.0 / 11.0; a1i = -4.0 * r2 / 11.0;
+        e2r = -3.0 * sc; e2i = -6.0 * r2 * sc;
+        a2r = 4.0 / 3.0; a2i = -2.0 * r2 / 3.0;
+    } else {
+        const double r3 = sqrt(3.0);
+        e1r = 2.0 / 3.0; e1i = 2.0 * r3 / 3.0;
+        a1r = 0.75; a1i = -r3 / 4.0;
+        e2r = -2.0 / 3.0 * sc; e2i = -8.0 * r3 / 3.0 * sc;
+        a2r = 6.0 / 7.0; a2i = -3.0 * r3 / 7.0;
+    }
+    c.eta[0] = e1r; c.eta_im[0] = e1i;
+    c.eta[1] = e2r; c.eta_im[1] = e2i;
+    for (int mu = 0; mu < d; ++mu) {
+        c.alpha[0][mu] = a1r; c.alpha_im[0][mu] = a1i;
+        c.alpha[1][mu] = a2r; c.alpha_im[1][mu] = a2i;
+    }
+    return c;
+}
+
 const double kSlotC[kSlots] = {1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0, 1.0, 1.0};
 const int kSlotEll[kSlots] = {1, 1, 2, 1, 2};
 const double kSlotW[kSlots] = {1.0 / 3.0, 2.0 / 3.0, 4.0 / 3.0, 1.0, 1.5};
@@ -108,7 +140,7 @@ int64_t numel(const ds_grid *g)
 ds_status check_grid(const ds_grid *g)
 {
     if (!g) return fail(DS_ERR_INVALID_ARG, "grid is NULL");
-    if (g->d < 2 || g->d > kMaxD) return fail(DS_ERR_INVALID_ARG, "d must be 2 or 3");
+    if (g->d < 2 || g->d > kMaxD) return fail(DS_ERR_INVALID_ARG, "d must be 2, 3 or 4");
     for (int q = 0; q < g->d; ++q)
         if (g->n[q] < 2 || g->n[q] > (1 << 20))
             return fail(DS_ERR_INVALID_ARG, "n_mu must be in [2, 2^20]");
@@ -173,7 +205,7 @@ int tucker_sum_f64x(ds_plan *p, int c, int slot, const double *X, double *acc, d
 {
     const ds_phi_set *s = p->set;
     const int d = s->d;
-    const SplitCoeffs &co = s->co[kSlotEll[slot] - 1];
+    const SplitCoeffs &co = s->co[s->scheme == DS_ETD2RKDS ? slot : kSlotEll[slot] - 1];
     int launches = 0;
     for (int i = 0; i < co.k; ++i) {
         const double *in = X;
@@ -305,11 +337,103 @@ int enqueue_step_f32(ds_plan *p, double *U, cudaStream_t st)
     return L;
 }
 
+// Complex scheme (FP64): acc = Re(sum_i eta_i T(X_c, {P_i{mu}})) for real X,
+// with complex P = Pr + i Pi.  Mode 1: two real products; middle modes: four;
+// the last mode two, against the matrices with Re(eta .) folded in.
+int tucker_sum_cplx(ds_plan *p, int c, int slot, const double *X, double *acc, double *w4,
+                    cudaStream_t st)
+{
+    const ds_phi_set *s = p->set;
+    const int d = s->d;
+    const int64_t N = p->N;
+    double *Yr = w4, *Yi = w4 + N, *Zr = w4 + 2 * N, *Zi = w4 + 3 * N;
+    int L = 0;
+    auto mp = [&](const double *in, int mu, const double *M, double *out, double alpha, double beta) {
+        p->prof.begin(st, 1, 2.0 * (double)N * (double)s->n[mu]);
+        launch_mode_product_f64(d, s->n, in, mu, M, 0, out, alpha, beta, st);
+        p->prof.end(st);
+        ++L;
+    };
+    for (int i = 0; i < s->k; ++i) {
+        const int64_t o0 = s->P_off[c][slot][i][0];
+        mp(X, 0, s->P_dev + o0, Yr, 1.0, 0.0);
+        mp(X, 0, s->Pim_dev + o0, Yi, 1.0, 0.0);
+        for (int mu = 1; mu < d - 1; ++mu) {
+            const int64_t o = s->P_off[c][slot][i][mu];
+            mp(Yr, mu, s->P_dev + o, Zr, 1.0, 0.0);
+            mp(Yi, mu, s->Pim_dev + o, Zr, -1.0, 1.0);
+            mp(Yr, mu, s->Pim_dev + o, Zi, 1.0, 0.0);
+            mp(Yi, mu, s->P_dev + o, Zi, 1.0, 1.0);
+            std::swap(Yr, Zr);
+            std::swap(Yi, Zi);
+        }
+        const double *M = s->Mf_dev + s->Mf_off[c][slot][i];
+        const int64_t nn = s->n[d - 1] * s->n[d - 1];
+        mp(Yr, d - 1, M, acc, 1.0, i > 0 ? 1.0 : 0.0);
+        mp(Yi, d - 1, M + nn, acc, 1.0, 1.0);
+    }
+    return L;
+}
+
+int enqueue_step_cplx_f64(ds_plan *p, double *U, cudaStream_t st)
+{
+    const int64_t N = p->N;
+    const double tau = p->set->tau;
+    double *F = p->ws, *a = p->ws + 2 * N, *b = p->ws + 4 * N, *D = p->ws + 6 * N, *w4 = p->ws + 8 * N;
+    int L = 0;
+    if (p->set->tridiag[0] && p->set->tridiag[1])
+        L += launch_rhs_f64(p->sten, p->model, N, U, F, st);
+    else
+        L += rhs_dense_f64(p, U, F, st);
+    for (int c = 0; c < 2; ++c) L += tucker_sum_cplx(p, c, 0, F + c * N, a + c * N, w4, st);
+    launch_stage_diff_f64(p->model, N, U, a, kSlotW[0] * tau, nullptr, 0.0, D, st);
+    ++L;
+    for (int c = 0; c < 2; ++c) {
+        L += tucker_sum_cplx(p, c, 1, F + c * N, a + c * N, w4, st);
+        L += tucker_sum_cplx(p, c, 2, D + c * N, b + c * N, w4, st);
+    }
+    launch_stage_diff_f64(p->model, N, U, a, kSlotW[1] * tau, b, kSlotW[2] * tau, D, st);
+    ++L;
+    for (int c = 0; c < 2; ++c) {
+        L += tucker_sum_cplx(p, c, 3, F + c * N, a + c * N, w4, st);
+        L += tucker_sum_cplx(p, c, 4, D + c * N, b + c * N, w4, st);
+    }
+    launch_final_f64(N, U, a, kSlotW[3] * tau, b, kSlotW[4] * tau, st);
+    ++L;
+    return L;
+}
+
+// ETD2RKDS (FP64): U2 = U + tau T(F, phi_1), U <- U2 + tau 2^(d-1) T(g(U2) - G, phi_2)
+int enqueue_step_etd2_f64(ds_plan *p, double *U, cudaStream_t st)
+{
+    const int64_t N = p->N;
+    const double tau = p->set->tau;
+    double *F = p->ws, *a = p->ws + 2 * N, *b = p->ws + 4 * N, *D = p->ws + 6 * N;
+    double *t1 = p->ws + 8 * N, *t2 = p->ws + 9 * N;
+    int L = 0;
+    if (p->set->tridiag[0] && p->set->tridiag[1])
+        L += launch_rhs_f64(p->sten, p->model, N, U, F, st);
+    else
+        L += rhs_dense_f64(p, U, F, st);
+    for (int c = 0; c < 2; ++c) L += tucker_sum_f64(p, c, 0, F + c * N, a + c * N, t1, t2, st);
+    launch_stage_diff_f64(p->model, N, U, a, tau, nullptr, 0.0, D, st);
+    ++L;
+    // tucker_sum applies eta = 2^(d-1) of the phi_2 term
+    for (int c = 0; c < 2; ++c) L += tucker_sum_f64(p, c, 1, D + c * N, b + c * N, t1, t2, st);
+    launch_final_f64(N, U, a, tau, b, tau, st);
+    ++L;
+    return L;
+}
+
 int enqueue_step(ds_plan *p, double *U, cudaStream_t st, bool profile)
 {
     p->prof.on = profile;
     int L;
-    if (p->prec == DS_PREC_F64)
+    if (p->set->scheme == DS_ETD2RKDS)
+        L = enqueue_step_etd2_f64(p, U, st);
+    else if (p->set->scheme == DS_EXPRK3DS_CPLX)
+        L = enqueue_step_cplx_f64(p, U, st);
+    else if (p->prec == DS_PREC_F64)
         L = enqueue_step_f64(p, U, st);
     else if (p->prec == DS_PREC_F32)
         L = enqueue_step_f32(p, U, st);
@@ -330,7 +454,15 @@ const char *ds_version(void) { return "ds3 0.1 (sm_103a)"; }
 ds_status ds_phi_setup(const ds_grid *grid, const double *A, int a_on_device, double tau,
                        ds_phi_set **out, void *stream)
 {
+    return ds_phi_setup_ex(grid, A, a_on_device, tau, DS_EXPRK3DS_REAL, out, stream);
+}
+
+ds_status ds_phi_setup_ex(const ds_grid *grid, const double *A, int a_on_device, double tau, int scheme,
+                          ds_phi_set **out, void *stream)
+{
     try {
+        if (scheme != DS_EXPRK3DS_REAL && scheme != DS_ETD2RKDS && scheme != DS_EXPRK3DS_CPLX)
+            return fail(DS_ERR_INVALID_ARG, "unknown scheme");
         ds_status r = check_grid(grid);
         if (r != DS_OK) return r;
         if (!A || !out) return fail(DS_ERR_INVALID_ARG, "A or out is NULL");
@@ -356,8 +488,27 @@ ds_status ds_phi_setup(const ds_grid *grid, const double *A, int a_on_device, do
         s->d = d;
         for (int q = 0; q < kMaxD; ++q) s->n[q] = q < d ? grid->n[q] : 1;
         s->tau = tau;
-        s->co[0] = split_coeffs(d, 1);
-        s->co[1] = split_coeffs(d, 2);
+        s->scheme = scheme;
+        if (scheme == DS_EXPRK3DS_REAL) {
+            s->co[0] = split_coeffs(d, 1);
+            s->co[1] = split_coeffs(d, 2);
+            s->nslots = kSlots;
+        } else if (scheme == DS_EXPRK3DS_CPLX) {
+            s->co[0] = split_coeffs_cplx(d, 1);
+            s->co[1] = split_coeffs_cplx(d, 2);
+            s->nslots = kSlots;
+        } else {
+            // second-order split: phi_l(tau K) ~ l!^(d-1) (x)_mu phi_l(tau A_mu)
+            for (int l = 1; l <= 2; ++l) {
+                SplitCoeffs &c = s->co[l - 1];
+                c = SplitCoeffs{};
+                c.k = 1;
+                c.ell_i[0] = l;
+                c.eta[0] = l == 1 ? 1.0 : ldexp(1.0, d - 1);
+                for (int mu = 0; mu < d; ++mu) c.alpha[0][mu] = 1.0;
+            }
+            s->nslots = 2;
+        }
         s->k = s->co[0].k;
         // A copy + tridiagonal bands
         int64_t off = 0, toff = 0;
@@ -386,7 +537,7 @@ ds_status ds_phi_setup(const ds_grid *grid, const double *A, int a_on_device, do
         // phi-matrix layout [c][slot][i][mu]
         int64_t poff = 0;
         for (int c = 0; c < 2; ++c)
-            for (int q = 0; q < kSlots; ++q)
+            for (int q = 0; q < s->nslots; ++q)
                 for (int i = 0; i < s->k; ++i)
                     for (int mu = 0; mu < d; ++mu) {
                         s->P_off[c][q][i][mu] = poff;
@@ -397,7 +548,20 @@ ds_status ds_phi_setup(const ds_grid *grid, const double *A, int a_on_device, do
         cudaError_t e2 = cudaMalloc(&s->tri_dev, sizeof(double) * toff);
         cudaError_t e3 = cudaMalloc(&s->P_dev, sizeof(double) * poff);
         cudaError_t e4 = cudaMalloc(&s->dP_dev, sizeof(double) * poff);
-        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || e4 != cudaSuccess) {
+        cudaError_t e5 = cudaSuccess, e6 = cudaSuccess;
+        if (scheme == DS_EXPRK3DS_CPLX) {
+            e5 = cudaMalloc(&s->Pim_dev, sizeof(double) * poff);
+            int64_t moff = 0;
+            for (int c = 0; c < 2; ++c)
+                for (int q = 0; q < kSlots; ++q)
+                    for (int i = 0; i < s->k; ++i) {
+                        s->Mf_off[c][q][i] = moff;
+                        moff += 2 * grid->n[d - 1] * grid->n[d - 1];
+                    }
+            e6 = cudaMalloc(&s->Mf_dev, sizeof(double) * moff);
+        }
+        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || e4 != cudaSuccess ||
+            e5 != cudaSuccess || e6 != cudaSuccess) {
             cudaGetLastError();
             ds_phi_set_destroy(s);
             return fail(DS_ERR_OOM, "phi-set device allocation");
@@ -407,22 +571,59 @@ ds_status ds_phi_setup(const ds_grid *grid, const double *A, int a_on_device, do
         // group the phi jobs by size
         std::map<int64_t, std::vector<PhiJob>> groups;
         for (int c = 0; c < 2; ++c)
-            for (int q = 0; q < kSlots; ++q) {
-                const SplitCoeffs &co = s->co[kSlotEll[q] - 1];
+            for (int q = 0; q < s->nslots; ++q) {
+                // ETD2RKDS: slot 0 = phi_1(tau A), slot 1 = phi_2(tau A)
+                const SplitCoeffs &co = s->co[scheme == DS_ETD2RKDS ? q : kSlotEll[q] - 1];
+                const double cq = scheme == DS_ETD2RKDS ? 1.0 : kSlotC[q];
                 for (int i = 0; i < s->k; ++i)
                     for (int mu = 0; mu < d; ++mu) {
                         PhiJob j;
                         j.A = s->A_dev + s->A_off[c][mu];
-                        j.z = kSlotC[q] * tau * co.alpha[i][mu];
+                        j.z = cq * tau * co.alpha[i][mu];
                         j.ell = co.ell_i[i];
                         j.out = s->P_dev + s->P_off[c][q][i][mu];
                         j.dout = s->dP_dev + s->P_off[c][q][i][mu];
                         groups[grid->n[mu]].push_back(j);
                     }
             }
-        for (auto &kv : groups) {
-            r = phi_batch_f64((int)kv.first, kv.second, st);
-            if (r != DS_OK) { ds_phi_set_destroy(s); return r; }
+        if (scheme == DS_EXPRK3DS_CPLX) {
+            std::map<int64_t, std::vector<PhiJobC>> cgroups;
+            for (int c = 0; c < 2; ++c)
+                for (int q = 0; q < kSlots; ++q) {
+                    const SplitCoeffs &co = s->co[kSlotEll[q] - 1];
+                    for (int i = 0; i < s->k; ++i)
+                        for (int mu = 0; mu < d; ++mu) {
+                            PhiJobC j;
+                            j.A = s->A_dev + s->A_off[c][mu];
+                            j.zr = kSlotC[q] * tau * co.alpha[i][mu];
+                            j.zi = kSlotC[q] * tau * co.alpha_im[i][mu];
+                            j.ell = co.ell_i[i];
+                            j.out_re = s->P_dev + s->P_off[c][q][i][mu];
+                            j.out_im = s->Pim_dev + s->P_off[c][q][i][mu];
+                            cgroups[grid->n[mu]].push_back(j);
+                        }
+                }
+            for (auto &kv : cgroups) {
+                r = phi_batch_cplx((int)kv.first, kv.second, st);
+                if (r != DS_OK) { ds_phi_set_destroy(s); return r; }
+            }
+            // last mode: Re(eta (Yr + i Yi) x_d (Qr + i Qi)) = Yr x_d M1 + Yi x_d M2
+            const int64_t nd = grid->n[d - 1], nn = nd * nd;
+            for (int c = 0; c < 2; ++c)
+                for (int q = 0; q < kSlots; ++q) {
+                    const SplitCoeffs &co = s->co[kSlotEll[q] - 1];
+                    for (int i = 0; i < s->k; ++i) {
+                        const int64_t o = s->P_off[c][q][i][d - 1];
+                        double *M = s->Mf_dev + s->Mf_off[c][q][i];
+                        launch_fold_cplx(nn, s->P_dev + o, s->Pim_dev + o, co.eta[i], co.eta_im[i], M, M + nn, st);
+                    }
+                }
+            DS_CUDA_TRY(cudaStreamSynchronize(st));
+        } else {
+            for (auto &kv : groups) {
+                r = phi_batch_f64((int)kv.first, kv.second, st);
+                if (r != DS_OK) { ds_phi_set_destroy(s); return r; }
+            }
         }
         *out = s;
         return DS_OK;
@@ -438,6 +639,8 @@ ds_status ds_phi_set_destroy(ds_phi_set *s)
     cudaFree(s->tri_dev);
     cudaFree(s->P_dev);
     cudaFree(s->dP_dev);
+    cudaFree(s->Pim_dev);
+    cudaFree(s->Mf_dev);
     delete s;
     return DS_OK;
 }
@@ -445,10 +648,23 @@ ds_status ds_phi_set_destroy(ds_phi_set *s)
 ds_status ds_phi_get(const ds_phi_set *s, int c, int slot, int term, int mu, double *host_out)
 {
     if (!s || !host_out) return fail(DS_ERR_INVALID_ARG, "NULL argument");
-    if (c < 0 || c > 1 || slot < 0 || slot >= kSlots || term < 0 || term >= s->k || mu < 0 || mu >= s->d)
+    if (c < 0 || c > 1 || slot < 0 || slot >= s->nslots || term < 0 || term >= s->k || mu < 0 || mu >= s->d)
         return fail(DS_ERR_INVALID_ARG, "index out of range");
     const int64_t n = s->n[mu];
     DS_CUDA_TRY(cudaMemcpy(host_out, s->P_dev + s->P_off[c][slot][term][mu], sizeof(double) * n * n,
+                           cudaMemcpyDeviceToHost));
+    return DS_OK;
+}
+
+ds_status ds_phi_get_ex(const ds_phi_set *s, int c, int slot, int term, int mu, int part, double *host_out)
+{
+    if (!s || !host_out) return fail(DS_ERR_INVALID_ARG, "NULL argument");
+    if (c < 0 || c > 1 || slot < 0 || slot >= s->nslots || term < 0 || term >= s->k || mu < 0 || mu >= s->d)
+        return fail(DS_ERR_INVALID_ARG, "index out of range");
+    const double *base = part == 0 ? s->P_dev : part == 1 ? s->Pim_dev : part == 2 ? s->dP_dev : nullptr;
+    if (!base) return fail(DS_ERR_INVALID_ARG, "this phi-set has no such part");
+    const int64_t n = s->n[mu];
+    DS_CUDA_TRY(cudaMemcpy(host_out, base + s->P_off[c][slot][term][mu], sizeof(double) * n * n,
                            cudaMemcpyDeviceToHost));
     return DS_OK;
 }
@@ -527,6 +743,8 @@ ds_status ds_plan_create(const ds_grid *grid, const ds_params *params, const ds_
             if (!isfinite(params->p[q])) return fail(DS_ERR_INVALID_ARG, "non-finite model parameter");
         if (precision != DS_PREC_F64 && precision != DS_PREC_BF16X6 && precision != DS_PREC_F32)
             return fail(DS_ERR_UNSUPPORTED, "unknown precision");
+        if (set->scheme != DS_EXPRK3DS_REAL && precision != DS_PREC_F64)
+            return fail(DS_ERR_UNSUPPORTED, "ETD2RKDS and EXPRK3DS_CPLX plans are FP64 only");
         if ((r = check_device()) != DS_OK) return r;
         ds_plan *p = new (std::nothrow) ds_plan();
         if (!p) return fail(DS_ERR_OOM, "host allocation");
@@ -555,7 +773,7 @@ ds_status ds_plan_create(const ds_grid *grid, const ds_params *params, const ds_
             return cleanup(DS_ERR_OOM, "status word");
         cudaMemset(p->status, 0, sizeof(DevStatus));
         if (precision == DS_PREC_F64) {
-            p->ws_count = 10 * p->N;
+            p->ws_count = (set->scheme == DS_EXPRK3DS_CPLX ? 12 : 10) * p->N;
             if (cudaMalloc(&p->ws, sizeof(double) * p->ws_count) != cudaSuccess) {
                 cudaGetLastError();
                 return cleanup(DS_ERR_OOM, "FP64 workspace");
@@ -619,6 +837,27 @@ ds_status ds_integrate(ds_plan *p, double *U, int64_t nsteps, void *stream)
     return DS_OK;
 }
 
+ds_status ds_integrate_ckpt(ds_plan *p, double *U, int64_t nsteps, int64_t ckpt_every, double *ckpt,
+                            void *stream)
+{
+    if (!p || !U || nsteps < 0 || ckpt_every <= 0) return fail(DS_ERR_INVALID_ARG, "bad argument");
+    if (nsteps >= ckpt_every && !ckpt) return fail(DS_ERR_INVALID_ARG, "NULL checkpoint buffer");
+    const int64_t n2 = 2 * p->N;
+    int64_t done = 0, j = 0;
+    while (done < nsteps) {
+        const int64_t m = std::min(ckpt_every, nsteps - done);
+        ds_status r = ds_integrate(p, U, m, stream);
+        if (r != DS_OK) return r;
+        done += m;
+        if (m == ckpt_every) {
+            DS_CUDA_TRY(cudaMemcpyAsync(ckpt + j * n2, U, sizeof(double) * n2, cudaMemcpyDeviceToDevice,
+                                        (cudaStream_t)stream));
+            ++j;
+        }
+    }
+    return DS_OK;
+}
+
 // dscale[c] += w sum_i eta_i sum_mu < lam_s_c, T(X_c, P with P_mu -> dP_mu) >
 static void dscale_family(ds_plan *p, int c, int slot, const double *X, const double *lam_s, double w,
                           double *out, double *t1, double *t2, double *dscale, cudaStream_t st)
@@ -645,6 +884,7 @@ ds_status ds_step_backward(ds_plan *p, const double *U, const double *lam, doubl
     if (!p || !U || !lam || !lam_n) return fail(DS_ERR_INVALID_ARG, "NULL argument");
     if (lam_n == lam || lam_n == U) return fail(DS_ERR_INVALID_ARG, "lam_n must not alias U or lam");
     if (p->prec != DS_PREC_F64) return fail(DS_ERR_UNSUPPORTED, "the adjoint step needs an FP64 plan");
+    if (p->set->scheme != DS_EXPRK3DS_REAL) return fail(DS_ERR_UNSUPPORTED, "the adjoint covers EXPRK3DS_REAL");
     const int64_t N = p->N;
     if (!p->bws) {
         cudaError_t e = cudaMalloc(&p->bws, sizeof(double) * 24 * N);
@@ -904,6 +1144,15 @@ ds_status ds_batch_sync(ds_batch *b)
 
 int64_t ds_batch_kernels_per_step(const ds_batch *b) { return b ? b->launches_per_step : -1; }
 
+ds_status ds_plan_tuning(const ds_plan *p, int group, int mu, int *ksplit, int64_t *tiles, float *times_ms)
+{
+    if (!p || !ksplit || !tiles || !times_ms) return fail(DS_ERR_INVALID_ARG, "NULL argument");
+    if (!p->mixed) return fail(DS_ERR_UNSUPPORTED, "only split-BF16 plans are tuned");
+    if (tc::mixed_plan_tuning(p->mixed, group, mu, ksplit, tiles, times_ms) != 0)
+        return fail(DS_ERR_INVALID_ARG, "group or mode out of range");
+    return DS_OK;
+}
+
 ds_status ds_plan_profile(ds_plan *p, int enable)
 {
     if (!p) return fail(DS_ERR_INVALID_ARG, "NULL plan");
@@ -911,10 +1160,15 @@ ds_status ds_plan_profile(ds_plan *p, int enable)
     return DS_OK;
 }
 
-ds_status ds_plan_profile_read(ds_plan *p, double *ms, int64_t *launches, double *flops)
+ds_status ds_plan_profile_read_ex(ds_plan *p, double *ms, int64_t *launches, double *flops, double *bytes)
 {
     if (!p || !ms || !launches || !flops) return fail(DS_ERR_INVALID_ARG, "NULL argument");
-    for (int k = 0; k < 3; ++k) { ms[k] = 0.0; launches[k] = 0; flops[k] = 0.0; }
+    for (int k = 0; k < 3; ++k) {
+        ms[k] = 0.0;
+        launches[k] = 0;
+        flops[k] = 0.0;
+        if (bytes) bytes[k] = 0.0;
+    }
     for (auto &r : p->prof.recs) {
         DS_CUDA_TRY(cudaEventSynchronize(r.b));
         float t = 0.f;
@@ -922,11 +1176,17 @@ ds_status ds_plan_profile_read(ds_plan *p, double *ms, int64_t *launches, double
         ms[r.kind] += t;
         launches[r.kind] += 1;
         flops[r.kind] += r.flops;
+        if (bytes) bytes[r.kind] += r.bytes;
         p->prof.pool.push_back(r.a);
         p->prof.pool.push_back(r.b);
     }
     p->prof.recs.clear();
     return DS_OK;
+}
+
+ds_status ds_plan_profile_read(ds_plan *p, double *ms, int64_t *launches, double *flops)
+{
+    return ds_plan_profile_read_ex(p, ms, launches, flops, nullptr);
 }
 
 ds_status ds_plan_destroy(ds_plan *p)

@@ -11,7 +11,7 @@
 
 namespace ds {
 
-constexpr int kMaxD = 3;      // d in {2, 3}
+constexpr int kMaxD = 4;      // d in {2, 3, 4}
 constexpr int kSlots = 5;     // (s2,l1) (s3,l1) (s3,l2) (sf,l1) (sf,l2)
 constexpr int kMaxTerms = 3;
 
@@ -21,8 +21,11 @@ struct SplitCoeffs {
     int ell_i[kMaxTerms];     // phi index of each term
     double eta[kMaxTerms];
     double alpha[kMaxTerms][kMaxD];
+    double eta_im[kMaxTerms];            // imaginary parts (complex scheme; else 0)
+    double alpha_im[kMaxTerms][kMaxD];
 };
 SplitCoeffs split_coeffs(int d, int ell);
+SplitCoeffs split_coeffs_cplx(int d, int ell);
 
 // Stage scalar c_s of each slot and target l of each slot.
 extern const double kSlotC[kSlots];
@@ -117,6 +120,19 @@ struct PhiJob {
 };
 ds_status phi_batch_f64(int n, const std::vector<PhiJob> &jobs, cudaStream_t st);
 
+// phi of complex multiples z_b A_b through the real 2n x 2n embedding
+// [[Re, -Im], [Im, Re]]; writes the real and imaginary parts.
+struct PhiJobC {
+    const double *A;   // device, real column-major n x n
+    double zr, zi;     // complex scalar multiplying A
+    int ell;
+    double *out_re, *out_im;
+};
+ds_status phi_batch_cplx(int n, const std::vector<PhiJobC> &jobs, cudaStream_t st);
+// M1 = er Qr - ei Qi, M2 = -(er Qi + ei Qr)  (n x n)
+void launch_fold_cplx(int64_t nn, const double *Qr, const double *Qi, double er, double ei, double *M1,
+                      double *M2, cudaStream_t st);
+
 // Non-finite scan: sets *flag (device int) to 1 if any entry is NaN/Inf.
 void launch_nonfinite_scan(const double *x, int64_t count, int *flag, cudaStream_t st);
 
@@ -127,6 +143,7 @@ struct Prof {
         cudaEvent_t a, b;
         int kind;
         double flops;
+        double bytes;   // algorithmic DRAM bytes: compulsory reads of inputs + writes of outputs
     };
     bool on = false;
     std::vector<Rec> recs;
@@ -142,10 +159,10 @@ struct Prof {
         pool.pop_back();
         return e;
     }
-    void begin(cudaStream_t st, int kind, double flops)
+    void begin(cudaStream_t st, int kind, double flops, double bytes = 0.0)
     {
         if (!on) return;
-        Rec r{take(), take(), kind, flops};
+        Rec r{take(), take(), kind, flops, bytes};
         cudaEventRecord(r.a, st);
         recs.push_back(r);
     }
@@ -173,6 +190,8 @@ struct DevStatus {
 
 // Library-owned objects ---------------------------------------------------
 struct ds_phi_set {
+    int scheme = 0;                         // ds_scheme
+    int nslots = 5;                         // 5 (EXPRK3DS_REAL) or 2 (ETD2RKDS)
     int d;
     int64_t n[ds::kMaxD];
     int k;
@@ -185,6 +204,9 @@ struct ds_phi_set {
     int64_t tri_off[2][ds::kMaxD];
     double *P_dev = nullptr;                // FP64 phi-matrices, column-major blocks
     double *dP_dev = nullptr;               // their derivatives w.r.t. a scaling of A (same offsets)
+    double *Pim_dev = nullptr;              // complex scheme: imaginary parts (same offsets)
+    double *Mf_dev = nullptr;               // complex scheme: last-mode matrices with Re(eta .) folded in
+    int64_t Mf_off[2][ds::kSlots][ds::kMaxTerms];
     int64_t P_off[2][ds::kSlots][ds::kMaxTerms][ds::kMaxD];
     int64_t P_count = 0;
 };

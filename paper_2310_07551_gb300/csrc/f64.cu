@@ -758,4 +758,77 @@ ds_status phi_batch_f64(int n, const std::vector<PhiJob> &jobs, cudaStream_t st)
     return DS_OK;
 }
 
+namespace {
+// Aemb (2n x 2n, column-major) = [[zr A, -zi A], [zi A, zr A]]
+__global__ void k_embed(int n, const double *__restrict__ A, double zr, double zi, double *__restrict__ E)
+{
+    const int64_t m = 2 * (int64_t)n, mm = m * m;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < mm;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e % m, c = e / m;
+        const int64_t i = r % n, j = c % n;
+        const double a = A[i + (int64_t)n * j];
+        const bool lower = r >= n, right = c >= n;
+        double v;
+        if (lower == right) v = zr * a;        // diagonal blocks
+        else if (lower) v = zi * a;            // bottom-left
+        else v = -zi * a;                      // top-right
+        E[e] = v;
+    }
+}
+// re = top-left n x n block, im = bottom-left block of a 2n x 2n matrix
+__global__ void k_unembed(int n, const double *__restrict__ E, double *__restrict__ re, double *__restrict__ im)
+{
+    const int64_t nn = (int64_t)n * n, m = 2 * (int64_t)n;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nn;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e % n, j = e / n;
+        re[e] = E[i + m * j];
+        im[e] = E[(i + n) + m * j];
+    }
+}
+__global__ void k_fold_cplx(int64_t nn, const double *__restrict__ Qr, const double *__restrict__ Qi, double er,
+                            double ei, double *__restrict__ M1, double *__restrict__ M2)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nn;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        M1[e] = er * Qr[e] - ei * Qi[e];
+        M2[e] = -(er * Qi[e] + ei * Qr[e]);
+    }
+}
+}  // namespace
+
+void launch_fold_cplx(int64_t nn, const double *Qr, const double *Qi, double er, double ei, double *M1,
+                      double *M2, cudaStream_t st)
+{
+    k_fold_cplx<<<grid_for(nn), 256, 0, st>>>(nn, Qr, Qi, er, ei, M1, M2);
+}
+
+ds_status phi_batch_cplx(int n, const std::vector<PhiJobC> &jobs, cudaStream_t st)
+{
+    const int nb = (int)jobs.size();
+    if (nb == 0) return DS_OK;
+    const int64_t m = 2 * (int64_t)n, mm = m * m;
+    double *buf = nullptr;
+    DS_CUDA_TRY(cudaMallocAsync(&buf, sizeof(double) * mm * nb * 2, st));
+    double *emb = buf, *res = buf + mm * nb;
+    std::vector<PhiJob> rj(nb);
+    for (int b = 0; b < nb; ++b) {
+        k_embed<<<grid_for(mm), 256, 0, st>>>(n, jobs[b].A, jobs[b].zr, jobs[b].zi, emb + b * mm);
+        rj[b].A = emb + b * mm;
+        rj[b].z = 1.0;
+        rj[b].ell = jobs[b].ell;
+        rj[b].out = res + b * mm;
+        rj[b].dout = nullptr;
+    }
+    ds_status r = phi_batch_f64((int)m, rj, st);
+    if (r != DS_OK) { cudaFreeAsync(buf, st); return r; }
+    for (int b = 0; b < nb; ++b)
+        k_unembed<<<grid_for((int64_t)n * n), 256, 0, st>>>(n, res + b * mm, jobs[b].out_re, jobs[b].out_im);
+    cudaFreeAsync(buf, st);
+    DS_CUDA_TRY(cudaStreamSynchronize(st));
+    DS_CUDA_TRY(cudaGetLastError());
+    return DS_OK;
+}
+
 }  // namespace ds

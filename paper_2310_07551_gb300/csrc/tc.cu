@@ -517,11 +517,23 @@ __device__ __forceinline__ void store_planes_f(bf16 *dst, int64_t plane, int64_t
 
 // g(u + du, v + dv) - g(u, v) written as a polynomial in the increments, so
 // the difference carries no cancellation and can be evaluated in FP32.
-__device__ __forceinline__ void react_diff(const Model &m, float u, float v, float du, float dv,
+// model parameters rounded to FP32 on the host
+struct ModelF {
+    int model;
+    float p[3];
+};
+static ModelF model_f(const Model &m)
+{
+    ModelF r;
+    r.model = m.model;
+    for (int k = 0; k < 3; ++k) r.p[k] = (float)m.p[k];
+    return r;
+}
+__device__ __forceinline__ void react_diff(const ModelF &m, float u, float v, float du, float dv,
                                            float &Du, float &Dv)
 {
     if (m.model == DS_SCHNAKENBERG) {
-        const float gam = (float)m.p[0];
+        const float gam = m.p[0];
         const float q = fmaf(2.0f * u, du, du * du);          // (u+du)^2 - u^2
         const float w = fmaf(q, v + dv, u * u * dv);            // (u+du)^2 (v+dv) - u^2 v
         Du = gam * (w - du);
@@ -529,7 +541,7 @@ __device__ __forceinline__ void react_diff(const Model &m, float u, float v, flo
     } else if (m.model == DS_FHN) {
         const float cub = du * fmaf(3.0f * u, u + du, du * du); // (u+du)^3 - u^3
         Du = (du - dv) - cub;
-        Dv = (float)m.p[0] * fmaf(-(float)m.p[1], dv, du);
+        Dv = m.p[0] * fmaf(-m.p[1], dv, du);
     } else {
         Du = 0.0f;
         Dv = 0.0f;
@@ -556,27 +568,46 @@ __device__ __forceinline__ double stencil_k(const Stencil &s, const double *U, i
     return acc;
 }
 
-// Exact split of an FP64 value into FP32 hi + lo with integer operations only
-// (GB300's FP64 pipe is ~1/64 of its FP32 rate, so the reduced-precision step
-// keeps FP64 arithmetic for the state update alone).  hi takes the leading
-// 24 significant bits, lo the next 29 rounded to 24: u = hi + lo to 2^-48
-// relative.  |u| outside [2^-74, 2^127] falls back to hi = (float)u, lo = 0.
+// Exact split of an FP64 value into FP32 hi + lo with integer and FP32
+// operations only (GB300's FP64 pipe, conversions included, runs at ~1/64 of
+// its FP32 rate, so the reduced-precision step keeps FP64 instructions out of
+// its pointwise kernels).  hi takes the leading 24 significant bits; lo the
+// next 29 rounded to 23, built as (1.m x 2^k) - 2^k (exact: Sterbenz), so
+// u = hi + lo to 2^-47 relative.  |u| < 2^-74 gives hi = lo = +-0;
+// |u| > 2^127 gives hi = +-inf (NaN stays NaN), lo = 0.
 __device__ __forceinline__ void split_hilo(double u, float &hi, float &lo)
 {
     const unsigned long long b = (unsigned long long)__double_as_longlong(u);
     const unsigned h32 = (unsigned)(b >> 32), l32 = (unsigned)b;
     const int e = (int)((h32 >> 20) & 0x7FF);
-    if (e < 949 || e > 1150) {
-        hi = (float)u;
-        lo = 0.0f;
-        return;
-    }
     const unsigned sign = h32 & 0x80000000u;
-    const unsigned top23 = ((h32 & 0xFFFFFu) << 3) | (l32 >> 29);
-    hi = __uint_as_float(sign | ((unsigned)(e - 1023 + 127) << 23) | top23);
-    const float rest = __uint2float_rn(l32 & 0x1FFFFFFFu);            // < 2^29
-    const float scale = __uint_as_float((unsigned)(e - 1075 + 127) << 23);  // 2^(e-1075)
-    lo = __uint_as_float(sign | __float_as_uint(rest * scale));
+    if (e >= 949 && e <= 1150) {
+        const unsigned top23 = ((h32 & 0xFFFFFu) << 3) | (l32 >> 29);
+        hi = __uint_as_float(sign | ((unsigned)(e - 1023 + 127) << 23) | top23);
+        const unsigned ebits = (unsigned)(e - 1046 + 127) << 23;                 // 2^(e-1046)
+        const unsigned m = ((l32 & 0x1FFFFFFFu) + 32u) >> 6;                    // <= 2^23
+        const float r = __fsub_rn(__uint_as_float(ebits + m), __uint_as_float(ebits));
+        lo = __uint_as_float(sign | __float_as_uint(r));
+    } else if (e < 949) {
+        hi = __uint_as_float(sign);
+        lo = 0.0f;
+    } else {
+        const bool nan = e == 0x7FF && ((h32 & 0xFFFFFu) | l32) != 0u;
+        hi = __uint_as_float(sign | 0x7F800000u | (nan ? 0x400000u : 0u));
+        lo = 0.0f;
+    }
+}
+
+// Exact FP32 -> FP64 widening with integer operations (subnormal floats, below
+// 2^-126, become +-0).
+__device__ __forceinline__ double widen_f(float x)
+{
+    const unsigned b = __float_as_uint(x);
+    const unsigned e = (b >> 23) & 0xFFu;
+    const unsigned sign = b & 0x80000000u, m = b & 0x7FFFFFu;
+    if (e == 0u) return __hiloint2double((int)sign, 0);
+    const unsigned ed = e == 0xFFu ? 0x7FFu : e + (1023u - 127u);
+    return __hiloint2double((int)(sign | (ed << 20) | (m >> 3)), (int)(m << 29));
 }
 
 // FP32 copy of the tridiagonal bands of one component.
@@ -585,23 +616,26 @@ struct StencilF {
     int64_t n[kMaxD];
     const float *lo[kMaxD], *up[kMaxD], *rsum[kMaxD];   // rsum = lo + di + up
     int has_rsum[kMaxD];
+    // r / n[mu] = (r * magic[mu]) >> shift[mu] for r < 2^31 (fast31: N < 2^31)
+    unsigned long long magic[kMaxD];
+    int shift[kMaxD];
+    int fast31;
 };
 
 // K u for one point of one component from hi/lo parts: each tridiagonal row
 // is written as lo (u_{i-1} - u_i) + up (u_{i+1} - u_i) + (lo + di + up) u_i,
 // with the differences formed as (h_a - h_b) + (l_a - l_b) in FP32, so the
 // cancellation of a smooth field costs no more than 2^-24 of the difference.
-__device__ __forceinline__ float stencil_hilo(const StencilF &s, const double *U, int64_t p, float hc,
-                                              float lc)
+__device__ __forceinline__ float stencil_hilo(const StencilF &s, const double *U, int64_t p, const int *idx,
+                                              float hc, float lc)
 {
     float acc = 0.0f;
-    int64_t stride = 1, rest = p;
+    int64_t stride = 1;
 #pragma unroll
     for (int mu = 0; mu < kMaxD; ++mu) {
         if (mu < s.d) {
             const int64_t nm = s.n[mu];
-            const int64_t i = rest % nm;
-            rest /= nm;
+            const int i = idx[mu];
             float r = 0.0f;
             if (i > 0) {
                 float h, l;
@@ -619,6 +653,28 @@ __device__ __forceinline__ float stencil_hilo(const StencilF &s, const double *U
         }
     }
     return acc;
+}
+
+// grid coordinates of linear index p: multiply-shift division when the grid
+// has fewer than 2^31 points (no integer divide instruction on the GPU)
+__device__ __forceinline__ void coords(const StencilF &s, int64_t p, int *idx)
+{
+    if (s.fast31) {
+        uint32_t r = (uint32_t)p;
+#pragma unroll
+        for (int mu = 0; mu < kMaxD; ++mu) {
+            const uint32_t q = (uint32_t)(((unsigned long long)r * s.magic[mu]) >> s.shift[mu]);
+            idx[mu] = (int)(r - q * (uint32_t)s.n[mu]);
+            r = q;
+        }
+    } else {
+        int64_t r = p;
+#pragma unroll
+        for (int mu = 0; mu < kMaxD; ++mu) {
+            idx[mu] = (int)(r % s.n[mu]);
+            r /= s.n[mu];
+        }
+    }
 }
 
 // Double-float arithmetic (a value is an unevaluated sum hi + lo of two
@@ -688,15 +744,17 @@ __global__ void k_rhs_planes(StencilF s0, StencilF s1, ModelDF m, int64_t N, con
         split_hilo(U[N + p], hv, lv);
         float gu, gv;
         react_df(m, dfl{hu, lu}, dfl{hv, lv}, gu, gv);
-        store_planes_f(Fp, N, p, stencil_hilo(s0, U, p, hu, lu) + gu);
-        store_planes_f(Fp + 3 * N, N, p, stencil_hilo(s1, U + N, p, hv, lv) + gv);
+        int idx[kMaxD];
+        coords(s0, p, idx);
+        store_planes_f(Fp, N, p, stencil_hilo(s0, U, p, idx, hu, lu) + gu);
+        store_planes_f(Fp + 3 * N, N, p, stencil_hilo(s1, U + N, p, idx, hv, lv) + gv);
     }
 }
 
 // D = g(U + a (+ b)) - g(U) for both components, as BF16 planes, from the
 // increment form of react_diff.  a, b: FP32 increments with component
 // stride cs_a / cs_b.
-__global__ void k_stage_planes(Model m, int64_t N, const double *__restrict__ U, const float *__restrict__ a,
+__global__ void k_stage_planes(ModelF m, int64_t N, const double *__restrict__ U, const float *__restrict__ a,
                                int64_t cs_a, const float *__restrict__ b, int64_t cs_b,
                                bf16 *__restrict__ Dp)
 {
@@ -718,14 +776,15 @@ __global__ void k_stage_planes(Model m, int64_t N, const double *__restrict__ U,
 }
 
 // U <- U + (a + b) in FP64 (both components); the two FP32 increments are
-// summed in FP32 first, so each value costs one conversion and one FP64 add.
+// summed in FP32 first and widened with integer operations, so each value
+// costs one FP64 add.
 __global__ void k_final_mixed(int64_t N, double *__restrict__ U, const float *__restrict__ a, int64_t cs_a,
                               const float *__restrict__ b, int64_t cs_b)
 {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < N;
          p += (int64_t)gridDim.x * blockDim.x) {
-        U[p] += (double)(a[p] + b[p]);
-        U[N + p] += (double)(a[cs_a + p] + b[cs_b + p]);
+        U[p] += widen_f(a[p] + b[p]);
+        U[N + p] += widen_f(a[cs_a + p] + b[cs_b + p]);
     }
 }
 
@@ -775,7 +834,7 @@ __global__ void k_rhs_f32(Stencil s0, Stencil s1, Model m, int64_t N, const doub
         F[N + p] = (float)(stencil_k(s1, U + N, p) + gv);
     }
 }
-__global__ void k_stage_f32(Model m, int64_t N, const double *__restrict__ U, const float *__restrict__ a,
+__global__ void k_stage_f32(ModelF m, int64_t N, const double *__restrict__ U, const float *__restrict__ a,
                             float w1, const float *__restrict__ b, float w2, float *__restrict__ D)
 {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < N;
@@ -819,7 +878,7 @@ void launch_rhs_f32(const Stencil *sten, const Model &m, int64_t N, const double
 void launch_stage_f32(const Model &m, int64_t N, const double *U, const float *a, double w1,
                       const float *b, double w2, float *D, cudaStream_t st)
 {
-    k_stage_f32<<<pw_grid(N), 256, 0, st>>>(m, N, U, a, (float)w1, b, (float)w2, D);
+    k_stage_f32<<<pw_grid(N), 256, 0, st>>>(model_f(m), N, U, a, (float)w1, b, (float)w2, D);
 }
 void launch_final_f32(int64_t N, double *U, const float *a, double w1, const float *b, double w2,
                       cudaStream_t st)
@@ -875,6 +934,7 @@ struct ModeLaunch {
     int grid = 0;
     int64_t base_tiles = 0;    // output tiles before the split-K factor
     int64_t N = 0;             // points per output combo
+    double alg_bytes = 0.0;    // distinct input planes + phi planes + output, read/written once
 };
 
 static int num_sms()
@@ -960,6 +1020,17 @@ static ds_status describe(ModeLaunch &L, int d, const int64_t *n, int mu, const 
     L.base_tiles = a.num_tiles;
     L.N = N;
     L.grid = (int)std::min<int64_t>(a.num_tiles, num_sms());
+    {
+        std::vector<char> used(xcombos, 0);
+        int nx = 0;
+        for (int s = 0; s < S; ++s)
+            for (int t = 0; t < T; ++t) {
+                const int x = (s / xs_div) * xs_stride + t;
+                if (x < xcombos && !used[x]) { used[x] = 1; ++nx; }
+            }
+        L.alg_bytes = 6.0 * nx * (double)N + 6.0 * S * T * (double)nm * (double)nm +
+                      (out_kind == 0 ? 6.0 : 4.0) * S * (double)N;
+    }
     return DS_OK;
 }
 
@@ -1019,8 +1090,8 @@ static void launch(const ModeLaunch &L, cudaStream_t st)
 
 // ---------------------------------------------------------------------------
 // Autotuner: for launches with fewer than two waves of output tiles, time
-// split-K factors 1..4 (each part keeping >= 4 K chunks) on the launch's own
-// buffers and keep the fastest.  Choices are cached per launch shape for the
+// split-K factors 1..8 (each part keeping >= 4 K chunks, at most 4 waves) on
+// the launch's own buffers and keep the fastest.  Choices are cached per launch shape for the
 // process, so equal shapes in different plans run identical arithmetic.
 // ---------------------------------------------------------------------------
 struct ShapeKey {
@@ -1038,11 +1109,33 @@ static std::map<ShapeKey, int> g_tuned;
 static int max_split(const ModeLaunch &L)
 {
     const int kiters = L.args.T * L.args.kchunks;
-    if (L.base_tiles >= 2 * (int64_t)num_sms()) return 1;
-    return std::max(1, std::min(4, kiters / 4));
+    const int64_t sms = num_sms();
+    if (L.base_tiles >= 2 * sms) return 1;
+    int k = 1;
+    // each part keeps >= 4 K chunks; stop once the split reaches 4 waves
+    while (k < 8 && kiters / (k + 1) >= 4 && L.base_tiles * (k + 1) <= 4 * sms) ++k;
+    return k;
 }
 
-static int autotune_split(ModeLaunch &L, float *ws, cudaStream_t st)
+// fastest of five individually timed launches, after two warm launches
+static float time_launch(const ModeLaunch &L, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1)
+{
+    launch(L, st);
+    launch(L, st);
+    float best = 1e30f;
+    for (int r = 0; r < 5; ++r) {
+        cudaEventRecord(e0, st);
+        launch(L, st);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        best = std::min(best, ms);
+    }
+    return best;
+}
+
+static int autotune_split(ModeLaunch &L, float *ws, cudaStream_t st, float *times)
 {
     const ShapeKey key{L.mode1, L.args.n, L.args.S, L.args.T, L.args.I, L.args.O};
     {
@@ -1059,14 +1152,13 @@ static int autotune_split(ModeLaunch &L, float *ws, cudaStream_t st)
         float best_ms = 1e30f;
         for (int k = 1; k <= kmax; ++k) {
             set_split(L, k, ws);
-            launch(L, st);
-            cudaEventRecord(e0, st);
-            for (int r = 0; r < 2; ++r) launch(L, st);
-            cudaEventRecord(e1, st);
-            cudaEventSynchronize(e1);
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best_ms * 0.97f) { best_ms = ms; best = k; }
+            const float ms = time_launch(L, st, e0, e1);
+            if (times) times[k - 1] = ms;
+            // a larger split has to win by 3%: it adds partial traffic
+            if (ms < best_ms * 0.97f) {
+                best_ms = ms;
+                best = k;
+            }
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
@@ -1102,11 +1194,12 @@ struct MixedPlan {
     bf16 *Fp = nullptr;        // [2][3][N]
     bf16 *Dp = nullptr;        // [2][3][N]
     bf16 *Z1 = nullptr;        // [3k][3][N]
-    bf16 *Z2 = nullptr;        // [3k][3][N] (d = 3)
+    bf16 *Z2 = nullptr;        // [3k][3][N] (d >= 3)
     float *incF = nullptr;     // [2][3][N]
     float *incD = nullptr;     // [2][N]
     float *bands = nullptr;    // FP32 bands [c][mu][lo, up, rowsum][n_mu]
     float *part_ws = nullptr;  // split-K partials
+    float tune_ms[3][kMaxD][8];  // autotuner: time of each split-K candidate (0 = not tried)
     StencilF stf[2];
     // launches[group][mode], both components in one launch;
     // group 0 = F, 1 = D2 (slot 2), 2 = D3 (slot 4)
@@ -1119,6 +1212,7 @@ ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatu
     if (r != DS_OK) return r;
     if (!encode_fn()) return fail(DS_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled unavailable");
     MixedPlan *mp = new MixedPlan();
+    memset(mp->tune_ms, 0, sizeof(mp->tune_ms));
     mp->d = set->d;
     mp->k = set->k;
     mp->N = 1;
@@ -1140,9 +1234,16 @@ ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatu
         int64_t off = 0;
         for (int c = 0; c < 2; ++c) {
             mp->stf[c].d = d;
+            mp->stf[c].fast31 = mp->N < ((int64_t)1 << 31);
             for (int mu = 0; mu < kMaxD; ++mu) {
-                mp->stf[c].n[mu] = mp->n[mu];
+                const int64_t nm = mp->n[mu];
+                mp->stf[c].n[mu] = nm;
                 mp->stf[c].has_rsum[mu] = 0;
+                // magic = floor(2^k / n) + 1, k = 31 + ceil(log2 n): exact quotients for r < 2^31
+                int l = 0;
+                while (((int64_t)1 << l) < nm) ++l;
+                mp->stf[c].shift[mu] = 31 + l;
+                mp->stf[c].magic[mu] = (unsigned long long)(((unsigned __int128)1 << (31 + l)) / (unsigned)nm) + 1ull;
             }
             for (int mu = 0; mu < d; ++mu) {
                 const int64_t nm = mp->n[mu];
@@ -1201,7 +1302,7 @@ ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatu
         cudaMalloc(&mp->Fp, sizeof(bf16) * 6 * N) != cudaSuccess ||
         cudaMalloc(&mp->Dp, sizeof(bf16) * 6 * N) != cudaSuccess ||
         cudaMalloc(&mp->Z1, sizeof(bf16) * 18 * k * N) != cudaSuccess ||
-        (d == 3 && cudaMalloc(&mp->Z2, sizeof(bf16) * 18 * k * N) != cudaSuccess) ||
+        (d >= 3 && cudaMalloc(&mp->Z2, sizeof(bf16) * 18 * k * N) != cudaSuccess) ||
         cudaMalloc(&mp->incF, sizeof(float) * 6 * N) != cudaSuccess ||
         cudaMalloc(&mp->incD, sizeof(float) * 2 * N) != cudaSuccess) {
         cudaGetLastError();
@@ -1276,7 +1377,7 @@ ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatu
             for (int g = 0; g < 3; ++g)
                 for (int mu = 0; mu < d; ++mu) {
                     ModeLaunch &L = mp->L[g][mu];
-                    const int k = autotune_split(L, mp->part_ws, ts);
+                    const int k = autotune_split(L, mp->part_ws, ts, mp->tune_ms[g][mu]);
                     set_split(L, k, k > 1 ? mp->part_ws : nullptr);
                 }
             cudaStreamSynchronize(ts);
@@ -1286,6 +1387,16 @@ ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatu
     }
     *out = mp;
     return DS_OK;
+}
+
+int mixed_plan_tuning(const MixedPlan *mp, int g, int mu, int *ksplit, int64_t *tiles, float *times)
+{
+    if (!mp || g < 0 || g > 2 || mu < 0 || mu >= mp->d) return -1;
+    const ModeLaunch &L = mp->L[g][mu];
+    *ksplit = L.args.ksplit;
+    *tiles = L.base_tiles;
+    for (int k = 0; k < 8; ++k) times[k] = mp->tune_ms[g][mu][k];
+    return 0;
 }
 
 void mixed_plan_destroy(MixedPlan *mp)
@@ -1332,30 +1443,32 @@ int enqueue_step_mixed(MixedPlan *mp, const ds_phi_set *set, const Model &model,
     Prof &P = prof ? *prof : dummy;
     auto group = [&](int g) {
         for (int mu = 0; mu < d; ++mu) {
-            P.begin(st, 0, launch_flops(mp->L[g][mu], N));
+            P.begin(st, 0, launch_flops(mp->L[g][mu], N), mp->L[g][mu].alg_bytes);
             launch(mp->L[g][mu], st);
             P.end(st);
             ++L;
         }
     };
-    P.begin(st, 2, 0.0);
+    const double Nd = (double)N;
+    // pointwise bytes: FP64 state 16 B/point, FP32 increments 4 B, BF16 planes 6 B per component
+    P.begin(st, 2, 0.0, Nd * (16 + 12));
     k_rhs_planes<<<pw_grid(N), 256, 0, st>>>(mp->stf[0], mp->stf[1], model_df(model), N, U, mp->Fp);
     P.end(st);
     ++L;
     group(0);
     // D2 = g(U + inc_2) - g(U)
-    P.begin(st, 2, 0.0);
-    k_stage_planes<<<pw_grid(N), 256, 0, st>>>(model, N, U, mp->incF, 3 * N, nullptr, 0, mp->Dp);
+    P.begin(st, 2, 0.0, Nd * (16 + 8 + 12));
+    k_stage_planes<<<pw_grid(N), 256, 0, st>>>(model_f(model), N, U, mp->incF, 3 * N, nullptr, 0, mp->Dp);
     P.end(st);
     ++L;
     group(1);
     // D3 = g(U + inc_3F + inc_3D) - g(U)
-    P.begin(st, 2, 0.0);
-    k_stage_planes<<<pw_grid(N), 256, 0, st>>>(model, N, U, mp->incF + N, 3 * N, mp->incD, N, mp->Dp);
+    P.begin(st, 2, 0.0, Nd * (16 + 16 + 12));
+    k_stage_planes<<<pw_grid(N), 256, 0, st>>>(model_f(model), N, U, mp->incF + N, 3 * N, mp->incD, N, mp->Dp);
     P.end(st);
     ++L;
     group(2);
-    P.begin(st, 2, 0.0);
+    P.begin(st, 2, 0.0, Nd * (32 + 16));
     k_final_mixed<<<pw_grid(N), 256, 0, st>>>(N, U, mp->incF + 2 * N, 3 * N, mp->incD, N);
     P.end(st);
     ++L;

@@ -55,7 +55,7 @@ extern "C" ds_status ds_tucker_static(const ds_grid *grid, const double *X, doub
                                       const double *const *L, int transpose, void *stream)
 {
     if (!grid || !X || !Y || !L) return ds::fail(DS_ERR_INVALID_ARG, "NULL argument");
-    if (grid->d < 2 || grid->d > ds::kMaxD) return ds::fail(DS_ERR_INVALID_ARG, "d must be 2 or 3");
+    if (grid->d < 2 || grid->d > ds::kMaxD) return ds::fail(DS_ERR_INVALID_ARG, "d must be 2, 3 or 4");
     int64_t N = 1;
     for (int q = 0; q < grid->d; ++q) {
         if (grid->n[q] < 2 || grid->n[q] > kStaticMaxPoints)

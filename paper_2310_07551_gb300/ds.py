@@ -20,6 +20,7 @@ STATUS_NAMES = ["DS_OK", "DS_ERR_INVALID_ARG", "DS_ERR_UNSUPPORTED", "DS_ERR_OOM
                 "DS_ERR_NONFINITE", "DS_ERR_TIMEOUT"]
 PREC = {"f64": 0, "bf16x6": 1, "f32": 2}
 MODELS = {"schnakenberg": 0, "fhn": 1, "linear": 2}
+SCHEMES = {"exprk3ds_real": 0, "etd2rkds": 1, "exprk3ds_cplx": 2}
 
 
 class DsError(RuntimeError):
@@ -50,19 +51,27 @@ def lib() -> ctypes.CDLL:
         gp, pp = ctypes.POINTER(Grid), ctypes.POINTER(Params)
         sig = {
             "ds_phi_setup": ([gp, _vp, ctypes.c_int, ctypes.c_double, ctypes.POINTER(_vp), _vp], ctypes.c_int),
+            "ds_phi_setup_ex": ([gp, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.POINTER(_vp), _vp],
+                                ctypes.c_int),
             "ds_phi_set_destroy": ([_vp], ctypes.c_int),
             "ds_phi_get": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp], ctypes.c_int),
+            "ds_phi_get_ex": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp],
+                              ctypes.c_int),
             "ds_tucker": ([gp, _vp, _vp, ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, _vp], ctypes.c_int),
             "ds_kronsum": ([_vp, ctypes.c_int, _vp, _vp, _vp], ctypes.c_int),
             "ds_tucker_static": ([gp, _vp, _vp, ctypes.POINTER(_vp), ctypes.c_int, _vp], ctypes.c_int),
             "ds_plan_create": ([gp, pp, _vp, ctypes.c_int, ctypes.POINTER(_vp)], ctypes.c_int),
             "ds_step": ([_vp, _vp, _vp], ctypes.c_int),
             "ds_integrate": ([_vp, _vp, ctypes.c_int64, _vp], ctypes.c_int),
+            "ds_integrate_ckpt": ([_vp, _vp, ctypes.c_int64, ctypes.c_int64, _vp, _vp], ctypes.c_int),
             "ds_step_backward": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
             "ds_plan_sync": ([_vp, _vp, ctypes.c_int], ctypes.c_int),
             "ds_plan_kernels_per_step": ([_vp], ctypes.c_int64),
             "ds_plan_profile": ([_vp, ctypes.c_int], ctypes.c_int),
+            "ds_plan_tuning": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
             "ds_plan_profile_read": ([_vp, _dp, ctypes.POINTER(ctypes.c_int64), _dp], ctypes.c_int),
+            "ds_plan_profile_read_ex": ([_vp, _dp, ctypes.POINTER(ctypes.c_int64), _dp, _dp], ctypes.c_int),
             "ds_plan_destroy": ([_vp], ctypes.c_int),
             "ds_batch_create": ([ctypes.c_int, gp, ctypes.POINTER(_vp), _dp, pp, ctypes.c_int,
                                  ctypes.POINTER(_vp)], ctypes.c_int),
@@ -116,19 +125,22 @@ def pack_A(As) -> np.ndarray:
 class PhiSet:
     """ds_phi_set: FP64 phi-matrices of Algorithms 1/2 for both components."""
 
-    def __init__(self, dims, As, tau: float, stream=None):
+    def __init__(self, dims, As, tau: float, stream=None, scheme: str = "exprk3ds_real"):
         self.dims = tuple(int(n) for n in dims)
         self.grid = make_grid(self.dims)
         self.tau = float(tau)
+        self.scheme = scheme
         host = pack_A(As)
         self._h = _vp()
-        check(lib().ds_phi_setup(ctypes.byref(self.grid), host.ctypes.data_as(_vp), 0, self.tau,
-                                 ctypes.byref(self._h), _stream_ptr(stream)))
+        check(lib().ds_phi_setup_ex(ctypes.byref(self.grid), host.ctypes.data_as(_vp), 0, self.tau,
+                                    SCHEMES[scheme], ctypes.byref(self._h), _stream_ptr(stream)))
 
-    def get(self, c: int, slot: int, term: int, mu: int) -> np.ndarray:
+    def get(self, c: int, slot: int, term: int, mu: int, part: int = 0) -> np.ndarray:
+        """phi-matrix (part 0; real part for the complex scheme), its imaginary
+        part (1) or its derivative w.r.t. a scaling of A (2), as (n, n)."""
         n = self.dims[mu]
         out = np.empty(n * n)
-        check(lib().ds_phi_get(self._h, c, slot, term, mu, out.ctypes.data_as(_dp)))
+        check(lib().ds_phi_get_ex(self._h, c, slot, term, mu, part, out.ctypes.data_as(_dp)))
         return out.reshape(n, n).T.copy()
 
     def kronsum(self, c: int, X, stream=None):
@@ -184,18 +196,47 @@ class Plan:
         check(lib().ds_integrate(self._h, _dptr(U), int(nsteps), _stream_ptr(stream)))
         return U
 
+    def integrate_ckpt(self, U, nsteps: int, ckpt_every: int, stream=None):
+        """Advance U by nsteps; returns the checkpoints, a tensor of shape
+        (nsteps // ckpt_every, *U.shape): entry j is the state after
+        (j + 1) * ckpt_every steps."""
+        import torch
+        nck = int(nsteps) // int(ckpt_every) if ckpt_every > 0 else 0
+        ck = torch.empty((nck,) + tuple(U.shape), dtype=torch.float64, device=U.device)
+        check(lib().ds_integrate_ckpt(self._h, _dptr(U), int(nsteps), int(ckpt_every),
+                                      _dptr(ck) if nck else None, _stream_ptr(stream)))
+        return ck
+
     def sync(self, U=None, check_state: bool = False):
         check(lib().ds_plan_sync(self._h, _dptr(U) if U is not None else None, int(check_state)))
+
+    def tuning(self):
+        """Autotuner record: [(group, mode, ksplit, tiles, {split: ms})] for
+        split-BF16 plans."""
+        out = []
+        for g in range(3):
+            for mu in range(len(self.dims)):
+                k = ctypes.c_int()
+                t = ctypes.c_int64()
+                ms = (ctypes.c_float * 8)()
+                check(lib().ds_plan_tuning(self._h, g, mu, ctypes.byref(k), ctypes.byref(t), ms))
+                out.append((g, mu + 1, k.value, t.value,
+                            {i + 1: round(ms[i], 4) for i in range(8) if ms[i] > 0}))
+        return out
 
     def profile(self, enable: bool = True):
         check(lib().ds_plan_profile(self._h, int(enable)))
 
-    def profile_read(self):
-        """{kind: (ms, launches, useful_flops)} for kinds 'tc', 'f64', 'pointwise'."""
+    def profile_read(self, with_bytes: bool = False):
+        """{kind: (ms, launches, useful_flops[, algorithmic_bytes])} for kinds
+        'tc', 'f64', 'pointwise'."""
         ms = (ctypes.c_double * 3)()
         n = (ctypes.c_int64 * 3)()
         fl = (ctypes.c_double * 3)()
-        check(lib().ds_plan_profile_read(self._h, ms, n, fl))
+        by = (ctypes.c_double * 3)()
+        check(lib().ds_plan_profile_read_ex(self._h, ms, n, fl, by))
+        if with_bytes:
+            return {k: (ms[i], n[i], fl[i], by[i]) for i, k in enumerate(("tc", "f64", "pointwise"))}
         return {k: (ms[i], n[i], fl[i]) for i, k in enumerate(("tc", "f64", "pointwise"))}
 
     @property

@@ -77,3 +77,23 @@ def exprk3_dense(U0, Ks, model, p, tau, m):
         u = np.stack([u[c] + tau * ph[c]["p1_1"] @ F[c]
                       + 1.5 * tau * ph[c]["p2_1"] @ D3[c] for c in range(2)])
     return u.reshape(shape)
+
+
+def etd2rk_dense(U0, Ks, model, p, tau, m):
+    """m steps of unsplit ETD2RK (Section 1, eq. ETD2RK) with dense phi(tau K)."""
+    shape = U0.shape
+    N = U0[0].size
+    u = U0.reshape(2, N).copy()
+    p1 = [dense_phi(tau * K, 1) for K in Ks]
+    p2 = [dense_phi(tau * K, 2) for K in Ks]
+
+    def g(w):
+        return np.stack(g_model(model, p, w[0], w[1]))
+
+    for _ in range(m):
+        G = g(u)
+        F = np.stack([Ks[c] @ u[c] for c in range(2)]) + G
+        u2 = np.stack([u[c] + tau * p1[c] @ F[c] for c in range(2)])
+        D = g(u2) - G
+        u = np.stack([u2[c] + tau * p2[c] @ D[c] for c in range(2)])
+    return u.reshape(shape)

@@ -141,3 +141,24 @@ def test_differentiation_workload_fhn96(ds):
         fd = (L_at(U0 + h * v, w.params) - L_at(U0 - h * v, w.params)) / (2 * h)
         an = float((gU * v).sum())
         assert abs(fd - an) <= 1e-6 * abs(fd) + 1e-14, (fd, an)
+
+
+def test_integrate_ckpt_matches_integrate(ds):
+    dims = (24, 20, 18)
+    Ds = [inputs.fd_neumann(n, -1.0, 1.0) for n in dims]
+    ps = ds.PhiSet(dims, [[D for D in Ds], [42.1887 * D for D in Ds]], 1e-3)
+    plan = ds.Plan(ps, "fhn", FHN, "f64")
+    U0 = torch.from_numpy(inputs.initial_state("fhn", dims, seed=3)).cuda()
+    U = U0.clone()
+    ck = plan.integrate_ckpt(U, 11, 4)            # checkpoints after 4 and 8 steps
+    assert ck.shape == (2,) + tuple(U0.shape)
+    R = U0.clone()
+    for j in range(2):
+        plan.integrate(R, 4)
+        plan.sync()
+        assert torch.equal(ck[j], R)
+    plan.integrate(R, 3)
+    plan.sync()
+    assert torch.equal(U, R)
+    with pytest.raises(ds.DsError):
+        plan.integrate_ckpt(U, 5, 0)

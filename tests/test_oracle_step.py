@@ -30,7 +30,8 @@ def relerr(a, b):
     return max(np.abs(a[c] - b[c]).max() / np.abs(b[c]).max() for c in range(2))
 
 
-@pytest.mark.parametrize("dims,ms", [((6, 6, 6), (64, 128, 256)), ((8, 7), (256, 512, 1024))])
+@pytest.mark.parametrize("dims,ms", [((6, 6, 6), (64, 128, 256)), ((8, 7), (256, 512, 1024)),
+                                     ((4, 4, 4, 4), (32, 64, 128))])
 def test_observed_order_three(dims, ms):
     """FHN on [-1,1]^d, T = 0.2, U[-1,1) data.  Reference: unsplit EXPRK3 with
     dense phi(tau K) at 8192 steps.  The step counts keep tau * rho(A_v)
@@ -46,7 +47,7 @@ def test_observed_order_three(dims, ms):
     assert all(2.8 <= s <= 3.4 for s in slopes), (errs, slopes)
 
 
-@pytest.mark.parametrize("dims", [(5, 6), (4, 5, 3)])
+@pytest.mark.parametrize("dims", [(5, 6), (4, 5, 3), (3, 4, 3, 3)])
 def test_linear_step_local_error_fourth_order(dims):
     """g = 0: one step is U + tau S_f^{(1)}(K U), a third-order split of
     tau phi_1(tau K) K U = (exp(tau K) - I) U, so the local error is O(tau^4)."""
