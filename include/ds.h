@@ -94,8 +94,15 @@ typedef struct {
  *   DS_EXPRK3DS_CPLX: EXPRK3 with the complex two-term split of Table 2
  *     (Section 2.2, Algorithm 1); each split action is complex and its real
  *     part is the increment; phi of complex multiples of A via the real
- *     2n x 2n embedding [[Re, -Im], [Im, Re]]; FP64 plans only. */
-typedef enum { DS_EXPRK3DS_REAL = 0, DS_ETD2RKDS = 1, DS_EXPRK3DS_CPLX = 2 } ds_scheme;
+ *     2n x 2n embedding [[Re, -Im], [Im, Re]]; FP64 plans only.
+ *   DS_EXPRK3_DENSE: the unsplit EXPRK3 (Section 2.4, eq. exprk3) that the
+ *     splits approximate: K_c = A_{c,d} (+) ... (+) A_{c,1} is assembled as a
+ *     dense N x N matrix (N = prod n_mu <= 4096) and phi_l(c tau K_c) is
+ *     formed densely (same Taylor + modified squaring), so a run of it next
+ *     to an EXPRK3DS_REAL run measures the splitting error; FP64 plans only,
+ *     no adjoint.  ds_phi_get/_ex return the N x N matrix of (c, slot) with
+ *     term = mu = 0. */
+typedef enum { DS_EXPRK3DS_REAL = 0, DS_ETD2RKDS = 1, DS_EXPRK3DS_CPLX = 2, DS_EXPRK3_DENSE = 3 } ds_scheme;
 
 typedef struct ds_phi_set ds_phi_set;
 typedef struct ds_plan ds_plan;
@@ -294,6 +301,21 @@ ds_status ds_plan_profile_read_ex(ds_plan *plan, double *ms, int64_t *launches, 
  * Synchronous; DS_ERR_UNSUPPORTED for other precisions. */
 ds_status ds_plan_tuning(const ds_plan *plan, int group, int mu, int *ksplit, int64_t *tiles,
                          float *times_ms);
+
+/* ds_plan_fusion -- for the split-BF16 plan's group (0 = F, 1 = D2, 2 = D3):
+ * whether its last mode product runs with the fused epilogue (the stage
+ * difference g(U_s) - G, or the final update of U, computed as the
+ * contraction's output is drained) or as a plain product followed by a
+ * separate stage kernel; the plan creation times both (fastest of five
+ * launches, milliseconds; 0 when the choice came from DS_TUNE_CACHE) and
+ * keeps the faster.  Both give the same values.  DS_ERR_UNSUPPORTED for other
+ * precisions. */
+ds_status ds_plan_fusion(const ds_plan *plan, int group, int *fused, float *ms_fused, float *ms_separate);
+
+/* ds_plan_set_fusion -- override that choice for group (fused != 0: fused
+ * epilogue).  Waits for the plan's stream and drops its captured graphs.
+ * DS_ERR_UNSUPPORTED for precisions other than split-BF16. */
+ds_status ds_plan_set_fusion(ds_plan *plan, int group, int fused);
 
 ds_status ds_plan_destroy(ds_plan *plan);
 

@@ -22,6 +22,9 @@
  * observed order 3, steady-state invariance); none is "parity unpinned".
  */
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -189,19 +192,40 @@ int orc_phi(int n, const double *X, int lmax, double *out)
 /* mu is 0-based here (mode mu + 1 in the paper).  Plain loops, FP64         */
 /* accumulator, natural j order.                                             */
 /* ------------------------------------------------------------------------ */
+/* Summation order of the mode products: 0 = j ascending (the default), */
+/* 1 = j descending.  Running a computation both ways measures its FP64     */
+/* rounding floor.                                                           */
+static int g_reverse_sum = 0;
+void orc_set_sum_order(int reverse) { g_reverse_sum = reverse != 0; }
+
+/* Number of OpenMP threads of later calls (no effect without OpenMP).      */
+int orc_set_threads(int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+    return omp_get_max_threads();
+#else
+    (void)nthreads;
+    return 1;
+#endif
+}
+
 void orc_mode_product(int d, const int64_t *n, const double *X, int mu,
                       const double *L, double *Y)
 {
     int64_t I = 1, O = 1, m = n[mu];
     for (int q = 0; q < mu; ++q) I *= n[q];
     for (int q = mu + 1; q < d; ++q) O *= n[q];
+    const int rev = g_reverse_sum;
     #pragma omp parallel for collapse(2) schedule(static)
     for (int64_t o = 0; o < O; ++o) {
         for (int64_t i = 0; i < m; ++i) {
             for (int64_t x = 0; x < I; ++x) {
                 double s = 0.0;
-                for (int64_t j = 0; j < m; ++j)
+                for (int64_t jj = 0; jj < m; ++jj) {
+                    const int64_t j = rev ? m - 1 - jj : jj;
                     s += L[i + m * j] * X[x + I * (j + m * o)];
+                }
                 Y[x + I * (i + m * o)] = s;
             }
         }
@@ -428,6 +452,105 @@ int orc_step(int d, const int64_t *n, const double *A, const double *P,
     rc = 0;
 done:
     free(G); free(F); free(U2); free(U3); free(Dt); free(Un); free(tmp);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Unsplit EXPRK3 (Section 2.4, eq. exprk3): the tableau of orc_step with    */
+/* every split action replaced by the dense phi_l(c tau K_c) applied to the  */
+/* vector, K_c = A_{c,d} (+) ... (+) A_{c,1} assembled as an N x N matrix    */
+/* (Section 1, eq. kronsum) and phi by orc_phi.  This is what the splits     */
+/* approximate; dense N x N matrices, so small grids only.                   */
+/* ------------------------------------------------------------------------ */
+static void kron_sum_dense(int d, const int64_t *n, const double *const *Ac, double *K)
+{
+    int64_t N = numel(d, n);
+    memset(K, 0, sizeof(double) * N * N);
+    for (int64_t j = 0; j < N; ++j) {
+        int64_t rest = j, stride = 1;
+        for (int mu = 0; mu < d; ++mu) {
+            const int64_t jm = rest % n[mu];
+            rest /= n[mu];
+            for (int64_t im = 0; im < n[mu]; ++im) {
+                const int64_t i = j + (im - jm) * stride;
+                K[i + N * j] += Ac[mu][im + n[mu] * jm];
+            }
+            stride *= n[mu];
+        }
+    }
+}
+
+/* out += w * (P x), P column-major N x N */
+static void dense_apply(int64_t N, const double *P, double w, const double *x, double *out)
+{
+    #pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < N; ++i) {
+        double s = 0.0;
+        for (int64_t j = 0; j < N; ++j) s += P[i + N * j] * x[j];
+        out[i] += w * s;
+    }
+}
+
+int orc_step_dense(int d, const int64_t *n, const double *A, int model, const double *p, double tau,
+                   double *U, int nsteps)
+{
+    if (d < 2 || d > ORC_MAXD || nsteps < 0 || !(tau > 0.0)) return -1;
+    const int64_t N = numel(d, n), NN = N * N;
+    const double *Ac[2][ORC_MAXD];
+    const double *Acur = A;
+    for (int c = 0; c < 2; ++c)
+        for (int mu = 0; mu < d; ++mu) { Ac[c][mu] = Acur; Acur += n[mu] * n[mu]; }
+    /* per component: phi_1(tau/3 K), phi_1(2tau/3 K), phi_2(2tau/3 K), phi_1(tau K), phi_2(tau K) */
+    double *Pm = malloc(sizeof(double) * NN * 10), *K = malloc(sizeof(double) * NN);
+    double *X = malloc(sizeof(double) * NN), *ph = malloc(sizeof(double) * NN * 3);
+    double *G = malloc(sizeof(double) * 2 * N), *F = malloc(sizeof(double) * 2 * N);
+    double *U2 = malloc(sizeof(double) * 2 * N), *U3 = malloc(sizeof(double) * 2 * N);
+    double *Dt = malloc(sizeof(double) * 2 * N), *Un = malloc(sizeof(double) * 2 * N);
+    int rc = -1;
+    if (!Pm || !K || !X || !ph || !G || !F || !U2 || !U3 || !Dt || !Un) goto done;
+    const double cq[3] = {1.0 / 3.0, 2.0 / 3.0, 1.0};
+    for (int c = 0; c < 2; ++c) {
+        kron_sum_dense(d, n, Ac[c], K);
+        for (int q = 0; q < 3; ++q) {
+            for (int64_t e = 0; e < NN; ++e) X[e] = cq[q] * tau * K[e];
+            if (orc_phi((int)N, X, 2, ph) < 0) goto done;
+            double *base = Pm + NN * 5 * c;
+            if (q == 0) memcpy(base, ph + NN, sizeof(double) * NN);
+            if (q == 1) { memcpy(base + NN, ph + NN, sizeof(double) * NN); memcpy(base + 2 * NN, ph + 2 * NN, sizeof(double) * NN); }
+            if (q == 2) { memcpy(base + 3 * NN, ph + NN, sizeof(double) * NN); memcpy(base + 4 * NN, ph + 2 * NN, sizeof(double) * NN); }
+        }
+    }
+    for (int step = 0; step < nsteps; ++step) {
+        orc_g(model, p, N, U, G);
+        for (int c = 0; c < 2; ++c) {
+            kron_sum_dense(d, n, Ac[c], K);
+            for (int64_t i = 0; i < N; ++i) {
+                double s = 0.0;
+                for (int64_t j = 0; j < N; ++j) s += K[i + N * j] * U[c * N + j];
+                F[c * N + i] = s + G[c * N + i];
+            }
+        }
+        memcpy(U2, U, sizeof(double) * 2 * N);
+        for (int c = 0; c < 2; ++c) dense_apply(N, Pm + NN * (5 * c + 0), tau / 3.0, F + c * N, U2 + c * N);
+        orc_g(model, p, N, U2, Dt);
+        for (int64_t e = 0; e < 2 * N; ++e) Dt[e] -= G[e];
+        memcpy(U3, U, sizeof(double) * 2 * N);
+        for (int c = 0; c < 2; ++c) {
+            dense_apply(N, Pm + NN * (5 * c + 1), 2.0 * tau / 3.0, F + c * N, U3 + c * N);
+            dense_apply(N, Pm + NN * (5 * c + 2), 4.0 * tau / 3.0, Dt + c * N, U3 + c * N);
+        }
+        orc_g(model, p, N, U3, Dt);
+        for (int64_t e = 0; e < 2 * N; ++e) Dt[e] -= G[e];
+        memcpy(Un, U, sizeof(double) * 2 * N);
+        for (int c = 0; c < 2; ++c) {
+            dense_apply(N, Pm + NN * (5 * c + 3), tau, F + c * N, Un + c * N);
+            dense_apply(N, Pm + NN * (5 * c + 4), 1.5 * tau, Dt + c * N, Un + c * N);
+        }
+        memcpy(U, Un, sizeof(double) * 2 * N);
+    }
+    rc = 0;
+done:
+    free(Pm); free(K); free(X); free(ph); free(G); free(F); free(U2); free(U3); free(Dt); free(Un);
     return rc;
 }
 

@@ -49,6 +49,13 @@ def lib():
             L.orc_phi.restype = ctypes.c_int
             L.orc_mode_product.argtypes = [ctypes.c_int, _i64p, _dp, ctypes.c_int, _dp, _dp]
             L.orc_mode_product.restype = None
+            L.orc_step_dense.argtypes = [ctypes.c_int, _i64p, _dp, ctypes.c_int, _dp, ctypes.c_double,
+                                         _dp, ctypes.c_int]
+            L.orc_step_dense.restype = ctypes.c_int
+            L.orc_set_sum_order.argtypes = [ctypes.c_int]
+            L.orc_set_sum_order.restype = None
+            L.orc_set_threads.argtypes = [ctypes.c_int]
+            L.orc_set_threads.restype = ctypes.c_int
             L.orc_tucker.argtypes = [ctypes.c_int, _i64p, _dp, ctypes.POINTER(_dp), _dp]
             L.orc_tucker.restype = ctypes.c_int
             L.orc_kronsum.argtypes = [ctypes.c_int, _i64p, _dp, ctypes.POINTER(_dp), _dp]
@@ -300,3 +307,41 @@ def step_cplx(dims, As, P, model: str, p, tau: float, U: np.ndarray, nsteps: int
     if rc != 0:
         raise RuntimeError("orc_step_cplx failed")
     return Uo
+
+
+def set_sum_order(reverse: bool) -> None:
+    """Mode-product summation order of later calls: j ascending (default) or
+    descending.  The difference of the two runs is the FP64 rounding floor."""
+    lib().orc_set_sum_order(1 if reverse else 0)
+
+
+def set_threads(n: int = 0) -> int:
+    """OpenMP threads of later calls (n <= 0 leaves it); returns the count in use."""
+    return int(lib().orc_set_threads(int(n)))
+
+
+def noise_floor(dims, As, model, p, tau, U0, m):
+    """max over components of the relative max-norm difference between m steps
+    with ascending and with descending summation in every mode product."""
+    P = phi_set(dims, As, tau)
+    a = step(dims, As, P, model, p, tau, U0, m)
+    set_sum_order(True)
+    try:
+        P2 = phi_set(dims, As, tau)
+        b = step(dims, As, P2, model, p, tau, U0, m)
+    finally:
+        set_sum_order(False)
+    return max(float(np.abs(a[c] - b[c]).max() / np.abs(a[c]).max()) for c in range(2)), a
+
+
+def step_dense(dims, As, model, p, tau, U0, nsteps):
+    """nsteps of the unsplit EXPRK3 with dense phi(c tau K) (orc_step_dense);
+    small grids only."""
+    d = len(dims)
+    A = _pack_A(As)
+    U = np.array(U0, dtype=np.float64, order="C", copy=True)
+    pp = np.asarray(list(p) + [0.0] * (8 - len(p)), dtype=np.float64)
+    rc = lib().orc_step_dense(d, _dims(dims), _ptr(A), MODELS[model], _ptr(pp), float(tau), _ptr(U), int(nsteps))
+    if rc != 0:
+        raise RuntimeError("orc_step_dense failed")
+    return U

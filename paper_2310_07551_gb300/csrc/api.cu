@@ -461,15 +461,19 @@ ds_status ds_phi_setup_ex(const ds_grid *grid, const double *A, int a_on_device,
                           ds_phi_set **out, void *stream)
 {
     try {
-        if (scheme != DS_EXPRK3DS_REAL && scheme != DS_ETD2RKDS && scheme != DS_EXPRK3DS_CPLX)
+        if (scheme != DS_EXPRK3DS_REAL && scheme != DS_ETD2RKDS && scheme != DS_EXPRK3DS_CPLX &&
+            scheme != DS_EXPRK3_DENSE)
             return fail(DS_ERR_INVALID_ARG, "unknown scheme");
         ds_status r = check_grid(grid);
         if (r != DS_OK) return r;
+        if (scheme == DS_EXPRK3_DENSE && numel(grid) > kDenseMaxPoints)
+            return fail(DS_ERR_UNSUPPORTED, "the dense scheme is limited to 4096 grid points");
         if (!A || !out) return fail(DS_ERR_INVALID_ARG, "A or out is NULL");
         if (!(tau > 0.0) || !isfinite(tau)) return fail(DS_ERR_INVALID_ARG, "tau must be finite and > 0");
         if ((r = check_device()) != DS_OK) return r;
         cudaStream_t st = (cudaStream_t)stream;
-        const int d = grid->d;
+        const ds_grid user = *grid;
+        int d = grid->d;
         int64_t Acount = 0;
         for (int c = 0; c < 2; ++c)
             for (int mu = 0; mu < d; ++mu) Acount += grid->n[mu] * grid->n[mu];
@@ -482,9 +486,41 @@ ds_status ds_phi_setup_ex(const ds_grid *grid, const double *A, int a_on_device,
         }
         for (int64_t e = 0; e < Acount; ++e)
             if (!isfinite(hA[e])) return fail(DS_ERR_NONFINITE, "A has a non-finite entry");
+        // The unsplit scheme is the split machinery on a one-direction problem:
+        // A = K_c, the assembled Kronecker sum, one term with eta = alpha = 1.
+        ds_grid gin = *grid;
+        if (scheme == DS_EXPRK3_DENSE) {
+            const int64_t N = numel(grid);
+            std::vector<double> hK((size_t)(2 * N * N), 0.0);
+            int64_t aoff = 0;
+            for (int c = 0; c < 2; ++c) {
+                double *K = hK.data() + c * N * N;
+                int64_t stride = 1;
+                for (int mu = 0; mu < d; ++mu) {
+                    const int64_t nm = grid->n[mu];
+                    const double *Am = hA.data() + aoff;
+                    for (int64_t j = 0; j < N; ++j) {
+                        const int64_t jm = (j / stride) % nm;
+                        for (int64_t im = 0; im < nm; ++im)
+                            K[(j + (im - jm) * stride) + N * j] += Am[im + nm * jm];
+                    }
+                    stride *= nm;
+                    aoff += nm * nm;
+                }
+            }
+            hA.swap(hK);
+            Acount = 2 * N * N;
+            gin.d = 1;
+            gin.n[0] = N;
+            for (int q = 1; q < 4; ++q) gin.n[q] = 1;
+        }
+        grid = &gin;
 
         ds_phi_set *s = new (std::nothrow) ds_phi_set();
         if (!s) return fail(DS_ERR_OOM, "host allocation");
+        s->user_d = d;
+        for (int q = 0; q < kMaxD; ++q) s->user_n[q] = q < user.d ? user.n[q] : 1;
+        d = grid->d;
         s->d = d;
         for (int q = 0; q < kMaxD; ++q) s->n[q] = q < d ? grid->n[q] : 1;
         s->tau = tau;
@@ -496,6 +532,16 @@ ds_status ds_phi_setup_ex(const ds_grid *grid, const double *A, int a_on_device,
         } else if (scheme == DS_EXPRK3DS_CPLX) {
             s->co[0] = split_coeffs_cplx(d, 1);
             s->co[1] = split_coeffs_cplx(d, 2);
+            s->nslots = kSlots;
+        } else if (scheme == DS_EXPRK3_DENSE) {
+            for (int l = 1; l <= 2; ++l) {
+                SplitCoeffs &c = s->co[l - 1];
+                c = SplitCoeffs{};
+                c.k = 1;
+                c.ell_i[0] = l;
+                c.eta[0] = 1.0;
+                c.alpha[0][0] = 1.0;
+            }
             s->nslots = kSlots;
         } else {
             // second-order split: phi_l(tau K) ~ l!^(d-1) (x)_mu phi_l(tau A_mu)
@@ -547,7 +593,8 @@ ds_status ds_phi_setup_ex(const ds_grid *grid, const double *A, int a_on_device,
         cudaError_t e1 = cudaMalloc(&s->A_dev, sizeof(double) * Acount);
         cudaError_t e2 = cudaMalloc(&s->tri_dev, sizeof(double) * toff);
         cudaError_t e3 = cudaMalloc(&s->P_dev, sizeof(double) * poff);
-        cudaError_t e4 = cudaMalloc(&s->dP_dev, sizeof(double) * poff);
+        // derivatives feed the adjoint's diffusion-scaling gradient (EXPRK3DS_REAL only)
+        cudaError_t e4 = scheme == DS_EXPRK3DS_REAL ? cudaMalloc(&s->dP_dev, sizeof(double) * poff) : cudaSuccess;
         cudaError_t e5 = cudaSuccess, e6 = cudaSuccess;
         if (scheme == DS_EXPRK3DS_CPLX) {
             e5 = cudaMalloc(&s->Pim_dev, sizeof(double) * poff);
@@ -582,7 +629,7 @@ ds_status ds_phi_setup_ex(const ds_grid *grid, const double *A, int a_on_device,
                         j.z = cq * tau * co.alpha[i][mu];
                         j.ell = co.ell_i[i];
                         j.out = s->P_dev + s->P_off[c][q][i][mu];
-                        j.dout = s->dP_dev + s->P_off[c][q][i][mu];
+                        j.dout = s->dP_dev ? s->dP_dev + s->P_off[c][q][i][mu] : nullptr;
                         groups[grid->n[mu]].push_back(j);
                     }
             }
@@ -735,16 +782,16 @@ ds_status ds_plan_create(const ds_grid *grid, const ds_params *params, const ds_
         ds_status r = check_grid(grid);
         if (r != DS_OK) return r;
         if (!params || !set || !out) return fail(DS_ERR_INVALID_ARG, "NULL argument");
-        if (grid->d != set->d) return fail(DS_ERR_INVALID_ARG, "grid does not match the phi-set");
+        if (grid->d != set->user_d) return fail(DS_ERR_INVALID_ARG, "grid does not match the phi-set");
         for (int q = 0; q < grid->d; ++q)
-            if (grid->n[q] != set->n[q]) return fail(DS_ERR_INVALID_ARG, "grid does not match the phi-set");
+            if (grid->n[q] != set->user_n[q]) return fail(DS_ERR_INVALID_ARG, "grid does not match the phi-set");
         if (params->model < 0 || params->model > 2) return fail(DS_ERR_INVALID_ARG, "unknown model");
         for (int q = 0; q < 8; ++q)
             if (!isfinite(params->p[q])) return fail(DS_ERR_INVALID_ARG, "non-finite model parameter");
         if (precision != DS_PREC_F64 && precision != DS_PREC_BF16X6 && precision != DS_PREC_F32)
             return fail(DS_ERR_UNSUPPORTED, "unknown precision");
         if (set->scheme != DS_EXPRK3DS_REAL && precision != DS_PREC_F64)
-            return fail(DS_ERR_UNSUPPORTED, "ETD2RKDS and EXPRK3DS_CPLX plans are FP64 only");
+            return fail(DS_ERR_UNSUPPORTED, "ETD2RKDS, EXPRK3DS_CPLX and dense EXPRK3 plans are FP64 only");
         if ((r = check_device()) != DS_OK) return r;
         ds_plan *p = new (std::nothrow) ds_plan();
         if (!p) return fail(DS_ERR_OOM, "host allocation");
@@ -1150,6 +1197,28 @@ ds_status ds_plan_tuning(const ds_plan *p, int group, int mu, int *ksplit, int64
     if (!p->mixed) return fail(DS_ERR_UNSUPPORTED, "only split-BF16 plans are tuned");
     if (tc::mixed_plan_tuning(p->mixed, group, mu, ksplit, tiles, times_ms) != 0)
         return fail(DS_ERR_INVALID_ARG, "group or mode out of range");
+    return DS_OK;
+}
+
+ds_status ds_plan_fusion(const ds_plan *p, int group, int *fused, float *ms_fused, float *ms_separate)
+{
+    if (!p || !fused || !ms_fused || !ms_separate) return fail(DS_ERR_INVALID_ARG, "NULL argument");
+    if (!p->mixed) return fail(DS_ERR_UNSUPPORTED, "only split-BF16 plans fuse epilogues");
+    if (tc::mixed_plan_fusion(p->mixed, group, fused, ms_fused, ms_separate) != 0)
+        return fail(DS_ERR_INVALID_ARG, "group out of range");
+    return DS_OK;
+}
+
+ds_status ds_plan_set_fusion(ds_plan *p, int group, int fused)
+{
+    if (!p) return fail(DS_ERR_INVALID_ARG, "NULL plan");
+    if (!p->mixed) return fail(DS_ERR_UNSUPPORTED, "only split-BF16 plans fuse epilogues");
+    if (p->st) cudaStreamSynchronize(p->st);
+    if (tc::mixed_plan_set_fusion(p->mixed, group, fused) != 0)
+        return fail(DS_ERR_INVALID_ARG, "group out of range");
+    // captured steps hold the previous launch sequence
+    for (auto &kv : p->graphs) cudaGraphExecDestroy(kv.second);
+    p->graphs.clear();
     return DS_OK;
 }
 

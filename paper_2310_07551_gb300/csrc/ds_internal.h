@@ -12,6 +12,7 @@
 namespace ds {
 
 constexpr int kMaxD = 4;      // d in {2, 3, 4}
+constexpr int64_t kDenseMaxPoints = 4096;   // DS_EXPRK3_DENSE: N x N phi-matrices
 constexpr int kSlots = 5;     // (s2,l1) (s3,l1) (s3,l2) (sf,l1) (sf,l2)
 constexpr int kMaxTerms = 3;
 
@@ -192,8 +193,10 @@ struct DevStatus {
 struct ds_phi_set {
     int scheme = 0;                         // ds_scheme
     int nslots = 5;                         // 5 (EXPRK3DS_REAL) or 2 (ETD2RKDS)
-    int d;
-    int64_t n[ds::kMaxD];
+    int user_d;                             // the caller's grid
+    int64_t user_n[ds::kMaxD];
+    int d;                                  // the grid of the phi-matrices: the caller's, or for the
+    int64_t n[ds::kMaxD];                   // dense scheme one direction of N points (A = K)
     int k;
     double tau;
     ds::SplitCoeffs co[2];                  // [l-1]

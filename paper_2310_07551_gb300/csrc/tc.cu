@@ -27,6 +27,8 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+#include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -58,6 +60,12 @@ constexpr long long kTimeoutCycles = 4000000000LL;   // ~2 s at 2 GHz
 // UMMA shared-memory descriptor layout types
 constexpr uint32_t kSw128 = 2, kSw64 = 4;
 
+// model parameters rounded to FP32 on the host
+struct ModelF {
+    int model;
+    float p[3];
+};
+
 struct alignas(128) TcArgs {
     CUtensorMap tmA;
     CUtensorMap tmB;
@@ -73,6 +81,22 @@ struct alignas(128) TcArgs {
     int ksplit, kpi;
     int64_t part_stride;
     float *part_ws;
+    // Work units: npair = 2 pairs tile s_pair (component 0) with tile
+    // s_pair + S/2 (component 1) of the same spatial tile, processed one after
+    // the other by one CTA; num_units = num_tiles / npair.
+    int npair;
+    int64_t num_units;
+    // Fused epilogue of a group's last mode (non-mode-1 launches, ksplit == 1;
+    // with split-K the reduction does it): 0 none; 1 stage difference on the
+    // pairs with s_pair == fuse_spair: D = g(U + extra + inc) - g(U) as BF16
+    // planes Dp[c][3][N], the component-0 increment travelling through out;
+    // 2 final update U_c += widen(extra_c + inc_c).
+    int epi, fuse_spair;
+    double *U;                 // FP64 state [2][N], set per launch
+    const float *extra;        // increments added first (stride extra_cs per component), or null
+    int64_t extra_cs;
+    bf16 *Dp;
+    ModelF model;
 };
 
 // ---------------------------------------------------------------------------
@@ -216,6 +240,96 @@ __device__ __forceinline__ void split3f(float x, bf16 &p0, bf16 &p1, bf16 &p2)
 }
 
 // ---------------------------------------------------------------------------
+// Pointwise helpers shared by the fused epilogues and the pointwise kernels.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void store_planes(bf16 *dst, int64_t plane, int64_t i, double x)
+{
+    bf16 p0, p1, p2;
+    split3(x, p0, p1, p2);
+    dst[i] = p0;
+    dst[i + plane] = p1;
+    dst[i + 2 * plane] = p2;
+}
+__device__ __forceinline__ void store_planes_f(bf16 *dst, int64_t plane, int64_t i, float x)
+{
+    bf16 p0, p1, p2;
+    split3f(x, p0, p1, p2);
+    dst[i] = p0;
+    dst[i + plane] = p1;
+    dst[i + 2 * plane] = p2;
+}
+
+// g(u + du, v + dv) - g(u, v) written as a polynomial in the increments, so
+// the difference carries no cancellation and can be evaluated in FP32.
+static ModelF model_f(const Model &m)
+{
+    ModelF r;
+    r.model = m.model;
+    for (int k = 0; k < 3; ++k) r.p[k] = (float)m.p[k];
+    return r;
+}
+__device__ __forceinline__ void react_diff(const ModelF &m, float u, float v, float du, float dv,
+                                           float &Du, float &Dv)
+{
+    if (m.model == DS_SCHNAKENBERG) {
+        const float gam = m.p[0];
+        const float q = fmaf(2.0f * u, du, du * du);          // (u+du)^2 - u^2
+        const float w = fmaf(q, v + dv, u * u * dv);            // (u+du)^2 (v+dv) - u^2 v
+        Du = gam * (w - du);
+        Dv = -gam * w;
+    } else if (m.model == DS_FHN) {
+        const float cub = du * fmaf(3.0f * u, u + du, du * du); // (u+du)^3 - u^3
+        Du = (du - dv) - cub;
+        Dv = m.p[0] * fmaf(-m.p[1], dv, du);
+    } else {
+        Du = 0.0f;
+        Dv = 0.0f;
+    }
+}
+
+// Exact split of an FP64 value into FP32 hi + lo with integer and FP32
+// operations only (GB300's FP64 pipe, conversions included, runs at ~1/64 of
+// its FP32 rate, so the reduced-precision step keeps FP64 instructions out of
+// its pointwise kernels).  hi takes the leading 24 significant bits; lo the
+// next 29 rounded to 23, built as (1.m x 2^k) - 2^k (exact: Sterbenz), so
+// u = hi + lo to 2^-47 relative.  |u| < 2^-74 gives hi = lo = +-0;
+// |u| > 2^127 gives hi = +-inf (NaN stays NaN), lo = 0.
+__device__ __forceinline__ void split_hilo(double u, float &hi, float &lo)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(u);
+    const unsigned h32 = (unsigned)(b >> 32), l32 = (unsigned)b;
+    const int e = (int)((h32 >> 20) & 0x7FF);
+    const unsigned sign = h32 & 0x80000000u;
+    if (e >= 949 && e <= 1150) {
+        const unsigned top23 = ((h32 & 0xFFFFFu) << 3) | (l32 >> 29);
+        hi = __uint_as_float(sign | ((unsigned)(e - 1023 + 127) << 23) | top23);
+        const unsigned ebits = (unsigned)(e - 1046 + 127) << 23;                 // 2^(e-1046)
+        const unsigned m = ((l32 & 0x1FFFFFFFu) + 32u) >> 6;                    // <= 2^23
+        const float r = __fsub_rn(__uint_as_float(ebits + m), __uint_as_float(ebits));
+        lo = __uint_as_float(sign | __float_as_uint(r));
+    } else if (e < 949) {
+        hi = __uint_as_float(sign);
+        lo = 0.0f;
+    } else {
+        const bool nan = e == 0x7FF && ((h32 & 0xFFFFFu) | l32) != 0u;
+        hi = __uint_as_float(sign | 0x7F800000u | (nan ? 0x400000u : 0u));
+        lo = 0.0f;
+    }
+}
+
+// Exact FP32 -> FP64 widening with integer operations (subnormal floats, below
+// 2^-126, become +-0).
+__device__ __forceinline__ double widen_f(float x)
+{
+    const unsigned b = __float_as_uint(x);
+    const unsigned e = (b >> 23) & 0xFFu;
+    const unsigned sign = b & 0x80000000u, m = b & 0x7FFFFFu;
+    if (e == 0u) return __hiloint2double((int)sign, 0);
+    const unsigned ed = e == 0xFFu ? 0x7FFu : e + (1023u - 127u);
+    return __hiloint2double((int)(sign | (ed << 20) | (m >> 3)), (int)(m << 29));
+}
+
+// ---------------------------------------------------------------------------
 // The mode-product kernel.
 // ---------------------------------------------------------------------------
 struct TileCoord {
@@ -241,6 +355,36 @@ __device__ __forceinline__ TileCoord decode(const TcArgs &a, int64_t t)
         c.o = t % a.O;
         c.s = (int)(t / a.O);
     }
+    return c;
+}
+
+// Work items wi = unit * npair + h, h < npair.  A CTA takes units blockIdx.x,
+// blockIdx.x + gridDim.x, ..., and within a unit its items in order, so the
+// two tiles of a pair go through the same CTA (and the same epilogue threads)
+// back to back.  All three roles walk the same sequence.
+__device__ __forceinline__ int64_t first_item(const TcArgs &a) { return (int64_t)blockIdx.x * a.npair; }
+__device__ __forceinline__ int64_t next_item(const TcArgs &a, int64_t wi)
+{
+    ++wi;
+    if (wi % a.npair == 0) wi += (int64_t)(gridDim.x - 1) * a.npair;
+    return wi;
+}
+
+// work unit -> (split-K part, tile); paired units hold the two components'
+// tiles of one spatial tile (h = component), in that order
+template <bool MODE1>
+__device__ __forceinline__ TileCoord work_item(const TcArgs &a, int64_t unit, int h, int &part)
+{
+    part = (int)(unit % a.ksplit);
+    int64_t t = unit / a.ksplit;
+    if (a.npair == 1) return decode<MODE1>(a, t);
+    TileCoord c;
+    c.nt = (int)(t % a.ntiles);
+    t /= a.ntiles;
+    c.mt = (int)(t % a.mtiles);
+    t /= a.mtiles;
+    c.o = t % a.O;
+    c.s = (int)(t / a.O) + h * (a.S / 2);
     return c;
 }
 
@@ -296,9 +440,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_mode_tc(const __grid_constant__
             int issued_phase[STAGES];
             for (int s = 0; s < STAGES; ++s) issued_phase[s] = -1;
             bool ok = true;
-            for (int64_t tile = blockIdx.x; ok && tile < a.num_tiles; tile += gridDim.x) {
-                const int part = (int)(tile % a.ksplit);
-                const TileCoord tc = decode<MODE1>(a, tile / a.ksplit);
+            for (int64_t wi = first_item(a); ok && wi < a.num_tiles; wi = next_item(a, wi)) {
+                int part;
+                const TileCoord tc = work_item<MODE1>(a, wi / a.npair, (int)(wi % a.npair), part);
                 const int it0 = part * a.kpi, it1 = min(it0 + a.kpi, kiters);
                 for (int it = it0; it < it1; ++it) {
                     const int tt = it / a.kchunks, kc = it % a.kchunks;
@@ -344,11 +488,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_mode_tc(const __grid_constant__
             int acc = 0;
             uint32_t acc_phase = 0;
             bool ok = true;
-            for (int64_t tile = blockIdx.x; ok && tile < a.num_tiles; tile += gridDim.x) {
+            for (int64_t wi = first_item(a); ok && wi < a.num_tiles; wi = next_item(a, wi)) {
                 if (!wait_bar(TEMPTY(acc), acc_phase ^ 1u, abort_flag, a.status, 2)) break;
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)acc * BN;
-                const int part = (int)(tile % a.ksplit);
+                const int part = (int)((wi / a.npair) % a.ksplit);
                 const int it0 = part * a.kpi, it1 = min(it0 + a.kpi, kiters);
                 for (int it = it0; it < it1; ++it) {
                     if (!wait_bar(FULL(stage), phase, abort_flag, a.status, 3)) { ok = false; break; }
@@ -391,9 +535,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_mode_tc(const __grid_constant__
         const int m = quarter * 32 + lane;
         int acc = 0;
         uint32_t acc_phase = 0;
-        for (int64_t tile = blockIdx.x; tile < a.num_tiles; tile += gridDim.x) {
-            const int part = (int)(tile % a.ksplit);
-            const TileCoord tc = decode<MODE1>(a, tile / a.ksplit);
+        for (int64_t wi = first_item(a); wi < a.num_tiles; wi = next_item(a, wi)) {
+            int part;
+            const TileCoord tc = work_item<MODE1>(a, wi / a.npair, (int)(wi % a.npair), part);
             // split-K parts write FP32 partials; the reduction writes the output
             const int out_kind = a.ksplit > 1 ? 1 : a.out_kind;
             void *const out_ptr = a.ksplit > 1 ? (void *)(a.part_ws + part * a.part_stride) : a.out;
@@ -452,11 +596,82 @@ __global__ void __launch_bounds__(kThreads, 1) k_mode_tc(const __grid_constant__
                             o2[off] = p2;
                         }
                     }
-                } else {
+                } else if (a.ksplit > 1 || a.epi == 0 ||
+                           (a.epi == 1 && (tc.s < a.S / 2 || tc.s - a.S / 2 != a.fuse_spair))) {
+                    // FP32 output (split-K partials; plain; the first tile of a
+                    // fused pair, whose values the second tile reads back)
                     float *o = (float *)out_ptr + e0;
 #pragma unroll
                     for (int j = 0; j < 32; ++j)
                         if (j < jmax) o[(uint32_t)j * col_stride] = __uint_as_float(v[j]) * a.alpha;
+                } else if (a.epi == 2) {
+                    // final update of component s: U_s += widen(extra_s + inc).
+                    // Loads of 8 columns are issued before their stores (the
+                    // compiler must assume U and extra may alias).
+                    const int64_t pb = e0 - (int64_t)tc.s * out_cs;
+                    double *Us = a.U + (int64_t)tc.s * a.out_ps + pb;
+                    const float *ex = a.extra + (int64_t)tc.s * a.extra_cs + pb;
+#pragma unroll
+                    for (int jb = 0; jb < 32; jb += 8) {
+                        double u[8];
+                        float e[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            if (jb + j < jmax) {
+                                const uint32_t off = (uint32_t)(jb + j) * col_stride;
+                                u[j] = Us[off];
+                                e[j] = ex[off];
+                            }
+                        }
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            if (jb + j < jmax)
+                                Us[(uint32_t)(jb + j) * col_stride] =
+                                    u[j] + widen_f(e[j] + __uint_as_float(v[jb + j]) * a.alpha);
+                    }
+                } else {
+                    // stage difference, second tile of the pair (component 1):
+                    // this thread stored the component-0 increment of the same
+                    // points for the first tile, so it reads its own writes back.
+                    // Loads of 4 columns are issued before their stores.
+                    const int64_t pb = e0 - (int64_t)tc.s * out_cs;
+                    const int64_t N = a.out_ps;
+                    const float *inc0 = (const float *)a.out + (int64_t)a.fuse_spair * out_cs + pb;
+                    const double *Uu = a.U + pb, *Uv = a.U + N + pb;
+                    const float *exu = a.extra ? a.extra + pb : nullptr;
+                    const float *exv = a.extra ? a.extra + a.extra_cs + pb : nullptr;
+#pragma unroll
+                    for (int jb = 0; jb < 32; jb += 4) {
+                        float du[4], dv[4];
+                        double uu[4], uv[4];
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            if (jb + j < jmax) {
+                                const uint32_t off = (uint32_t)(jb + j) * col_stride;
+                                du[j] = inc0[off];
+                                dv[j] = __uint_as_float(v[jb + j]) * a.alpha;
+                                uu[j] = Uu[off];
+                                uv[j] = Uv[off];
+                                if (exu) {
+                                    du[j] = exu[off] + du[j];
+                                    dv[j] = exv[off] + dv[j];
+                                }
+                            }
+                        }
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            if (jb + j < jmax) {
+                                const int64_t p = pb + (int64_t)(jb + j) * col_stride;
+                                float hu, lu, hv, lv;
+                                split_hilo(uu[j], hu, lu);
+                                split_hilo(uv[j], hv, lv);
+                                float Du, Dv;
+                                react_diff(a.model, hu + lu, hv + lv, du[j], dv[j], Du, Dv);
+                                store_planes_f(a.Dp, N, p, Du);
+                                store_planes_f(a.Dp + 3 * N, N, p, Dv);
+                            }
+                        }
+                    }
                 }
             }
             tc_fence_before();
@@ -498,56 +713,6 @@ __device__ void react_d(const Model &m, double u, double v, double &gu, double &
     }
 }
 
-__device__ __forceinline__ void store_planes(bf16 *dst, int64_t plane, int64_t i, double x)
-{
-    bf16 p0, p1, p2;
-    split3(x, p0, p1, p2);
-    dst[i] = p0;
-    dst[i + plane] = p1;
-    dst[i + 2 * plane] = p2;
-}
-__device__ __forceinline__ void store_planes_f(bf16 *dst, int64_t plane, int64_t i, float x)
-{
-    bf16 p0, p1, p2;
-    split3f(x, p0, p1, p2);
-    dst[i] = p0;
-    dst[i + plane] = p1;
-    dst[i + 2 * plane] = p2;
-}
-
-// g(u + du, v + dv) - g(u, v) written as a polynomial in the increments, so
-// the difference carries no cancellation and can be evaluated in FP32.
-// model parameters rounded to FP32 on the host
-struct ModelF {
-    int model;
-    float p[3];
-};
-static ModelF model_f(const Model &m)
-{
-    ModelF r;
-    r.model = m.model;
-    for (int k = 0; k < 3; ++k) r.p[k] = (float)m.p[k];
-    return r;
-}
-__device__ __forceinline__ void react_diff(const ModelF &m, float u, float v, float du, float dv,
-                                           float &Du, float &Dv)
-{
-    if (m.model == DS_SCHNAKENBERG) {
-        const float gam = m.p[0];
-        const float q = fmaf(2.0f * u, du, du * du);          // (u+du)^2 - u^2
-        const float w = fmaf(q, v + dv, u * u * dv);            // (u+du)^2 (v+dv) - u^2 v
-        Du = gam * (w - du);
-        Dv = -gam * w;
-    } else if (m.model == DS_FHN) {
-        const float cub = du * fmaf(3.0f * u, u + du, du * du); // (u+du)^3 - u^3
-        Du = (du - dv) - cub;
-        Dv = m.p[0] * fmaf(-m.p[1], dv, du);
-    } else {
-        Du = 0.0f;
-        Dv = 0.0f;
-    }
-}
-
 __device__ __forceinline__ double stencil_k(const Stencil &s, const double *U, int64_t p)
 {
     double acc = 0.0;
@@ -566,48 +731,6 @@ __device__ __forceinline__ double stencil_k(const Stencil &s, const double *U, i
         }
     }
     return acc;
-}
-
-// Exact split of an FP64 value into FP32 hi + lo with integer and FP32
-// operations only (GB300's FP64 pipe, conversions included, runs at ~1/64 of
-// its FP32 rate, so the reduced-precision step keeps FP64 instructions out of
-// its pointwise kernels).  hi takes the leading 24 significant bits; lo the
-// next 29 rounded to 23, built as (1.m x 2^k) - 2^k (exact: Sterbenz), so
-// u = hi + lo to 2^-47 relative.  |u| < 2^-74 gives hi = lo = +-0;
-// |u| > 2^127 gives hi = +-inf (NaN stays NaN), lo = 0.
-__device__ __forceinline__ void split_hilo(double u, float &hi, float &lo)
-{
-    const unsigned long long b = (unsigned long long)__double_as_longlong(u);
-    const unsigned h32 = (unsigned)(b >> 32), l32 = (unsigned)b;
-    const int e = (int)((h32 >> 20) & 0x7FF);
-    const unsigned sign = h32 & 0x80000000u;
-    if (e >= 949 && e <= 1150) {
-        const unsigned top23 = ((h32 & 0xFFFFFu) << 3) | (l32 >> 29);
-        hi = __uint_as_float(sign | ((unsigned)(e - 1023 + 127) << 23) | top23);
-        const unsigned ebits = (unsigned)(e - 1046 + 127) << 23;                 // 2^(e-1046)
-        const unsigned m = ((l32 & 0x1FFFFFFFu) + 32u) >> 6;                    // <= 2^23
-        const float r = __fsub_rn(__uint_as_float(ebits + m), __uint_as_float(ebits));
-        lo = __uint_as_float(sign | __float_as_uint(r));
-    } else if (e < 949) {
-        hi = __uint_as_float(sign);
-        lo = 0.0f;
-    } else {
-        const bool nan = e == 0x7FF && ((h32 & 0xFFFFFu) | l32) != 0u;
-        hi = __uint_as_float(sign | 0x7F800000u | (nan ? 0x400000u : 0u));
-        lo = 0.0f;
-    }
-}
-
-// Exact FP32 -> FP64 widening with integer operations (subnormal floats, below
-// 2^-126, become +-0).
-__device__ __forceinline__ double widen_f(float x)
-{
-    const unsigned b = __float_as_uint(x);
-    const unsigned e = (b >> 23) & 0xFFu;
-    const unsigned sign = b & 0x80000000u, m = b & 0x7FFFFFu;
-    if (e == 0u) return __hiloint2double((int)sign, 0);
-    const unsigned ed = e == 0xFFu ? 0x7FFu : e + (1023u - 127u);
-    return __hiloint2double((int)(sign | (ed << 20) | (m >> 3)), (int)(m << 29));
 }
 
 // FP32 copy of the tridiagonal bands of one component.
@@ -751,6 +874,159 @@ __global__ void k_rhs_planes(StencilF s0, StencilF s1, ModelDF m, int64_t N, con
     }
 }
 
+// Tiled form of k_rhs_planes for d = 2, 3.  A TX x TY block owns a tile of
+// the (x, y) plane (d = 3) or of the x line (d = 2, TY = 1) and marches over
+// TZ planes of the last direction ("z": mu = d - 1).  Every state value is
+// loaded and split once per tile (plus a one-point halo): the z neighbours
+// stay in registers, the x and y neighbours come from a shared-memory copy
+// of the plane, and the raw values of the next plane (and of its halo) are
+// loaded one iteration ahead so that their latency overlaps the current
+// plane's work.  Coordinates come from the thread index, so no division.
+// Same arithmetic, in the same order (directions mu = 0, 1, 2), as
+// k_rhs_planes.  Idx: 32-bit offsets when the grid has < 2^31 points.
+__device__ __forceinline__ float stencil_dir(float lo_c, float up_c, float rs_c, bool has_lo, bool has_up,
+                                             int has_rs, float hm, float lm, float hp, float lp, float hc,
+                                             float lc)
+{
+    float r = 0.0f;
+    if (has_lo) r = fmaf(lo_c, (hm - hc) + (lm - lc), r);
+    if (has_up) r = fmaf(up_c, (hp - hc) + (lp - lc), r);
+    if (has_rs) r = fmaf(rs_c, hc + lc, r);
+    return r;
+}
+
+template <int TX, int TY, int TZ, typename Idx>
+__global__ void __launch_bounds__(TX * TY) k_rhs_tiled(StencilF s0, StencilF s1, ModelDF m, int64_t N64,
+                                                       const double *__restrict__ U, bf16 *__restrict__ Fp)
+{
+    __shared__ float sh[2][2][TY + 2][TX + 2];   // [component][hi, lo][y][x], one-point halo
+    const StencilF *st[2] = {&s0, &s1};
+    const int d = s0.d, dz = d - 1;
+    const int n1 = (int)s0.n[0], n2 = d == 3 ? (int)s0.n[1] : 1, n3 = (int)s0.n[dz];
+    const Idx N = (Idx)N64;
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    const int x = blockIdx.x * TX + tx, y = blockIdx.y * TY + ty;
+    const bool in = x < n1 && y < n2;
+    const int z0 = blockIdx.z * TZ;
+    const int z1 = min(z0 + TZ, n3);
+    const Idx plane = (Idx)n1 * n2;
+    const Idx col = (Idx)y * n1 + x;
+    // halo roles: a row above/below the tile (first/last warp row), a column
+    // left/right of it (first/last lane of a row)
+    int yh = -1, xh = -1;
+    Idx yoff = 0, xoff = 0;
+    if (TY > 1 && x < n1) {
+        if (ty == 0 && y > 0) { yh = 0; yoff = col - n1; }
+        else if (ty == TY - 1 && y + 1 < n2) { yh = TY + 1; yoff = col + n1; }
+    }
+    if (y < n2) {
+        if (tx == 0 && x > 0) { xh = 0; xoff = col - 1; }
+        else if (tx == TX - 1 && x + 1 < n1) { xh = TX + 1; xoff = col + 1; }
+    }
+    float cx[2][3] = {}, cy[2][3] = {};
+    float hp[2] = {}, lp[2] = {}, hc[2] = {}, lc[2] = {}, hn[2] = {}, ln[2] = {};
+    double rn[2] = {}, ry[2] = {}, rx[2] = {};   // raw values loaded one iteration ahead
+    {
+        const Idx pz = (Idx)z0 * plane;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            if (in) {
+                cx[c][0] = st[c]->lo[0][x];
+                cx[c][1] = st[c]->up[0][x];
+                cx[c][2] = st[c]->rsum[0][x];
+                if (TY > 1) {
+                    cy[c][0] = st[c]->lo[1][y];
+                    cy[c][1] = st[c]->up[1][y];
+                    cy[c][2] = st[c]->rsum[1][y];
+                }
+                split_hilo(U[c * N + pz + col], hc[c], lc[c]);
+                if (z0 > 0) split_hilo(U[c * N + pz - plane + col], hp[c], lp[c]);
+                if (z0 + 1 < n3) rn[c] = U[c * N + pz + plane + col];
+            }
+            if (yh >= 0) ry[c] = U[c * N + pz + yoff];
+            if (xh >= 0) rx[c] = U[c * N + pz + xoff];
+        }
+    }
+    for (int z = z0; z < z1; ++z) {
+        const Idx pz = (Idx)z * plane;
+        const bool more = z + 1 < z1;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            if (in) {
+                if (z + 1 < n3) split_hilo(rn[c], hn[c], ln[c]);
+                sh[c][0][ty + 1][tx + 1] = hc[c];
+                sh[c][1][ty + 1][tx + 1] = lc[c];
+                if (more && z + 2 < n3) rn[c] = U[c * N + pz + 2 * plane + col];
+            }
+            if (yh >= 0) {
+                split_hilo(ry[c], sh[c][0][yh][tx + 1], sh[c][1][yh][tx + 1]);
+                if (more) ry[c] = U[c * N + pz + plane + yoff];
+            }
+            if (xh >= 0) {
+                split_hilo(rx[c], sh[c][0][ty + 1][xh], sh[c][1][ty + 1][xh]);
+                if (more) rx[c] = U[c * N + pz + plane + xoff];
+            }
+        }
+        __syncthreads();
+        if (in) {
+            float F[2];
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const StencilF &sc = *st[c];
+                float acc = stencil_dir(cx[c][0], cx[c][1], cx[c][2], x > 0, x + 1 < n1, sc.has_rsum[0],
+                                        sh[c][0][ty + 1][tx], sh[c][1][ty + 1][tx], sh[c][0][ty + 1][tx + 2],
+                                        sh[c][1][ty + 1][tx + 2], hc[c], lc[c]);
+                if (TY > 1)
+                    acc += stencil_dir(cy[c][0], cy[c][1], cy[c][2], y > 0, y + 1 < n2, sc.has_rsum[1],
+                                       sh[c][0][ty][tx + 1], sh[c][1][ty][tx + 1], sh[c][0][ty + 2][tx + 1],
+                                       sh[c][1][ty + 2][tx + 1], hc[c], lc[c]);
+                acc += stencil_dir(sc.lo[dz][z], sc.up[dz][z], sc.rsum[dz][z], z > 0, z + 1 < n3,
+                                   sc.has_rsum[dz], hp[c], lp[c], hn[c], ln[c], hc[c], lc[c]);
+                F[c] = acc;
+            }
+            float gu, gv;
+            react_df(m, dfl{hc[0], lc[0]}, dfl{hc[1], lc[1]}, gu, gv);
+            store_planes_f(Fp, (int64_t)N, (int64_t)(pz + col), F[0] + gu);
+            store_planes_f(Fp + 3 * (int64_t)N, (int64_t)N, (int64_t)(pz + col), F[1] + gv);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            hp[c] = hc[c];
+            lp[c] = lc[c];
+            hc[c] = hn[c];
+            lc[c] = ln[c];
+        }
+    }
+}
+
+// tile shapes: 3D 32 x 8 (x, y) tiles over 32 planes; 2D 128-wide x tiles over 8 rows
+constexpr int RT3_X = 32, RT3_Y = 8, RT3_Z = 32, RT2_X = 128, RT2_Z = 8;
+
+static void launch_rhs_tiled(const StencilF &s0, const StencilF &s1, const ModelDF &m, int64_t N, const double *U,
+                             bf16 *Fp, cudaStream_t st)
+{
+    const int d = s0.d;
+    const int64_t n1 = s0.n[0], n2 = d == 3 ? s0.n[1] : 1, n3 = s0.n[d - 1];
+    const bool small = N < ((int64_t)1 << 31);
+    if (d == 3) {
+        const dim3 g((unsigned)((n1 + RT3_X - 1) / RT3_X), (unsigned)((n2 + RT3_Y - 1) / RT3_Y),
+                     (unsigned)((n3 + RT3_Z - 1) / RT3_Z));
+        if (small)
+            k_rhs_tiled<RT3_X, RT3_Y, RT3_Z, int32_t><<<g, RT3_X * RT3_Y, 0, st>>>(s0, s1, m, N, U, Fp);
+        else
+            k_rhs_tiled<RT3_X, RT3_Y, RT3_Z, int64_t><<<g, RT3_X * RT3_Y, 0, st>>>(s0, s1, m, N, U, Fp);
+    } else {
+        const dim3 g((unsigned)((n1 + RT2_X - 1) / RT2_X), 1u, (unsigned)((n3 + RT2_Z - 1) / RT2_Z));
+        if (small)
+            k_rhs_tiled<RT2_X, 1, RT2_Z, int32_t><<<g, RT2_X, 0, st>>>(s0, s1, m, N, U, Fp);
+        else
+            k_rhs_tiled<RT2_X, 1, RT2_Z, int64_t><<<g, RT2_X, 0, st>>>(s0, s1, m, N, U, Fp);
+    }
+}
+
+// Separate (unfused) stage kernels, used when timing at plan creation finds them
+// faster than the fused epilogues.
 // D = g(U + a (+ b)) - g(U) for both components, as BF16 planes, from the
 // increment form of react_diff.  a, b: FP32 increments with component
 // stride cs_a / cs_b.
@@ -1017,9 +1293,12 @@ static ds_status describe(ModeLaunch &L, int d, const int64_t *n, int mu, const 
     a.kpi = a.T * a.kchunks;
     a.part_stride = (int64_t)S * N;
     a.part_ws = nullptr;
+    a.npair = 1;
+    a.num_units = a.num_tiles;
+    a.epi = 0;
     L.base_tiles = a.num_tiles;
     L.N = N;
-    L.grid = (int)std::min<int64_t>(a.num_tiles, num_sms());
+    L.grid = (int)std::min<int64_t>(a.num_units, num_sms());
     {
         std::vector<char> used(xcombos, 0);
         int nx = 0;
@@ -1043,7 +1322,30 @@ static void set_split(ModeLaunch &L, int ksplit, float *ws)
     a.kpi = (kiters + ksplit - 1) / ksplit;
     a.part_ws = ws;
     a.num_tiles = L.base_tiles * ksplit;
-    L.grid = (int)std::min<int64_t>(a.num_tiles, num_sms());
+    a.num_units = a.num_tiles / a.npair;
+    L.grid = (int)std::min<int64_t>(a.num_units, num_sms());
+}
+
+// Turn a last-mode launch (FP32 output, S = 2 S0 with s = component * S0 + x)
+// into a fused one: stage differences on x == 0 (epi 1, paired) or the final
+// update (epi 2).  Adjusts the algorithmic bytes: the fused outputs are not
+// written; the state, the added increments and the D planes are.
+static void set_fused(ModeLaunch &L, int epi, const float *extra, int64_t extra_cs, bf16 *Dp)
+{
+    TcArgs &a = L.args;
+    const double Nd = (double)L.N;
+    a.epi = epi;
+    a.fuse_spair = 0;
+    a.extra = extra;
+    a.extra_cs = extra_cs;
+    a.Dp = Dp;
+    a.npair = epi == 1 ? 2 : 1;
+    a.num_units = a.num_tiles / a.npair;
+    L.grid = (int)std::min<int64_t>(a.num_units, num_sms());
+    if (epi == 1)
+        L.alg_bytes += Nd * (-8.0 + 16.0 + (extra ? 8.0 : 0.0) + 12.0);
+    else
+        L.alg_bytes += Nd * (-8.0 + 32.0 + 8.0);
 }
 
 // Sum the split-K partials in part order (deterministic) and write the
@@ -1069,7 +1371,51 @@ __global__ void k_split_reduce(int64_t total, int64_t N, int ksplit, const float
     }
 }
 
-static void launch(const ModeLaunch &L, cudaStream_t st)
+// Split-K reduction of a fused last-mode launch: the same epilogue as the
+// kernel's, applied to the part sums (summed in part order).
+__global__ void k_split_reduce_epi(const __grid_constant__ TcArgs a)
+{
+    const int64_t N = a.out_ps, ps = a.part_stride;
+    const int S2 = a.S / 2;
+    const int64_t total = a.epi == 2 ? (int64_t)a.S * N : (int64_t)S2 * N;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(e / N);
+        const int64_t p = e - x * N;
+        if (a.epi == 2) {
+            float v = a.part_ws[e];
+            for (int q = 1; q < a.ksplit; ++q) v += a.part_ws[q * ps + e];
+            a.U[x * N + p] += widen_f(a.extra[x * a.extra_cs + p] + v);
+            continue;
+        }
+        const int64_t e0 = e, e1 = (int64_t)(S2 + x) * N + p;
+        float v0 = a.part_ws[e0], v1 = a.part_ws[e1];
+        for (int q = 1; q < a.ksplit; ++q) {
+            v0 += a.part_ws[q * ps + e0];
+            v1 += a.part_ws[q * ps + e1];
+        }
+        if (x != a.fuse_spair) {
+            ((float *)a.out)[e0] = v0;
+            ((float *)a.out)[e1] = v1;
+            continue;
+        }
+        float du = v0, dv = v1;
+        if (a.extra) {
+            du = a.extra[p] + du;
+            dv = a.extra[a.extra_cs + p] + dv;
+        }
+        float hu, lu, hv, lv;
+        split_hilo(a.U[p], hu, lu);
+        split_hilo(a.U[N + p], hv, lv);
+        float Du, Dv;
+        react_diff(a.model, hu + lu, hv + lv, du, dv, Du, Dv);
+        store_planes_f(a.Dp, N, p, Du);
+        store_planes_f(a.Dp + 3 * N, N, p, Dv);
+    }
+}
+
+// U and model: the state and reaction parameters of fused launches (ignored otherwise)
+static void launch(const ModeLaunch &L, cudaStream_t st, double *U = nullptr, const ModelF *model = nullptr)
 {
     static std::once_flag once;
     std::call_once(once, [] {
@@ -1077,14 +1423,22 @@ static void launch(const ModeLaunch &L, cudaStream_t st)
         cudaFuncSetAttribute(k_mode_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     });
     if (L.args.num_tiles <= 0) return;
+    TcArgs a = L.args;
+    if (a.epi) {
+        a.U = U;
+        if (model) a.model = *model;
+    }
     if (L.mode1)
-        k_mode_tc<true><<<L.grid, kThreads, SMEM_BYTES, st>>>(L.args);
+        k_mode_tc<true><<<L.grid, kThreads, SMEM_BYTES, st>>>(a);
     else
-        k_mode_tc<false><<<L.grid, kThreads, SMEM_BYTES, st>>>(L.args);
-    if (L.args.ksplit > 1) {
-        const int64_t total = L.args.part_stride;
-        k_split_reduce<<<(int)std::min<int64_t>((total + 255) / 256, 152 * 8), 256, 0, st>>>(
-            total, L.N, L.args.ksplit, L.args.part_ws, L.args.out_kind, L.args.out);
+        k_mode_tc<false><<<L.grid, kThreads, SMEM_BYTES, st>>>(a);
+    if (a.ksplit > 1) {
+        const int64_t total = a.part_stride;
+        const int g = (int)std::min<int64_t>((total + 255) / 256, 152 * 8);
+        if (a.epi)
+            k_split_reduce_epi<<<g, 256, 0, st>>>(a);
+        else
+            k_split_reduce<<<g, 256, 0, st>>>(total, L.N, a.ksplit, a.part_ws, a.out_kind, a.out);
     }
 }
 
@@ -1098,34 +1452,68 @@ struct ShapeKey {
     bool mode1;
     int n, S, T;
     int64_t I, O;
+    int epi;
     bool operator<(const ShapeKey &o) const
     {
-        return std::tie(mode1, n, S, T, I, O) < std::tie(o.mode1, o.n, o.S, o.T, o.I, o.O);
+        return std::tie(mode1, n, S, T, I, O, epi) < std::tie(o.mode1, o.n, o.S, o.T, o.I, o.O, o.epi);
     }
 };
 static std::mutex g_tune_mu;
 static std::map<ShapeKey, int> g_tuned;
+static bool g_tune_loaded = false;
+
+// Optional persistent record of the autotuner's choices: when the environment
+// variable DS_TUNE_CACHE names a file, its lines "mode1 n S T I O ksplit" are
+// loaded once (caller holds g_tune_mu) and every new choice is appended, so a
+// later process (a profiler run, say) replays the same launch configuration.
+// Line format: "mode1 n S T I O epi ksplit".
+static void tune_cache_load()
+{
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char *path = getenv("DS_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE *f = fopen(path, "r");
+    if (!f) return;
+    int m1, n, S, T, epi, k;
+    long long I, O;
+    while (fscanf(f, "%d %d %d %d %lld %lld %d %d", &m1, &n, &S, &T, &I, &O, &epi, &k) == 8)
+        if (k >= 1 && k <= 8) g_tuned[ShapeKey{m1 != 0, n, S, T, (int64_t)I, (int64_t)O, epi}] = k;
+    fclose(f);
+}
+
+static void tune_cache_append(const ShapeKey &key, int k)
+{
+    const char *path = getenv("DS_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE *f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "%d %d %d %d %lld %lld %d %d\n", key.mode1 ? 1 : 0, key.n, key.S, key.T, (long long)key.I,
+            (long long)key.O, key.epi, k);
+    fclose(f);
+}
 
 static int max_split(const ModeLaunch &L)
 {
     const int kiters = L.args.T * L.args.kchunks;
     const int64_t sms = num_sms();
-    if (L.base_tiles >= 2 * sms) return 1;
+    const int64_t units = L.base_tiles / L.args.npair;   // CTA work units (pairs count once)
+    if (units >= 2 * sms) return 1;
     int k = 1;
     // each part keeps >= 4 K chunks; stop once the split reaches 4 waves
-    while (k < 8 && kiters / (k + 1) >= 4 && L.base_tiles * (k + 1) <= 4 * sms) ++k;
+    while (k < 8 && kiters / (k + 1) >= 4 && units * (k + 1) <= 4 * sms) ++k;
     return k;
 }
 
 // fastest of five individually timed launches, after two warm launches
-static float time_launch(const ModeLaunch &L, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1)
+static float time_launch(const ModeLaunch &L, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, double *U)
 {
-    launch(L, st);
-    launch(L, st);
+    launch(L, st, U);
+    launch(L, st, U);
     float best = 1e30f;
     for (int r = 0; r < 5; ++r) {
         cudaEventRecord(e0, st);
-        launch(L, st);
+        launch(L, st, U);
         cudaEventRecord(e1, st);
         cudaEventSynchronize(e1);
         float ms = 0.f;
@@ -1135,13 +1523,15 @@ static float time_launch(const ModeLaunch &L, cudaStream_t st, cudaEvent_t e0, c
     return best;
 }
 
-static int autotune_split(ModeLaunch &L, float *ws, cudaStream_t st, float *times)
+// U: a scratch FP64 state [2][N] for the fused launches' epilogues
+static int autotune_split(ModeLaunch &L, float *ws, cudaStream_t st, float *times, double *U)
 {
-    const ShapeKey key{L.mode1, L.args.n, L.args.S, L.args.T, L.args.I, L.args.O};
+    const ShapeKey key{L.mode1, L.args.n, L.args.S, L.args.T, L.args.I, L.args.O, L.args.epi};
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
+        tune_cache_load();
         auto it = g_tuned.find(key);
-        if (it != g_tuned.end()) return it->second;
+        if (it != g_tuned.end()) return std::min(it->second, max_split(L));
     }
     const int kmax = max_split(L);
     int best = 1;
@@ -1152,7 +1542,7 @@ static int autotune_split(ModeLaunch &L, float *ws, cudaStream_t st, float *time
         float best_ms = 1e30f;
         for (int k = 1; k <= kmax; ++k) {
             set_split(L, k, ws);
-            const float ms = time_launch(L, st, e0, e1);
+            const float ms = time_launch(L, st, e0, e1, U);
             if (times) times[k - 1] = ms;
             // a larger split has to win by 3%: it adds partial traffic
             if (ms < best_ms * 0.97f) {
@@ -1165,6 +1555,7 @@ static int autotune_split(ModeLaunch &L, float *ws, cudaStream_t st, float *time
     }
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tuned[key] = best;
+    if (kmax > 1) tune_cache_append(key, best);
     return best;
 }
 
@@ -1198,13 +1589,86 @@ struct MixedPlan {
     float *incF = nullptr;     // [2][3][N]
     float *incD = nullptr;     // [2][N]
     float *bands = nullptr;    // FP32 bands [c][mu][lo, up, rowsum][n_mu]
+    bool rhs_tiled = false;    // k_rhs_tiled (d <= 3) instead of k_rhs_planes
     float *part_ws = nullptr;  // split-K partials
     float tune_ms[3][kMaxD][8];  // autotuner: time of each split-K candidate (0 = not tried)
     StencilF stf[2];
     // launches[group][mode], both components in one launch;
-    // group 0 = F, 1 = D2 (slot 2), 2 = D3 (slot 4)
+    // group 0 = F, 1 = D2 (slot 2), 2 = D3 (slot 4).  The last mode's launch
+    // has the fused epilogue; Lsep[g] is the same product writing its FP32
+    // increments for the separate stage kernel.  fused[g] records which of the
+    // two the plan runs (the faster at creation), fuse_ms[g] = {fused, separate}.
     ModeLaunch L[3][kMaxD];
+    ModeLaunch Lsep[3];
+    bool fused[3] = {true, true, true};
+    float fuse_ms[3][2] = {};
 };
+
+// the separate stage kernel of group g (D2, D3 planes or the final update)
+static void launch_stage_kernel(const MixedPlan *mp, int g, const ModelF &mf, double *U, cudaStream_t st)
+{
+    const int64_t N = mp->N;
+    if (g == 0)
+        k_stage_planes<<<pw_grid(N), 256, 0, st>>>(mf, N, U, mp->incF, 3 * N, nullptr, 0, mp->Dp);
+    else if (g == 1)
+        k_stage_planes<<<pw_grid(N), 256, 0, st>>>(mf, N, U, mp->incF + N, 3 * N, mp->incD, N, mp->Dp);
+    else
+        k_final_mixed<<<pw_grid(N), 256, 0, st>>>(N, U, mp->incF + 2 * N, 3 * N, mp->incD, N);
+}
+
+// For each group, time its last mode with the fused epilogue against the
+// plain product plus the separate stage kernel (fastest of five after two
+// warm launches, on the plan's buffers and a scratch state) and keep the
+// faster.  The choice is cached per shape like the split factors (cache key
+// epi = 10 + group, value 1 = separate, 2 = fused).
+static void decide_fusion(MixedPlan *mp, cudaStream_t st, double *Us)
+{
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const ModelF mf{DS_SCHNAKENBERG, {1.0f, 0.1f, 0.9f}};
+    for (int g = 0; g < 3; ++g) {
+        const ModeLaunch &F = mp->L[g][mp->d - 1], &S = mp->Lsep[g];
+        const ShapeKey key{F.mode1, F.args.n, F.args.S, F.args.T, F.args.I, F.args.O, 10 + g};
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            tune_cache_load();
+            auto it = g_tuned.find(key);
+            if (it != g_tuned.end()) {
+                mp->fused[g] = it->second == 2;
+                continue;
+            }
+        }
+        auto timed = [&](auto &&fn) {
+            fn();
+            fn();
+            float best = 1e30f;
+            for (int r = 0; r < 5; ++r) {
+                cudaEventRecord(e0, st);
+                fn();
+                cudaEventRecord(e1, st);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                best = std::min(best, ms);
+            }
+            return best;
+        };
+        const float tf = timed([&] { launch(F, st, Us, &mf); });
+        const float ts = timed([&] {
+            launch(S, st);
+            launch_stage_kernel(mp, g, mf, Us, st);
+        });
+        mp->fuse_ms[g][0] = tf;
+        mp->fuse_ms[g][1] = ts;
+        mp->fused[g] = tf <= ts;
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned[key] = mp->fused[g] ? 2 : 1;
+        tune_cache_append(key, mp->fused[g] ? 2 : 1);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+}
 
 ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatus *status, MixedPlan **out)
 {
@@ -1277,6 +1741,12 @@ ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatu
             }
     }
     const int64_t N = mp->N;
+    {
+        // k_rhs_tiled grid limits: y and z grid dimensions <= 65535
+        const int64_t gy = d == 3 ? (mp->n[1] + RT3_Y - 1) / RT3_Y : 1;
+        const int64_t gz = d == 3 ? (mp->n[2] + RT3_Z - 1) / RT3_Z : (mp->n[1] + RT2_Z - 1) / RT2_Z;
+        mp->rhs_tiled = d <= 3 && gy <= 65535 && gz <= 65535 && mp->n[0] <= INT32_MAX;
+    }
     // phi planes: per component, per group, per mode, combos
     //   group F: mode 0 and middle: 3k combos (stage q' in {slot 0, 1, 3}, term i)
     //            last mode: 3k combos with w_q tau eta^{(1)}_i folded in
@@ -1356,37 +1826,76 @@ ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatu
             r = describe(mp->L[g][mu], d, mp->n, mu, X, xcombos, P, 2 * S0, ldp, S, T, xs, xdiv, out, kind,
                          1.0f, status);
             if (r != DS_OK) { mixed_plan_destroy(mp); return r; }
+            // the last mode's epilogue does the pointwise work of the stage:
+            //   F:  D2 = g(U + tau/3 S_2(F)) - g(U)                     (s = c * 3 + stage)
+            //   D2: D3 = g(U + 2tau/3 S_3(F) + 4tau/3 S_3(D2)) - g(U)   (s = c)
+            //   D3: U += tau S_f(F) + 3tau/2 S_f(D3)
+            if (last) {
+                mp->Lsep[g] = mp->L[g][mu];
+                if (g == 0) set_fused(mp->L[g][mu], 1, nullptr, 0, mp->Dp);
+                else if (g == 1) set_fused(mp->L[g][mu], 1, mp->incF + N, 3 * N, mp->Dp);
+                else set_fused(mp->L[g][mu], 2, mp->incF + 2 * N, 3 * N, nullptr);
+            }
         }
     }
     if (cudaDeviceSynchronize() != cudaSuccess) return cleanup(DS_ERR_CUDA, "phi plane split");
-    // split-K autotuning for launches with too few output tiles
+    // split-K autotuning for launches with too few output tiles, then the
+    // fused-or-separate choice for each group's last mode
     {
         int64_t ws_elems = 0;
+        auto need = [&](const ModeLaunch &L) {
+            if (max_split(L) > 1) ws_elems = std::max<int64_t>(ws_elems, max_split(L) * L.args.part_stride);
+        };
         for (int g = 0; g < 3; ++g)
-            for (int mu = 0; mu < d; ++mu) {
-                const ModeLaunch &L = mp->L[g][mu];
-                if (max_split(L) > 1) ws_elems = std::max<int64_t>(ws_elems, max_split(L) * L.args.part_stride);
-            }
-        if (ws_elems > 0) {
-            if (cudaMalloc(&mp->part_ws, sizeof(float) * ws_elems) != cudaSuccess) {
-                cudaGetLastError();
-                return cleanup(DS_ERR_OOM, "split-K workspace");
-            }
-            cudaStream_t ts;
-            cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking);
-            for (int g = 0; g < 3; ++g)
-                for (int mu = 0; mu < d; ++mu) {
-                    ModeLaunch &L = mp->L[g][mu];
-                    const int k = autotune_split(L, mp->part_ws, ts, mp->tune_ms[g][mu]);
-                    set_split(L, k, k > 1 ? mp->part_ws : nullptr);
-                }
-            cudaStreamSynchronize(ts);
-            cudaStreamDestroy(ts);
-            if (cudaGetLastError() != cudaSuccess) return cleanup(DS_ERR_CUDA, "split-K autotuning");
+            for (int mu = 0; mu < d; ++mu) need(mp->L[g][mu]);
+        if (ws_elems > 0 && cudaMalloc(&mp->part_ws, sizeof(float) * ws_elems) != cudaSuccess) {
+            cudaGetLastError();
+            return cleanup(DS_ERR_OOM, "split-K workspace");
         }
+        // scratch state for the fused epilogues while timing
+        double *Us = nullptr;
+        if (cudaMalloc(&Us, sizeof(double) * 2 * N) != cudaSuccess) {
+            cudaGetLastError();
+            return cleanup(DS_ERR_OOM, "autotuning scratch");
+        }
+        cudaMemset(Us, 0, sizeof(double) * 2 * N);
+        cudaStream_t ts;
+        cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking);
+        for (int g = 0; g < 3; ++g) {
+            for (int mu = 0; mu < d; ++mu) {
+                ModeLaunch &L = mp->L[g][mu];
+                const int k = autotune_split(L, mp->part_ws, ts, mp->tune_ms[g][mu], Us);
+                set_split(L, k, k > 1 ? mp->part_ws : nullptr);
+            }
+            // the separate form runs the same contraction with the same split
+            // factor, so both forms give identical values
+            const int k = mp->L[g][d - 1].args.ksplit;
+            set_split(mp->Lsep[g], k, k > 1 ? mp->part_ws : nullptr);
+        }
+        decide_fusion(mp, ts, Us);
+        cudaStreamSynchronize(ts);
+        cudaStreamDestroy(ts);
+        cudaFree(Us);
+        if (cudaGetLastError() != cudaSuccess) return cleanup(DS_ERR_CUDA, "autotuning");
     }
     *out = mp;
     return DS_OK;
+}
+
+int mixed_plan_fusion(const MixedPlan *mp, int g, int *fused, float *ms_fused, float *ms_separate)
+{
+    if (!mp || g < 0 || g > 2) return -1;
+    *fused = mp->fused[g] ? 1 : 0;
+    *ms_fused = mp->fuse_ms[g][0];
+    *ms_separate = mp->fuse_ms[g][1];
+    return 0;
+}
+
+int mixed_plan_set_fusion(MixedPlan *mp, int g, int fused)
+{
+    if (!mp || g < 0 || g > 2) return -1;
+    mp->fused[g] = fused != 0;
+    return 0;
 }
 
 int mixed_plan_tuning(const MixedPlan *mp, int g, int mu, int *ksplit, int64_t *tiles, float *times)
@@ -1436,42 +1945,44 @@ int enqueue_step_mixed(MixedPlan *mp, const ds_phi_set *set, const Model &model,
                        double *U, cudaStream_t st, Prof *prof)
 {
     (void)set;
+    (void)sten;
     const int64_t N = mp->N;
     const int d = mp->d;
+    const ModelF mf = model_f(model);
     int L = 0;
     Prof dummy;
     Prof &P = prof ? *prof : dummy;
+    // one group of mode products; the last one's epilogue finishes the stage
+    // (or, where timing chose it, a separate stage kernel does)
     auto group = [&](int g) {
         for (int mu = 0; mu < d; ++mu) {
-            P.begin(st, 0, launch_flops(mp->L[g][mu], N), mp->L[g][mu].alg_bytes);
-            launch(mp->L[g][mu], st);
+            const bool sep = mu == d - 1 && !mp->fused[g];
+            const ModeLaunch &ML = sep ? mp->Lsep[g] : mp->L[g][mu];
+            P.begin(st, 0, launch_flops(ML, N), ML.alg_bytes);
+            launch(ML, st, U, &mf);
             P.end(st);
-            ++L;
+            L += ML.args.ksplit > 1 ? 2 : 1;
+            if (sep) {
+                // stage kernels: U 16 B + increments 8-16 B + planes 12 B per point; final 48 B
+                const double b = g == 0 ? 36.0 : g == 1 ? 44.0 : 48.0;
+                P.begin(st, 2, 0.0, (double)N * b);
+                launch_stage_kernel(mp, g, mf, U, st);
+                P.end(st);
+                ++L;
+            }
         }
     };
-    const double Nd = (double)N;
-    // pointwise bytes: FP64 state 16 B/point, FP32 increments 4 B, BF16 planes 6 B per component
-    P.begin(st, 2, 0.0, Nd * (16 + 12));
-    k_rhs_planes<<<pw_grid(N), 256, 0, st>>>(mp->stf[0], mp->stf[1], model_df(model), N, U, mp->Fp);
+    // F = K U + g(U) as BF16 planes: FP64 state 16 B/point in, 2 x 6 B planes out
+    P.begin(st, 2, 0.0, (double)N * (16 + 12));
+    if (mp->rhs_tiled)
+        launch_rhs_tiled(mp->stf[0], mp->stf[1], model_df(model), N, U, mp->Fp, st);
+    else
+        k_rhs_planes<<<pw_grid(N), 256, 0, st>>>(mp->stf[0], mp->stf[1], model_df(model), N, U, mp->Fp);
     P.end(st);
     ++L;
-    group(0);
-    // D2 = g(U + inc_2) - g(U)
-    P.begin(st, 2, 0.0, Nd * (16 + 8 + 12));
-    k_stage_planes<<<pw_grid(N), 256, 0, st>>>(model_f(model), N, U, mp->incF, 3 * N, nullptr, 0, mp->Dp);
-    P.end(st);
-    ++L;
-    group(1);
-    // D3 = g(U + inc_3F + inc_3D) - g(U)
-    P.begin(st, 2, 0.0, Nd * (16 + 16 + 12));
-    k_stage_planes<<<pw_grid(N), 256, 0, st>>>(model_f(model), N, U, mp->incF + N, 3 * N, mp->incD, N, mp->Dp);
-    P.end(st);
-    ++L;
-    group(2);
-    P.begin(st, 2, 0.0, Nd * (32 + 16));
-    k_final_mixed<<<pw_grid(N), 256, 0, st>>>(N, U, mp->incF + 2 * N, 3 * N, mp->incD, N);
-    P.end(st);
-    ++L;
+    group(0);   // stage increments of F; epilogue: D2
+    group(1);   // 4tau/3 S_3(D2); epilogue: D3
+    group(2);   // 3tau/2 S_f(D3); epilogue: U update
     return L;
 }
 

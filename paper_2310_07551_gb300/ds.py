@@ -20,7 +20,7 @@ STATUS_NAMES = ["DS_OK", "DS_ERR_INVALID_ARG", "DS_ERR_UNSUPPORTED", "DS_ERR_OOM
                 "DS_ERR_NONFINITE", "DS_ERR_TIMEOUT"]
 PREC = {"f64": 0, "bf16x6": 1, "f32": 2}
 MODELS = {"schnakenberg": 0, "fhn": 1, "linear": 2}
-SCHEMES = {"exprk3ds_real": 0, "etd2rkds": 1, "exprk3ds_cplx": 2}
+SCHEMES = {"exprk3ds_real": 0, "etd2rkds": 1, "exprk3ds_cplx": 2, "exprk3_dense": 3}
 
 
 class DsError(RuntimeError):
@@ -71,6 +71,9 @@ def lib() -> ctypes.CDLL:
             "ds_plan_tuning": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                 ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
             "ds_plan_profile_read": ([_vp, _dp, ctypes.POINTER(ctypes.c_int64), _dp], ctypes.c_int),
+            "ds_plan_set_fusion": ([_vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+            "ds_plan_fusion": ([_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float),
+                                ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
             "ds_plan_profile_read_ex": ([_vp, _dp, ctypes.POINTER(ctypes.c_int64), _dp, _dp], ctypes.c_int),
             "ds_plan_destroy": ([_vp], ctypes.c_int),
             "ds_batch_create": ([ctypes.c_int, gp, ctypes.POINTER(_vp), _dp, pp, ctypes.c_int,
@@ -137,8 +140,9 @@ class PhiSet:
 
     def get(self, c: int, slot: int, term: int, mu: int, part: int = 0) -> np.ndarray:
         """phi-matrix (part 0; real part for the complex scheme), its imaginary
-        part (1) or its derivative w.r.t. a scaling of A (2), as (n, n)."""
-        n = self.dims[mu]
+        part (1) or its derivative w.r.t. a scaling of A (2), as (n, n).  The
+        dense scheme has one N x N matrix per (c, slot): term = mu = 0."""
+        n = int(np.prod(self.dims)) if self.scheme == "exprk3_dense" else self.dims[mu]
         out = np.empty(n * n)
         check(lib().ds_phi_get_ex(self._h, c, slot, term, mu, part, out.ctypes.data_as(_dp)))
         return out.reshape(n, n).T.copy()
@@ -206,6 +210,21 @@ class Plan:
         check(lib().ds_integrate_ckpt(self._h, _dptr(U), int(nsteps), int(ckpt_every),
                                       _dptr(ck) if nck else None, _stream_ptr(stream)))
         return ck
+
+    def fusion(self):
+        """[(group, fused, ms_fused, ms_separate)] for split-BF16 plans: whether
+        each group's last mode product finishes the stage in its epilogue."""
+        out = []
+        for g in range(3):
+            fz = ctypes.c_int()
+            a = ctypes.c_float()
+            b = ctypes.c_float()
+            check(lib().ds_plan_fusion(self._h, g, ctypes.byref(fz), ctypes.byref(a), ctypes.byref(b)))
+            out.append((g, bool(fz.value), float(a.value), float(b.value)))
+        return out
+
+    def set_fusion(self, group: int, fused: bool):
+        check(lib().ds_plan_set_fusion(self._h, int(group), int(bool(fused))))
 
     def sync(self, U=None, check_state: bool = False):
         check(lib().ds_plan_sync(self._h, _dptr(U) if U is not None else None, int(check_state)))

@@ -29,7 +29,8 @@ def relmax(a, b):
     return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
 
 
-@pytest.mark.parametrize("dims,tau", [((64, 64), 1e-3), ((24, 20, 16), 1e-3), ((70, 33), 1e-4)])
+@pytest.mark.parametrize("dims,tau", [((64, 64), 1e-3), ((24, 20, 16), 1e-3), ((70, 33), 1e-4),
+                                      ((12, 10, 9, 7), 1e-3)])
 def test_phi_setup_matches_oracle(ds, dims, tau):
     As = problem(dims, -1.0, 1.0, (1.0, 42.1887))
     ref = O.phi_set_blocks(dims, O.phi_set(dims, As, tau))
@@ -45,7 +46,7 @@ def test_phi_setup_matches_oracle(ds, dims, tau):
     assert worst < 1e-13, worst
 
 
-@pytest.mark.parametrize("dims", [(70, 65), (33, 70, 9), (128, 64, 40), (2, 3, 5)])
+@pytest.mark.parametrize("dims", [(70, 65), (33, 70, 9), (128, 64, 40), (2, 3, 5), (17, 9, 12, 6)])
 @pytest.mark.parametrize("transpose", [0, 1])
 def test_tucker_f64_matches_oracle(ds, dims, transpose):
     X = inputs.random_tensor(dims, seed=3)
@@ -83,14 +84,20 @@ def run_both(ds, dims, lo, hi, delta, model, p, tau, U0, m, integrate=True):
 
 
 def test_schnakenberg_64_full_horizon(ds):
+    """Tolerance: max(1e-12, 10 x the oracle's FP64 floor), the floor being the
+    difference between the oracle run with ascending and with descending
+    summation in every mode product (Turing-unstable growth amplifies
+    rounding over the horizon)."""
     w = configs.WORKLOADS["schnak2d_64"]
     U0 = inputs.initial_state("schnakenberg", w.dims, seed=w.seed)
     got, ref, _ = run_both(ds, w.dims, w.lo, w.hi, w.delta, "schnakenberg", w.params, w.tau, U0, w.steps)
+    floor, _ = O.noise_floor(w.dims, problem(w.dims, w.lo, w.hi, w.delta), "schnakenberg", w.params,
+                             w.tau, U0, w.steps)
     errs = [relmax(got[c], ref[c]) for c in range(2)]
-    assert max(errs) < 1e-12, errs
+    assert max(errs) <= max(1e-12, 10 * floor), (errs, floor)
 
 
-@pytest.mark.parametrize("dims", [(20, 18, 16), (33, 9, 70)])
+@pytest.mark.parametrize("dims", [(20, 18, 16), (33, 9, 70), (12, 10, 9, 7)])
 def test_fhn_3d_steps(ds, dims):
     U0 = inputs.initial_state("fhn", dims, seed=1)
     got, ref, plan = run_both(ds, dims, -1.0, 1.0, (1.0, 42.1887), "fhn", (0.1, 2.0, -0.1), 1e-3, U0, 5)

@@ -31,7 +31,8 @@ def problem(dims, lo, hi, delta):
 
 # shapes: several 128x256 tiles, ragged tails in every mode, mode-1 n not a
 # multiple of the 32-wide K chunk, inner sizes below the 64-wide TMA box
-SHAPES = [(64, 64), (136, 40), (32, 24, 16), (64, 48, 40), (40, 33, 70), (256, 256), (96, 72, 20)]
+SHAPES = [(64, 64), (136, 40), (32, 24, 16), (64, 48, 40), (40, 33, 70), (256, 256), (96, 72, 20),
+          (24, 16, 12, 10)]
 
 
 @pytest.mark.parametrize("dims", SHAPES)
@@ -71,7 +72,7 @@ def relmax(a, b):
     return max(np.abs(a[c] - b[c]).max() / np.abs(b[c]).max() for c in range(2))
 
 
-@pytest.mark.parametrize("dims,m", [((32, 24, 16), 5), ((40, 33, 70), 3)])
+@pytest.mark.parametrize("dims,m", [((32, 24, 16), 5), ((40, 33, 70), 3), ((16, 12, 10, 9), 3)])
 def test_fhn_3d_mixed_step(ds, dims, m):
     """White-noise FHN data: each step's increment is a sum of Tucker terms
     with eta of alternating sign (Table 3: sum |eta_i| phi-weights ~ 10 times
@@ -96,3 +97,27 @@ def test_schnakenberg_64_mixed_full_horizon(ds):
     err = relmax(got, ref)
     print("schnak64 mixed rel err", err)
     assert err < 1e-6, err
+
+
+@pytest.mark.parametrize("dims,model,p,lo,hi,delta,tau", [
+    ((40, 33, 70), "fhn", (0.1, 2.0, -0.1), -1.0, 1.0, (1.0, 42.1887), 1e-3),
+    ((136, 40), "schnakenberg", (1000.0, 0.1, 0.9), 0.0, 1.0, (1.0, 10.0), 1e-4),
+])
+def test_fused_epilogues_match_separate_kernels_bitwise(ds, dims, model, p, lo, hi, delta, tau):
+    """The last mode's fused epilogue (stage difference / final update) and
+    the plain product followed by the separate stage kernel compute the same
+    values in the same order: results agree bit for bit."""
+    As = problem(dims, lo, hi, delta)
+    U0 = inputs.initial_state(model, dims, seed=9)
+    ps = ds.PhiSet(dims, As, tau)
+    plan = ds.Plan(ps, model, p, "bf16x6")
+    out = []
+    for fused in (True, False):
+        for g in range(3):
+            plan.set_fusion(g, fused)
+        assert all(f == fused for _, f, _, _ in plan.fusion())
+        U = torch.from_numpy(U0.copy()).cuda()
+        plan.integrate(U, 3)
+        plan.sync(U, check_state=True)
+        out.append(U.cpu().numpy())
+    assert np.array_equal(out[0], out[1])
