@@ -40,8 +40,9 @@ UNIT = "grid-point*steps/s"
 # dram__bytes_write.sum), keyed by "<hash of the kernel source>:<workload>";
 # a changed kernel reports null.
 NCU_TRAFFIC = {
-    # launches14_fhn: 9 k_mode_tc launches of one step, mean of read + write
-    "dfad67c0e1aba76c:fhn3d_256": 1.444e9,
+    # profiles/launches_*.md: mean over one step's k_mode_tc launches of read + write
+    "ca149bcf95ccf84c:fhn3d_256": 1.502e9,
+    "ca149bcf95ccf84c:schnak2d_1024": 1.089e8,
 }
 
 
