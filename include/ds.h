@@ -294,13 +294,26 @@ ds_status ds_plan_profile_read(ds_plan *plan, double *ms, int64_t *launches, dou
 ds_status ds_plan_profile_read_ex(ds_plan *plan, double *ms, int64_t *launches, double *flops,
                                   double *bytes);
 
-/* ds_plan_tuning -- what the split-K autotuner chose for the split-BF16
- * plan's mode-product launch of group (0 = the F group, 1 = D2, 2 = D3) and
- * mode mu: the split factor, the number of output tiles, and the measured
- * time (ms, fastest of five) of each candidate factor 1..8 (0 = not tried).
- * Synchronous; DS_ERR_UNSUPPORTED for other precisions. */
+/* ds_plan_tuning -- what the autotuner chose for the split-BF16 plan's mode
+ * product launch of group (0 = the F group, 1 = D2, 2 = D3) and mode mu: the
+ * split-K factor, the number of output tiles, and the measured time (ms,
+ * fastest of five) of each candidate factor 1..8 at the chosen tile width
+ * (0 = not tried).  Synchronous; DS_ERR_UNSUPPORTED for other precisions. */
 ds_status ds_plan_tuning(const ds_plan *plan, int group, int mu, int *ksplit, int64_t *tiles,
                          float *times_ms);
+
+/* ds_plan_tuning_ex -- ds_plan_tuning plus the chosen output tile width
+ * tile_n (256 or 128 columns; the tiles have 128 rows) and times_ms[16]:
+ * [w * 8 + k - 1] for width w (0: 256, 1: 128) and split factor k. */
+ds_status ds_plan_tuning_ex(const ds_plan *plan, int group, int mu, int *ksplit, int64_t *tiles, int *tile_n,
+                            float *times_ms);
+
+/* ds_plan_set_tiles -- override the autotuner for one launch: output tile
+ * width tile_n (256 or 128) and split-K factor (1 .. the largest factor the
+ * tuner considered for that width; DS_ERR_INVALID_ARG otherwise).  The tile
+ * width does not change any element's summation order; the split factor
+ * does.  Waits for the plan's stream and drops its captured graphs. */
+ds_status ds_plan_set_tiles(ds_plan *plan, int group, int mu, int tile_n, int ksplit);
 
 /* ds_plan_fusion -- for the split-BF16 plan's group (0 = F, 1 = D2, 2 = D3):
  * whether its last mode product runs with the fused epilogue (the stage

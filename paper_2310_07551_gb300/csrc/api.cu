@@ -1191,12 +1191,25 @@ ds_status ds_batch_sync(ds_batch *b)
 
 int64_t ds_batch_kernels_per_step(const ds_batch *b) { return b ? b->launches_per_step : -1; }
 
+ds_status ds_plan_tuning_ex(const ds_plan *p, int group, int mu, int *ksplit, int64_t *tiles, int *tile_n,
+                            float *times_ms)
+{
+    if (!p || !ksplit || !tiles || !tile_n || !times_ms) return fail(DS_ERR_INVALID_ARG, "NULL argument");
+    if (!p->mixed) return fail(DS_ERR_UNSUPPORTED, "only split-BF16 plans are tuned");
+    if (tc::mixed_plan_tuning(p->mixed, group, mu, ksplit, tiles, tile_n, times_ms) != 0)
+        return fail(DS_ERR_INVALID_ARG, "group or mode out of range");
+    return DS_OK;
+}
+
 ds_status ds_plan_tuning(const ds_plan *p, int group, int mu, int *ksplit, int64_t *tiles, float *times_ms)
 {
-    if (!p || !ksplit || !tiles || !times_ms) return fail(DS_ERR_INVALID_ARG, "NULL argument");
-    if (!p->mixed) return fail(DS_ERR_UNSUPPORTED, "only split-BF16 plans are tuned");
-    if (tc::mixed_plan_tuning(p->mixed, group, mu, ksplit, tiles, times_ms) != 0)
-        return fail(DS_ERR_INVALID_ARG, "group or mode out of range");
+    if (!times_ms) return fail(DS_ERR_INVALID_ARG, "NULL argument");
+    int tile_n = 0;
+    float t16[16];
+    ds_status r = ds_plan_tuning_ex(p, group, mu, ksplit, tiles, &tile_n, t16);
+    if (r != DS_OK) return r;
+    const int w = tile_n == 128 ? 1 : 0;
+    for (int k = 0; k < 8; ++k) times_ms[k] = t16[w * 8 + k];
     return DS_OK;
 }
 
@@ -1217,6 +1230,19 @@ ds_status ds_plan_set_fusion(ds_plan *p, int group, int fused)
     if (tc::mixed_plan_set_fusion(p->mixed, group, fused) != 0)
         return fail(DS_ERR_INVALID_ARG, "group out of range");
     // captured steps hold the previous launch sequence
+    for (auto &kv : p->graphs) cudaGraphExecDestroy(kv.second);
+    p->graphs.clear();
+    return DS_OK;
+}
+
+ds_status ds_plan_set_tiles(ds_plan *p, int group, int mu, int tile_n, int ksplit)
+{
+    if (!p) return fail(DS_ERR_INVALID_ARG, "NULL plan");
+    if (!p->mixed) return fail(DS_ERR_UNSUPPORTED, "only split-BF16 plans have tile choices");
+    if (p->st) cudaStreamSynchronize(p->st);
+    const int r = tc::mixed_plan_set_tiles(p->mixed, group, mu, tile_n, ksplit);
+    if (r == -1) return fail(DS_ERR_INVALID_ARG, "group, mode or tile width out of range");
+    if (r == -2) return fail(DS_ERR_INVALID_ARG, "split factor outside the tuned range");
     for (auto &kv : p->graphs) cudaGraphExecDestroy(kv.second);
     p->graphs.clear();
     return DS_OK;

@@ -44,17 +44,24 @@ namespace tc {
 
 using bf16 = __nv_bfloat16;
 
-constexpr int BM = 128, BN = 256, BK = 32, STAGES = 3;
+constexpr int BM = 128, BK = 32;
 constexpr int kThreads = 320;            // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
 constexpr int kEpiThreads = 256;
 constexpr uint32_t A_PLANE = BM * BK * 2;          // 8 KiB
-constexpr uint32_t B_PLANE = BN * BK * 2;          // 16 KiB
 constexpr uint32_t STAGE_A = 3 * A_PLANE;
-constexpr uint32_t STAGE_B = 3 * B_PLANE;
-constexpr uint32_t STAGE_BYTES = STAGE_A + STAGE_B;  // 72 KiB
-constexpr uint32_t BAR_BYTES = 8 * (2 * STAGES + 5) + 16;
-constexpr uint32_t SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + BAR_BYTES;
 constexpr uint32_t TMEM_COLS = 512;
+
+// Output tiles are BM x BNT: 256 columns (3-stage ring of 72 KiB) or 128
+// columns (4-stage ring of 48 KiB) for launches with few tiles.  The plan's
+// autotuner picks the width per launch.
+template <int BNT>
+struct TileCfg {
+    static constexpr int STAGES = BNT == 256 ? 3 : 4;
+    static constexpr uint32_t B_PLANE = BNT * BK * 2;
+    static constexpr uint32_t STAGE_BYTES = STAGE_A + 3 * B_PLANE;
+    static constexpr uint32_t BAR_BYTES = 8 * (2 * STAGES + 5) + 16;
+    static constexpr uint32_t SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + BAR_BYTES;
+};
 constexpr long long kTimeoutCycles = 4000000000LL;   // ~2 s at 2 GHz
 
 // UMMA shared-memory descriptor layout types
@@ -238,6 +245,22 @@ __device__ __forceinline__ void split3f(float x, bf16 &p0, bf16 &p1, bf16 &p2)
     r -= __bfloat162float(p1);
     p2 = __float2bfloat16_rn(r);
 }
+// split3f of two values at once, each element rounded exactly as split3f
+// does; q_k packs part k of (x0, x1) as BF16 x0 in the low half
+__device__ __forceinline__ void split3_pair(float x0, float x1, uint32_t &q0, uint32_t &q1, uint32_t &q2)
+{
+    const __nv_bfloat162 p0 = __floats2bfloat162_rn(x0, x1);
+    const float2 f0 = __bfloat1622float2(p0);
+    float r0 = x0 - f0.x, r1 = x1 - f0.y;
+    const __nv_bfloat162 p1 = __floats2bfloat162_rn(r0, r1);
+    const float2 f1 = __bfloat1622float2(p1);
+    r0 -= f1.x;
+    r1 -= f1.y;
+    const __nv_bfloat162 p2 = __floats2bfloat162_rn(r0, r1);
+    q0 = *reinterpret_cast<const uint32_t *>(&p0);
+    q1 = *reinterpret_cast<const uint32_t *>(&p1);
+    q2 = *reinterpret_cast<const uint32_t *>(&p2);
+}
 
 // ---------------------------------------------------------------------------
 // Pointwise helpers shared by the fused epilogues and the pointwise kernels.
@@ -388,9 +411,13 @@ __device__ __forceinline__ TileCoord work_item(const TcArgs &a, int64_t unit, in
     return c;
 }
 
-template <bool MODE1>
+template <bool MODE1, int BNT>
 __global__ void __launch_bounds__(kThreads, 1) k_mode_tc(const __grid_constant__ TcArgs a)
 {
+    constexpr int BN = BNT;
+    constexpr int STAGES = TileCfg<BNT>::STAGES;
+    constexpr uint32_t B_PLANE = TileCfg<BNT>::B_PLANE;
+    constexpr uint32_t STAGE_BYTES = TileCfg<BNT>::STAGE_BYTES;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
@@ -577,29 +604,48 @@ __global__ void __launch_bounds__(kThreads, 1) k_mode_tc(const __grid_constant__
                 tmem_ld32(tmem + (uint32_t)acc * BN + (uint32_t)(half * (BN / 2) + c * 32) +
                               ((uint32_t)(quarter * 32) << 16),
                           v);
-                if (!row_ok) continue;
                 const int jmax = (col_lim - col0 >= 32) ? 32 : (int)(col_lim - col0);
                 // offsets from here are below 32 * col_stride < 2^32
                 const int64_t e0 = rbase + (int64_t)(c * 32) * col_stride;
-                if (out_kind == 0) {
-                    bf16 *o0 = (bf16 *)out_ptr + e0;
-                    bf16 *o1 = o0 + a.out_ps;
-                    bf16 *o2 = o1 + a.out_ps;
+                // The first tile of a fused stage pair keeps per-element stores:
+                // the second tile's thread reads its own values back.
+                const bool readback = a.ksplit == 1 && a.epi == 1 && tc.s == a.fuse_spair;
+                if (out_kind == 0 || (a.ksplit > 1 || a.epi == 0 ||
+                                      (a.epi == 1 && !readback && tc.s - a.S / 2 != a.fuse_spair))) {
+                    // Plain outputs, as pairs of rows: adjacent rows are adjacent
+                    // elements held by lanes 2k, 2k+1; one exchange gives the even
+                    // lane rows (r, r+1) of column j and the odd lane rows
+                    // (r-1, r) of column j+1, stored as one 4-byte (BF16 planes) or
+                    // 8-byte (FP32) access.  Row bounds are even, so both rows of a
+                    // pair are in range or neither; every lane takes part in the
+                    // exchange.
+                    const int odd = lane & 1;
+                    const int64_t eb = e0 - odd;
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        if (j < jmax) {
-                            bf16 p0, p1, p2;
-                            split3f(__uint_as_float(v[j]) * a.alpha, p0, p1, p2);
-                            const uint32_t off = (uint32_t)j * col_stride;
-                            o0[off] = p0;
-                            o1[off] = p1;
-                            o2[off] = p2;
+                    for (int j = 0; j < 32; j += 2) {
+                        const float a0 = __uint_as_float(v[j]) * a.alpha;
+                        const float a1 = __uint_as_float(v[j + 1]) * a.alpha;
+                        const float recv = __shfl_xor_sync(0xffffffffu, odd ? a0 : a1, 1);
+                        const float x0 = odd ? recv : a0, x1 = odd ? a1 : recv;
+                        const int jj = j + odd;
+                        if (row_ok && jj < jmax) {
+                            const uint32_t off = (uint32_t)jj * col_stride;
+                            if (out_kind == 0) {
+                                uint32_t q0, q1, q2;
+                                split3_pair(x0, x1, q0, q1, q2);
+                                uint32_t *w0 = (uint32_t *)((bf16 *)out_ptr + eb + off);
+                                w0[0] = q0;
+                                *(uint32_t *)((bf16 *)out_ptr + eb + off + a.out_ps) = q1;
+                                *(uint32_t *)((bf16 *)out_ptr + eb + off + 2 * a.out_ps) = q2;
+                            } else {
+                                *(float2 *)((float *)out_ptr + eb + off) = make_float2(x0, x1);
+                            }
                         }
                     }
-                } else if (a.ksplit > 1 || a.epi == 0 ||
-                           (a.epi == 1 && (tc.s < a.S / 2 || tc.s - a.S / 2 != a.fuse_spair))) {
-                    // FP32 output (split-K partials; plain; the first tile of a
-                    // fused pair, whose values the second tile reads back)
+                    continue;
+                }
+                if (!row_ok) continue;
+                if (readback) {
                     float *o = (float *)out_ptr + e0;
 #pragma unroll
                     for (int j = 0; j < 32; ++j)
@@ -847,9 +893,11 @@ __device__ __forceinline__ void react_df(const ModelDF &m, dfl u, dfl v, float &
         gu = df_val(df_mul(m.p[0], df_add(df_add(m.p[1], df_neg(u)), u2v)));
         gv = df_val(df_mul(m.p[0], df_add(m.p[2], df_neg(u2v))));
     } else if (m.model == DS_FHN) {
-        const dfl u3 = df_mul(df_mul(u, u), u);
-        gu = df_val(df_add(df_add(u, df_neg(u3)), df_neg(v)));
-        gv = df_val(df_mul(m.p[0], df_add(df_add(u, df_neg(df_mul(m.p[1], v))), df_neg(m.p[2]))));
+        // FitzHugh-Nagumo: O(1) terms and no large factor, so FP32 from the
+        // hi + lo value errs by ~2^-24 absolute, far below F's own rounding
+        const float uf = u.hi + u.lo, vf = v.hi + v.lo;
+        gu = (uf - uf * uf * uf) - vf;
+        gv = m.p[0].hi * ((uf - m.p[1].hi * vf) - m.p[2].hi);
     } else {
         gu = 0.0f;
         gv = 0.0f;
@@ -1207,6 +1255,7 @@ static bool make_map(CUtensorMap *m, const void *ptr, int rank, const uint64_t *
 struct ModeLaunch {
     TcArgs args;
     bool mode1 = false;
+    int bn = 256;              // output tile width (columns): 256 or 128
     int grid = 0;
     int64_t base_tiles = 0;    // output tiles before the split-K factor
     int64_t N = 0;             // points per output combo
@@ -1232,8 +1281,10 @@ static int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 //   out: planes [S][3][N] (out_kind 0) or FP32 [S][N] (out_kind 1)
 static ds_status describe(ModeLaunch &L, int d, const int64_t *n, int mu, const bf16 *X, int xcombos,
                           const bf16 *P, int pcombos, int ldp, int S, int T, int xs_stride, int xs_div,
-                          void *out, int out_kind, float alpha, DevStatus *status)
+                          void *out, int out_kind, float alpha, DevStatus *status, int bn = 256)
 {
+    const int BN = bn;
+    L.bn = bn;
     int64_t N = 1;
     for (int q = 0; q < d; ++q) N *= n[q];
     int64_t I = 1, O = 1;
@@ -1252,7 +1303,7 @@ static ds_status describe(ModeLaunch &L, int d, const int64_t *n, int mu, const 
         uint32_t pb[4] = {BK, BM, 1, 1};
         uint64_t xd[4] = {(uint64_t)nm, (uint64_t)R, 3, (uint64_t)xcombos};
         uint64_t xs[3] = {nm * e2, N * e2, 3 * N * e2};
-        uint32_t xb[4] = {BK, BN, 1, 1};
+        uint32_t xb[4] = {BK, (uint32_t)BN, 1, 1};
         ok = make_map(&a.tmA, P, 4, pd, ps, pb, CU_TENSOR_MAP_SWIZZLE_64B) &&
              make_map(&a.tmB, X, 4, xd, xs, xb, CU_TENSOR_MAP_SWIZZLE_64B);
         a.mtiles = (int)cdiv(nm, BM);
@@ -1267,7 +1318,7 @@ static ds_status describe(ModeLaunch &L, int d, const int64_t *n, int mu, const 
         uint32_t xb[5] = {64, BK, 1, 1, 1};
         uint64_t pd[4] = {(uint64_t)nm, (uint64_t)nm, 3, (uint64_t)pcombos};
         uint64_t ps[3] = {ldp * e2, nm * ldp * e2, 3 * nm * ldp * e2};
-        uint32_t pb[4] = {BK, BN, 1, 1};
+        uint32_t pb[4] = {BK, (uint32_t)BN, 1, 1};
         ok = make_map(&a.tmA, X, 5, xd, xs, xb, CU_TENSOR_MAP_SWIZZLE_128B) &&
              make_map(&a.tmB, P, 4, pd, ps, pb, CU_TENSOR_MAP_SWIZZLE_64B);
         a.mtiles = (int)cdiv(I, BM);
@@ -1419,8 +1470,14 @@ static void launch(const ModeLaunch &L, cudaStream_t st, double *U = nullptr, co
 {
     static std::once_flag once;
     std::call_once(once, [] {
-        cudaFuncSetAttribute(k_mode_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-        cudaFuncSetAttribute(k_mode_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+        cudaFuncSetAttribute(k_mode_tc<true, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             TileCfg<256>::SMEM_BYTES);
+        cudaFuncSetAttribute(k_mode_tc<false, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             TileCfg<256>::SMEM_BYTES);
+        cudaFuncSetAttribute(k_mode_tc<true, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             TileCfg<128>::SMEM_BYTES);
+        cudaFuncSetAttribute(k_mode_tc<false, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             TileCfg<128>::SMEM_BYTES);
     });
     if (L.args.num_tiles <= 0) return;
     TcArgs a = L.args;
@@ -1428,10 +1485,17 @@ static void launch(const ModeLaunch &L, cudaStream_t st, double *U = nullptr, co
         a.U = U;
         if (model) a.model = *model;
     }
-    if (L.mode1)
-        k_mode_tc<true><<<L.grid, kThreads, SMEM_BYTES, st>>>(a);
-    else
-        k_mode_tc<false><<<L.grid, kThreads, SMEM_BYTES, st>>>(a);
+    if (L.bn == 256) {
+        if (L.mode1)
+            k_mode_tc<true, 256><<<L.grid, kThreads, TileCfg<256>::SMEM_BYTES, st>>>(a);
+        else
+            k_mode_tc<false, 256><<<L.grid, kThreads, TileCfg<256>::SMEM_BYTES, st>>>(a);
+    } else {
+        if (L.mode1)
+            k_mode_tc<true, 128><<<L.grid, kThreads, TileCfg<128>::SMEM_BYTES, st>>>(a);
+        else
+            k_mode_tc<false, 128><<<L.grid, kThreads, TileCfg<128>::SMEM_BYTES, st>>>(a);
+    }
     if (a.ksplit > 1) {
         const int64_t total = a.part_stride;
         const int g = (int)std::min<int64_t>((total + 255) / 256, 152 * 8);
@@ -1466,7 +1530,8 @@ static bool g_tune_loaded = false;
 // variable DS_TUNE_CACHE names a file, its lines "mode1 n S T I O ksplit" are
 // loaded once (caller holds g_tune_mu) and every new choice is appended, so a
 // later process (a profiler run, say) replays the same launch configuration.
-// Line format: "mode1 n S T I O epi ksplit".
+// Line format: "mode1 n S T I O epi choice", choice = ksplit | (narrow tile << 4)
+// (for the fusion records, epi = 10 + group: 1 separate, 2 fused).
 static void tune_cache_load()
 {
     if (g_tune_loaded) return;
@@ -1478,7 +1543,8 @@ static void tune_cache_load()
     int m1, n, S, T, epi, k;
     long long I, O;
     while (fscanf(f, "%d %d %d %d %lld %lld %d %d", &m1, &n, &S, &T, &I, &O, &epi, &k) == 8)
-        if (k >= 1 && k <= 8) g_tuned[ShapeKey{m1 != 0, n, S, T, (int64_t)I, (int64_t)O, epi}] = k;
+        if ((k & 15) >= 1 && (k & 15) <= 8 && (k >> 4) <= 1)
+            g_tuned[ShapeKey{m1 != 0, n, S, T, (int64_t)I, (int64_t)O, epi}] = k;
     fclose(f);
 }
 
@@ -1523,39 +1589,48 @@ static float time_launch(const ModeLaunch &L, cudaStream_t st, cudaEvent_t e0, c
     return best;
 }
 
-// U: a scratch FP64 state [2][N] for the fused launches' epilogues
-static int autotune_split(ModeLaunch &L, float *ws, cudaStream_t st, float *times, double *U)
+// Tile width and split-K factor of one launch.  c[0] / c[1]: the launch
+// described with 256- / 128-column tiles (same operands).  Every (width,
+// split) pair within max_split is timed on the launch's own buffers (U: a
+// scratch FP64 state for fused epilogues); a narrower tile or a larger split
+// has to win by 3 %.  times[w * 8 + k - 1] receives the timings (0 = not
+// tried).  Returns k | (w << 4); cached per shape (and in DS_TUNE_CACHE).
+static int autotune_launch(ModeLaunch *c, float *ws, cudaStream_t st, float *times, double *U)
 {
-    const ShapeKey key{L.mode1, L.args.n, L.args.S, L.args.T, L.args.I, L.args.O, L.args.epi};
+    const ModeLaunch &L0 = c[0];
+    const ShapeKey key{L0.mode1, L0.args.n, L0.args.S, L0.args.T, L0.args.I, L0.args.O, L0.args.epi};
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         tune_cache_load();
         auto it = g_tuned.find(key);
-        if (it != g_tuned.end()) return std::min(it->second, max_split(L));
+        if (it != g_tuned.end()) {
+            const int w = (it->second >> 4) & 1;
+            return std::min(it->second & 15, max_split(c[w])) | (w << 4);
+        }
     }
-    const int kmax = max_split(L);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best_ms = 1e30f;
     int best = 1;
-    if (kmax > 1) {
-        cudaEvent_t e0, e1;
-        cudaEventCreate(&e0);
-        cudaEventCreate(&e1);
-        float best_ms = 1e30f;
+    for (int w = 0; w < 2; ++w) {
+        const int kmax = max_split(c[w]);
         for (int k = 1; k <= kmax; ++k) {
-            set_split(L, k, ws);
-            const float ms = time_launch(L, st, e0, e1, U);
-            if (times) times[k - 1] = ms;
-            // a larger split has to win by 3%: it adds partial traffic
+            set_split(c[w], k, k > 1 ? ws : nullptr);
+            const float ms = time_launch(c[w], st, e0, e1, U);
+            if (times) times[w * 8 + k - 1] = ms;
             if (ms < best_ms * 0.97f) {
                 best_ms = ms;
-                best = k;
+                best = k | (w << 4);
             }
         }
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
+        set_split(c[w], 1, nullptr);
     }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tuned[key] = best;
-    if (kmax > 1) tune_cache_append(key, best);
+    tune_cache_append(key, best);
     return best;
 }
 
@@ -1591,7 +1666,7 @@ struct MixedPlan {
     float *bands = nullptr;    // FP32 bands [c][mu][lo, up, rowsum][n_mu]
     bool rhs_tiled = false;    // k_rhs_tiled (d <= 3) instead of k_rhs_planes
     float *part_ws = nullptr;  // split-K partials
-    float tune_ms[3][kMaxD][8];  // autotuner: time of each split-K candidate (0 = not tried)
+    float tune_ms[3][kMaxD][16];  // autotuner: time of each (tile width, split) candidate (0 = not tried)
     StencilF stf[2];
     // launches[group][mode], both components in one launch;
     // group 0 = F, 1 = D2 (slot 2), 2 = D3 (slot 4).  The last mode's launch
@@ -1600,6 +1675,9 @@ struct MixedPlan {
     // two the plan runs (the faster at creation), fuse_ms[g] = {fused, separate}.
     ModeLaunch L[3][kMaxD];
     ModeLaunch Lsep[3];
+    // candidates per tile width (0: 256 columns, 1: 128), before tuning
+    ModeLaunch C[3][kMaxD][2];
+    ModeLaunch Csep[3][2];
     bool fused[3] = {true, true, true};
     float fuse_ms[3][2] = {};
 };
@@ -1823,19 +1901,24 @@ ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatu
                 if (mu == 0) { xs = 1; xdiv = S / 2; T = 1; }   // not reached for d >= 2
                 out = g == 0 ? (void *)mp->incF : (void *)mp->incD;
             }
-            r = describe(mp->L[g][mu], d, mp->n, mu, X, xcombos, P, 2 * S0, ldp, S, T, xs, xdiv, out, kind,
-                         1.0f, status);
-            if (r != DS_OK) { mixed_plan_destroy(mp); return r; }
-            // the last mode's epilogue does the pointwise work of the stage:
-            //   F:  D2 = g(U + tau/3 S_2(F)) - g(U)                     (s = c * 3 + stage)
-            //   D2: D3 = g(U + 2tau/3 S_3(F) + 4tau/3 S_3(D2)) - g(U)   (s = c)
-            //   D3: U += tau S_f(F) + 3tau/2 S_f(D3)
-            if (last) {
-                mp->Lsep[g] = mp->L[g][mu];
-                if (g == 0) set_fused(mp->L[g][mu], 1, nullptr, 0, mp->Dp);
-                else if (g == 1) set_fused(mp->L[g][mu], 1, mp->incF + N, 3 * N, mp->Dp);
-                else set_fused(mp->L[g][mu], 2, mp->incF + 2 * N, 3 * N, nullptr);
+            for (int w = 0; w < 2; ++w) {
+                ModeLaunch &Cw = mp->C[g][mu][w];
+                r = describe(Cw, d, mp->n, mu, X, xcombos, P, 2 * S0, ldp, S, T, xs, xdiv, out, kind, 1.0f,
+                             status, w ? 128 : 256);
+                if (r != DS_OK) { mixed_plan_destroy(mp); return r; }
+                // the last mode's epilogue does the pointwise work of the stage:
+                //   F:  D2 = g(U + tau/3 S_2(F)) - g(U)                     (s = c * 3 + stage)
+                //   D2: D3 = g(U + 2tau/3 S_3(F) + 4tau/3 S_3(D2)) - g(U)   (s = c)
+                //   D3: U += tau S_f(F) + 3tau/2 S_f(D3)
+                if (last) {
+                    mp->Csep[g][w] = Cw;
+                    if (g == 0) set_fused(Cw, 1, nullptr, 0, mp->Dp);
+                    else if (g == 1) set_fused(Cw, 1, mp->incF + N, 3 * N, mp->Dp);
+                    else set_fused(Cw, 2, mp->incF + 2 * N, 3 * N, nullptr);
+                }
             }
+            mp->L[g][mu] = mp->C[g][mu][0];
+            if (last) mp->Lsep[g] = mp->Csep[g][0];
         }
     }
     if (cudaDeviceSynchronize() != cudaSuccess) return cleanup(DS_ERR_CUDA, "phi plane split");
@@ -1847,7 +1930,8 @@ ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatu
             if (max_split(L) > 1) ws_elems = std::max<int64_t>(ws_elems, max_split(L) * L.args.part_stride);
         };
         for (int g = 0; g < 3; ++g)
-            for (int mu = 0; mu < d; ++mu) need(mp->L[g][mu]);
+            for (int mu = 0; mu < d; ++mu)
+                for (int w = 0; w < 2; ++w) need(mp->C[g][mu][w]);
         if (ws_elems > 0 && cudaMalloc(&mp->part_ws, sizeof(float) * ws_elems) != cudaSuccess) {
             cudaGetLastError();
             return cleanup(DS_ERR_OOM, "split-K workspace");
@@ -1863,14 +1947,18 @@ ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatu
         cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking);
         for (int g = 0; g < 3; ++g) {
             for (int mu = 0; mu < d; ++mu) {
+                const int code = autotune_launch(mp->C[g][mu], mp->part_ws, ts, mp->tune_ms[g][mu], Us);
+                const int w = code >> 4, k = code & 15;
                 ModeLaunch &L = mp->L[g][mu];
-                const int k = autotune_split(L, mp->part_ws, ts, mp->tune_ms[g][mu], Us);
+                L = mp->C[g][mu][w];
                 set_split(L, k, k > 1 ? mp->part_ws : nullptr);
+                // the separate form of the last mode runs the same contraction
+                // with the same tiles and split, so both forms give identical values
+                if (mu == d - 1) {
+                    mp->Lsep[g] = mp->Csep[g][w];
+                    set_split(mp->Lsep[g], k, k > 1 ? mp->part_ws : nullptr);
+                }
             }
-            // the separate form runs the same contraction with the same split
-            // factor, so both forms give identical values
-            const int k = mp->L[g][d - 1].args.ksplit;
-            set_split(mp->Lsep[g], k, k > 1 ? mp->part_ws : nullptr);
         }
         decide_fusion(mp, ts, Us);
         cudaStreamSynchronize(ts);
@@ -1891,6 +1979,22 @@ int mixed_plan_fusion(const MixedPlan *mp, int g, int *fused, float *ms_fused, f
     return 0;
 }
 
+int mixed_plan_set_tiles(MixedPlan *mp, int g, int mu, int tile_n, int ksplit)
+{
+    if (!mp || g < 0 || g > 2 || mu < 0 || mu >= mp->d || (tile_n != 256 && tile_n != 128)) return -1;
+    const int w = tile_n == 128 ? 1 : 0;
+    ModeLaunch &C = mp->C[g][mu][w];
+    // the split-K workspace was sized for the autotuner's range
+    if (ksplit < 1 || ksplit > max_split(C) || (ksplit > 1 && !mp->part_ws)) return -2;
+    mp->L[g][mu] = C;
+    set_split(mp->L[g][mu], ksplit, ksplit > 1 ? mp->part_ws : nullptr);
+    if (mu == mp->d - 1) {
+        mp->Lsep[g] = mp->Csep[g][w];
+        set_split(mp->Lsep[g], ksplit, ksplit > 1 ? mp->part_ws : nullptr);
+    }
+    return 0;
+}
+
 int mixed_plan_set_fusion(MixedPlan *mp, int g, int fused)
 {
     if (!mp || g < 0 || g > 2) return -1;
@@ -1898,13 +2002,14 @@ int mixed_plan_set_fusion(MixedPlan *mp, int g, int fused)
     return 0;
 }
 
-int mixed_plan_tuning(const MixedPlan *mp, int g, int mu, int *ksplit, int64_t *tiles, float *times)
+int mixed_plan_tuning(const MixedPlan *mp, int g, int mu, int *ksplit, int64_t *tiles, int *tile_n, float *times)
 {
     if (!mp || g < 0 || g > 2 || mu < 0 || mu >= mp->d) return -1;
     const ModeLaunch &L = mp->L[g][mu];
     *ksplit = L.args.ksplit;
     *tiles = L.base_tiles;
-    for (int k = 0; k < 8; ++k) times[k] = mp->tune_ms[g][mu][k];
+    *tile_n = L.bn;
+    for (int k = 0; k < 16; ++k) times[k] = mp->tune_ms[g][mu][k];
     return 0;
 }
 

@@ -13,9 +13,10 @@ ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatu
 void mixed_plan_destroy(MixedPlan *mp);
 // autotuner record of launch (group g, mode mu): chosen split, output tiles,
 // candidate times in ms (0 = not tried); -1 on bad indices
-int mixed_plan_tuning(const MixedPlan *mp, int g, int mu, int *ksplit, int64_t *tiles, float *times);
+int mixed_plan_tuning(const MixedPlan *mp, int g, int mu, int *ksplit, int64_t *tiles, int *tile_n, float *times);
 int mixed_plan_fusion(const MixedPlan *mp, int g, int *fused, float *ms_fused, float *ms_separate);
 int mixed_plan_set_fusion(MixedPlan *mp, int g, int fused);
+int mixed_plan_set_tiles(MixedPlan *mp, int g, int mu, int tile_n, int ksplit);
 // Enqueue one EXPRK3DS_REAL step on the split-BF16 path; returns the number
 // of kernel launches, or -1 on failure.
 int enqueue_step_mixed(MixedPlan *mp, const ds_phi_set *set, const Model &model,

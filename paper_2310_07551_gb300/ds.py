@@ -72,6 +72,10 @@ def lib() -> ctypes.CDLL:
                                 ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
             "ds_plan_profile_read": ([_vp, _dp, ctypes.POINTER(ctypes.c_int64), _dp], ctypes.c_int),
             "ds_plan_set_fusion": ([_vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+            "ds_plan_set_tiles": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+            "ds_plan_tuning_ex": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                   ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int),
+                                   ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
             "ds_plan_fusion": ([_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float),
                                 ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
             "ds_plan_profile_read_ex": ([_vp, _dp, ctypes.POINTER(ctypes.c_int64), _dp, _dp], ctypes.c_int),
@@ -223,6 +227,11 @@ class Plan:
             out.append((g, bool(fz.value), float(a.value), float(b.value)))
         return out
 
+    def set_tiles(self, group: int, mode: int, tile_n: int, ksplit: int = 1):
+        """Override the autotuner for the launch of group (0 F, 1 D2, 2 D3)
+        and mode (1-based): output tile width 256 or 128, split-K factor."""
+        check(lib().ds_plan_set_tiles(self._h, int(group), int(mode) - 1, int(tile_n), int(ksplit)))
+
     def set_fusion(self, group: int, fused: bool):
         check(lib().ds_plan_set_fusion(self._h, int(group), int(bool(fused))))
 
@@ -230,17 +239,20 @@ class Plan:
         check(lib().ds_plan_sync(self._h, _dptr(U) if U is not None else None, int(check_state)))
 
     def tuning(self):
-        """Autotuner record: [(group, mode, ksplit, tiles, {split: ms})] for
-        split-BF16 plans."""
+        """Autotuner record: [(group, mode, ksplit, tiles, tile_n, {"<tile_n>x<split>": ms})]
+        for split-BF16 plans."""
         out = []
         for g in range(3):
             for mu in range(len(self.dims)):
                 k = ctypes.c_int()
                 t = ctypes.c_int64()
-                ms = (ctypes.c_float * 8)()
-                check(lib().ds_plan_tuning(self._h, g, mu, ctypes.byref(k), ctypes.byref(t), ms))
-                out.append((g, mu + 1, k.value, t.value,
-                            {i + 1: round(ms[i], 4) for i in range(8) if ms[i] > 0}))
+                tn = ctypes.c_int()
+                ms = (ctypes.c_float * 16)()
+                check(lib().ds_plan_tuning_ex(self._h, g, mu, ctypes.byref(k), ctypes.byref(t),
+                                              ctypes.byref(tn), ms))
+                out.append((g, mu + 1, k.value, t.value, tn.value,
+                            {f"{256 if i < 8 else 128}x{i % 8 + 1}": round(ms[i], 4)
+                             for i in range(16) if ms[i] > 0}))
         return out
 
     def profile(self, enable: bool = True):

@@ -121,3 +121,31 @@ def test_fused_epilogues_match_separate_kernels_bitwise(ds, dims, model, p, lo, 
         plan.sync(U, check_state=True)
         out.append(U.cpu().numpy())
     assert np.array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("dims,model,p,lo,hi,delta,tau", [
+    ((40, 33, 70), "fhn", (0.1, 2.0, -0.1), -1.0, 1.0, (1.0, 42.1887), 1e-3),
+    ((136, 40), "schnakenberg", (1000.0, 0.1, 0.9), 0.0, 1.0, (1.0, 10.0), 1e-4),
+    ((24, 16, 12, 10), "fhn", (0.1, 2.0, -0.1), -1.0, 1.0, (1.0, 5.0), 1e-3),
+])
+def test_tile_widths_agree_bitwise(ds, dims, model, p, lo, hi, delta, tau):
+    """128- and 256-column output tiles change which CTA computes an element,
+    not the order of its sums: with split-K off, results agree bit for bit
+    (and both are within the oracle tolerance of the other tests)."""
+    As = problem(dims, lo, hi, delta)
+    U0 = inputs.initial_state(model, dims, seed=4)
+    ps = ds.PhiSet(dims, As, tau)
+    plan = ds.Plan(ps, model, p, "bf16x6")
+    out = []
+    for tn in (256, 128):
+        for g in range(3):
+            for mode in range(1, len(dims) + 1):
+                plan.set_tiles(g, mode, tn, 1)
+        assert all(t[4] == tn and t[2] == 1 for t in plan.tuning())
+        U = torch.from_numpy(U0.copy()).cuda()
+        plan.integrate(U, 3)
+        plan.sync(U, check_state=True)
+        out.append(U.cpu().numpy())
+    assert np.array_equal(out[0], out[1])
+    with pytest.raises(ds.DsError):
+        plan.set_tiles(0, 1, 192, 1)
