@@ -62,8 +62,14 @@ typedef enum {
  *                    parts x = x0 + x1 + x2; the six partial products of
  *                    weight >= 2^-16 run on the tcgen05 tensor cores with FP32
  *                    accumulation in tensor memory.  The state u_{n+1}, the
- *                    stage sums and the phi-matrices stay FP64. */
-typedef enum { DS_PREC_F64 = 0, DS_PREC_BF16X6 = 1, DS_PREC_F32 = 2 } ds_precision;
+ *                    stage sums and the phi-matrices stay FP64.
+ *   DS_PREC_BF16X6C: DS_PREC_BF16X6 with compensated accumulation: the main
+ *                    product x0 y0 and the five cross products accumulate in
+ *                    two tensor-memory accumulators, added with
+ *                    round-to-nearest.  The tensor core's accumulation
+ *                    truncates; this keeps its bias about six times smaller
+ *                    (128-column tiles, same arithmetic otherwise). */
+typedef enum { DS_PREC_F64 = 0, DS_PREC_BF16X6 = 1, DS_PREC_F32 = 2, DS_PREC_BF16X6C = 3 } ds_precision;
 
 /* Reaction term g of the two-component systems (Section 3).
  *   DS_SCHNAKENBERG, p = (gamma, a, b):
@@ -159,7 +165,7 @@ ds_status ds_phi_get_ex(const ds_phi_set *set, int c, int slot, int term, int mu
  *   L: host array of d device pointers to column-major n_mu x n_mu FP64
  *      matrices (L[0] is L_1).
  *   transpose = 1 uses L_mu^T instead of L_mu (the adjoint operator).
- *   precision: DS_PREC_F64, DS_PREC_F32 or DS_PREC_BF16X6 (the latter needs
+ *   precision: DS_PREC_F64, DS_PREC_F32, DS_PREC_BF16X6 or DS_PREC_BF16X6C (the latter two need
  *      n_1 % 8 == 0; for both reduced precisions intermediates are FP32 and
  *      Y is written in FP64).
  *   Temporary device memory is allocated per call and released before the

@@ -728,7 +728,8 @@ ds_status ds_tucker(const ds_grid *grid, const double *X, double *Y, const doubl
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t N = numel(grid);
     const int d = grid->d;
-    if (precision == DS_PREC_BF16X6) return tc::tucker_mixed(grid, X, Y, L, transpose, st);
+    if (precision == DS_PREC_BF16X6 || precision == DS_PREC_BF16X6C)
+        return tc::tucker_mixed(grid, X, Y, L, transpose, st, precision == DS_PREC_BF16X6C);
     if (precision == DS_PREC_F32) {
         int64_t pm = 0;
         for (int mu = 0; mu < d; ++mu) pm += grid->n[mu] * grid->n[mu];
@@ -788,7 +789,8 @@ ds_status ds_plan_create(const ds_grid *grid, const ds_params *params, const ds_
         if (params->model < 0 || params->model > 2) return fail(DS_ERR_INVALID_ARG, "unknown model");
         for (int q = 0; q < 8; ++q)
             if (!isfinite(params->p[q])) return fail(DS_ERR_INVALID_ARG, "non-finite model parameter");
-        if (precision != DS_PREC_F64 && precision != DS_PREC_BF16X6 && precision != DS_PREC_F32)
+        if (precision != DS_PREC_F64 && precision != DS_PREC_BF16X6 && precision != DS_PREC_F32 &&
+            precision != DS_PREC_BF16X6C)
             return fail(DS_ERR_UNSUPPORTED, "unknown precision");
         if (set->scheme != DS_EXPRK3DS_REAL && precision != DS_PREC_F64)
             return fail(DS_ERR_UNSUPPORTED, "ETD2RKDS, EXPRK3DS_CPLX and dense EXPRK3 plans are FP64 only");
@@ -835,7 +837,7 @@ ds_status ds_plan_create(const ds_grid *grid, const ds_params *params, const ds_
             }
             tc::launch_convert_f64_f32(set->P_count, set->P_dev, p->P32, 0);
         } else {
-            r = tc::mixed_plan_create(grid, set, p->status, &p->mixed);
+            r = tc::mixed_plan_create(grid, set, p->status, &p->mixed, precision == DS_PREC_BF16X6C);
             if (r != DS_OK) { ds_plan_destroy(p); return r; }
         }
         cudaDeviceSynchronize();

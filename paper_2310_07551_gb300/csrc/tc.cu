@@ -411,10 +411,18 @@ __device__ __forceinline__ TileCoord work_item(const TcArgs &a, int64_t unit, in
     return c;
 }
 
-template <bool MODE1, int BNT>
+// DUAL (128-column tiles only): the main product a0 b0 and the five cross
+// products accumulate in two TMEM accumulators that the epilogue adds with
+// round-to-nearest.  The tensor core's FP32 accumulation truncates toward
+// zero; with one accumulator every one of the six products per 16-wide K
+// step truncates at the scale of the full sum, with two the cross products
+// truncate at ~2^-8 of it, so the bias drops about sixfold.
+template <bool MODE1, int BNT, bool DUAL>
 __global__ void __launch_bounds__(kThreads, 1) k_mode_tc(const __grid_constant__ TcArgs a)
 {
+    static_assert(!DUAL || BNT == 128, "dual accumulators need 128-column tiles");
     constexpr int BN = BNT;
+    constexpr uint32_t ACC_COLS = DUAL ? 2 * BNT : BNT;   // TMEM columns per accumulator buffer
     constexpr int STAGES = TileCfg<BNT>::STAGES;
     constexpr uint32_t B_PLANE = TileCfg<BNT>::B_PLANE;
     constexpr uint32_t STAGE_BYTES = TileCfg<BNT>::STAGE_BYTES;
@@ -518,7 +526,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mode_tc(const __grid_constant__
             for (int64_t wi = first_item(a); ok && wi < a.num_tiles; wi = next_item(a, wi)) {
                 if (!wait_bar(TEMPTY(acc), acc_phase ^ 1u, abort_flag, a.status, 2)) break;
                 tc_fence_after();
-                const uint32_t d = tmem + (uint32_t)acc * BN;
+                const uint32_t d = tmem + (uint32_t)acc * ACC_COLS;
                 const int part = (int)((wi / a.npair) % a.ksplit);
                 const int it0 = part * a.kpi, it1 = min(it0 + a.kpi, kiters);
                 for (int it = it0; it < it1; ++it) {
@@ -538,7 +546,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_mode_tc(const __grid_constant__
                                 ad = sdesc(sA + pa * A_PLANE + ks * 2048, A_PLANE / 2, 1024, kSw128);
                             }
                             bd = sdesc(sB + pb * B_PLANE + ks * 32, 16, 512, kSw64);
-                            mma_bf16(d, ad, bd, idesc, (it > it0 || ks > 0 || q > 0) ? 1u : 0u);
+                            if (DUAL) {
+                                const bool first = it == it0 && ks == 0 && (q == 0 || q == 1);
+                                mma_bf16(q == 0 ? d : d + BN, ad, bd, idesc, first ? 0u : 1u);
+                            } else {
+                                mma_bf16(d, ad, bd, idesc, (it > it0 || ks > 0 || q > 0) ? 1u : 0u);
+                            }
                         }
                     }
                     mma_commit(EMPTY(stage));
@@ -601,9 +614,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_mode_tc(const __grid_constant__
                 const int64_t col0 = cbase + c * 32;
                 if (col0 >= col_lim) break;
                 uint32_t v[32];
-                tmem_ld32(tmem + (uint32_t)acc * BN + (uint32_t)(half * (BN / 2) + c * 32) +
-                              ((uint32_t)(quarter * 32) << 16),
-                          v);
+                const uint32_t taddr = tmem + (uint32_t)acc * ACC_COLS + (uint32_t)(half * (BN / 2) + c * 32) +
+                                       ((uint32_t)(quarter * 32) << 16);
+                tmem_ld32(taddr, v);
+                if (DUAL) {
+                    uint32_t w[32];
+                    tmem_ld32(taddr + BN, w);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        v[j] = __float_as_uint(__uint_as_float(v[j]) + __uint_as_float(w[j]));
+                }
                 const int jmax = (col_lim - col0 >= 32) ? 32 : (int)(col_lim - col0);
                 // offsets from here are below 32 * col_stride < 2^32
                 const int64_t e0 = rbase + (int64_t)(c * 32) * col_stride;
@@ -1256,6 +1276,7 @@ struct ModeLaunch {
     TcArgs args;
     bool mode1 = false;
     int bn = 256;              // output tile width (columns): 256 or 128
+    bool dual = false;         // two accumulators (128-column tiles, compensated precision)
     int grid = 0;
     int64_t base_tiles = 0;    // output tiles before the split-K factor
     int64_t N = 0;             // points per output combo
@@ -1281,10 +1302,12 @@ static int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 //   out: planes [S][3][N] (out_kind 0) or FP32 [S][N] (out_kind 1)
 static ds_status describe(ModeLaunch &L, int d, const int64_t *n, int mu, const bf16 *X, int xcombos,
                           const bf16 *P, int pcombos, int ldp, int S, int T, int xs_stride, int xs_div,
-                          void *out, int out_kind, float alpha, DevStatus *status, int bn = 256)
+                          void *out, int out_kind, float alpha, DevStatus *status, int bn = 256,
+                          bool dual = false)
 {
     const int BN = bn;
     L.bn = bn;
+    L.dual = dual && bn == 128;
     int64_t N = 1;
     for (int q = 0; q < d; ++q) N *= n[q];
     int64_t I = 1, O = 1;
@@ -1470,13 +1493,17 @@ static void launch(const ModeLaunch &L, cudaStream_t st, double *U = nullptr, co
 {
     static std::once_flag once;
     std::call_once(once, [] {
-        cudaFuncSetAttribute(k_mode_tc<true, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_mode_tc<true, 256, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              TileCfg<256>::SMEM_BYTES);
-        cudaFuncSetAttribute(k_mode_tc<false, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_mode_tc<false, 256, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              TileCfg<256>::SMEM_BYTES);
-        cudaFuncSetAttribute(k_mode_tc<true, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_mode_tc<true, 128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              TileCfg<128>::SMEM_BYTES);
-        cudaFuncSetAttribute(k_mode_tc<false, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_mode_tc<false, 128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             TileCfg<128>::SMEM_BYTES);
+        cudaFuncSetAttribute(k_mode_tc<true, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             TileCfg<128>::SMEM_BYTES);
+        cudaFuncSetAttribute(k_mode_tc<false, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              TileCfg<128>::SMEM_BYTES);
     });
     if (L.args.num_tiles <= 0) return;
@@ -1487,14 +1514,19 @@ static void launch(const ModeLaunch &L, cudaStream_t st, double *U = nullptr, co
     }
     if (L.bn == 256) {
         if (L.mode1)
-            k_mode_tc<true, 256><<<L.grid, kThreads, TileCfg<256>::SMEM_BYTES, st>>>(a);
+            k_mode_tc<true, 256, false><<<L.grid, kThreads, TileCfg<256>::SMEM_BYTES, st>>>(a);
         else
-            k_mode_tc<false, 256><<<L.grid, kThreads, TileCfg<256>::SMEM_BYTES, st>>>(a);
+            k_mode_tc<false, 256, false><<<L.grid, kThreads, TileCfg<256>::SMEM_BYTES, st>>>(a);
+    } else if (!L.dual) {
+        if (L.mode1)
+            k_mode_tc<true, 128, false><<<L.grid, kThreads, TileCfg<128>::SMEM_BYTES, st>>>(a);
+        else
+            k_mode_tc<false, 128, false><<<L.grid, kThreads, TileCfg<128>::SMEM_BYTES, st>>>(a);
     } else {
         if (L.mode1)
-            k_mode_tc<true, 128><<<L.grid, kThreads, TileCfg<128>::SMEM_BYTES, st>>>(a);
+            k_mode_tc<true, 128, true><<<L.grid, kThreads, TileCfg<128>::SMEM_BYTES, st>>>(a);
         else
-            k_mode_tc<false, 128><<<L.grid, kThreads, TileCfg<128>::SMEM_BYTES, st>>>(a);
+            k_mode_tc<false, 128, true><<<L.grid, kThreads, TileCfg<128>::SMEM_BYTES, st>>>(a);
     }
     if (a.ksplit > 1) {
         const int64_t total = a.part_stride;
@@ -1595,16 +1627,18 @@ static float time_launch(const ModeLaunch &L, cudaStream_t st, cudaEvent_t e0, c
 // scratch FP64 state for fused epilogues); a narrower tile or a larger split
 // has to win by 3 %.  times[w * 8 + k - 1] receives the timings (0 = not
 // tried).  Returns k | (w << 4); cached per shape (and in DS_TUNE_CACHE).
-static int autotune_launch(ModeLaunch *c, float *ws, cudaStream_t st, float *times, double *U)
+static int autotune_launch(ModeLaunch *c, int ncand, float *ws, cudaStream_t st, float *times, double *U)
 {
     const ModeLaunch &L0 = c[0];
-    const ShapeKey key{L0.mode1, L0.args.n, L0.args.S, L0.args.T, L0.args.I, L0.args.O, L0.args.epi};
+    // dual-accumulator launches are a different kernel: their own cache entries
+    const ShapeKey key{L0.mode1, L0.args.n, L0.args.S, L0.args.T, L0.args.I, L0.args.O,
+                       L0.args.epi + (L0.dual ? 32 : 0)};
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         tune_cache_load();
         auto it = g_tuned.find(key);
         if (it != g_tuned.end()) {
-            const int w = (it->second >> 4) & 1;
+            const int w = ((it->second >> 4) & 1) && ncand > 1 ? 1 : 0;
             return std::min(it->second & 15, max_split(c[w])) | (w << 4);
         }
     }
@@ -1613,7 +1647,7 @@ static int autotune_launch(ModeLaunch *c, float *ws, cudaStream_t st, float *tim
     cudaEventCreate(&e1);
     float best_ms = 1e30f;
     int best = 1;
-    for (int w = 0; w < 2; ++w) {
+    for (int w = 0; w < ncand; ++w) {
         const int kmax = max_split(c[w]);
         for (int k = 1; k <= kmax; ++k) {
             set_split(c[w], k, k > 1 ? ws : nullptr);
@@ -1679,6 +1713,7 @@ struct MixedPlan {
     ModeLaunch C[3][kMaxD][2];
     ModeLaunch Csep[3][2];
     bool fused[3] = {true, true, true};
+    bool compensated = false;
     float fuse_ms[3][2] = {};
 };
 
@@ -1707,7 +1742,8 @@ static void decide_fusion(MixedPlan *mp, cudaStream_t st, double *Us)
     const ModelF mf{DS_SCHNAKENBERG, {1.0f, 0.1f, 0.9f}};
     for (int g = 0; g < 3; ++g) {
         const ModeLaunch &F = mp->L[g][mp->d - 1], &S = mp->Lsep[g];
-        const ShapeKey key{F.mode1, F.args.n, F.args.S, F.args.T, F.args.I, F.args.O, 10 + g};
+        const ShapeKey key{F.mode1, F.args.n, F.args.S, F.args.T, F.args.I, F.args.O,
+                           10 + g + (F.dual ? 32 : 0)};
         {
             std::lock_guard<std::mutex> lk(g_tune_mu);
             tune_cache_load();
@@ -1748,13 +1784,15 @@ static void decide_fusion(MixedPlan *mp, cudaStream_t st, double *Us)
     cudaEventDestroy(e1);
 }
 
-ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatus *status, MixedPlan **out)
+ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatus *status, MixedPlan **out,
+                            bool compensated)
 {
     ds_status r = check_shape(set->d, set->n);
     if (r != DS_OK) return r;
     if (!encode_fn()) return fail(DS_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled unavailable");
     MixedPlan *mp = new MixedPlan();
     memset(mp->tune_ms, 0, sizeof(mp->tune_ms));
+    mp->compensated = compensated;
     mp->d = set->d;
     mp->k = set->k;
     mp->N = 1;
@@ -1903,8 +1941,9 @@ ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatu
             }
             for (int w = 0; w < 2; ++w) {
                 ModeLaunch &Cw = mp->C[g][mu][w];
+                // compensated plans have one candidate: 128-column tiles, two accumulators
                 r = describe(Cw, d, mp->n, mu, X, xcombos, P, 2 * S0, ldp, S, T, xs, xdiv, out, kind, 1.0f,
-                             status, w ? 128 : 256);
+                             status, (w || compensated) ? 128 : 256, compensated);
                 if (r != DS_OK) { mixed_plan_destroy(mp); return r; }
                 // the last mode's epilogue does the pointwise work of the stage:
                 //   F:  D2 = g(U + tau/3 S_2(F)) - g(U)                     (s = c * 3 + stage)
@@ -1947,7 +1986,8 @@ ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatu
         cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking);
         for (int g = 0; g < 3; ++g) {
             for (int mu = 0; mu < d; ++mu) {
-                const int code = autotune_launch(mp->C[g][mu], mp->part_ws, ts, mp->tune_ms[g][mu], Us);
+                const int code =
+                    autotune_launch(mp->C[g][mu], compensated ? 1 : 2, mp->part_ws, ts, mp->tune_ms[g][mu], Us);
                 const int w = code >> 4, k = code & 15;
                 ModeLaunch &L = mp->L[g][mu];
                 L = mp->C[g][mu][w];
@@ -1982,7 +2022,8 @@ int mixed_plan_fusion(const MixedPlan *mp, int g, int *fused, float *ms_fused, f
 int mixed_plan_set_tiles(MixedPlan *mp, int g, int mu, int tile_n, int ksplit)
 {
     if (!mp || g < 0 || g > 2 || mu < 0 || mu >= mp->d || (tile_n != 256 && tile_n != 128)) return -1;
-    const int w = tile_n == 128 ? 1 : 0;
+    if (mp->compensated && tile_n != 128) return -1;
+    const int w = tile_n == 128 && !mp->compensated ? 1 : 0;
     ModeLaunch &C = mp->C[g][mu][w];
     // the split-K workspace was sized for the autotuner's range
     if (ksplit < 1 || ksplit > max_split(C) || (ksplit > 1 && !mp->part_ws)) return -2;
@@ -2106,7 +2147,7 @@ static DevStatus *global_status()
 }
 
 ds_status tucker_mixed(const ds_grid *grid, const double *X, double *Y, const double *const *L,
-                       int transpose, cudaStream_t st)
+                       int transpose, cudaStream_t st, bool compensated)
 {
     const int d = grid->d;
     ds_status r = check_shape(d, grid->n);
@@ -2135,7 +2176,8 @@ ds_status tucker_mixed(const ds_grid *grid, const double *X, double *Y, const do
         const bool last = (mu == d - 1);
         void *out = last ? (void *)outf : (void *)bufs[mu % 2];
         ModeLaunch ml;
-        r = describe(ml, d, grid->n, mu, in, 1, pcur, 1, ldp, 1, 1, 0, 1, out, last ? 1 : 0, 1.0f, status);
+        r = describe(ml, d, grid->n, mu, in, 1, pcur, 1, ldp, 1, 1, 0, 1, out, last ? 1 : 0, 1.0f, status,
+                     compensated ? 128 : 256, compensated);
         if (r != DS_OK) { cudaFreeAsync(ws, st); return r; }
         launch(ml, st);
         in = bufs[mu % 2];

@@ -8,8 +8,9 @@ namespace tc {
 
 struct MixedPlan;
 
+// compensated: dual-accumulator 128-column tiles (DS_PREC_BF16X6C)
 ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatus *status,
-                            MixedPlan **out);
+                            MixedPlan **out, bool compensated = false);
 void mixed_plan_destroy(MixedPlan *mp);
 // autotuner record of launch (group g, mode mu): chosen split, output tiles,
 // candidate times in ms (0 = not tried); -1 on bad indices
@@ -31,7 +32,7 @@ void launch_final_f32(int64_t N, double *U, const float *a, double w1, const flo
 void launch_convert_f64_f32(int64_t n, const double *x, float *y, cudaStream_t st);
 void launch_convert_f32_f64(int64_t n, const float *x, double *y, cudaStream_t st);
 ds_status tucker_mixed(const ds_grid *grid, const double *X, double *Y, const double *const *L,
-                       int transpose, cudaStream_t st);
+                       int transpose, cudaStream_t st, bool compensated = false);
 
 }  // namespace tc
 }  // namespace ds
