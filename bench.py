@@ -41,7 +41,7 @@ UNIT = "grid-point*steps/s"
 # a changed kernel reports null.
 NCU_TRAFFIC = {
     # profiles/launches_*.md: mean over one step's k_mode_tc launches of read + write
-    "742789ac3e3024f8:schnak2d_1024": 1.088e8,
+    "293c42446f20c84a:fhn3d_256": 1.501e9,
 }
 
 

@@ -799,73 +799,6 @@ __device__ __forceinline__ double stencil_k(const Stencil &s, const double *U, i
     return acc;
 }
 
-// FP32 copy of the tridiagonal bands of one component.
-struct StencilF {
-    int d;
-    int64_t n[kMaxD];
-    const float *lo[kMaxD], *up[kMaxD], *rsum[kMaxD];   // rsum = lo + di + up
-    int has_rsum[kMaxD];
-    // r / n[mu] = (r * magic[mu]) >> shift[mu] for r < 2^31 (fast31: N < 2^31)
-    unsigned long long magic[kMaxD];
-    int shift[kMaxD];
-    int fast31;
-};
-
-// K u for one point of one component from hi/lo parts: each tridiagonal row
-// is written as lo (u_{i-1} - u_i) + up (u_{i+1} - u_i) + (lo + di + up) u_i,
-// with the differences formed as (h_a - h_b) + (l_a - l_b) in FP32, so the
-// cancellation of a smooth field costs no more than 2^-24 of the difference.
-__device__ __forceinline__ float stencil_hilo(const StencilF &s, const double *U, int64_t p, const int *idx,
-                                              float hc, float lc)
-{
-    float acc = 0.0f;
-    int64_t stride = 1;
-#pragma unroll
-    for (int mu = 0; mu < kMaxD; ++mu) {
-        if (mu < s.d) {
-            const int64_t nm = s.n[mu];
-            const int i = idx[mu];
-            float r = 0.0f;
-            if (i > 0) {
-                float h, l;
-                split_hilo(U[p - stride], h, l);
-                r = fmaf(s.lo[mu][i], (h - hc) + (l - lc), r);
-            }
-            if (i + 1 < nm) {
-                float h, l;
-                split_hilo(U[p + stride], h, l);
-                r = fmaf(s.up[mu][i], (h - hc) + (l - lc), r);
-            }
-            if (s.has_rsum[mu]) r = fmaf(s.rsum[mu][i], hc + lc, r);
-            acc += r;
-            stride *= nm;
-        }
-    }
-    return acc;
-}
-
-// grid coordinates of linear index p: multiply-shift division when the grid
-// has fewer than 2^31 points (no integer divide instruction on the GPU)
-__device__ __forceinline__ void coords(const StencilF &s, int64_t p, int *idx)
-{
-    if (s.fast31) {
-        uint32_t r = (uint32_t)p;
-#pragma unroll
-        for (int mu = 0; mu < kMaxD; ++mu) {
-            const uint32_t q = (uint32_t)(((unsigned long long)r * s.magic[mu]) >> s.shift[mu]);
-            idx[mu] = (int)(r - q * (uint32_t)s.n[mu]);
-            r = q;
-        }
-    } else {
-        int64_t r = p;
-#pragma unroll
-        for (int mu = 0; mu < kMaxD; ++mu) {
-            idx[mu] = (int)(r % s.n[mu]);
-            r /= s.n[mu];
-        }
-    }
-}
-
 // Double-float arithmetic (a value is an unevaluated sum hi + lo of two
 // floats): Knuth's two-sum and the FMA two-product (Dekker 1971) give the
 // rounding error of a float sum or product exactly, so g can be evaluated to
@@ -899,6 +832,95 @@ __device__ __forceinline__ dfl df_mul(dfl a, dfl b)
 }
 __device__ __forceinline__ dfl df_neg(dfl a) { return {-a.hi, -a.lo}; }
 __device__ __forceinline__ float df_val(dfl a) { return a.hi + a.lo; }
+
+// a + b for a double-float a and a float b (Knuth's two-sum, renormalised)
+__device__ __forceinline__ dfl df_add_f(dfl a, float b)
+{
+    const dfl s = df_two_sum(a.hi, b);
+    const float t = __fadd_rn(s.lo, a.lo);
+    const float h = __fadd_rn(s.hi, t);
+    return {h, __fsub_rn(t, __fsub_rn(h, s.hi))};
+}
+
+// FP32 bands of one component's tridiagonal A_mu, as hs = (lo + up) / 2,
+// hd = (up - lo) / 2 and rsum = lo + di + up (each formed in FP64, then
+// rounded): row i of A_mu u is hs (d_- + d_+) + hd (d_+ - d_-) + rsum u_i with
+// d_-+ = u_{i-+1} - u_i (0 where the neighbour is missing).
+struct StencilF {
+    int d;
+    int64_t n[kMaxD];
+    const float *hs[kMaxD], *hd[kMaxD], *rsum[kMaxD];
+    int has_rsum[kMaxD];
+    // r / n[mu] = (r * magic[mu]) >> shift[mu] for r < 2^31 (fast31: N < 2^31)
+    unsigned long long magic[kMaxD];
+    int shift[kMaxD];
+    int fast31;
+};
+
+// One direction's part of A u at a point, from hi/lo parts (h + l = u to
+// 2^-47).  Writing the row as hs (d_- + d_+) + hd (d_+ - d_-) avoids the
+// cancellation of lo d_- + up d_+ on smooth data, where the two products are
+// ~1/(h k) times their sum: the hi differences and their sum are exact there
+// (Sterbenz), the lo parts are added after, so the second difference keeps
+// ~2^-24 of its own size (on the interior rows of a uniform grid hd = 0).
+__device__ __forceinline__ float stencil_dir(float hs, float hd, float rs, bool has_m, bool has_p, int has_rs,
+                                             float hm, float lm, float hp, float lp, float hc, float lc)
+{
+    const float dmh = has_m ? hm - hc : 0.0f, dml = has_m ? lm - lc : 0.0f;
+    const float dph = has_p ? hp - hc : 0.0f, dpl = has_p ? lp - lc : 0.0f;
+    const float S = (dmh + dph) + (dml + dpl);
+    const float T = (dph - dmh) + (dpl - dml);
+    float r = fmaf(hs, S, hd * T);
+    if (has_rs) r = fmaf(rs, hc + lc, r);
+    return r;
+}
+
+// K u + g for one point of one component from hi/lo parts (generic grids):
+// the directions' parts and g are summed in double-float, so partial
+// cancellation between directions does not cost accuracy either.
+__device__ __forceinline__ float stencil_hilo(const StencilF &s, const double *U, int64_t p, const int *idx,
+                                              float hc, float lc, float g)
+{
+    dfl acc{0.0f, 0.0f};
+    int64_t stride = 1;
+#pragma unroll
+    for (int mu = 0; mu < kMaxD; ++mu) {
+        if (mu < s.d) {
+            const int64_t nm = s.n[mu];
+            const int i = idx[mu];
+            float hm = 0.0f, lm = 0.0f, hp = 0.0f, lp = 0.0f;
+            if (i > 0) split_hilo(U[p - stride], hm, lm);
+            if (i + 1 < nm) split_hilo(U[p + stride], hp, lp);
+            acc = df_add_f(acc, stencil_dir(s.hs[mu][i], s.hd[mu][i], s.rsum[mu][i], i > 0, i + 1 < nm,
+                                            s.has_rsum[mu], hm, lm, hp, lp, hc, lc));
+            stride *= nm;
+        }
+    }
+    acc = df_add_f(acc, g);
+    return acc.hi + acc.lo;
+}
+
+// grid coordinates of linear index p: multiply-shift division when the grid
+// has fewer than 2^31 points (no integer divide instruction on the GPU)
+__device__ __forceinline__ void coords(const StencilF &s, int64_t p, int *idx)
+{
+    if (s.fast31) {
+        uint32_t r = (uint32_t)p;
+#pragma unroll
+        for (int mu = 0; mu < kMaxD; ++mu) {
+            const uint32_t q = (uint32_t)(((unsigned long long)r * s.magic[mu]) >> s.shift[mu]);
+            idx[mu] = (int)(r - q * (uint32_t)s.n[mu]);
+            r = q;
+        }
+    } else {
+        int64_t r = p;
+#pragma unroll
+        for (int mu = 0; mu < kMaxD; ++mu) {
+            idx[mu] = (int)(r % s.n[mu]);
+            r /= s.n[mu];
+        }
+    }
+}
 
 // g(u, v) in double-float from the hi/lo parts of the FP64 state.  The
 // parameters come pre-split on the host (pp[k] = hi/lo of p[k]).
@@ -937,8 +959,8 @@ __global__ void k_rhs_planes(StencilF s0, StencilF s1, ModelDF m, int64_t N, con
         react_df(m, dfl{hu, lu}, dfl{hv, lv}, gu, gv);
         int idx[kMaxD];
         coords(s0, p, idx);
-        store_planes_f(Fp, N, p, stencil_hilo(s0, U, p, idx, hu, lu) + gu);
-        store_planes_f(Fp + 3 * N, N, p, stencil_hilo(s1, U + N, p, idx, hv, lv) + gv);
+        store_planes_f(Fp, N, p, stencil_hilo(s0, U, p, idx, hu, lu, gu));
+        store_planes_f(Fp + 3 * N, N, p, stencil_hilo(s1, U + N, p, idx, hv, lv, gv));
     }
 }
 
@@ -951,17 +973,8 @@ __global__ void k_rhs_planes(StencilF s0, StencilF s1, ModelDF m, int64_t N, con
 // loaded one iteration ahead so that their latency overlaps the current
 // plane's work.  Coordinates come from the thread index, so no division.
 // Same arithmetic, in the same order (directions mu = 0, 1, 2), as
-// k_rhs_planes.  Idx: 32-bit offsets when the grid has < 2^31 points.
-__device__ __forceinline__ float stencil_dir(float lo_c, float up_c, float rs_c, bool has_lo, bool has_up,
-                                             int has_rs, float hm, float lm, float hp, float lp, float hc,
-                                             float lc)
-{
-    float r = 0.0f;
-    if (has_lo) r = fmaf(lo_c, (hm - hc) + (lm - lc), r);
-    if (has_up) r = fmaf(up_c, (hp - hc) + (lp - lc), r);
-    if (has_rs) r = fmaf(rs_c, hc + lc, r);
-    return r;
-}
+// k_rhs_planes (stencil_dir per direction, double-float sum with g).  Idx:
+// 32-bit offsets when the grid has < 2^31 points.
 
 template <int TX, int TY, int TZ, typename Idx>
 __global__ void __launch_bounds__(TX * TY) k_rhs_tiled(StencilF s0, StencilF s1, ModelDF m, int64_t N64,
@@ -999,12 +1012,12 @@ __global__ void __launch_bounds__(TX * TY) k_rhs_tiled(StencilF s0, StencilF s1,
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
             if (in) {
-                cx[c][0] = st[c]->lo[0][x];
-                cx[c][1] = st[c]->up[0][x];
+                cx[c][0] = st[c]->hs[0][x];
+                cx[c][1] = st[c]->hd[0][x];
                 cx[c][2] = st[c]->rsum[0][x];
                 if (TY > 1) {
-                    cy[c][0] = st[c]->lo[1][y];
-                    cy[c][1] = st[c]->up[1][y];
+                    cy[c][0] = st[c]->hs[1][y];
+                    cy[c][1] = st[c]->hd[1][y];
                     cy[c][2] = st[c]->rsum[1][y];
                 }
                 split_hilo(U[c * N + pz + col], hc[c], lc[c]);
@@ -1037,25 +1050,28 @@ __global__ void __launch_bounds__(TX * TY) k_rhs_tiled(StencilF s0, StencilF s1,
         }
         __syncthreads();
         if (in) {
+            float g[2];
+            react_df(m, dfl{hc[0], lc[0]}, dfl{hc[1], lc[1]}, g[0], g[1]);
             float F[2];
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
                 const StencilF &sc = *st[c];
-                float acc = stencil_dir(cx[c][0], cx[c][1], cx[c][2], x > 0, x + 1 < n1, sc.has_rsum[0],
-                                        sh[c][0][ty + 1][tx], sh[c][1][ty + 1][tx], sh[c][0][ty + 1][tx + 2],
-                                        sh[c][1][ty + 1][tx + 2], hc[c], lc[c]);
+                dfl acc{stencil_dir(cx[c][0], cx[c][1], cx[c][2], x > 0, x + 1 < n1, sc.has_rsum[0],
+                                    sh[c][0][ty + 1][tx], sh[c][1][ty + 1][tx], sh[c][0][ty + 1][tx + 2],
+                                    sh[c][1][ty + 1][tx + 2], hc[c], lc[c]),
+                        0.0f};
                 if (TY > 1)
-                    acc += stencil_dir(cy[c][0], cy[c][1], cy[c][2], y > 0, y + 1 < n2, sc.has_rsum[1],
-                                       sh[c][0][ty][tx + 1], sh[c][1][ty][tx + 1], sh[c][0][ty + 2][tx + 1],
-                                       sh[c][1][ty + 2][tx + 1], hc[c], lc[c]);
-                acc += stencil_dir(sc.lo[dz][z], sc.up[dz][z], sc.rsum[dz][z], z > 0, z + 1 < n3,
-                                   sc.has_rsum[dz], hp[c], lp[c], hn[c], ln[c], hc[c], lc[c]);
-                F[c] = acc;
+                    acc = df_add_f(acc, stencil_dir(cy[c][0], cy[c][1], cy[c][2], y > 0, y + 1 < n2,
+                                                    sc.has_rsum[1], sh[c][0][ty][tx + 1], sh[c][1][ty][tx + 1],
+                                                    sh[c][0][ty + 2][tx + 1], sh[c][1][ty + 2][tx + 1], hc[c],
+                                                    lc[c]));
+                acc = df_add_f(acc, stencil_dir(sc.hs[dz][z], sc.hd[dz][z], sc.rsum[dz][z], z > 0, z + 1 < n3,
+                                                sc.has_rsum[dz], hp[c], lp[c], hn[c], ln[c], hc[c], lc[c]));
+                acc = df_add_f(acc, g[c]);
+                F[c] = acc.hi + acc.lo;
             }
-            float gu, gv;
-            react_df(m, dfl{hc[0], lc[0]}, dfl{hc[1], lc[1]}, gu, gv);
-            store_planes_f(Fp, (int64_t)N, (int64_t)(pz + col), F[0] + gu);
-            store_planes_f(Fp + 3 * (int64_t)N, (int64_t)N, (int64_t)(pz + col), F[1] + gv);
+            store_planes_f(Fp, (int64_t)N, (int64_t)(pz + col), F[0]);
+            store_planes_f(Fp + 3 * (int64_t)N, (int64_t)N, (int64_t)(pz + col), F[1]);
         }
         __syncthreads();
 #pragma unroll
@@ -1806,7 +1822,8 @@ ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatu
         delete mp;
         return fail(DS_ERR_UNSUPPORTED, "reduced-precision paths need tridiagonal A_mu (use DS_PREC_F64)");
     }
-    // FP32 bands: lower, upper and row sum (lo + di + up; zero for the Neumann Laplacian)
+    // FP32 bands: half sum and half difference of the off-diagonals, and the
+    // row sum (lo + di + up; zero for the Neumann Laplacian)
     {
         int64_t tot = 0;
         for (int mu = 0; mu < d; ++mu) tot += 2 * 3 * mp->n[mu];
@@ -1831,13 +1848,13 @@ ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatu
                 cudaMemcpy(band.data(), set->tri_dev + set->tri_off[c][mu], sizeof(double) * 3 * nm,
                            cudaMemcpyDeviceToHost);
                 for (int64_t i = 0; i < nm; ++i) {
-                    hb[off + i] = (float)band[i];
-                    hb[off + nm + i] = (float)band[2 * nm + i];
+                    hb[off + i] = (float)(0.5 * (band[i] + band[2 * nm + i]));        // hs
+                    hb[off + nm + i] = (float)(0.5 * (band[2 * nm + i] - band[i]));   // hd
                     const double rsum = band[i] + band[nm + i] + band[2 * nm + i];
                     hb[off + 2 * nm + i] = (float)rsum;
                     if (rsum != 0.0) mp->stf[c].has_rsum[mu] = 1;
                 }
-                mp->stf[c].lo[mu] = (const float *)(intptr_t)off;   // fixed up below
+                mp->stf[c].hs[mu] = (const float *)(intptr_t)off;   // fixed up below
                 off += 3 * nm;
             }
         }
@@ -1849,10 +1866,10 @@ ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatu
         cudaMemcpy(mp->bands, hb.data(), sizeof(float) * tot, cudaMemcpyHostToDevice);
         for (int c = 0; c < 2; ++c)
             for (int mu = 0; mu < d; ++mu) {
-                const int64_t o = (int64_t)(intptr_t)mp->stf[c].lo[mu];
+                const int64_t o = (int64_t)(intptr_t)mp->stf[c].hs[mu];
                 const int64_t nm = mp->n[mu];
-                mp->stf[c].lo[mu] = mp->bands + o;
-                mp->stf[c].up[mu] = mp->bands + o + nm;
+                mp->stf[c].hs[mu] = mp->bands + o;
+                mp->stf[c].hd[mu] = mp->bands + o + nm;
                 mp->stf[c].rsum[mu] = mp->bands + o + 2 * nm;
             }
     }
