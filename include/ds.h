@@ -344,10 +344,15 @@ ds_status ds_plan_destroy(ds_plan *plan);
  *   ninst entries; A[i] is the host pointer of instance i's packed matrices
  *   (layout of ds_phi_setup).  Synchronous.
  * ds_batch_integrate -- nsteps steps of every instance; U: host array of
- *   ninst device pointers to the instances' FP64 states.  The steps of all
- *   instances are captured into one CUDA graph with one captured stream per
- *   instance (fork/join), so independent instances run concurrently; a graph
- *   covers up to 10 steps and is cached per set of U pointers.  Asynchronous.
+ *   ninst device pointers to the instances' FP64 states.  The steps are
+ *   captured into CUDA graphs (up to 10 steps each, cached per set of U
+ *   pointers).  Split-BF16 batches (all instances of one d): per step, each
+ *   instance's F = K U + g(U) runs on its own captured stream, then each of
+ *   the 3 d mode products of all instances runs as one grouped persistent
+ *   launch (the instances' tiles in one work list, their arguments in a
+ *   device table; 128-column tiles, with two accumulators for
+ *   DS_PREC_BF16X6C; no split-K; fused epilogues).  Other precisions: each
+ *   instance's steps on its own captured stream.  Asynchronous.
  * ds_batch_sync -- wait and report the first instance's device-side error.
  * ds_batch_kernels_per_step -- library kernel launches per batch step.
  * The paper has no batching; the instances are independent problems. */

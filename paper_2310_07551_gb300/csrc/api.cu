@@ -1048,6 +1048,7 @@ struct ds_batch {
         std::vector<double *> U;
         int steps;
         cudaGraphExec_t exec;
+        tc::MixedGroup *group = nullptr;   // grouped launches' tables for these state pointers
     };
     std::vector<Graph> graphs;
     int64_t launches_per_step = 0;
@@ -1062,30 +1063,67 @@ ds_status batch_graph(ds_batch *b, double *const *U, int steps, cudaGraphExec_t 
         for (int i = 0; i < b->ninst && same; ++i) same = (g.U[i] == U[i]);
         if (same) { *out = g.exec; return DS_OK; }
     }
+    // split-BF16 batches: per step, every instance's F = K U + g(U) on its own
+    // stream, then each mode product of all instances as one grouped launch;
+    // other precisions: each instance's steps on its own stream
+    bool grouped = true;
+    for (auto *p : b->plans) grouped = grouped && p->mixed != nullptr;
+    tc::MixedGroup *G = nullptr;
+    if (grouped) {
+        std::vector<tc::MixedPlan *> mps;
+        std::vector<double *> Us(U, U + b->ninst);
+        std::vector<Model> models;
+        for (auto *p : b->plans) {
+            mps.push_back(p->mixed);
+            models.push_back(p->model);
+        }
+        ds_status r = tc::mixed_group_create(mps, Us, models, &G);
+        if (r != DS_OK) return r;
+    }
     cudaGraph_t graph;
     DS_CUDA_TRY(cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal));
-    cudaEventRecord(b->fork, b->origin);
     int64_t L = 0;
     bool bad = false;
-    for (int i = 0; i < b->ninst; ++i) {
-        cudaStream_t s = b->streams[i];
-        cudaStreamWaitEvent(s, b->fork, 0);
+    if (grouped) {
         for (int k = 0; k < steps; ++k) {
-            int l = enqueue_step(b->plans[i], U[i], s, false);
-            if (l < 0) bad = true;
-            L += l;
+            cudaEventRecord(b->fork, b->origin);
+            for (int i = 0; i < b->ninst; ++i) {
+                cudaStream_t s = b->streams[i];
+                cudaStreamWaitEvent(s, b->fork, 0);
+                L += tc::enqueue_rhs_mixed(b->plans[i]->mixed, b->plans[i]->model, U[i], s);
+                cudaEventRecord(b->join[i], s);
+                cudaStreamWaitEvent(b->origin, b->join[i], 0);
+            }
+            L += tc::mixed_group_enqueue(G, b->origin, nullptr);
         }
-        cudaEventRecord(b->join[i], s);
-        cudaStreamWaitEvent(b->origin, b->join[i], 0);
+    } else {
+        cudaEventRecord(b->fork, b->origin);
+        for (int i = 0; i < b->ninst; ++i) {
+            cudaStream_t s = b->streams[i];
+            cudaStreamWaitEvent(s, b->fork, 0);
+            for (int k = 0; k < steps; ++k) {
+                int l = enqueue_step(b->plans[i], U[i], s, false);
+                if (l < 0) bad = true;
+                L += l;
+            }
+            cudaEventRecord(b->join[i], s);
+            cudaStreamWaitEvent(b->origin, b->join[i], 0);
+        }
     }
     cudaError_t e = cudaStreamEndCapture(b->origin, &graph);
-    if (e != cudaSuccess || bad) return fail(DS_ERR_CUDA, std::string("batch capture: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess || bad) {
+        tc::mixed_group_destroy(G);
+        return fail(DS_ERR_CUDA, std::string("batch capture: ") + cudaGetErrorString(e));
+    }
     cudaGraphExec_t ex;
     e = cudaGraphInstantiate(&ex, graph, 0);
     cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return fail(DS_ERR_CUDA, std::string("batch instantiate: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) {
+        tc::mixed_group_destroy(G);
+        return fail(DS_ERR_CUDA, std::string("batch instantiate: ") + cudaGetErrorString(e));
+    }
     b->launches_per_step = L / steps;
-    b->graphs.push_back({std::vector<double *>(U, U + b->ninst), steps, ex});
+    b->graphs.push_back({std::vector<double *>(U, U + b->ninst), steps, ex, G});
     *out = ex;
     return DS_OK;
 }
@@ -1097,7 +1135,10 @@ ds_status ds_batch_destroy(ds_batch *b)
 {
     if (!b) return DS_OK;
     if (b->origin) cudaStreamSynchronize(b->origin);
-    for (auto &g : b->graphs) cudaGraphExecDestroy(g.exec);
+    for (auto &g : b->graphs) {
+        cudaGraphExecDestroy(g.exec);
+        tc::mixed_group_destroy(g.group);
+    }
     for (auto p : b->plans) ds_plan_destroy(p);
     for (auto s : b->sets) ds_phi_set_destroy(s);
     for (auto s : b->streams) cudaStreamDestroy(s);

@@ -381,16 +381,57 @@ __device__ __forceinline__ TileCoord decode(const TcArgs &a, int64_t t)
     return c;
 }
 
-// Work items wi = unit * npair + h, h < npair.  A CTA takes units blockIdx.x,
-// blockIdx.x + gridDim.x, ..., and within a unit its items in order, so the
-// two tiles of a pair go through the same CTA (and the same epilogue threads)
-// back to back.  All three roles walk the same sequence.
-__device__ __forceinline__ int64_t first_item(const TcArgs &a) { return (int64_t)blockIdx.x * a.npair; }
-__device__ __forceinline__ int64_t next_item(const TcArgs &a, int64_t wi)
+// Work items.  A CTA takes work units blockIdx.x, blockIdx.x + gridDim.x, ...
+// and each unit's npair tiles in order (h = 0, 1), so the two tiles of a pair
+// go through the same CTA (and the same epilogue threads) back to back.  All
+// three roles walk the same sequence.  A grouped launch runs the same mode
+// product of several independent problems: its units are those of every
+// problem in turn (prefix[i] = units before problem i), each with its own
+// arguments from a device table.
+template <bool GROUPED>
+struct ItemIter {
+    const TcArgs *tab;
+    const int64_t *prefix;
+    int ninst;
+    int64_t total, unit, lu;   // lu: the unit within its problem
+    int h;
+    const TcArgs *a;           // arguments of the current item's problem
+    __device__ __forceinline__ ItemIter(const TcArgs &a0, const TcArgs *t, const int64_t *p, int n,
+                                        int64_t units)
+        : tab(GROUPED ? t : &a0), prefix(p), ninst(n), total(GROUPED ? units : a0.num_units),
+          unit(blockIdx.x), lu(0), h(0), a(nullptr)
+    {
+    }
+    __device__ __forceinline__ bool next()
+    {
+        if (a) {
+            if (++h < a->npair) return true;
+            unit += gridDim.x;
+            h = 0;
+        }
+        if (unit >= total) return false;
+        if (GROUPED) {
+            int lo = 0, hi = ninst - 1;   // last problem with prefix <= unit
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (prefix[mid] <= unit) lo = mid;
+                else hi = mid - 1;
+            }
+            a = tab + lo;
+            lu = unit - prefix[lo];
+        } else {
+            a = tab;
+            lu = unit;
+        }
+        return true;
+    }
+};
+
+// tensor maps of a grouped launch live in global memory (written by the
+// host before the launch): make them visible to the tensor-map proxy
+__device__ __forceinline__ void tmap_acquire(const CUtensorMap *tm)
 {
-    ++wi;
-    if (wi % a.npair == 0) wi += (int64_t)(gridDim.x - 1) * a.npair;
-    return wi;
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tm) : "memory");
 }
 
 // work unit -> (split-K part, tile); paired units hold the two components'
@@ -417,8 +458,10 @@ __device__ __forceinline__ TileCoord work_item(const TcArgs &a, int64_t unit, in
 // zero; with one accumulator every one of the six products per 16-wide K
 // step truncates at the scale of the full sum, with two the cross products
 // truncate at ~2^-8 of it, so the bias drops about sixfold.
-template <bool MODE1, int BNT, bool DUAL>
-__global__ void __launch_bounds__(kThreads, 1) k_mode_tc(const __grid_constant__ TcArgs a)
+template <bool MODE1, int BNT, bool DUAL, bool GROUPED>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_mode_tc(const __grid_constant__ TcArgs a0, const TcArgs *__restrict__ gtab, const int64_t *__restrict__ gprefix,
+              int ginst, int64_t gunits)
 {
     static_assert(!DUAL || BNT == 128, "dual accumulators need 128-column tiles");
     constexpr int BN = BNT;
@@ -465,7 +508,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_mode_tc(const __grid_constant__
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    const int kiters = a.T * a.kchunks;
 
     if (warp == 0) {
         if (lane == 0) {
@@ -475,9 +517,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_mode_tc(const __grid_constant__
             int issued_phase[STAGES];
             for (int s = 0; s < STAGES; ++s) issued_phase[s] = -1;
             bool ok = true;
-            for (int64_t wi = first_item(a); ok && wi < a.num_tiles; wi = next_item(a, wi)) {
+            ItemIter<GROUPED> itr(a0, gtab, gprefix, ginst, gunits);
+            const TcArgs *seen = nullptr;
+            while (ok && itr.next()) {
+                const TcArgs &a = GROUPED ? *itr.a : a0;   // ungrouped: the kernel parameter itself
+                if (GROUPED && itr.a != seen) {
+                    tmap_acquire(&a.tmA);
+                    tmap_acquire(&a.tmB);
+                    seen = itr.a;
+                }
                 int part;
-                const TileCoord tc = work_item<MODE1>(a, wi / a.npair, (int)(wi % a.npair), part);
+                const TileCoord tc = work_item<MODE1>(a, itr.lu, itr.h, part);
+                const int kiters = a.T * a.kchunks;
                 const int it0 = part * a.kpi, it1 = min(it0 + a.kpi, kiters);
                 for (int it = it0; it < it1; ++it) {
                     const int tt = it / a.kchunks, kc = it % a.kchunks;
@@ -523,11 +574,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_mode_tc(const __grid_constant__
             int acc = 0;
             uint32_t acc_phase = 0;
             bool ok = true;
-            for (int64_t wi = first_item(a); ok && wi < a.num_tiles; wi = next_item(a, wi)) {
+            ItemIter<GROUPED> itr(a0, gtab, gprefix, ginst, gunits);
+            while (ok && itr.next()) {
+                const TcArgs &a = GROUPED ? *itr.a : a0;   // ungrouped: the kernel parameter itself
                 if (!wait_bar(TEMPTY(acc), acc_phase ^ 1u, abort_flag, a.status, 2)) break;
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)acc * ACC_COLS;
-                const int part = (int)((wi / a.npair) % a.ksplit);
+                const int part = (int)(itr.lu % a.ksplit);
+                const int kiters = a.T * a.kchunks;
                 const int it0 = part * a.kpi, it1 = min(it0 + a.kpi, kiters);
                 for (int it = it0; it < it1; ++it) {
                     if (!wait_bar(FULL(stage), phase, abort_flag, a.status, 3)) { ok = false; break; }
@@ -575,9 +629,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_mode_tc(const __grid_constant__
         const int m = quarter * 32 + lane;
         int acc = 0;
         uint32_t acc_phase = 0;
-        for (int64_t wi = first_item(a); wi < a.num_tiles; wi = next_item(a, wi)) {
+        ItemIter<GROUPED> itr(a0, gtab, gprefix, ginst, gunits);
+        while (itr.next()) {
+            const TcArgs &a = GROUPED ? *itr.a : a0;   // ungrouped: the kernel parameter itself
             int part;
-            const TileCoord tc = work_item<MODE1>(a, wi / a.npair, (int)(wi % a.npair), part);
+            const TileCoord tc = work_item<MODE1>(a, itr.lu, itr.h, part);
             // split-K parts write FP32 partials; the reduction writes the output
             const int out_kind = a.ksplit > 1 ? 1 : a.out_kind;
             void *const out_ptr = a.ksplit > 1 ? (void *)(a.part_ws + part * a.part_stride) : a.out;
@@ -1505,45 +1561,67 @@ __global__ void k_split_reduce_epi(const __grid_constant__ TcArgs a)
 }
 
 // U and model: the state and reaction parameters of fused launches (ignored otherwise)
-static void launch(const ModeLaunch &L, cudaStream_t st, double *U = nullptr, const ModelF *model = nullptr)
+// the k_mode_tc instantiation for (mode 1?, tile width, dual accumulators, grouped)
+template <bool GROUPED>
+static void launch_tc(bool mode1, int bn, bool dual, int grid, cudaStream_t st, const TcArgs &a,
+                      const TcArgs *gtab = nullptr, const int64_t *gprefix = nullptr, int ginst = 0,
+                      int64_t gunits = 0)
+{
+    if (bn == 256) {
+        if (mode1)
+            k_mode_tc<true, 256, false, GROUPED><<<grid, kThreads, TileCfg<256>::SMEM_BYTES, st>>>(a, gtab, gprefix,
+                                                                                                  ginst, gunits);
+        else
+            k_mode_tc<false, 256, false, GROUPED><<<grid, kThreads, TileCfg<256>::SMEM_BYTES, st>>>(a, gtab, gprefix,
+                                                                                                   ginst, gunits);
+    } else if (!dual) {
+        if (mode1)
+            k_mode_tc<true, 128, false, GROUPED><<<grid, kThreads, TileCfg<128>::SMEM_BYTES, st>>>(a, gtab, gprefix,
+                                                                                                  ginst, gunits);
+        else
+            k_mode_tc<false, 128, false, GROUPED><<<grid, kThreads, TileCfg<128>::SMEM_BYTES, st>>>(a, gtab, gprefix,
+                                                                                                   ginst, gunits);
+    } else {
+        if (mode1)
+            k_mode_tc<true, 128, true, GROUPED><<<grid, kThreads, TileCfg<128>::SMEM_BYTES, st>>>(a, gtab, gprefix,
+                                                                                                 ginst, gunits);
+        else
+            k_mode_tc<false, 128, true, GROUPED><<<grid, kThreads, TileCfg<128>::SMEM_BYTES, st>>>(a, gtab, gprefix,
+                                                                                                  ginst, gunits);
+    }
+}
+
+static void set_smem_limits()
 {
     static std::once_flag once;
     std::call_once(once, [] {
-        cudaFuncSetAttribute(k_mode_tc<true, 256, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             TileCfg<256>::SMEM_BYTES);
-        cudaFuncSetAttribute(k_mode_tc<false, 256, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             TileCfg<256>::SMEM_BYTES);
-        cudaFuncSetAttribute(k_mode_tc<true, 128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             TileCfg<128>::SMEM_BYTES);
-        cudaFuncSetAttribute(k_mode_tc<false, 128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             TileCfg<128>::SMEM_BYTES);
-        cudaFuncSetAttribute(k_mode_tc<true, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             TileCfg<128>::SMEM_BYTES);
-        cudaFuncSetAttribute(k_mode_tc<false, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             TileCfg<128>::SMEM_BYTES);
+        const int s256 = (int)TileCfg<256>::SMEM_BYTES, s128 = (int)TileCfg<128>::SMEM_BYTES;
+        cudaFuncSetAttribute(k_mode_tc<true, 256, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s256);
+        cudaFuncSetAttribute(k_mode_tc<false, 256, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s256);
+        cudaFuncSetAttribute(k_mode_tc<true, 128, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s128);
+        cudaFuncSetAttribute(k_mode_tc<false, 128, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s128);
+        cudaFuncSetAttribute(k_mode_tc<true, 128, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s128);
+        cudaFuncSetAttribute(k_mode_tc<false, 128, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s128);
+        cudaFuncSetAttribute(k_mode_tc<true, 256, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s256);
+        cudaFuncSetAttribute(k_mode_tc<false, 256, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s256);
+        cudaFuncSetAttribute(k_mode_tc<true, 128, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s128);
+        cudaFuncSetAttribute(k_mode_tc<false, 128, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s128);
+        cudaFuncSetAttribute(k_mode_tc<true, 128, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s128);
+        cudaFuncSetAttribute(k_mode_tc<false, 128, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s128);
     });
+}
+
+// U and model: the state and reaction parameters of fused launches (ignored otherwise)
+static void launch(const ModeLaunch &L, cudaStream_t st, double *U = nullptr, const ModelF *model = nullptr)
+{
+    set_smem_limits();
     if (L.args.num_tiles <= 0) return;
     TcArgs a = L.args;
     if (a.epi) {
         a.U = U;
         if (model) a.model = *model;
     }
-    if (L.bn == 256) {
-        if (L.mode1)
-            k_mode_tc<true, 256, false><<<L.grid, kThreads, TileCfg<256>::SMEM_BYTES, st>>>(a);
-        else
-            k_mode_tc<false, 256, false><<<L.grid, kThreads, TileCfg<256>::SMEM_BYTES, st>>>(a);
-    } else if (!L.dual) {
-        if (L.mode1)
-            k_mode_tc<true, 128, false><<<L.grid, kThreads, TileCfg<128>::SMEM_BYTES, st>>>(a);
-        else
-            k_mode_tc<false, 128, false><<<L.grid, kThreads, TileCfg<128>::SMEM_BYTES, st>>>(a);
-    } else {
-        if (L.mode1)
-            k_mode_tc<true, 128, true><<<L.grid, kThreads, TileCfg<128>::SMEM_BYTES, st>>>(a);
-        else
-            k_mode_tc<false, 128, true><<<L.grid, kThreads, TileCfg<128>::SMEM_BYTES, st>>>(a);
-    }
+    launch_tc<false>(L.mode1, L.bn, L.dual, L.grid, st, a);
     if (a.ksplit > 1) {
         const int64_t total = a.part_stride;
         const int g = (int)std::min<int64_t>((total + 255) / 256, 152 * 8);
@@ -2104,6 +2182,124 @@ static double launch_flops(const ModeLaunch &L, int64_t N)
     return (double)L.args.S * L.args.T * 2.0 * (double)N * L.args.n;
 }
 
+int enqueue_rhs_mixed(MixedPlan *mp, const Model &model, double *U, cudaStream_t st)
+{
+    const int64_t N = mp->N;
+    if (mp->rhs_tiled)
+        launch_rhs_tiled(mp->stf[0], mp->stf[1], model_df(model), N, U, mp->Fp, st);
+    else
+        k_rhs_planes<<<pw_grid(N), 256, 0, st>>>(mp->stf[0], mp->stf[1], model_df(model), N, U, mp->Fp);
+    return 1;
+}
+
+// ---------------------------------------------------------------------------
+// Grouped launches for batches: the same mode product (group g, mode mu) of
+// every problem in one persistent launch, the problems' arguments in a
+// device table.  Each problem runs 128-column tiles without split-K and with
+// the fused last-mode epilogues.
+// ---------------------------------------------------------------------------
+struct MixedGroup {
+    int d = 0;
+    struct Slot {
+        bool mode1 = false;
+        int bn = 256;
+        bool dual = false;
+        TcArgs *tab = nullptr;     // device [ninst]
+        int64_t *prefix = nullptr; // device [ninst]
+        int ninst = 0;
+        int64_t units = 0;
+        int grid = 0;
+        TcArgs a0;                 // parameter copy (status word of the first problem)
+        double flops = 0.0;
+    };
+    std::vector<Slot> slots;       // [g * d + mu]
+};
+
+void mixed_group_destroy(MixedGroup *G)
+{
+    if (!G) return;
+    for (auto &sl : G->slots) {
+        cudaFree(sl.tab);
+        cudaFree(sl.prefix);
+    }
+    delete G;
+}
+
+ds_status mixed_group_create(const std::vector<MixedPlan *> &mps, const std::vector<double *> &U,
+                             const std::vector<Model> &models, MixedGroup **out)
+{
+    const int ninst = (int)mps.size();
+    if (ninst == 0 || U.size() != mps.size() || models.size() != mps.size())
+        return fail(DS_ERR_INVALID_ARG, "grouped launch: inconsistent problem lists");
+    const int d = mps[0]->d;
+    for (auto *mp : mps)
+        if (mp->d != d || mp->compensated != mps[0]->compensated)
+            return fail(DS_ERR_UNSUPPORTED, "grouped launch: problems differ in dimension or precision");
+    MixedGroup *G = new MixedGroup();
+    G->d = d;
+    G->slots.resize(3 * d);
+    for (int g = 0; g < 3; ++g)
+        for (int mu = 0; mu < d; ++mu) {
+            MixedGroup::Slot &sl = G->slots[g * d + mu];
+            std::vector<TcArgs> tab(ninst);
+            std::vector<int64_t> prefix(ninst);
+            int64_t units = 0;
+            for (int i = 0; i < ninst; ++i) {
+                // 128-column tiles (with dual accumulators for compensated plans): a
+                // batch's problems are small, and the narrower tiles fill the SMs
+                // better (measured on the 64-instance Schnakenberg batch)
+                ModeLaunch L = mps[i]->C[g][mu][mps[i]->compensated ? 0 : 1];
+                set_split(L, 1, nullptr);
+                TcArgs &a = L.args;
+                if (a.epi) {
+                    a.U = U[i];
+                    a.model = model_f(models[i]);
+                }
+                tab[i] = a;
+                prefix[i] = units;
+                units += a.num_units;
+                sl.flops += launch_flops(L, L.N);
+                if (i == 0) {
+                    sl.mode1 = L.mode1;
+                    sl.bn = L.bn;
+                    sl.dual = L.dual;
+                    sl.a0 = a;
+                }
+            }
+            sl.ninst = ninst;
+            sl.units = units;
+            sl.grid = (int)std::min<int64_t>(units, num_sms());
+            if (cudaMalloc(&sl.tab, sizeof(TcArgs) * ninst) != cudaSuccess ||
+                cudaMalloc(&sl.prefix, sizeof(int64_t) * ninst) != cudaSuccess) {
+                cudaGetLastError();
+                mixed_group_destroy(G);
+                return fail(DS_ERR_OOM, "grouped launch tables");
+            }
+            cudaMemcpy(sl.tab, tab.data(), sizeof(TcArgs) * ninst, cudaMemcpyHostToDevice);
+            cudaMemcpy(sl.prefix, prefix.data(), sizeof(int64_t) * ninst, cudaMemcpyHostToDevice);
+        }
+    *out = G;
+    return DS_OK;
+}
+
+// the 3 d grouped launches of one step (after every problem's F planes are
+// written); returns the launch count
+int mixed_group_enqueue(const MixedGroup *G, cudaStream_t st, Prof *prof)
+{
+    set_smem_limits();
+    Prof dummy;
+    Prof &P = prof ? *prof : dummy;
+    int L = 0;
+    for (const auto &sl : G->slots) {
+        if (sl.units <= 0) continue;
+        P.begin(st, 0, sl.flops);
+        launch_tc<true>(sl.mode1, sl.bn, sl.dual, sl.grid, st, sl.a0, sl.tab, sl.prefix, sl.ninst, sl.units);
+        P.end(st);
+        ++L;
+    }
+    return L;
+}
+
 int enqueue_step_mixed(MixedPlan *mp, const ds_phi_set *set, const Model &model, const Stencil *sten,
                        double *U, cudaStream_t st, Prof *prof)
 {
@@ -2137,12 +2333,8 @@ int enqueue_step_mixed(MixedPlan *mp, const ds_phi_set *set, const Model &model,
     };
     // F = K U + g(U) as BF16 planes: FP64 state 16 B/point in, 2 x 6 B planes out
     P.begin(st, 2, 0.0, (double)N * (16 + 12));
-    if (mp->rhs_tiled)
-        launch_rhs_tiled(mp->stf[0], mp->stf[1], model_df(model), N, U, mp->Fp, st);
-    else
-        k_rhs_planes<<<pw_grid(N), 256, 0, st>>>(mp->stf[0], mp->stf[1], model_df(model), N, U, mp->Fp);
+    L += enqueue_rhs_mixed(mp, model, U, st);
     P.end(st);
-    ++L;
     group(0);   // stage increments of F; epilogue: D2
     group(1);   // 4tau/3 S_3(D2); epilogue: D3
     group(2);   // 3tau/2 S_f(D3); epilogue: U update

@@ -1,6 +1,8 @@
 // Tensor-core (tcgen05) split-BF16 path: internal interface.
 #pragma once
 
+#include <vector>
+
 #include "ds_internal.h"
 
 namespace ds {
@@ -22,6 +24,15 @@ int mixed_plan_set_tiles(MixedPlan *mp, int g, int mu, int tile_n, int ksplit);
 // of kernel launches, or -1 on failure.
 int enqueue_step_mixed(MixedPlan *mp, const ds_phi_set *set, const Model &model,
                        const Stencil *sten, double *U, cudaStream_t st, Prof *prof);
+// F = K U + g(U) of one problem (the first kernel of its step)
+int enqueue_rhs_mixed(MixedPlan *mp, const Model &model, double *U, cudaStream_t st);
+// Grouped launches for batches: the same mode product of every problem in
+// one persistent launch (tables built for one set of state pointers).
+struct MixedGroup;
+ds_status mixed_group_create(const std::vector<MixedPlan *> &mps, const std::vector<double *> &U,
+                             const std::vector<Model> &models, MixedGroup **out);
+void mixed_group_destroy(MixedGroup *G);
+int mixed_group_enqueue(const MixedGroup *G, cudaStream_t st, Prof *prof);
 // FP32 CUDA-core path pointwise kernels (two components, N points each)
 void launch_rhs_f32(const Stencil *sten, const Model &m, int64_t N, const double *U, float *F,
                     cudaStream_t st);

@@ -1,6 +1,9 @@
 """Batched independent instances (ds_batch): every instance of a batch must
 give what its own plan gives (bitwise: same kernels, same data) and, on the
-FP64 path, what the oracle gives; grids are uneven and non-square."""
+FP64 path, what the oracle gives; grids are uneven and non-square.  Split-BF16
+batches run each mode product of all instances as one grouped launch
+(128-column tiles, no split-K, fused epilogues): the single plans compared
+with them are set to the same configuration."""
 import numpy as np
 import pytest
 
@@ -33,7 +36,7 @@ def problem(inst):
     return [[dl * D for D in Ds] for dl in inst.delta]
 
 
-@pytest.mark.parametrize("precision", ["f64", "bf16x6"])
+@pytest.mark.parametrize("precision", ["f64", "bf16x6", "bf16x6c"])
 def test_batch_matches_individual_plans_and_oracle(ds, precision):
     insts = small_instances()
     As = [problem(i) for i in insts]
@@ -49,6 +52,11 @@ def test_batch_matches_individual_plans_and_oracle(ds, precision):
     for k, inst in enumerate(insts):
         ps = ds.PhiSet(inst.dims, As[k], inst.tau)
         plan = ds.Plan(ps, "schnakenberg", inst.params, precision)
+        if precision != "f64":
+            for g in range(3):
+                plan.set_fusion(g, True)
+                for mode in range(1, len(inst.dims) + 1):
+                    plan.set_tiles(g, mode, 128, 1)
         Ui = torch.from_numpy(U0[k].copy()).cuda()
         plan.integrate(Ui, m)
         plan.sync()
