@@ -1496,23 +1496,43 @@ static void set_fused(ModeLaunch &L, int epi, const float *extra, int64_t extra_
 
 // Sum the split-K partials in part order (deterministic) and write the
 // launch's real output: BF16 planes [S][3][N] or FP32 [S][N].
+// Four consecutive elements per thread (N is a multiple of 8, so a group of
+// four never straddles two outputs and every access is 16-byte aligned).
+__device__ __forceinline__ float4 part_sum4(const float *__restrict__ ws, int64_t stride, int ksplit, int64_t e)
+{
+    float4 v = *reinterpret_cast<const float4 *>(ws + e);
+    for (int p = 1; p < ksplit; ++p) {
+        const float4 w = *reinterpret_cast<const float4 *>(ws + p * stride + e);
+        v.x += w.x;
+        v.y += w.y;
+        v.z += w.z;
+        v.w += w.w;
+    }
+    return v;
+}
+
+// the three BF16 planes of four consecutive values, as 8-byte stores
+__device__ __forceinline__ void store_planes4(bf16 *dst, int64_t plane, int64_t i, float4 v)
+{
+    uint32_t a0, a1, a2, b0, b1, b2;
+    split3_pair(v.x, v.y, a0, a1, a2);
+    split3_pair(v.z, v.w, b0, b1, b2);
+    *reinterpret_cast<uint2 *>(dst + i) = make_uint2(a0, b0);
+    *reinterpret_cast<uint2 *>(dst + i + plane) = make_uint2(a1, b1);
+    *reinterpret_cast<uint2 *>(dst + i + 2 * plane) = make_uint2(a2, b2);
+}
+
 __global__ void k_split_reduce(int64_t total, int64_t N, int ksplit, const float *__restrict__ ws, int out_kind,
                                void *out)
 {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        float v = ws[e];
-        for (int p = 1; p < ksplit; ++p) v += ws[p * total + e];
+    for (int64_t e = 4 * (blockIdx.x * (int64_t)blockDim.x + threadIdx.x); e < total;
+         e += 4 * (int64_t)gridDim.x * blockDim.x) {
+        const float4 v = part_sum4(ws, total, ksplit, e);
         if (out_kind == 0) {
             const int64_t s = e / N, i = e - s * N;
-            bf16 p0, p1, p2;
-            split3f(v, p0, p1, p2);
-            bf16 *o = (bf16 *)out + s * 3 * N + i;
-            o[0] = p0;
-            o[N] = p1;
-            o[2 * N] = p2;
+            store_planes4((bf16 *)out + s * 3 * N, N, i, v);
         } else {
-            ((float *)out)[e] = v;
+            *reinterpret_cast<float4 *>((float *)out + e) = v;
         }
     }
 }
@@ -1524,39 +1544,58 @@ __global__ void k_split_reduce_epi(const __grid_constant__ TcArgs a)
     const int64_t N = a.out_ps, ps = a.part_stride;
     const int S2 = a.S / 2;
     const int64_t total = a.epi == 2 ? (int64_t)a.S * N : (int64_t)S2 * N;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t e = 4 * (blockIdx.x * (int64_t)blockDim.x + threadIdx.x); e < total;
+         e += 4 * (int64_t)gridDim.x * blockDim.x) {
         const int x = (int)(e / N);
         const int64_t p = e - x * N;
         if (a.epi == 2) {
-            float v = a.part_ws[e];
-            for (int q = 1; q < a.ksplit; ++q) v += a.part_ws[q * ps + e];
-            a.U[x * N + p] += widen_f(a.extra[x * a.extra_cs + p] + v);
+            const float4 v = part_sum4(a.part_ws, ps, a.ksplit, e);
+            const float4 ex = *reinterpret_cast<const float4 *>(a.extra + x * a.extra_cs + p);
+            double *u = a.U + x * N + p;
+            const double2 u01 = *reinterpret_cast<const double2 *>(u);
+            const double2 u23 = *reinterpret_cast<const double2 *>(u + 2);
+            *reinterpret_cast<double2 *>(u) =
+                make_double2(u01.x + widen_f(ex.x + v.x), u01.y + widen_f(ex.y + v.y));
+            *reinterpret_cast<double2 *>(u + 2) =
+                make_double2(u23.x + widen_f(ex.z + v.z), u23.y + widen_f(ex.w + v.w));
             continue;
         }
-        const int64_t e0 = e, e1 = (int64_t)(S2 + x) * N + p;
-        float v0 = a.part_ws[e0], v1 = a.part_ws[e1];
-        for (int q = 1; q < a.ksplit; ++q) {
-            v0 += a.part_ws[q * ps + e0];
-            v1 += a.part_ws[q * ps + e1];
-        }
+        const int64_t e1 = (int64_t)(S2 + x) * N + p;
+        const float4 v0 = part_sum4(a.part_ws, ps, a.ksplit, e);
+        const float4 v1 = part_sum4(a.part_ws, ps, a.ksplit, e1);
         if (x != a.fuse_spair) {
-            ((float *)a.out)[e0] = v0;
-            ((float *)a.out)[e1] = v1;
+            *reinterpret_cast<float4 *>((float *)a.out + e) = v0;
+            *reinterpret_cast<float4 *>((float *)a.out + e1) = v1;
             continue;
         }
-        float du = v0, dv = v1;
+        float du[4] = {v0.x, v0.y, v0.z, v0.w}, dv[4] = {v1.x, v1.y, v1.z, v1.w};
         if (a.extra) {
-            du = a.extra[p] + du;
-            dv = a.extra[a.extra_cs + p] + dv;
+            const float4 eu = *reinterpret_cast<const float4 *>(a.extra + p);
+            const float4 ev = *reinterpret_cast<const float4 *>(a.extra + a.extra_cs + p);
+            du[0] = eu.x + du[0];
+            du[1] = eu.y + du[1];
+            du[2] = eu.z + du[2];
+            du[3] = eu.w + du[3];
+            dv[0] = ev.x + dv[0];
+            dv[1] = ev.y + dv[1];
+            dv[2] = ev.z + dv[2];
+            dv[3] = ev.w + dv[3];
         }
-        float hu, lu, hv, lv;
-        split_hilo(a.U[p], hu, lu);
-        split_hilo(a.U[N + p], hv, lv);
-        float Du, Dv;
-        react_diff(a.model, hu + lu, hv + lv, du, dv, Du, Dv);
-        store_planes_f(a.Dp, N, p, Du);
-        store_planes_f(a.Dp + 3 * N, N, p, Dv);
+        const double2 uu01 = *reinterpret_cast<const double2 *>(a.U + p);
+        const double2 uu23 = *reinterpret_cast<const double2 *>(a.U + p + 2);
+        const double2 uv01 = *reinterpret_cast<const double2 *>(a.U + N + p);
+        const double2 uv23 = *reinterpret_cast<const double2 *>(a.U + N + p + 2);
+        const double uu[4] = {uu01.x, uu01.y, uu23.x, uu23.y}, uv[4] = {uv01.x, uv01.y, uv23.x, uv23.y};
+        float Du[4], Dv[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            float hu, lu, hv, lv;
+            split_hilo(uu[j], hu, lu);
+            split_hilo(uv[j], hv, lv);
+            react_diff(a.model, hu + lu, hv + lv, du[j], dv[j], Du[j], Dv[j]);
+        }
+        store_planes4(a.Dp, N, p, make_float4(Du[0], Du[1], Du[2], Du[3]));
+        store_planes4(a.Dp + 3 * N, N, p, make_float4(Dv[0], Dv[1], Dv[2], Dv[3]));
     }
 }
 
@@ -1624,7 +1663,7 @@ static void launch(const ModeLaunch &L, cudaStream_t st, double *U = nullptr, co
     launch_tc<false>(L.mode1, L.bn, L.dual, L.grid, st, a);
     if (a.ksplit > 1) {
         const int64_t total = a.part_stride;
-        const int g = (int)std::min<int64_t>((total + 255) / 256, 152 * 8);
+        const int g = (int)std::min<int64_t>((total / 4 + 255) / 256, 152 * 8);
         if (a.epi)
             k_split_reduce_epi<<<g, 256, 0, st>>>(a);
         else
