@@ -42,6 +42,7 @@ UNIT = "grid-point*steps/s"
 NCU_TRAFFIC = {
     # profiles/launches_*.md: mean over one step's k_mode_tc launches of read + write
     "7ccd0d262698c7f7:schnak2d_1024": 1.091e8,
+    "7ccd0d262698c7f7:fhn3d_256": 1.502e9,
 }
 
 
