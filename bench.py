@@ -254,6 +254,11 @@ def run_batch(args, rank, world):
     batch.sync()
     t = e0.elapsed_time(e1) / 1e3
     value = npts * args.steps / t
+    # the timed graphs' fused-or-separate choices (ms 0: replayed from DS_TUNE_CACHE)
+    fusion = None
+    if args.precision != "f64":
+        fusion = {("F", "D2", "D3")[g]: {"fused": f, "ms_fused": a, "ms_separate": b}
+                  for g, f, a, b in batch.fusion()}
     useful = sum(40.0 * np.prod(i.dims) * sum(i.dims) for i in insts)   # flops per batch step
     err = None
     if args.precision != "f64" and args.err_steps != 0:
@@ -286,6 +291,8 @@ def run_batch(args, rank, world):
         "gpu_launches": batch.kernels_per_step * args.steps,
         "clocks": clk,
     }
+    if fusion is not None:
+        line["config"]["epilogue_fusion"] = fusion
     print(json.dumps(line), flush=True)
     batch.close()
 

@@ -351,7 +351,9 @@ ds_status ds_plan_destroy(ds_plan *plan);
  *   the 3 d mode products of all instances runs as one grouped persistent
  *   launch (the instances' tiles in one work list, their arguments in a
  *   device table; 128-column tiles, with two accumulators for
- *   DS_PREC_BF16X6C; no split-K; fused epilogues).  Other precisions: each
+ *   DS_PREC_BF16X6C; no split-K; each group's last mode with the fused
+ *   epilogue or, where that timed slower, followed by one grouped stage
+ *   kernel: see ds_batch_fusion).  Other precisions: each
  *   instance's steps on its own captured stream.  Asynchronous.
  * ds_batch_sync -- wait and report the first instance's device-side error.
  * ds_batch_kernels_per_step -- library kernel launches per batch step.
@@ -362,6 +364,21 @@ ds_status ds_batch_create(int ninst, const ds_grid *grids, const double *const *
 ds_status ds_batch_integrate(ds_batch *batch, double *const *U, int64_t nsteps, void *stream);
 ds_status ds_batch_sync(ds_batch *batch);
 int64_t ds_batch_kernels_per_step(const ds_batch *batch);
+
+/* ds_batch_fusion -- for the grouped launches of the most recently captured
+ * split-BF16 batch graph: whether group g's (0 = F, 1 = D2, 2 = D3) last
+ * mode product runs with the fused epilogue or as the plain grouped product
+ * followed by one grouped stage kernel over all instances' points.  Building
+ * the first graph of a batch shape times both on scratch states (fastest of
+ * five, milliseconds; later graphs replay the choice; 0 when it came from
+ * DS_TUNE_CACHE or ds_batch_set_fusion) and keeps the faster.  Both give the same values.  DS_ERR_UNSUPPORTED before the
+ * first ds_batch_integrate or for other precisions. */
+ds_status ds_batch_fusion(const ds_batch *batch, int group, int *fused, float *ms_fused, float *ms_separate);
+
+/* ds_batch_set_fusion -- fix that choice for group g in graphs built from now
+ * on: fused = 1 fused epilogue, 0 separate stage kernel, -1 timed (default).
+ * Waits for the batch's stream and drops its captured graphs. */
+ds_status ds_batch_set_fusion(ds_batch *batch, int group, int fused);
 ds_status ds_batch_destroy(ds_batch *batch);
 
 /* Message of the last failed call on this thread ("" if none). */

@@ -1052,6 +1052,7 @@ struct ds_batch {
     };
     std::vector<Graph> graphs;
     int64_t launches_per_step = 0;
+    int force_fused[3] = {-1, -1, -1};   // ds_batch_set_fusion
 };
 
 namespace {
@@ -1063,8 +1064,9 @@ ds_status batch_graph(ds_batch *b, double *const *U, int steps, cudaGraphExec_t 
         for (int i = 0; i < b->ninst && same; ++i) same = (g.U[i] == U[i]);
         if (same) { *out = g.exec; return DS_OK; }
     }
-    // split-BF16 batches: per step, every instance's F = K U + g(U) on its own
-    // stream, then each mode product of all instances as one grouped launch;
+    // split-BF16 batches: per step, every instance's F = K U + g(U) in one
+    // grouped launch (else each on its own stream), then each mode product of
+    // all instances as one grouped launch;
     // other precisions: each instance's steps on its own stream
     bool grouped = true;
     for (auto *p : b->plans) grouped = grouped && p->mixed != nullptr;
@@ -1077,7 +1079,10 @@ ds_status batch_graph(ds_batch *b, double *const *U, int steps, cudaGraphExec_t 
             mps.push_back(p->mixed);
             models.push_back(p->model);
         }
-        ds_status r = tc::mixed_group_create(mps, Us, models, &G);
+        // the group's creation times launches on the plans' work buffers:
+        // nothing of an earlier graph may still be running on them
+        cudaStreamSynchronize(b->origin);
+        ds_status r = tc::mixed_group_create(mps, Us, models, b->force_fused, &G);
         if (r != DS_OK) return r;
     }
     cudaGraph_t graph;
@@ -1086,13 +1091,17 @@ ds_status batch_graph(ds_batch *b, double *const *U, int steps, cudaGraphExec_t 
     bool bad = false;
     if (grouped) {
         for (int k = 0; k < steps; ++k) {
-            cudaEventRecord(b->fork, b->origin);
-            for (int i = 0; i < b->ninst; ++i) {
-                cudaStream_t s = b->streams[i];
-                cudaStreamWaitEvent(s, b->fork, 0);
-                L += tc::enqueue_rhs_mixed(b->plans[i]->mixed, b->plans[i]->model, U[i], s);
-                cudaEventRecord(b->join[i], s);
-                cudaStreamWaitEvent(b->origin, b->join[i], 0);
+            const int lr = tc::mixed_group_enqueue_rhs(G, b->origin);
+            L += lr;
+            if (!lr) {
+                cudaEventRecord(b->fork, b->origin);
+                for (int i = 0; i < b->ninst; ++i) {
+                    cudaStream_t s = b->streams[i];
+                    cudaStreamWaitEvent(s, b->fork, 0);
+                    L += tc::enqueue_rhs_mixed(b->plans[i]->mixed, b->plans[i]->model, U[i], s);
+                    cudaEventRecord(b->join[i], s);
+                    cudaStreamWaitEvent(b->origin, b->join[i], 0);
+                }
             }
             L += tc::mixed_group_enqueue(G, b->origin, nullptr);
         }
@@ -1148,6 +1157,43 @@ ds_status ds_batch_destroy(ds_batch *b)
     if (b->ev_out) cudaEventDestroy(b->ev_out);
     if (b->origin) cudaStreamDestroy(b->origin);
     delete b;
+    return DS_OK;
+}
+
+ds_status ds_batch_fusion(const ds_batch *b, int group, int *fused, float *ms_fused, float *ms_separate)
+{
+    if (!b || !fused || !ms_fused || !ms_separate) return fail(DS_ERR_INVALID_ARG, "NULL argument");
+    if (group < 0 || group > 2) return fail(DS_ERR_INVALID_ARG, "group out of range");
+    // the choice of the latest graph; the times of the latest one that
+    // measured them (later graphs of the same batch replay the choice)
+    bool any = false;
+    *ms_fused = *ms_separate = 0.f;
+    for (const auto &g : b->graphs) {
+        if (!g.group) continue;
+        float a = 0.f, s = 0.f;
+        tc::mixed_group_fusion(g.group, group, fused, &a, &s);
+        if (a > 0.f) {
+            *ms_fused = a;
+            *ms_separate = s;
+        }
+        any = true;
+    }
+    if (!any) return fail(DS_ERR_UNSUPPORTED, "no grouped launches built (split-BF16 batches, after an integrate)");
+    return DS_OK;
+}
+
+ds_status ds_batch_set_fusion(ds_batch *b, int group, int fused)
+{
+    if (!b) return fail(DS_ERR_INVALID_ARG, "NULL batch");
+    if (group < 0 || group > 2 || fused < -1 || fused > 1) return fail(DS_ERR_INVALID_ARG, "group or choice out of range");
+    if (b->origin) cudaStreamSynchronize(b->origin);
+    b->force_fused[group] = fused;
+    // captured steps hold the previous launch sequence
+    for (auto &g : b->graphs) {
+        cudaGraphExecDestroy(g.exec);
+        tc::mixed_group_destroy(g.group);
+    }
+    b->graphs.clear();
     return DS_OK;
 }
 

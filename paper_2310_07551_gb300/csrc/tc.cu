@@ -1030,21 +1030,59 @@ __global__ void k_rhs_planes(StencilF s0, StencilF s1, ModelDF m, int64_t N, con
 // plane's work.  Coordinates come from the thread index, so no division.
 // Same arithmetic, in the same order (directions mu = 0, 1, 2), as
 // k_rhs_planes (stencil_dir per direction, double-float sum with g).  Idx:
-// 32-bit offsets when the grid has < 2^31 points.
+// 32-bit offsets when the grid has < 2^31 points.  GROUPED: the problems of
+// a batch in one launch, a one-dimensional grid whose blocks
+// [prefix[i], prefix[i+1]) are problem i's tiles (x fastest, then y, z), each
+// problem's arguments from the device table.
 
-template <int TX, int TY, int TZ, typename Idx>
-__global__ void __launch_bounds__(TX * TY) k_rhs_tiled(StencilF s0, StencilF s1, ModelDF m, int64_t N64,
-                                                       const double *__restrict__ U, bf16 *__restrict__ Fp)
+struct RhsArgs {
+    StencilF s0, s1;
+    ModelDF m;
+    int64_t N;
+    const double *U;
+    bf16 *Fp;
+    int gx, gy;   // tiles along x and y (grouped launches)
+};
+
+template <int TX, int TY, int TZ, typename Idx, bool GROUPED>
+__global__ void __launch_bounds__(TX * TY) k_rhs_tiled(const __grid_constant__ RhsArgs a0,
+                                                       const RhsArgs *__restrict__ gtab,
+                                                       const int *__restrict__ gprefix, int ginst)
 {
     __shared__ float sh[2][2][TY + 2][TX + 2];   // [component][hi, lo][y][x], one-point halo
-    const StencilF *st[2] = {&s0, &s1};
-    const int d = s0.d, dz = d - 1;
-    const int n1 = (int)s0.n[0], n2 = d == 3 ? (int)s0.n[1] : 1, n3 = (int)s0.n[dz];
-    const Idx N = (Idx)N64;
+    int gi = 0, lb = 0;
+    if (GROUPED) {
+        int lo = 0, hi = ginst - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (gprefix[mid] <= (int)blockIdx.x) lo = mid;
+            else hi = mid - 1;
+        }
+        gi = lo;
+        lb = (int)blockIdx.x - gprefix[lo];
+    }
+    const RhsArgs &a = GROUPED ? gtab[gi] : a0;
+    int bx, by, bz;
+    if (GROUPED) {
+        bx = lb % a.gx;
+        by = (lb / a.gx) % a.gy;
+        bz = lb / (a.gx * a.gy);
+    } else {
+        bx = blockIdx.x;
+        by = blockIdx.y;
+        bz = blockIdx.z;
+    }
+    const double *__restrict__ U = a.U;
+    bf16 *__restrict__ Fp = a.Fp;
+    const ModelDF &m = a.m;
+    const StencilF *st[2] = {&a.s0, &a.s1};
+    const int d = a.s0.d, dz = d - 1;
+    const int n1 = (int)a.s0.n[0], n2 = d == 3 ? (int)a.s0.n[1] : 1, n3 = (int)a.s0.n[dz];
+    const Idx N = (Idx)a.N;
     const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-    const int x = blockIdx.x * TX + tx, y = blockIdx.y * TY + ty;
+    const int x = bx * TX + tx, y = by * TY + ty;
     const bool in = x < n1 && y < n2;
-    const int z0 = blockIdx.z * TZ;
+    const int z0 = bz * TZ;
     const int z1 = min(z0 + TZ, n3);
     const Idx plane = (Idx)n1 * n2;
     const Idx col = (Idx)y * n1 + x;
@@ -1143,26 +1181,52 @@ __global__ void __launch_bounds__(TX * TY) k_rhs_tiled(StencilF s0, StencilF s1,
 // tile shapes: 3D 32 x 8 (x, y) tiles over 32 planes; 2D 128-wide x tiles over 8 rows
 constexpr int RT3_X = 32, RT3_Y = 8, RT3_Z = 32, RT2_X = 128, RT2_Z = 8;
 
-static void launch_rhs_tiled(const StencilF &s0, const StencilF &s1, const ModelDF &m, int64_t N, const double *U,
-                             bf16 *Fp, cudaStream_t st)
+// tiles of one problem along x, y and z
+static dim3 rhs_tiles(const StencilF &s0)
 {
     const int d = s0.d;
     const int64_t n1 = s0.n[0], n2 = d == 3 ? s0.n[1] : 1, n3 = s0.n[d - 1];
+    if (d == 3)
+        return dim3((unsigned)((n1 + RT3_X - 1) / RT3_X), (unsigned)((n2 + RT3_Y - 1) / RT3_Y),
+                    (unsigned)((n3 + RT3_Z - 1) / RT3_Z));
+    return dim3((unsigned)((n1 + RT2_X - 1) / RT2_X), 1u, (unsigned)((n3 + RT2_Z - 1) / RT2_Z));
+}
+
+static RhsArgs rhs_args(const StencilF &s0, const StencilF &s1, const ModelDF &m, int64_t N, const double *U,
+                        bf16 *Fp)
+{
+    const dim3 g = rhs_tiles(s0);
+    return RhsArgs{s0, s1, m, N, U, Fp, (int)g.x, (int)g.y};
+}
+
+static void launch_rhs_tiled(const StencilF &s0, const StencilF &s1, const ModelDF &m, int64_t N, const double *U,
+                             bf16 *Fp, cudaStream_t st)
+{
+    const RhsArgs a = rhs_args(s0, s1, m, N, U, Fp);
+    const dim3 g = rhs_tiles(s0);
     const bool small = N < ((int64_t)1 << 31);
-    if (d == 3) {
-        const dim3 g((unsigned)((n1 + RT3_X - 1) / RT3_X), (unsigned)((n2 + RT3_Y - 1) / RT3_Y),
-                     (unsigned)((n3 + RT3_Z - 1) / RT3_Z));
+    if (s0.d == 3) {
         if (small)
-            k_rhs_tiled<RT3_X, RT3_Y, RT3_Z, int32_t><<<g, RT3_X * RT3_Y, 0, st>>>(s0, s1, m, N, U, Fp);
+            k_rhs_tiled<RT3_X, RT3_Y, RT3_Z, int32_t, false><<<g, RT3_X * RT3_Y, 0, st>>>(a, nullptr, nullptr, 0);
         else
-            k_rhs_tiled<RT3_X, RT3_Y, RT3_Z, int64_t><<<g, RT3_X * RT3_Y, 0, st>>>(s0, s1, m, N, U, Fp);
+            k_rhs_tiled<RT3_X, RT3_Y, RT3_Z, int64_t, false><<<g, RT3_X * RT3_Y, 0, st>>>(a, nullptr, nullptr, 0);
     } else {
-        const dim3 g((unsigned)((n1 + RT2_X - 1) / RT2_X), 1u, (unsigned)((n3 + RT2_Z - 1) / RT2_Z));
         if (small)
-            k_rhs_tiled<RT2_X, 1, RT2_Z, int32_t><<<g, RT2_X, 0, st>>>(s0, s1, m, N, U, Fp);
+            k_rhs_tiled<RT2_X, 1, RT2_Z, int32_t, false><<<g, RT2_X, 0, st>>>(a, nullptr, nullptr, 0);
         else
-            k_rhs_tiled<RT2_X, 1, RT2_Z, int64_t><<<g, RT2_X, 0, st>>>(s0, s1, m, N, U, Fp);
+            k_rhs_tiled<RT2_X, 1, RT2_Z, int64_t, false><<<g, RT2_X, 0, st>>>(a, nullptr, nullptr, 0);
     }
+}
+
+// every problem's F planes in one launch (problems of one d, each < 2^31
+// points, at most 2^31 tiles in all)
+static void launch_rhs_group(int d, const RhsArgs *tab, const int *prefix, int ninst, int blocks, cudaStream_t st)
+{
+    if (d == 3)
+        k_rhs_tiled<RT3_X, RT3_Y, RT3_Z, int32_t, true><<<blocks, RT3_X * RT3_Y, 0, st>>>(RhsArgs{}, tab, prefix,
+                                                                                         ninst);
+    else
+        k_rhs_tiled<RT2_X, 1, RT2_Z, int32_t, true><<<blocks, RT2_X, 0, st>>>(RhsArgs{}, tab, prefix, ninst);
 }
 
 // Separate (unfused) stage kernels, used when timing at plan creation finds them
@@ -1201,6 +1265,56 @@ __global__ void k_final_mixed(int64_t N, double *__restrict__ U, const float *__
          p += (int64_t)gridDim.x * blockDim.x) {
         U[p] += widen_f(a[p] + b[p]);
         U[N + p] += widen_f(a[cs_a + p] + b[cs_b + p]);
+    }
+}
+
+// The separate stage kernels over every problem of a batch in one launch:
+// problem i owns points [prefix[i], prefix[i+1]) of the flattened range.
+// kind 0: D2 = g(U + incF_0) - g(U); kind 1: D3 = g(U + incF_1 + incD) - g(U);
+// kind 2: U += incF_2 + incD.  Same arithmetic as k_stage_planes /
+// k_final_mixed.
+struct StageArgs {
+    int64_t N;
+    double *U;
+    const float *incF, *incD;
+    bf16 *Dp;
+    ModelF model;
+};
+__global__ void k_stage_group(const StageArgs *__restrict__ tab, const int64_t *__restrict__ prefix, int ninst,
+                              int64_t total, int kind)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = ninst - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (prefix[mid] <= e) lo = mid;
+            else hi = mid - 1;
+        }
+        const StageArgs &a = tab[lo];
+        const int64_t p = e - prefix[lo], N = a.N;
+        if (kind == 2) {
+            a.U[p] += widen_f(a.incF[2 * N + p] + a.incD[p]);
+            a.U[N + p] += widen_f(a.incF[3 * N + 2 * N + p] + a.incD[N + p]);
+            continue;
+        }
+        float hu, lu, hv, lv;
+        split_hilo(a.U[p], hu, lu);
+        split_hilo(a.U[N + p], hv, lv);
+        float du, dv;
+        if (kind == 0) {
+            du = a.incF[p];
+            dv = a.incF[3 * N + p];
+        } else {
+            du = a.incF[N + p];
+            dv = a.incF[3 * N + N + p];
+            du += a.incD[p];
+            dv += a.incD[N + p];
+        }
+        float Du, Dv;
+        react_diff(a.model, hu + lu, hv + lv, du, dv, Du, Dv);
+        store_planes_f(a.Dp, N, p, Du);
+        store_planes_f(a.Dp + 3 * N, N, p, Dv);
     }
 }
 
@@ -2250,8 +2364,27 @@ struct MixedGroup {
         int grid = 0;
         TcArgs a0;                 // parameter copy (status word of the first problem)
         double flops = 0.0;
+        // last mode only: the plain product writing the FP32 increments
+        // (tab_sep) and one grouped stage kernel over all problems' points,
+        // used instead of the fused epilogue where that timed faster
+        bool sep = false;
+        int kind = 0;              // k_stage_group kind (= group)
+        TcArgs *tab_sep = nullptr;
+        int64_t *prefix_sep = nullptr;   // its own work units (no tile pairs)
+        int64_t units_sep = 0;
+        int grid_sep = 0;
+        TcArgs a0_sep;
+        StageArgs *stab = nullptr; // device [ninst]
+        int64_t *sprefix = nullptr;
+        int64_t points = 0;
+        float ms[2] = {};          // {fused, separate} at creation (0 = replayed)
     };
     std::vector<Slot> slots;       // [g * d + mu]
+    // every problem's F = K U + g(U) in one launch (all problems tiled)
+    RhsArgs *rtab = nullptr;       // device [ninst]
+    int *rprefix = nullptr;        // device [ninst], first tile of each problem
+    int rinst = 0;
+    int rblocks = 0;               // 0: per-problem launches
 };
 
 void mixed_group_destroy(MixedGroup *G)
@@ -2260,12 +2393,29 @@ void mixed_group_destroy(MixedGroup *G)
     for (auto &sl : G->slots) {
         cudaFree(sl.tab);
         cudaFree(sl.prefix);
+        cudaFree(sl.tab_sep);
+        cudaFree(sl.prefix_sep);
+        cudaFree(sl.stab);
+        cudaFree(sl.sprefix);
     }
+    cudaFree(G->rtab);
+    cudaFree(G->rprefix);
     delete G;
 }
 
+static void launch_group_slot(const MixedGroup::Slot &sl, bool sep, cudaStream_t st)
+{
+    if (sep)
+        launch_tc<true>(sl.mode1, sl.bn, sl.dual, sl.grid_sep, st, sl.a0_sep, sl.tab_sep, sl.prefix_sep, sl.ninst,
+                        sl.units_sep);
+    else
+        launch_tc<true>(sl.mode1, sl.bn, sl.dual, sl.grid, st, sl.a0, sl.tab, sl.prefix, sl.ninst, sl.units);
+    if (sep)
+        k_stage_group<<<pw_grid(sl.points), 256, 0, st>>>(sl.stab, sl.sprefix, sl.ninst, sl.points, sl.kind);
+}
+
 ds_status mixed_group_create(const std::vector<MixedPlan *> &mps, const std::vector<double *> &U,
-                             const std::vector<Model> &models, MixedGroup **out)
+                             const std::vector<Model> &models, const int force_fused[3], MixedGroup **out)
 {
     const int ninst = (int)mps.size();
     if (ninst == 0 || U.size() != mps.size() || models.size() != mps.size())
@@ -2277,48 +2427,174 @@ ds_status mixed_group_create(const std::vector<MixedPlan *> &mps, const std::vec
     MixedGroup *G = new MixedGroup();
     G->d = d;
     G->slots.resize(3 * d);
-    for (int g = 0; g < 3; ++g)
-        for (int mu = 0; mu < d; ++mu) {
+    auto dev_copy = [&](auto **dst, const auto &v) {
+        using T = typename std::decay_t<decltype(v)>::value_type;
+        if (cudaMalloc((void **)dst, sizeof(T) * v.size()) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
+        return true;
+    };
+    // the fused-or-separate choice is timed on a zeroed scratch copy of the
+    // states, as the fused final epilogue updates them in place
+    int64_t Ntot = 0;
+    for (auto *mp : mps) Ntot += mp->N;
+    double *Us = nullptr;
+    if (cudaMalloc(&Us, sizeof(double) * 2 * Ntot) != cudaSuccess) {
+        cudaGetLastError();
+        delete G;
+        return fail(DS_ERR_OOM, "grouped launch scratch state");
+    }
+    cudaMemset(Us, 0, sizeof(double) * 2 * Ntot);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    set_smem_limits();
+    ds_status r = DS_OK;
+    for (int g = 0; g < 3 && r == DS_OK; ++g)
+        for (int mu = 0; mu < d && r == DS_OK; ++mu) {
             MixedGroup::Slot &sl = G->slots[g * d + mu];
-            std::vector<TcArgs> tab(ninst);
-            std::vector<int64_t> prefix(ninst);
-            int64_t units = 0;
+            const bool last = mu == d - 1;
+            std::vector<TcArgs> tab(ninst), tab_sep, tab_s(ninst);
+            std::vector<StageArgs> stab, stab_s;
+            std::vector<int64_t> prefix(ninst), sprefix, prefix_sep;
+            int64_t units = 0, units_sep = 0, points = 0, off = 0;
             for (int i = 0; i < ninst; ++i) {
                 // 128-column tiles (with dual accumulators for compensated plans): a
                 // batch's problems are small, and the narrower tiles fill the SMs
                 // better (measured on the 64-instance Schnakenberg batch)
-                ModeLaunch L = mps[i]->C[g][mu][mps[i]->compensated ? 0 : 1];
+                const int w = mps[i]->compensated ? 0 : 1;
+                ModeLaunch L = mps[i]->C[g][mu][w];
                 set_split(L, 1, nullptr);
                 TcArgs &a = L.args;
+                const ModelF mf = model_f(models[i]);
                 if (a.epi) {
                     a.U = U[i];
-                    a.model = model_f(models[i]);
+                    a.model = mf;
                 }
                 tab[i] = a;
+                tab_s[i] = a;
+                if (a.epi) tab_s[i].U = Us + 2 * off;
+                if (last) {
+                    ModeLaunch S = mps[i]->Csep[g][w];
+                    set_split(S, 1, nullptr);
+                    tab_sep.push_back(S.args);
+                    prefix_sep.push_back(units_sep);
+                    units_sep += S.args.num_units;
+                    const StageArgs sa{mps[i]->N, U[i], mps[i]->incF, mps[i]->incD, mps[i]->Dp, mf};
+                    stab.push_back(sa);
+                    stab_s.push_back(sa);
+                    stab_s.back().U = Us + 2 * off;
+                    sprefix.push_back(points);
+                    points += mps[i]->N;
+                }
                 prefix[i] = units;
                 units += a.num_units;
+                off += mps[i]->N;
                 sl.flops += launch_flops(L, L.N);
                 if (i == 0) {
                     sl.mode1 = L.mode1;
                     sl.bn = L.bn;
                     sl.dual = L.dual;
                     sl.a0 = a;
+                    if (last) sl.a0_sep = tab_sep[0];
                 }
             }
             sl.ninst = ninst;
             sl.units = units;
             sl.grid = (int)std::min<int64_t>(units, num_sms());
-            if (cudaMalloc(&sl.tab, sizeof(TcArgs) * ninst) != cudaSuccess ||
-                cudaMalloc(&sl.prefix, sizeof(int64_t) * ninst) != cudaSuccess) {
-                cudaGetLastError();
-                mixed_group_destroy(G);
-                return fail(DS_ERR_OOM, "grouped launch tables");
+            sl.units_sep = units_sep;
+            sl.grid_sep = (int)std::min<int64_t>(units_sep, num_sms());
+            sl.kind = g;
+            sl.points = points;
+            if (!dev_copy(&sl.tab, tab_s) || !dev_copy(&sl.prefix, prefix) ||
+                (last && (!dev_copy(&sl.tab_sep, tab_sep) || !dev_copy(&sl.prefix_sep, prefix_sep) ||
+                          !dev_copy(&sl.stab, stab_s) ||
+                          !dev_copy(&sl.sprefix, sprefix)))) {
+                r = fail(DS_ERR_OOM, "grouped launch tables");
+                break;
+            }
+            if (last && units > 0) {
+                const ShapeKey key{false, ninst, g, d, Ntot, units, 20 + (sl.dual ? 32 : 0)};
+                int cached = 0;
+                {
+                    std::lock_guard<std::mutex> lk(g_tune_mu);
+                    tune_cache_load();
+                    auto it = g_tuned.find(key);
+                    if (it != g_tuned.end()) cached = it->second;
+                }
+                if (force_fused[g] >= 0) {
+                    sl.sep = force_fused[g] == 0;
+                } else if (cached) {
+                    sl.sep = cached == 1;
+                } else {
+                    auto timed = [&](bool sep) {
+                        launch_group_slot(sl, sep, 0);
+                        launch_group_slot(sl, sep, 0);
+                        float best = 1e30f;
+                        for (int rep = 0; rep < 5; ++rep) {
+                            cudaEventRecord(e0, 0);
+                            launch_group_slot(sl, sep, 0);
+                            cudaEventRecord(e1, 0);
+                            cudaEventSynchronize(e1);
+                            float ms = 0.f;
+                            cudaEventElapsedTime(&ms, e0, e1);
+                            best = std::min(best, ms);
+                        }
+                        return best;
+                    };
+                    sl.ms[0] = timed(false);
+                    sl.ms[1] = timed(true);
+                    sl.sep = sl.ms[1] < sl.ms[0];
+                    std::lock_guard<std::mutex> lk(g_tune_mu);
+                    g_tuned[key] = sl.sep ? 1 : 2;
+                    tune_cache_append(key, sl.sep ? 1 : 2);
+                }
+            }
+            // the problems' own states from here on
+            if (cudaDeviceSynchronize() != cudaSuccess) {
+                r = fail(DS_ERR_CUDA, "grouped launch timing");
+                break;
             }
             cudaMemcpy(sl.tab, tab.data(), sizeof(TcArgs) * ninst, cudaMemcpyHostToDevice);
-            cudaMemcpy(sl.prefix, prefix.data(), sizeof(int64_t) * ninst, cudaMemcpyHostToDevice);
+            if (last) cudaMemcpy(sl.stab, stab.data(), sizeof(StageArgs) * ninst, cudaMemcpyHostToDevice);
         }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(Us);
+    if (r == DS_OK) {
+        bool tiled = d <= 3;
+        int64_t blocks = 0;
+        std::vector<RhsArgs> rt;
+        std::vector<int> rp;
+        for (int i = 0; i < ninst && tiled; ++i) {
+            const MixedPlan *mp = mps[i];
+            tiled = mp->rhs_tiled && mp->N < ((int64_t)1 << 31);
+            rt.push_back(rhs_args(mp->stf[0], mp->stf[1], model_df(models[i]), mp->N, U[i], mp->Fp));
+            rp.push_back((int)blocks);
+            const dim3 g = rhs_tiles(mp->stf[0]);
+            blocks += (int64_t)g.x * g.y * g.z;
+        }
+        if (tiled && blocks > 0 && blocks < INT32_MAX) {
+            if (!dev_copy(&G->rtab, rt) || !dev_copy(&G->rprefix, rp)) r = fail(DS_ERR_OOM, "grouped rhs tables");
+            G->rinst = ninst;
+            G->rblocks = (int)blocks;
+        }
+    }
+    if (r != DS_OK) {
+        mixed_group_destroy(G);
+        return r;
+    }
     *out = G;
     return DS_OK;
+}
+
+int mixed_group_enqueue_rhs(const MixedGroup *G, cudaStream_t st)
+{
+    if (!G || G->rblocks <= 0) return 0;
+    launch_rhs_group(G->d, G->rtab, G->rprefix, G->rinst, G->rblocks, st);
+    return 1;
 }
 
 // the 3 d grouped launches of one step (after every problem's F planes are
@@ -2332,11 +2608,21 @@ int mixed_group_enqueue(const MixedGroup *G, cudaStream_t st, Prof *prof)
     for (const auto &sl : G->slots) {
         if (sl.units <= 0) continue;
         P.begin(st, 0, sl.flops);
-        launch_tc<true>(sl.mode1, sl.bn, sl.dual, sl.grid, st, sl.a0, sl.tab, sl.prefix, sl.ninst, sl.units);
+        launch_group_slot(sl, sl.sep, st);
         P.end(st);
-        ++L;
+        L += sl.sep ? 2 : 1;
     }
     return L;
+}
+
+int mixed_group_fusion(const MixedGroup *G, int g, int *fused, float *ms_fused, float *ms_separate)
+{
+    if (!G || g < 0 || g > 2) return -1;
+    const MixedGroup::Slot &sl = G->slots[g * G->d + G->d - 1];
+    *fused = sl.sep ? 0 : 1;
+    *ms_fused = sl.ms[0];
+    *ms_separate = sl.ms[1];
+    return 0;
 }
 
 int enqueue_step_mixed(MixedPlan *mp, const ds_phi_set *set, const Model &model, const Stencil *sten,

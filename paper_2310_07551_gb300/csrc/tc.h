@@ -29,10 +29,16 @@ int enqueue_rhs_mixed(MixedPlan *mp, const Model &model, double *U, cudaStream_t
 // Grouped launches for batches: the same mode product of every problem in
 // one persistent launch (tables built for one set of state pointers).
 struct MixedGroup;
+// force_fused[g]: -1 = timed choice (or DS_TUNE_CACHE), 0 = separate stage
+// kernel, 1 = fused epilogue for group g's last mode
 ds_status mixed_group_create(const std::vector<MixedPlan *> &mps, const std::vector<double *> &U,
-                             const std::vector<Model> &models, MixedGroup **out);
+                             const std::vector<Model> &models, const int force_fused[3], MixedGroup **out);
 void mixed_group_destroy(MixedGroup *G);
 int mixed_group_enqueue(const MixedGroup *G, cudaStream_t st, Prof *prof);
+// every problem's F planes in one launch; 0 (nothing launched) where some
+// problem's grid has no tiled stencil kernel
+int mixed_group_enqueue_rhs(const MixedGroup *G, cudaStream_t st);
+int mixed_group_fusion(const MixedGroup *G, int g, int *fused, float *ms_fused, float *ms_separate);
 // FP32 CUDA-core path pointwise kernels (two components, N points each)
 void launch_rhs_f32(const Stencil *sten, const Model &m, int64_t N, const double *U, float *F,
                     cudaStream_t st);

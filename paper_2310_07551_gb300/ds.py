@@ -86,6 +86,9 @@ def lib() -> ctypes.CDLL:
             "ds_batch_sync": ([_vp], ctypes.c_int),
             "ds_batch_kernels_per_step": ([_vp], ctypes.c_int64),
             "ds_batch_destroy": ([_vp], ctypes.c_int),
+            "ds_batch_fusion": ([_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float),
+                                 ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
+            "ds_batch_set_fusion": ([_vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
             "ds_last_error": ([], ctypes.c_char_p),
             "ds_version": ([], ctypes.c_char_p),
         }
@@ -344,6 +347,23 @@ class Batch:
     @property
     def kernels_per_step(self) -> int:
         return int(lib().ds_batch_kernels_per_step(self._h))
+
+    def fusion(self):
+        """[(group, fused, ms_fused, ms_separate)] of the grouped launches of the
+        last captured split-BF16 graph (after an integrate)."""
+        out = []
+        for g in range(3):
+            fz = ctypes.c_int()
+            a = ctypes.c_float()
+            b = ctypes.c_float()
+            check(lib().ds_batch_fusion(self._h, g, ctypes.byref(fz), ctypes.byref(a), ctypes.byref(b)))
+            out.append((g, bool(fz.value), float(a.value), float(b.value)))
+        return out
+
+    def set_fusion(self, group: int, fused):
+        """Fix group's choice: True fused epilogue, False grouped stage kernel,
+        None timed (default)."""
+        check(lib().ds_batch_set_fusion(self._h, int(group), -1 if fused is None else int(bool(fused))))
 
     def close(self):
         if self._h:

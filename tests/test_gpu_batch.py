@@ -2,8 +2,9 @@
 give what its own plan gives (bitwise: same kernels, same data) and, on the
 FP64 path, what the oracle gives; grids are uneven and non-square.  Split-BF16
 batches run each mode product of all instances as one grouped launch
-(128-column tiles, no split-K, fused epilogues): the single plans compared
-with them are set to the same configuration."""
+(128-column tiles, no split-K, fused epilogues or a grouped stage kernel,
+which give the same values): the single plans compared with them are set to
+the same configuration."""
 import numpy as np
 import pytest
 
@@ -36,12 +37,17 @@ def problem(inst):
     return [[dl * D for D in Ds] for dl in inst.delta]
 
 
-@pytest.mark.parametrize("precision", ["f64", "bf16x6", "bf16x6c"])
-def test_batch_matches_individual_plans_and_oracle(ds, precision):
+@pytest.mark.parametrize("precision,fusion", [("f64", None), ("bf16x6", None), ("bf16x6", True),
+                                              ("bf16x6", False), ("bf16x6c", None)])
+def test_batch_matches_individual_plans_and_oracle(ds, precision, fusion):
     insts = small_instances()
     As = [problem(i) for i in insts]
     batch = ds.Batch([i.dims for i in insts], As, [i.tau for i in insts], "schnakenberg",
                      [i.params for i in insts], precision)
+    if fusion is not None:
+        # every group's last mode fused, or all followed by the grouped stage kernel
+        for g in range(3):
+            batch.set_fusion(g, fusion)
     U0 = [inputs.initial_state("schnakenberg", i.dims, seed=3 + k, a=i.params[1], b=i.params[2])
           for k, i in enumerate(insts)]
     Ub = [torch.from_numpy(u.copy()).cuda() for u in U0]
@@ -49,6 +55,14 @@ def test_batch_matches_individual_plans_and_oracle(ds, precision):
     batch.integrate(Ub, m)
     batch.sync()
     assert batch.kernels_per_step > 0
+    if precision != "f64":
+        fz = batch.fusion()
+        if fusion is not None:
+            assert all(f == fusion for _, f, _, _ in fz)
+            # one grouped stencil launch + 3 d grouped products (+ 3 stage kernels)
+            assert batch.kernels_per_step == 1 + 6 + (0 if fusion else 3)
+        else:
+            assert all(a > 0 and b > 0 for _, _, a, b in fz) or all(a == 0 for _, _, a, _ in fz)
     for k, inst in enumerate(insts):
         ps = ds.PhiSet(inst.dims, As[k], inst.tau)
         plan = ds.Plan(ps, "schnakenberg", inst.params, precision)
