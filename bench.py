@@ -498,7 +498,8 @@ def main():
         "clocks": clk,
     }
     if args.precision in ("bf16x6", "bf16x6c"):
-        line["autotuner"] = [{"group": ["F", "D2", "D3"][g], "mode": mu, "split_k": k, "tiles": t,
+        line["autotuner"] = [{"group": ["F", "D2", "D3"][g], "mode": mu, "split_k": k or None, "stream_k": k == 0,
+                              "tiles": t,
                               "tile_n": tn, "candidates_ms": c} for g, mu, k, t, tn, c in plan.tuning()]
         line["epilogue_fusion"] = [{"group": ["F", "D2", "D3"][g], "fused": fz,
                                     "ms_fused": round(a, 4), "ms_separate": round(b, 4)}

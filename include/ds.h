@@ -302,9 +302,10 @@ ds_status ds_plan_profile_read_ex(ds_plan *plan, double *ms, int64_t *launches, 
 
 /* ds_plan_tuning -- what the autotuner chose for the split-BF16 plan's mode
  * product launch of group (0 = the F group, 1 = D2, 2 = D3) and mode mu: the
- * split-K factor, the number of output tiles, and the measured time (ms,
- * fastest of five) of each candidate factor 1..8 at the chosen tile width
- * (0 = not tried).  Synchronous; DS_ERR_UNSUPPORTED for other precisions. */
+ * split-K factor (0: stream-K, see ds_plan_streamk_times), the number of
+ * output tiles, and the measured time (ms, fastest of five) of each
+ * candidate factor 1..8 at the chosen tile width (0 = not tried).
+ * Synchronous; DS_ERR_UNSUPPORTED for other precisions. */
 ds_status ds_plan_tuning(const ds_plan *plan, int group, int mu, int *ksplit, int64_t *tiles,
                          float *times_ms);
 
@@ -314,11 +315,20 @@ ds_status ds_plan_tuning(const ds_plan *plan, int group, int mu, int *ksplit, in
 ds_status ds_plan_tuning_ex(const ds_plan *plan, int group, int mu, int *ksplit, int64_t *tiles, int *tile_n,
                             float *times_ms);
 
+/* ds_plan_streamk_times -- times_ms[2]: the measured time of the launch's
+ * stream-K candidate at 256- and 128-column tiles (0 = not tried).  In
+ * stream-K form one CTA per SM takes an equal contiguous share of the
+ * launch's (tile, K chunk) iterations; a tile shared by several CTAs is
+ * summed from their FP32 partials, in CTA order, by the last CTA to deliver
+ * one, which then runs the tile's epilogue (no CTA waits for another). */
+ds_status ds_plan_streamk_times(const ds_plan *plan, int group, int mu, float *times_ms);
+
 /* ds_plan_set_tiles -- override the autotuner for one launch: output tile
  * width tile_n (256 or 128) and split-K factor (1 .. the largest factor the
- * tuner considered for that width; DS_ERR_INVALID_ARG otherwise).  The tile
- * width does not change any element's summation order; the split factor
- * does.  Waits for the plan's stream and drops its captured graphs. */
+ * tuner considered for that width, or 0 for stream-K where the tuner offered
+ * it; DS_ERR_INVALID_ARG otherwise).  The tile width does not change any
+ * element's summation order; the split factor and stream-K do.  Waits for
+ * the plan's stream and drops its captured graphs. */
 ds_status ds_plan_set_tiles(ds_plan *plan, int group, int mu, int tile_n, int ksplit);
 
 /* ds_plan_fusion -- for the split-BF16 plan's group (0 = F, 1 = D2, 2 = D3):

@@ -1290,6 +1290,15 @@ ds_status ds_plan_tuning_ex(const ds_plan *p, int group, int mu, int *ksplit, in
     return DS_OK;
 }
 
+ds_status ds_plan_streamk_times(const ds_plan *p, int group, int mu, float *times_ms)
+{
+    if (!p || !times_ms) return fail(DS_ERR_INVALID_ARG, "NULL argument");
+    if (!p->mixed) return fail(DS_ERR_UNSUPPORTED, "only split-BF16 plans are tuned");
+    if (tc::mixed_plan_streamk_times(p->mixed, group, mu, times_ms) != 0)
+        return fail(DS_ERR_INVALID_ARG, "group or mode out of range");
+    return DS_OK;
+}
+
 ds_status ds_plan_tuning(const ds_plan *p, int group, int mu, int *ksplit, int64_t *tiles, float *times_ms)
 {
     if (!times_ms) return fail(DS_ERR_INVALID_ARG, "NULL argument");
@@ -1331,7 +1340,7 @@ ds_status ds_plan_set_tiles(ds_plan *p, int group, int mu, int tile_n, int kspli
     if (p->st) cudaStreamSynchronize(p->st);
     const int r = tc::mixed_plan_set_tiles(p->mixed, group, mu, tile_n, ksplit);
     if (r == -1) return fail(DS_ERR_INVALID_ARG, "group, mode or tile width out of range");
-    if (r == -2) return fail(DS_ERR_INVALID_ARG, "split factor outside the tuned range");
+    if (r == -2) return fail(DS_ERR_INVALID_ARG, "split factor outside the tuned range (or no stream-K form)");
     for (auto &kv : p->graphs) cudaGraphExecDestroy(kv.second);
     p->graphs.clear();
     return DS_OK;

@@ -59,7 +59,7 @@ struct TileCfg {
     static constexpr int STAGES = BNT == 256 ? 3 : 4;
     static constexpr uint32_t B_PLANE = BNT * BK * 2;
     static constexpr uint32_t STAGE_BYTES = STAGE_A + 3 * B_PLANE;
-    static constexpr uint32_t BAR_BYTES = 8 * (2 * STAGES + 5) + 16;
+    static constexpr uint32_t BAR_BYTES = 8 * (2 * STAGES + 7) + 16;
     static constexpr uint32_t SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + BAR_BYTES;
 };
 constexpr long long kTimeoutCycles = 4000000000LL;   // ~2 s at 2 GHz
@@ -93,6 +93,18 @@ struct alignas(128) TcArgs {
     // the other by one CTA; num_units = num_tiles / npair.
     int npair;
     int64_t num_units;
+    // Stream-K (ungrouped launches, ksplit == 1): with G = gridDim.x, the
+    // first dp = (num_units / G - 1) G units (0 below two waves) run whole,
+    // unit b + i G on CTA b; the Q = (num_units - dp) * npair * kchunks * T
+    // iterations of the rest (unit, tile h of the unit, K chunk; K fastest)
+    // are cut into G equal contiguous ranges, CTA b taking [b Q / G,
+    // (b + 1) Q / G).  A unit that spans several CTAs is finished by the last
+    // CTA to deliver its FP32 partials (sk_cnt[unit] counts the deliveries):
+    // it sums the partials of each tile in CTA order and runs the tile's
+    // epilogue.  Partial slots: sk_ws[(4 b + 2 tail + h) BM BN].
+    int sk;
+    float *sk_ws;
+    int *sk_cnt;               // [num_units], zero between launches
     // Fused epilogue of a group's last mode (non-mode-1 launches, ksplit == 1;
     // with split-K the reduction does it): 0 none; 1 stage difference on the
     // pairs with s_pair == fuse_spair: D = g(U + extra + inc) - g(U) as BF16
@@ -223,6 +235,19 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
           "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+        "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, "
+        "%17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]),
+        "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]),
+        "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]),
+        "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
+        : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
 // three-way BF16 split of a double: x = p0 + p1 + p2 + O(2^-24 |x|)
@@ -388,7 +413,15 @@ __device__ __forceinline__ TileCoord decode(const TcArgs &a, int64_t t)
 // product of several independent problems: its units are those of every
 // problem in turn (prefix[i] = units before problem i), each with its own
 // arguments from a device table.
-template <bool GROUPED>
+// stream-K: units run whole before the stream-K region (all but the last
+// one to two waves)
+__host__ __device__ __forceinline__ int64_t sk_dp_units(int64_t units, int G)
+{
+    const int64_t w = units / G;
+    return w >= 2 ? (w - 1) * G : 0;
+}
+
+template <bool GROUPED, bool SK = false>
 struct ItemIter {
     const TcArgs *tab;
     const int64_t *prefix;
@@ -396,14 +429,61 @@ struct ItemIter {
     int64_t total, unit, lu;   // lu: the unit within its problem
     int h;
     const TcArgs *a;           // arguments of the current item's problem
+    // stream-K (SK, ungrouped): this CTA's iteration range [qbeg, qend), the next
+    // iteration q, iterations per unit L and per tile kit; for the current
+    // item its K chunks [k0, k1), whether its unit is shared with other CTAs
+    // and the partial slot it delivers to
+    bool sk;
+    int64_t qbeg, qend, q, L, dp;
+    int kit, k0, k1, slot;
+    bool split;
     __device__ __forceinline__ ItemIter(const TcArgs &a0, const TcArgs *t, const int64_t *p, int n,
                                         int64_t units)
         : tab(GROUPED ? t : &a0), prefix(p), ninst(n), total(GROUPED ? units : a0.num_units),
-          unit(blockIdx.x), lu(0), h(0), a(nullptr)
+          unit(blockIdx.x), lu(0), h(0), a(nullptr), sk(SK && !GROUPED), qbeg(0), qend(0), q(0), L(1), dp(0),
+          kit(1), k0(0), k1(0), slot(0), split(false)
     {
+        if (SK && !GROUPED) {
+            kit = a0.T * a0.kchunks;
+            L = (int64_t)a0.npair * kit;
+            dp = sk_dp_units(a0.num_units, gridDim.x);
+            const int64_t Q = (a0.num_units - dp) * L;
+            qbeg = Q * blockIdx.x / gridDim.x;
+            qend = Q * (blockIdx.x + 1) / gridDim.x;
+            q = qbeg;
+        }
     }
     __device__ __forceinline__ bool next()
     {
+        if (SK && !GROUPED) {
+            // whole units first, then the rest of the current tile within
+            // this CTA's stream-K range
+            if (a && unit < dp) {
+                if (++h < a->npair) return true;
+                unit += gridDim.x;
+                h = 0;
+            }
+            a = tab;
+            if (unit < dp) {
+                lu = unit;
+                k0 = 0;
+                k1 = kit;
+                split = false;
+                return true;
+            }
+            if (q >= qend) return false;
+            const int64_t v = q / L;   // unit within the stream-K region
+            lu = dp + v;
+            const int64_t r = q - v * L;
+            h = (int)(r / kit);
+            k0 = (int)(r - (int64_t)h * kit);
+            const int64_t e = min(qend, v * L + (int64_t)(h + 1) * kit);
+            k1 = k0 + (int)(e - q);
+            q = e;
+            split = v * L < qbeg || (v + 1) * L > qend;
+            slot = (int)(4 * blockIdx.x) + (v == qbeg / L ? 0 : 2) + h;
+            return true;
+        }
         if (a) {
             if (++h < a->npair) return true;
             unit += gridDim.x;
@@ -426,6 +506,36 @@ struct ItemIter {
         return true;
     }
 };
+
+__device__ __forceinline__ int atom_add_acq_rel(int *p, int v)
+{
+    int old;
+    asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+// stream-K: the CTA whose range holds iteration q (ranges [b Q / G, (b + 1) Q / G))
+__device__ __forceinline__ int sk_owner(int64_t Q, int64_t q, int G)
+{
+    return (int)(((q + 1) * G - 1) / Q);
+}
+
+// stream-K: partial deliveries of a shared unit, one per (CTA, tile) pair
+// with a non-empty share
+__device__ __forceinline__ int sk_deliveries(const TcArgs &a, int64_t unit)
+{
+    const int kit = a.T * a.kchunks, G = gridDim.x;
+    const int64_t dp = sk_dp_units(a.num_units, G);
+    const int64_t L = (int64_t)a.npair * kit, Q = (a.num_units - dp) * L;
+    unit -= dp;
+    int n = 0;
+    for (int h = 0; h < a.npair; ++h) {
+        const int64_t s = unit * L + (int64_t)h * kit, e = s + kit;
+        for (int b = sk_owner(Q, s, G); b <= sk_owner(Q, e - 1, G); ++b)
+            if (max(Q * b / G, s) < min(Q * (b + 1) / G, e)) ++n;
+    }
+    return n;
+}
 
 // tensor maps of a grouped launch live in global memory (written by the
 // host before the launch): make them visible to the tensor-map proxy
@@ -452,13 +562,231 @@ __device__ __forceinline__ TileCoord work_item(const TcArgs &a, int64_t unit, in
     return c;
 }
 
+// Output addressing of one tile for an epilogue thread (accumulator row m,
+// column half `half` of the tile).
+struct EpiTile {
+    int64_t rbase;             // element offset of column cbase in this row
+    int64_t cbase, col_lim;
+    uint32_t col_stride;       // output stride between consecutive accumulator columns
+    bool row_ok;
+    int out_kind;
+    void *out_ptr;
+    int64_t out_cs;
+};
+
+template <bool MODE1, int BN>
+__device__ __forceinline__ EpiTile epi_tile(const TcArgs &a, const TileCoord &tc, int part, int m, int half)
+{
+    EpiTile t;
+    // split-K parts write FP32 partials; the reduction writes the output
+    t.out_kind = a.ksplit > 1 ? 1 : a.out_kind;
+    t.out_ptr = a.ksplit > 1 ? (void *)(a.part_ws + part * a.part_stride) : a.out;
+    t.out_cs = a.ksplit > 1 ? a.out_ps : a.out_cs;
+    int64_t row_index;
+    if (MODE1) {
+        const int i = tc.mt * BM + m;
+        t.row_ok = i < a.n;
+        row_index = i;
+        t.col_stride = (uint32_t)a.n;       // consecutive fibres r
+    } else {
+        const int64_t x = (int64_t)tc.mt * BM + m;
+        t.row_ok = x < a.I;
+        row_index = x + a.I * ((int64_t)a.n * tc.o);
+        t.col_stride = (uint32_t)a.I;       // consecutive output indices i
+    }
+    t.col_lim = MODE1 ? a.O : (int64_t)a.n;
+    t.cbase = (int64_t)tc.nt * BN + half * (BN / 2);
+    t.rbase = (int64_t)tc.s * t.out_cs + row_index + t.cbase * (int64_t)t.col_stride;
+    return t;
+}
+
+// The epilogue of accumulator columns [32 c, 32 c + 32) of this thread's half
+// row: plain outputs (BF16 planes or FP32), or the fused stage difference /
+// final update of a group's last mode.
+__device__ __forceinline__ void epi_chunk(const TcArgs &a, const TileCoord &tc, const EpiTile &t, int c, int lane,
+                                          const uint32_t (&v)[32])
+{
+    const int64_t col0 = t.cbase + c * 32, col_lim = t.col_lim, rbase = t.rbase;
+    const uint32_t col_stride = t.col_stride;
+    const int out_kind = t.out_kind;
+    void *const out_ptr = t.out_ptr;
+    const int64_t out_cs = t.out_cs;
+    const bool row_ok = t.row_ok;
+    const int jmax = (col_lim - col0 >= 32) ? 32 : (int)(col_lim - col0);
+    // offsets from here are below 32 * col_stride < 2^32
+    const int64_t e0 = rbase + (int64_t)(c * 32) * col_stride;
+    // The first tile of a fused stage pair keeps per-element stores:
+    // the second tile's thread reads its own values back.
+    const bool readback = a.ksplit == 1 && a.epi == 1 && tc.s == a.fuse_spair;
+    if (out_kind == 0 || (a.ksplit > 1 || a.epi == 0 ||
+                          (a.epi == 1 && !readback && tc.s - a.S / 2 != a.fuse_spair))) {
+        // Plain outputs, as pairs of rows: adjacent rows are adjacent
+        // elements held by lanes 2k, 2k+1; one exchange gives the even
+        // lane rows (r, r+1) of column j and the odd lane rows
+        // (r-1, r) of column j+1, stored as one 4-byte (BF16 planes) or
+        // 8-byte (FP32) access.  Row bounds are even, so both rows of a
+        // pair are in range or neither; every lane takes part in the
+        // exchange.
+        const int odd = lane & 1;
+        const int64_t eb = e0 - odd;
+#pragma unroll
+        for (int j = 0; j < 32; j += 2) {
+            const float a0 = __uint_as_float(v[j]) * a.alpha;
+            const float a1 = __uint_as_float(v[j + 1]) * a.alpha;
+            const float recv = __shfl_xor_sync(0xffffffffu, odd ? a0 : a1, 1);
+            const float x0 = odd ? recv : a0, x1 = odd ? a1 : recv;
+            const int jj = j + odd;
+            if (row_ok && jj < jmax) {
+                const uint32_t off = (uint32_t)jj * col_stride;
+                if (out_kind == 0) {
+                    uint32_t q0, q1, q2;
+                    split3_pair(x0, x1, q0, q1, q2);
+                    uint32_t *w0 = (uint32_t *)((bf16 *)out_ptr + eb + off);
+                    w0[0] = q0;
+                    *(uint32_t *)((bf16 *)out_ptr + eb + off + a.out_ps) = q1;
+                    *(uint32_t *)((bf16 *)out_ptr + eb + off + 2 * a.out_ps) = q2;
+                } else {
+                    *(float2 *)((float *)out_ptr + eb + off) = make_float2(x0, x1);
+                }
+            }
+        }
+        return;
+    }
+    if (!row_ok) return;
+    if (readback) {
+        float *o = (float *)out_ptr + e0;
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            if (j < jmax) o[(uint32_t)j * col_stride] = __uint_as_float(v[j]) * a.alpha;
+    } else if (a.epi == 2) {
+        // final update of component s: U_s += widen(extra_s + inc).
+        // Loads of 8 columns are issued before their stores (the
+        // compiler must assume U and extra may alias).
+        const int64_t pb = e0 - (int64_t)tc.s * out_cs;
+        double *Us = a.U + (int64_t)tc.s * a.out_ps + pb;
+        const float *ex = a.extra + (int64_t)tc.s * a.extra_cs + pb;
+#pragma unroll
+        for (int jb = 0; jb < 32; jb += 8) {
+            double u[8];
+            float e[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                if (jb + j < jmax) {
+                    const uint32_t off = (uint32_t)(jb + j) * col_stride;
+                    u[j] = Us[off];
+                    e[j] = ex[off];
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (jb + j < jmax)
+                    Us[(uint32_t)(jb + j) * col_stride] =
+                        u[j] + widen_f(e[j] + __uint_as_float(v[jb + j]) * a.alpha);
+        }
+    } else {
+        // stage difference, second tile of the pair (component 1):
+        // this thread stored the component-0 increment of the same
+        // points for the first tile, so it reads its own writes back.
+        // Loads of 4 columns are issued before their stores.
+        const int64_t pb = e0 - (int64_t)tc.s * out_cs;
+        const int64_t N = a.out_ps;
+        const float *inc0 = (const float *)a.out + (int64_t)a.fuse_spair * out_cs + pb;
+        const double *Uu = a.U + pb, *Uv = a.U + N + pb;
+        const float *exu = a.extra ? a.extra + pb : nullptr;
+        const float *exv = a.extra ? a.extra + a.extra_cs + pb : nullptr;
+#pragma unroll
+        for (int jb = 0; jb < 32; jb += 4) {
+            float du[4], dv[4];
+            double uu[4], uv[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (jb + j < jmax) {
+                    const uint32_t off = (uint32_t)(jb + j) * col_stride;
+                    du[j] = inc0[off];
+                    dv[j] = __uint_as_float(v[jb + j]) * a.alpha;
+                    uu[j] = Uu[off];
+                    uv[j] = Uv[off];
+                    if (exu) {
+                        du[j] = exu[off] + du[j];
+                        dv[j] = exv[off] + dv[j];
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (jb + j < jmax) {
+                    const int64_t p = pb + (int64_t)(jb + j) * col_stride;
+                    float hu, lu, hv, lv;
+                    split_hilo(uu[j], hu, lu);
+                    split_hilo(uv[j], hv, lv);
+                    float Du, Dv;
+                    react_diff(a.model, hu + lu, hv + lv, du[j], dv[j], Du, Dv);
+                    store_planes_f(a.Dp, N, p, Du);
+                    store_planes_f(a.Dp + 3 * N, N, p, Dv);
+                }
+            }
+        }
+    }
+}
+
+// 32 accumulator columns from TMEM (with DUAL and add2, the second
+// accumulator's columns added)
+template <bool DUAL, int BN>
+__device__ __forceinline__ void load_acc(uint32_t taddr, uint32_t (&v)[32], bool add2)
+{
+    tmem_ld32(taddr, v);
+    if (DUAL && add2) {
+        uint32_t w[32];
+        tmem_ld32(taddr + BN, w);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = __float_as_uint(__uint_as_float(v[j]) + __uint_as_float(w[j]));
+    }
+}
+
+// stream-K: the sum, in CTA order, of the partials of tile h of a shared
+// unit, for this thread's row and column half, into accumulator buffer 0
+// (tlane: its TMEM address for this thread's lane quarter and half).  Not
+// inlined: it runs at most four times per CTA, after the CTA's own items,
+// and inlined its registers would add to those of the epilogue loop.
+template <int BN>
+__device__ __noinline__ void sk_fill(const TcArgs &a, int64_t unit, int h, const EpiTile &t, int m, int half,
+                                        uint32_t tlane)
+{
+    const int kit = a.T * a.kchunks, G = gridDim.x;
+    const int64_t dp = sk_dp_units(a.num_units, G);
+    const int64_t L = (int64_t)a.npair * kit, Q = (a.num_units - dp) * L;
+    unit -= dp;
+    const int64_t s = unit * L + (int64_t)h * kit, e = s + kit;
+    const int b0 = sk_owner(Q, s, G), b1 = sk_owner(Q, e - 1, G);
+#pragma unroll 1
+    for (int c = 0; c < BN / 64; ++c) {
+        if (t.cbase + c * 32 >= t.col_lim) break;
+        uint32_t v[32];
+        bool first = true;
+#pragma unroll 1
+        for (int b = b0; b <= b1; ++b) {
+            const int64_t blo = Q * b / G;
+            if (max(blo, s) >= min(Q * (b + 1) / G, e)) continue;
+            const int slot = 4 * b + (unit == blo / L ? 0 : 2) + h;
+            const float *ws = a.sk_ws + (int64_t)slot * (BM * BN) + (half * (BN / 2) + c * 32) * BM + m;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const float p = __ldcg(ws + j * BM);
+                v[j] = __float_as_uint(first ? p : __uint_as_float(v[j]) + p);
+            }
+            first = false;
+        }
+        tmem_st32(tlane + (uint32_t)(c * 32), v);
+    }
+}
+
 // DUAL (128-column tiles only): the main product a0 b0 and the five cross
 // products accumulate in two TMEM accumulators that the epilogue adds with
 // round-to-nearest.  The tensor core's FP32 accumulation truncates toward
 // zero; with one accumulator every one of the six products per 16-wide K
 // step truncates at the scale of the full sum, with two the cross products
 // truncate at ~2^-8 of it, so the bias drops about sixfold.
-template <bool MODE1, int BNT, bool DUAL, bool GROUPED>
+template <bool MODE1, int BNT, bool DUAL, bool GROUPED, bool SK>
 __global__ void __launch_bounds__(kThreads, 1)
     k_mode_tc(const __grid_constant__ TcArgs a0, const TcArgs *__restrict__ gtab, const int64_t *__restrict__ gprefix,
               int ginst, int64_t gunits)
@@ -474,13 +802,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t *gbase = smem_raw + (base - raw);
     const uint32_t bar0 = base + STAGES * STAGE_BYTES;
-    uint32_t *tmem_slot = (uint32_t *)(gbase + STAGES * STAGE_BYTES + 8 * (2 * STAGES + 5));
+    uint32_t *tmem_slot = (uint32_t *)(gbase + STAGES * STAGE_BYTES + 8 * (2 * STAGES + 7));
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+    volatile int *sk_flag = (volatile int *)(tmem_slot + 2);
 #define FULL(s) (bar0 + 8u * (s))
 #define EMPTY(s) (bar0 + 8u * (STAGES + (s)))
 #define TFULL(b) (bar0 + 8u * (2 * STAGES + (b)))
 #define TEMPTY(b) (bar0 + 8u * (2 * STAGES + 2 + (b)))
 #define DRAIN (bar0 + 8u * (2 * STAGES + 4))
+#define EPI_BAR (bar0 + 8u * (2 * STAGES + 5))
+#define EPI_DEC (bar0 + 8u * (2 * STAGES + 6))
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     if (threadIdx.x == 0) {
@@ -493,7 +824,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(TEMPTY(b), kEpiThreads);
         }
         mbar_init(DRAIN, 1);
+        mbar_init(EPI_BAR, kEpiThreads);
+        mbar_init(EPI_DEC, 1);
         *abort_flag = 0;
+        *sk_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -517,7 +851,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             int issued_phase[STAGES];
             for (int s = 0; s < STAGES; ++s) issued_phase[s] = -1;
             bool ok = true;
-            ItemIter<GROUPED> itr(a0, gtab, gprefix, ginst, gunits);
+            ItemIter<GROUPED, SK> itr(a0, gtab, gprefix, ginst, gunits);
             const TcArgs *seen = nullptr;
             while (ok && itr.next()) {
                 const TcArgs &a = GROUPED ? *itr.a : a0;   // ungrouped: the kernel parameter itself
@@ -529,7 +863,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 int part;
                 const TileCoord tc = work_item<MODE1>(a, itr.lu, itr.h, part);
                 const int kiters = a.T * a.kchunks;
-                const int it0 = part * a.kpi, it1 = min(it0 + a.kpi, kiters);
+                constexpr bool sk = SK && !GROUPED;
+                const int it0 = sk ? itr.k0 : part * a.kpi, it1 = sk ? itr.k1 : min(it0 + a.kpi, kiters);
                 for (int it = it0; it < it1; ++it) {
                     const int tt = it / a.kchunks, kc = it % a.kchunks;
                     if (!wait_bar(EMPTY(stage), phase ^ 1u, abort_flag, a.status, 1)) { ok = false; break; }
@@ -574,7 +909,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             int acc = 0;
             uint32_t acc_phase = 0;
             bool ok = true;
-            ItemIter<GROUPED> itr(a0, gtab, gprefix, ginst, gunits);
+            ItemIter<GROUPED, SK> itr(a0, gtab, gprefix, ginst, gunits);
             while (ok && itr.next()) {
                 const TcArgs &a = GROUPED ? *itr.a : a0;   // ungrouped: the kernel parameter itself
                 if (!wait_bar(TEMPTY(acc), acc_phase ^ 1u, abort_flag, a.status, 2)) break;
@@ -582,7 +917,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t d = tmem + (uint32_t)acc * ACC_COLS;
                 const int part = (int)(itr.lu % a.ksplit);
                 const int kiters = a.T * a.kchunks;
-                const int it0 = part * a.kpi, it1 = min(it0 + a.kpi, kiters);
+                constexpr bool sk = SK && !GROUPED;
+                const int it0 = sk ? itr.k0 : part * a.kpi, it1 = sk ? itr.k1 : min(it0 + a.kpi, kiters);
                 for (int it = it0; it < it1; ++it) {
                     if (!wait_bar(FULL(stage), phase, abort_flag, a.status, 3)) { ok = false; break; }
                     tc_fence_after();
@@ -622,184 +958,290 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else {
         // ---------------- epilogue (warps 2..9) ----------------
-        // TMEM lane quarter = warp % 4; the two warps of a quarter split the
-        // 256 accumulator columns into halves.
-        const int quarter = warp % 4;
-        const int half = (warp - 2) / 4;
-        const int m = quarter * 32 + lane;
-        int acc = 0;
-        uint32_t acc_phase = 0;
-        ItemIter<GROUPED> itr(a0, gtab, gprefix, ginst, gunits);
-        while (itr.next()) {
-            const TcArgs &a = GROUPED ? *itr.a : a0;   // ungrouped: the kernel parameter itself
-            int part;
-            const TileCoord tc = work_item<MODE1>(a, itr.lu, itr.h, part);
-            // split-K parts write FP32 partials; the reduction writes the output
-            const int out_kind = a.ksplit > 1 ? 1 : a.out_kind;
-            void *const out_ptr = a.ksplit > 1 ? (void *)(a.part_ws + part * a.part_stride) : a.out;
-            const int64_t out_cs = a.ksplit > 1 ? a.out_ps : a.out_cs;
-            // every lane waits, and the warp leaves together: tcgen05.ld below is
-            // .sync.aligned, so no lane may skip one that its warp executes
-            const bool ready = wait_bar(TFULL(acc), acc_phase, abort_flag, a.status, 4);
-            if (!__all_sync(0xffffffffu, ready)) break;
-            tc_fence_after();
-            // row of the accumulator this thread owns, and the output stride
-            // between consecutive accumulator columns
-            int64_t row_index;
-            bool row_ok;
-            uint32_t col_stride;
-            if (MODE1) {
-                const int i = tc.mt * BM + m;
-                row_ok = i < a.n;
-                row_index = i;
-                col_stride = (uint32_t)a.n;       // consecutive fibres r
-            } else {
-                const int64_t x = (int64_t)tc.mt * BM + m;
-                row_ok = x < a.I;
-                row_index = x + a.I * ((int64_t)a.n * tc.o);
-                col_stride = (uint32_t)a.I;       // consecutive output indices i
-            }
-            const int64_t col_lim = MODE1 ? a.O : (int64_t)a.n;
-            const int64_t cbase = (int64_t)tc.nt * BN + half * (BN / 2);
-            // element offset of column cbase in this row
-            const int64_t rbase = (int64_t)tc.s * out_cs + row_index + cbase * (int64_t)col_stride;
-#pragma unroll 1
-            for (int c = 0; c < BN / 64; ++c) {
-                // warp-uniform exit (depends on the tile and c only), taken before
-                // the collective load so that every lane issues the same loads
-                const int64_t col0 = cbase + c * 32;
-                if (col0 >= col_lim) break;
-                uint32_t v[32];
-                const uint32_t taddr = tmem + (uint32_t)acc * ACC_COLS + (uint32_t)(half * (BN / 2) + c * 32) +
-                                       ((uint32_t)(quarter * 32) << 16);
-                tmem_ld32(taddr, v);
-                if (DUAL) {
-                    uint32_t w[32];
-                    tmem_ld32(taddr + BN, w);
-#pragma unroll
-                    for (int j = 0; j < 32; ++j)
-                        v[j] = __float_as_uint(__uint_as_float(v[j]) + __uint_as_float(w[j]));
-                }
-                const int jmax = (col_lim - col0 >= 32) ? 32 : (int)(col_lim - col0);
-                // offsets from here are below 32 * col_stride < 2^32
-                const int64_t e0 = rbase + (int64_t)(c * 32) * col_stride;
-                // The first tile of a fused stage pair keeps per-element stores:
-                // the second tile's thread reads its own values back.
-                const bool readback = a.ksplit == 1 && a.epi == 1 && tc.s == a.fuse_spair;
-                if (out_kind == 0 || (a.ksplit > 1 || a.epi == 0 ||
-                                      (a.epi == 1 && !readback && tc.s - a.S / 2 != a.fuse_spair))) {
-                    // Plain outputs, as pairs of rows: adjacent rows are adjacent
-                    // elements held by lanes 2k, 2k+1; one exchange gives the even
-                    // lane rows (r, r+1) of column j and the odd lane rows
-                    // (r-1, r) of column j+1, stored as one 4-byte (BF16 planes) or
-                    // 8-byte (FP32) access.  Row bounds are even, so both rows of a
-                    // pair are in range or neither; every lane takes part in the
-                    // exchange.
-                    const int odd = lane & 1;
-                    const int64_t eb = e0 - odd;
-#pragma unroll
-                    for (int j = 0; j < 32; j += 2) {
-                        const float a0 = __uint_as_float(v[j]) * a.alpha;
-                        const float a1 = __uint_as_float(v[j + 1]) * a.alpha;
-                        const float recv = __shfl_xor_sync(0xffffffffu, odd ? a0 : a1, 1);
-                        const float x0 = odd ? recv : a0, x1 = odd ? a1 : recv;
-                        const int jj = j + odd;
-                        if (row_ok && jj < jmax) {
-                            const uint32_t off = (uint32_t)jj * col_stride;
-                            if (out_kind == 0) {
-                                uint32_t q0, q1, q2;
-                                split3_pair(x0, x1, q0, q1, q2);
-                                uint32_t *w0 = (uint32_t *)((bf16 *)out_ptr + eb + off);
-                                w0[0] = q0;
-                                *(uint32_t *)((bf16 *)out_ptr + eb + off + a.out_ps) = q1;
-                                *(uint32_t *)((bf16 *)out_ptr + eb + off + 2 * a.out_ps) = q2;
-                            } else {
-                                *(float2 *)((float *)out_ptr + eb + off) = make_float2(x0, x1);
-                            }
-                        }
+        if constexpr (SK && !GROUPED) {
+            // TMEM lane quarter = warp % 4; the two warps of a quarter split the
+            // 256 accumulator columns into halves.
+            const int quarter = warp % 4;
+            const int half = (warp - 2) / 4;
+            const int m = quarter * 32 + lane;
+            int acc = 0;
+            uint32_t acc_phase = 0, epi_phase = 0;
+            // stream-K: shared units this CTA completed the count of (its first and
+            // its last unit at most), finished after its own items, tile by tile,
+            // from the partials summed into accumulator buffer 0
+            int64_t fin[2] = {-1, -1};
+            int vitem = -1;
+            ItemIter<GROUPED, SK> itr(a0, gtab, gprefix, ginst, gunits);
+            while (true) {
+                int64_t unit = 0;
+                int h = 0;
+                if (vitem < 0) {
+                    if (itr.next()) {
+                        unit = itr.lu;
+                        h = itr.h;
+                    } else {
+                        if (fin[0] < 0) break;
+                        vitem = 0;
                     }
+                }
+                if (vitem >= 0) {
+                    const int np = a0.npair;
+                    while (vitem < 2 * np && fin[vitem / np] < 0) ++vitem;
+                    if (vitem >= 2 * np) break;
+                    unit = fin[vitem / np];
+                    h = vitem % np;
+                    ++vitem;
+                }
+                const bool virt = vitem >= 0;
+                const TcArgs &a = GROUPED ? *itr.a : a0;   // ungrouped: the kernel parameter itself
+                int part;
+                const TileCoord tc = work_item<MODE1>(a, unit, h, part);
+                const EpiTile t = epi_tile<MODE1, BN>(a, tc, part, m, half);
+                const uint32_t tq = tmem + (uint32_t)(half * (BN / 2)) + ((uint32_t)(quarter * 32) << 16);
+                if (virt) {
+                    sk_fill<BN>(a, unit, h, t, m, half, tq);
+                } else {
+                    // every lane waits, and the warp leaves together: tcgen05.ld below is
+                    // .sync.aligned, so no lane may skip one that its warp executes
+                    const bool ready = wait_bar(TFULL(acc), acc_phase, abort_flag, a.status, 4);
+                    if (!__all_sync(0xffffffffu, ready)) break;
+                    tc_fence_after();
+                }
+                const uint32_t tbase = tq + (virt ? 0u : (uint32_t)acc * ACC_COLS);
+                if (!GROUPED && !virt && itr.split) {
+                    // stream-K share of a unit that other CTAs share: the FP32
+                    // partial to this CTA's slot (coalesced over the rows m)
+                    float *ws = a.sk_ws + (int64_t)itr.slot * (BM * BN) + (half * (BN / 2)) * BM + m;
+    #pragma unroll 1
+                    for (int c = 0; c < BN / 64; ++c) {
+                        if (t.cbase + c * 32 >= t.col_lim) break;
+                        uint32_t v[32];
+                        load_acc<DUAL, BN>(tbase + (uint32_t)(c * 32), v, true);
+    #pragma unroll
+                        for (int j = 0; j < 32; ++j) __stcg(ws + (c * 32 + j) * BM, __uint_as_float(v[j]));
+                    }
+                    tc_fence_before();
+                    mbar_arrive(TEMPTY(acc));
+                    acc ^= 1;
+                    if (acc == 0) acc_phase ^= 1u;
+                    // count the delivery: the CTA's partial stores reach thread 64
+                    // through the barrier and the other CTAs through its
+                    // acquire-release add; the CTA that completes the count
+                    // finishes the unit
+                    mbar_arrive(EPI_BAR);
+                    if (threadIdx.x == 64) {
+                        int last = 0;
+                        if (wait_bar(EPI_BAR, epi_phase, abort_flag, a.status, 5)) {
+                            const int need = sk_deliveries(a, itr.lu);
+                            const int old = atom_add_acq_rel(a.sk_cnt + itr.lu, 1);
+                            last = old == need - 1;
+                            if (last) atomicExch(a.sk_cnt + itr.lu, 0);   // ready for the next launch
+                        }
+                        *sk_flag = last;
+                        mbar_arrive(EPI_DEC);
+                    }
+                    const bool got = wait_bar(EPI_DEC, epi_phase, abort_flag, a.status, 6);
+                    epi_phase ^= 1u;
+                    if (!__all_sync(0xffffffffu, got)) break;
+                    if (*sk_flag) fin[fin[0] < 0 ? 0 : 1] = itr.lu;
                     continue;
                 }
-                if (!row_ok) continue;
-                if (readback) {
-                    float *o = (float *)out_ptr + e0;
-#pragma unroll
-                    for (int j = 0; j < 32; ++j)
-                        if (j < jmax) o[(uint32_t)j * col_stride] = __uint_as_float(v[j]) * a.alpha;
-                } else if (a.epi == 2) {
-                    // final update of component s: U_s += widen(extra_s + inc).
-                    // Loads of 8 columns are issued before their stores (the
-                    // compiler must assume U and extra may alias).
-                    const int64_t pb = e0 - (int64_t)tc.s * out_cs;
-                    double *Us = a.U + (int64_t)tc.s * a.out_ps + pb;
-                    const float *ex = a.extra + (int64_t)tc.s * a.extra_cs + pb;
-#pragma unroll
-                    for (int jb = 0; jb < 32; jb += 8) {
-                        double u[8];
-                        float e[8];
-#pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            if (jb + j < jmax) {
-                                const uint32_t off = (uint32_t)(jb + j) * col_stride;
-                                u[j] = Us[off];
-                                e[j] = ex[off];
-                            }
-                        }
-#pragma unroll
-                        for (int j = 0; j < 8; ++j)
-                            if (jb + j < jmax)
-                                Us[(uint32_t)(jb + j) * col_stride] =
-                                    u[j] + widen_f(e[j] + __uint_as_float(v[jb + j]) * a.alpha);
-                    }
+    #pragma unroll 1
+                for (int c = 0; c < BN / 64; ++c) {
+                    // warp-uniform exit (depends on the tile and c only), taken before
+                    // the collective load so that every lane issues the same loads
+                    if (t.cbase + c * 32 >= t.col_lim) break;
+                    uint32_t v[32];
+                    load_acc<DUAL, BN>(tbase + (uint32_t)(c * 32), v, !virt);
+                    epi_chunk(a, tc, t, c, lane, v);
+                }
+                if (!virt) {
+                    tc_fence_before();
+                    mbar_arrive(TEMPTY(acc));
+                    acc ^= 1;
+                    if (acc == 0) acc_phase ^= 1u;
+                }
+            }
+        } else {
+            // TMEM lane quarter = warp % 4; the two warps of a quarter split the
+            // 256 accumulator columns into halves.
+            const int quarter = warp % 4;
+            const int half = (warp - 2) / 4;
+            const int m = quarter * 32 + lane;
+            int acc = 0;
+            uint32_t acc_phase = 0;
+            ItemIter<GROUPED> itr(a0, gtab, gprefix, ginst, gunits);
+            while (itr.next()) {
+                const TcArgs &a = GROUPED ? *itr.a : a0;   // ungrouped: the kernel parameter itself
+                int part;
+                const TileCoord tc = work_item<MODE1>(a, itr.lu, itr.h, part);
+                // split-K parts write FP32 partials; the reduction writes the output
+                const int out_kind = a.ksplit > 1 ? 1 : a.out_kind;
+                void *const out_ptr = a.ksplit > 1 ? (void *)(a.part_ws + part * a.part_stride) : a.out;
+                const int64_t out_cs = a.ksplit > 1 ? a.out_ps : a.out_cs;
+                // every lane waits, and the warp leaves together: tcgen05.ld below is
+                // .sync.aligned, so no lane may skip one that its warp executes
+                const bool ready = wait_bar(TFULL(acc), acc_phase, abort_flag, a.status, 4);
+                if (!__all_sync(0xffffffffu, ready)) break;
+                tc_fence_after();
+                // row of the accumulator this thread owns, and the output stride
+                // between consecutive accumulator columns
+                int64_t row_index;
+                bool row_ok;
+                uint32_t col_stride;
+                if (MODE1) {
+                    const int i = tc.mt * BM + m;
+                    row_ok = i < a.n;
+                    row_index = i;
+                    col_stride = (uint32_t)a.n;       // consecutive fibres r
                 } else {
-                    // stage difference, second tile of the pair (component 1):
-                    // this thread stored the component-0 increment of the same
-                    // points for the first tile, so it reads its own writes back.
-                    // Loads of 4 columns are issued before their stores.
-                    const int64_t pb = e0 - (int64_t)tc.s * out_cs;
-                    const int64_t N = a.out_ps;
-                    const float *inc0 = (const float *)a.out + (int64_t)a.fuse_spair * out_cs + pb;
-                    const double *Uu = a.U + pb, *Uv = a.U + N + pb;
-                    const float *exu = a.extra ? a.extra + pb : nullptr;
-                    const float *exv = a.extra ? a.extra + a.extra_cs + pb : nullptr;
-#pragma unroll
-                    for (int jb = 0; jb < 32; jb += 4) {
-                        float du[4], dv[4];
-                        double uu[4], uv[4];
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            if (jb + j < jmax) {
-                                const uint32_t off = (uint32_t)(jb + j) * col_stride;
-                                du[j] = inc0[off];
-                                dv[j] = __uint_as_float(v[jb + j]) * a.alpha;
-                                uu[j] = Uu[off];
-                                uv[j] = Uv[off];
-                                if (exu) {
-                                    du[j] = exu[off] + du[j];
-                                    dv[j] = exv[off] + dv[j];
+                    const int64_t x = (int64_t)tc.mt * BM + m;
+                    row_ok = x < a.I;
+                    row_index = x + a.I * ((int64_t)a.n * tc.o);
+                    col_stride = (uint32_t)a.I;       // consecutive output indices i
+                }
+                const int64_t col_lim = MODE1 ? a.O : (int64_t)a.n;
+                const int64_t cbase = (int64_t)tc.nt * BN + half * (BN / 2);
+                // element offset of column cbase in this row
+                const int64_t rbase = (int64_t)tc.s * out_cs + row_index + cbase * (int64_t)col_stride;
+    #pragma unroll 1
+                for (int c = 0; c < BN / 64; ++c) {
+                    // warp-uniform exit (depends on the tile and c only), taken before
+                    // the collective load so that every lane issues the same loads
+                    const int64_t col0 = cbase + c * 32;
+                    if (col0 >= col_lim) break;
+                    uint32_t v[32];
+                    const uint32_t taddr = tmem + (uint32_t)acc * ACC_COLS + (uint32_t)(half * (BN / 2) + c * 32) +
+                                           ((uint32_t)(quarter * 32) << 16);
+                    tmem_ld32(taddr, v);
+                    if (DUAL) {
+                        uint32_t w[32];
+                        tmem_ld32(taddr + BN, w);
+    #pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            v[j] = __float_as_uint(__uint_as_float(v[j]) + __uint_as_float(w[j]));
+                    }
+                    const int jmax = (col_lim - col0 >= 32) ? 32 : (int)(col_lim - col0);
+                    // offsets from here are below 32 * col_stride < 2^32
+                    const int64_t e0 = rbase + (int64_t)(c * 32) * col_stride;
+                    // The first tile of a fused stage pair keeps per-element stores:
+                    // the second tile's thread reads its own values back.
+                    const bool readback = a.ksplit == 1 && a.epi == 1 && tc.s == a.fuse_spair;
+                    if (out_kind == 0 || (a.ksplit > 1 || a.epi == 0 ||
+                                          (a.epi == 1 && !readback && tc.s - a.S / 2 != a.fuse_spair))) {
+                        // Plain outputs, as pairs of rows: adjacent rows are adjacent
+                        // elements held by lanes 2k, 2k+1; one exchange gives the even
+                        // lane rows (r, r+1) of column j and the odd lane rows
+                        // (r-1, r) of column j+1, stored as one 4-byte (BF16 planes) or
+                        // 8-byte (FP32) access.  Row bounds are even, so both rows of a
+                        // pair are in range or neither; every lane takes part in the
+                        // exchange.
+                        const int odd = lane & 1;
+                        const int64_t eb = e0 - odd;
+    #pragma unroll
+                        for (int j = 0; j < 32; j += 2) {
+                            const float a0 = __uint_as_float(v[j]) * a.alpha;
+                            const float a1 = __uint_as_float(v[j + 1]) * a.alpha;
+                            const float recv = __shfl_xor_sync(0xffffffffu, odd ? a0 : a1, 1);
+                            const float x0 = odd ? recv : a0, x1 = odd ? a1 : recv;
+                            const int jj = j + odd;
+                            if (row_ok && jj < jmax) {
+                                const uint32_t off = (uint32_t)jj * col_stride;
+                                if (out_kind == 0) {
+                                    uint32_t q0, q1, q2;
+                                    split3_pair(x0, x1, q0, q1, q2);
+                                    uint32_t *w0 = (uint32_t *)((bf16 *)out_ptr + eb + off);
+                                    w0[0] = q0;
+                                    *(uint32_t *)((bf16 *)out_ptr + eb + off + a.out_ps) = q1;
+                                    *(uint32_t *)((bf16 *)out_ptr + eb + off + 2 * a.out_ps) = q2;
+                                } else {
+                                    *(float2 *)((float *)out_ptr + eb + off) = make_float2(x0, x1);
                                 }
                             }
                         }
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            if (jb + j < jmax) {
-                                const int64_t p = pb + (int64_t)(jb + j) * col_stride;
-                                float hu, lu, hv, lv;
-                                split_hilo(uu[j], hu, lu);
-                                split_hilo(uv[j], hv, lv);
-                                float Du, Dv;
-                                react_diff(a.model, hu + lu, hv + lv, du[j], dv[j], Du, Dv);
-                                store_planes_f(a.Dp, N, p, Du);
-                                store_planes_f(a.Dp + 3 * N, N, p, Dv);
+                        continue;
+                    }
+                    if (!row_ok) continue;
+                    if (readback) {
+                        float *o = (float *)out_ptr + e0;
+    #pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            if (j < jmax) o[(uint32_t)j * col_stride] = __uint_as_float(v[j]) * a.alpha;
+                    } else if (a.epi == 2) {
+                        // final update of component s: U_s += widen(extra_s + inc).
+                        // Loads of 8 columns are issued before their stores (the
+                        // compiler must assume U and extra may alias).
+                        const int64_t pb = e0 - (int64_t)tc.s * out_cs;
+                        double *Us = a.U + (int64_t)tc.s * a.out_ps + pb;
+                        const float *ex = a.extra + (int64_t)tc.s * a.extra_cs + pb;
+    #pragma unroll
+                        for (int jb = 0; jb < 32; jb += 8) {
+                            double u[8];
+                            float e[8];
+    #pragma unroll
+                            for (int j = 0; j < 8; ++j) {
+                                if (jb + j < jmax) {
+                                    const uint32_t off = (uint32_t)(jb + j) * col_stride;
+                                    u[j] = Us[off];
+                                    e[j] = ex[off];
+                                }
+                            }
+    #pragma unroll
+                            for (int j = 0; j < 8; ++j)
+                                if (jb + j < jmax)
+                                    Us[(uint32_t)(jb + j) * col_stride] =
+                                        u[j] + widen_f(e[j] + __uint_as_float(v[jb + j]) * a.alpha);
+                        }
+                    } else {
+                        // stage difference, second tile of the pair (component 1):
+                        // this thread stored the component-0 increment of the same
+                        // points for the first tile, so it reads its own writes back.
+                        // Loads of 4 columns are issued before their stores.
+                        const int64_t pb = e0 - (int64_t)tc.s * out_cs;
+                        const int64_t N = a.out_ps;
+                        const float *inc0 = (const float *)a.out + (int64_t)a.fuse_spair * out_cs + pb;
+                        const double *Uu = a.U + pb, *Uv = a.U + N + pb;
+                        const float *exu = a.extra ? a.extra + pb : nullptr;
+                        const float *exv = a.extra ? a.extra + a.extra_cs + pb : nullptr;
+    #pragma unroll
+                        for (int jb = 0; jb < 32; jb += 4) {
+                            float du[4], dv[4];
+                            double uu[4], uv[4];
+    #pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                if (jb + j < jmax) {
+                                    const uint32_t off = (uint32_t)(jb + j) * col_stride;
+                                    du[j] = inc0[off];
+                                    dv[j] = __uint_as_float(v[jb + j]) * a.alpha;
+                                    uu[j] = Uu[off];
+                                    uv[j] = Uv[off];
+                                    if (exu) {
+                                        du[j] = exu[off] + du[j];
+                                        dv[j] = exv[off] + dv[j];
+                                    }
+                                }
+                            }
+    #pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                if (jb + j < jmax) {
+                                    const int64_t p = pb + (int64_t)(jb + j) * col_stride;
+                                    float hu, lu, hv, lv;
+                                    split_hilo(uu[j], hu, lu);
+                                    split_hilo(uv[j], hv, lv);
+                                    float Du, Dv;
+                                    react_diff(a.model, hu + lu, hv + lv, du[j], dv[j], Du, Dv);
+                                    store_planes_f(a.Dp, N, p, Du);
+                                    store_planes_f(a.Dp + 3 * N, N, p, Dv);
+                                }
                             }
                         }
                     }
                 }
+                tc_fence_before();
+                mbar_arrive(TEMPTY(acc));
+                acc ^= 1;
+                if (acc == 0) acc_phase ^= 1u;
             }
-            tc_fence_before();
-            mbar_arrive(TEMPTY(acc));
-            acc ^= 1;
-            if (acc == 0) acc_phase ^= 1u;
         }
     }
     tc_fence_before();
@@ -815,6 +1257,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 #undef TFULL
 #undef TEMPTY
 #undef DRAIN
+#undef EPI_BAR
+#undef EPI_DEC
 }
 
 // ---------------------------------------------------------------------------
@@ -1583,7 +2027,37 @@ static void set_split(ModeLaunch &L, int ksplit, float *ws)
     a.part_ws = ws;
     a.num_tiles = L.base_tiles * ksplit;
     a.num_units = a.num_tiles / a.npair;
+    a.sk = 0;
+    a.sk_ws = nullptr;
+    a.sk_cnt = nullptr;
     L.grid = (int)std::min<int64_t>(a.num_units, num_sms());
+}
+
+// Stream-K partial slots: four per CTA of a num_sms() grid, each a 128 x 256
+// FP32 tile.
+static int64_t streamk_ws_floats() { return 4 * (int64_t)num_sms() * BM * 256; }
+
+// Stream-K grid: one CTA per SM, fewer where the launch has less than four
+// K chunks per SM (at least two CTAs).  npair: the order of the work units
+// (2 pairs the two components' tiles of a spatial tile); a separate
+// last-mode product takes the fused launch's pairing so that both cut the K
+// sums at the same places.
+static int streamk_grid(const ModeLaunch &L)
+{
+    const int64_t Q = L.base_tiles * (int64_t)(L.args.T * L.args.kchunks);
+    return (int)std::min<int64_t>(num_sms(), Q / 4);
+}
+static bool streamk_ok(const ModeLaunch &L) { return streamk_grid(L) >= 2; }
+static void set_streamk(ModeLaunch &L, float *ws, int *cnt, int npair)
+{
+    set_split(L, 1, nullptr);
+    TcArgs &a = L.args;
+    a.npair = npair;
+    a.num_units = a.num_tiles / npair;
+    a.sk = 1;
+    a.sk_ws = ws;
+    a.sk_cnt = cnt;
+    L.grid = streamk_grid(L);
 }
 
 // Turn a last-mode launch (FP32 output, S = 2 S0 with s = component * S0 + x)
@@ -1715,33 +2189,44 @@ __global__ void k_split_reduce_epi(const __grid_constant__ TcArgs a)
 
 // U and model: the state and reaction parameters of fused launches (ignored otherwise)
 // the k_mode_tc instantiation for (mode 1?, tile width, dual accumulators, grouped)
-template <bool GROUPED>
-static void launch_tc(bool mode1, int bn, bool dual, int grid, cudaStream_t st, const TcArgs &a,
+template <bool GROUPED, bool SK>
+static void launch_tc_k(bool mode1, int bn, bool dual, int grid, cudaStream_t st, const TcArgs &a,
                       const TcArgs *gtab = nullptr, const int64_t *gprefix = nullptr, int ginst = 0,
                       int64_t gunits = 0)
 {
     if (bn == 256) {
         if (mode1)
-            k_mode_tc<true, 256, false, GROUPED><<<grid, kThreads, TileCfg<256>::SMEM_BYTES, st>>>(a, gtab, gprefix,
+            k_mode_tc<true, 256, false, GROUPED, SK><<<grid, kThreads, TileCfg<256>::SMEM_BYTES, st>>>(a, gtab, gprefix,
                                                                                                   ginst, gunits);
         else
-            k_mode_tc<false, 256, false, GROUPED><<<grid, kThreads, TileCfg<256>::SMEM_BYTES, st>>>(a, gtab, gprefix,
+            k_mode_tc<false, 256, false, GROUPED, SK><<<grid, kThreads, TileCfg<256>::SMEM_BYTES, st>>>(a, gtab, gprefix,
                                                                                                    ginst, gunits);
     } else if (!dual) {
         if (mode1)
-            k_mode_tc<true, 128, false, GROUPED><<<grid, kThreads, TileCfg<128>::SMEM_BYTES, st>>>(a, gtab, gprefix,
+            k_mode_tc<true, 128, false, GROUPED, SK><<<grid, kThreads, TileCfg<128>::SMEM_BYTES, st>>>(a, gtab, gprefix,
                                                                                                   ginst, gunits);
         else
-            k_mode_tc<false, 128, false, GROUPED><<<grid, kThreads, TileCfg<128>::SMEM_BYTES, st>>>(a, gtab, gprefix,
+            k_mode_tc<false, 128, false, GROUPED, SK><<<grid, kThreads, TileCfg<128>::SMEM_BYTES, st>>>(a, gtab, gprefix,
                                                                                                    ginst, gunits);
     } else {
         if (mode1)
-            k_mode_tc<true, 128, true, GROUPED><<<grid, kThreads, TileCfg<128>::SMEM_BYTES, st>>>(a, gtab, gprefix,
+            k_mode_tc<true, 128, true, GROUPED, SK><<<grid, kThreads, TileCfg<128>::SMEM_BYTES, st>>>(a, gtab, gprefix,
                                                                                                  ginst, gunits);
         else
-            k_mode_tc<false, 128, true, GROUPED><<<grid, kThreads, TileCfg<128>::SMEM_BYTES, st>>>(a, gtab, gprefix,
+            k_mode_tc<false, 128, true, GROUPED, SK><<<grid, kThreads, TileCfg<128>::SMEM_BYTES, st>>>(a, gtab, gprefix,
                                                                                                   ginst, gunits);
     }
+}
+
+// stream-K launches (ungrouped only) run their own instantiations, so the
+// other launches keep the kernel without the stream-K code
+template <bool GROUPED>
+static void launch_tc(bool mode1, int bn, bool dual, int grid, cudaStream_t st, const TcArgs &a,
+                      const TcArgs *gtab = nullptr, const int64_t *gprefix = nullptr, int ginst = 0,
+                      int64_t gunits = 0)
+{
+    if (!GROUPED && a.sk) launch_tc_k<false, true>(mode1, bn, dual, grid, st, a);
+    else launch_tc_k<GROUPED, false>(mode1, bn, dual, grid, st, a, gtab, gprefix, ginst, gunits);
 }
 
 static void set_smem_limits()
@@ -1749,18 +2234,24 @@ static void set_smem_limits()
     static std::once_flag once;
     std::call_once(once, [] {
         const int s256 = (int)TileCfg<256>::SMEM_BYTES, s128 = (int)TileCfg<128>::SMEM_BYTES;
-        cudaFuncSetAttribute(k_mode_tc<true, 256, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s256);
-        cudaFuncSetAttribute(k_mode_tc<false, 256, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s256);
-        cudaFuncSetAttribute(k_mode_tc<true, 128, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s128);
-        cudaFuncSetAttribute(k_mode_tc<false, 128, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s128);
-        cudaFuncSetAttribute(k_mode_tc<true, 128, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s128);
-        cudaFuncSetAttribute(k_mode_tc<false, 128, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s128);
-        cudaFuncSetAttribute(k_mode_tc<true, 256, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s256);
-        cudaFuncSetAttribute(k_mode_tc<false, 256, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s256);
-        cudaFuncSetAttribute(k_mode_tc<true, 128, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s128);
-        cudaFuncSetAttribute(k_mode_tc<false, 128, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s128);
-        cudaFuncSetAttribute(k_mode_tc<true, 128, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s128);
-        cudaFuncSetAttribute(k_mode_tc<false, 128, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s128);
+        cudaFuncSetAttribute(k_mode_tc<true, 256, false, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s256);
+        cudaFuncSetAttribute(k_mode_tc<true, 256, false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s256);
+        cudaFuncSetAttribute(k_mode_tc<false, 256, false, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s256);
+        cudaFuncSetAttribute(k_mode_tc<false, 256, false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s256);
+        cudaFuncSetAttribute(k_mode_tc<true, 128, false, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s128);
+        cudaFuncSetAttribute(k_mode_tc<true, 128, false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s128);
+        cudaFuncSetAttribute(k_mode_tc<false, 128, false, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s128);
+        cudaFuncSetAttribute(k_mode_tc<false, 128, false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s128);
+        cudaFuncSetAttribute(k_mode_tc<true, 128, true, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s128);
+        cudaFuncSetAttribute(k_mode_tc<true, 128, true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s128);
+        cudaFuncSetAttribute(k_mode_tc<false, 128, true, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s128);
+        cudaFuncSetAttribute(k_mode_tc<false, 128, true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s128);
+        cudaFuncSetAttribute(k_mode_tc<true, 256, false, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s256);
+        cudaFuncSetAttribute(k_mode_tc<false, 256, false, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s256);
+        cudaFuncSetAttribute(k_mode_tc<true, 128, false, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s128);
+        cudaFuncSetAttribute(k_mode_tc<false, 128, false, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s128);
+        cudaFuncSetAttribute(k_mode_tc<true, 128, true, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s128);
+        cudaFuncSetAttribute(k_mode_tc<false, 128, true, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s128);
     });
 }
 
@@ -1868,13 +2359,16 @@ static float time_launch(const ModeLaunch &L, cudaStream_t st, cudaEvent_t e0, c
     return best;
 }
 
-// Tile width and split-K factor of one launch.  c[0] / c[1]: the launch
+// Tile width and K decomposition of one launch.  c[0] / c[1]: the launch
 // described with 256- / 128-column tiles (same operands).  Every (width,
-// split) pair within max_split is timed on the launch's own buffers (U: a
-// scratch FP64 state for fused epilogues); a narrower tile or a larger split
-// has to win by 3 %.  times[w * 8 + k - 1] receives the timings (0 = not
-// tried).  Returns k | (w << 4); cached per shape (and in DS_TUNE_CACHE).
-static int autotune_launch(ModeLaunch *c, int ncand, float *ws, cudaStream_t st, float *times, double *U)
+// split) pair within max_split, and stream-K at each width, is timed on the
+// launch's own buffers (U: a scratch FP64 state for fused epilogues); a
+// narrower tile, a larger split or stream-K has to win by 3 %.
+// times[w * 8 + k - 1] receives the split timings, times[16 + w] stream-K's
+// (0 = not tried).  Returns k | (w << 4) | (stream-K << 6); cached per shape
+// (and in DS_TUNE_CACHE).
+static int autotune_launch(ModeLaunch *c, int ncand, float *ws, float *skws, int *skcnt, cudaStream_t st,
+                           float *times, double *U)
 {
     const ModeLaunch &L0 = c[0];
     // dual-accumulator launches are a different kernel: their own cache entries
@@ -1886,7 +2380,8 @@ static int autotune_launch(ModeLaunch *c, int ncand, float *ws, cudaStream_t st,
         auto it = g_tuned.find(key);
         if (it != g_tuned.end()) {
             const int w = ((it->second >> 4) & 1) && ncand > 1 ? 1 : 0;
-            return std::min(it->second & 15, max_split(c[w])) | (w << 4);
+            if (((it->second >> 6) & 1) && skws && streamk_ok(c[w])) return 1 | (w << 4) | (1 << 6);
+            return std::max(1, std::min(it->second & 15, max_split(c[w]))) | (w << 4);
         }
     }
     cudaEvent_t e0, e1;
@@ -1903,6 +2398,15 @@ static int autotune_launch(ModeLaunch *c, int ncand, float *ws, cudaStream_t st,
             if (ms < best_ms * 0.97f) {
                 best_ms = ms;
                 best = k | (w << 4);
+            }
+        }
+        if (skws && streamk_ok(c[w])) {
+            set_streamk(c[w], skws, skcnt, c[w].args.npair);
+            const float ms = time_launch(c[w], st, e0, e1, U);
+            if (times) times[16 + w] = ms;
+            if (ms < best_ms * 0.97f) {
+                best_ms = ms;
+                best = 1 | (w << 4) | (1 << 6);
             }
         }
         set_split(c[w], 1, nullptr);
@@ -1947,7 +2451,10 @@ struct MixedPlan {
     float *bands = nullptr;    // FP32 bands [c][mu][lo, up, rowsum][n_mu]
     bool rhs_tiled = false;    // k_rhs_tiled (d <= 3) instead of k_rhs_planes
     float *part_ws = nullptr;  // split-K partials
-    float tune_ms[3][kMaxD][16];  // autotuner: time of each (tile width, split) candidate (0 = not tried)
+    float *sk_ws = nullptr;    // stream-K partial slots
+    int *sk_cnt = nullptr;     // stream-K delivery counters (zero between launches)
+    // autotuner: time of each (tile width, split) candidate, [16 + w] stream-K (0 = not tried)
+    float tune_ms[3][kMaxD][18];
     StencilF stf[2];
     // launches[group][mode], both components in one launch;
     // group 0 = F, 1 = D2 (slot 2), 2 = D3 (slot 4).  The last mode's launch
@@ -2223,6 +2730,25 @@ ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatu
             cudaGetLastError();
             return cleanup(DS_ERR_OOM, "split-K workspace");
         }
+        // stream-K slots and one delivery counter per work unit of the largest launch
+        {
+            int64_t units = 0;
+            bool any = false;
+            for (int g = 0; g < 3; ++g)
+                for (int mu = 0; mu < d; ++mu)
+                    for (int w = 0; w < 2; ++w) {
+                        units = std::max<int64_t>(units, mp->C[g][mu][w].base_tiles);
+                        any = any || streamk_ok(mp->C[g][mu][w]);
+                    }
+            if (any) {
+                if (cudaMalloc(&mp->sk_ws, sizeof(float) * streamk_ws_floats()) != cudaSuccess ||
+                    cudaMalloc(&mp->sk_cnt, sizeof(int) * units) != cudaSuccess) {
+                    cudaGetLastError();
+                    return cleanup(DS_ERR_OOM, "stream-K workspace");
+                }
+                cudaMemset(mp->sk_cnt, 0, sizeof(int) * units);
+            }
+        }
         // scratch state for the fused epilogues while timing
         double *Us = nullptr;
         if (cudaMalloc(&Us, sizeof(double) * 2 * N) != cudaSuccess) {
@@ -2234,17 +2760,21 @@ ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatu
         cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking);
         for (int g = 0; g < 3; ++g) {
             for (int mu = 0; mu < d; ++mu) {
-                const int code =
-                    autotune_launch(mp->C[g][mu], compensated ? 1 : 2, mp->part_ws, ts, mp->tune_ms[g][mu], Us);
-                const int w = code >> 4, k = code & 15;
+                const int code = autotune_launch(mp->C[g][mu], compensated ? 1 : 2, mp->part_ws, mp->sk_ws,
+                                                 mp->sk_cnt, ts, mp->tune_ms[g][mu], Us);
+                const int w = (code >> 4) & 1, k = code & 15;
+                const bool sk = (code >> 6) & 1;
                 ModeLaunch &L = mp->L[g][mu];
                 L = mp->C[g][mu][w];
-                set_split(L, k, k > 1 ? mp->part_ws : nullptr);
+                if (sk) set_streamk(L, mp->sk_ws, mp->sk_cnt, L.args.npair);
+                else set_split(L, k, k > 1 ? mp->part_ws : nullptr);
                 // the separate form of the last mode runs the same contraction
-                // with the same tiles and split, so both forms give identical values
+                // with the same tiles and K decomposition, so both forms give
+                // identical values
                 if (mu == d - 1) {
                     mp->Lsep[g] = mp->Csep[g][w];
-                    set_split(mp->Lsep[g], k, k > 1 ? mp->part_ws : nullptr);
+                    if (sk) set_streamk(mp->Lsep[g], mp->sk_ws, mp->sk_cnt, L.args.npair);
+                    else set_split(mp->Lsep[g], k, k > 1 ? mp->part_ws : nullptr);
                 }
             }
         }
@@ -2273,7 +2803,17 @@ int mixed_plan_set_tiles(MixedPlan *mp, int g, int mu, int tile_n, int ksplit)
     if (mp->compensated && tile_n != 128) return -1;
     const int w = tile_n == 128 && !mp->compensated ? 1 : 0;
     ModeLaunch &C = mp->C[g][mu][w];
-    // the split-K workspace was sized for the autotuner's range
+    // ksplit 0: stream-K; the split-K workspace was sized for the autotuner's range
+    if (ksplit == 0) {
+        if (!mp->sk_ws || !streamk_ok(C)) return -2;
+        mp->L[g][mu] = C;
+        set_streamk(mp->L[g][mu], mp->sk_ws, mp->sk_cnt, C.args.npair);
+        if (mu == mp->d - 1) {
+            mp->Lsep[g] = mp->Csep[g][w];
+            set_streamk(mp->Lsep[g], mp->sk_ws, mp->sk_cnt, C.args.npair);
+        }
+        return 0;
+    }
     if (ksplit < 1 || ksplit > max_split(C) || (ksplit > 1 && !mp->part_ws)) return -2;
     mp->L[g][mu] = C;
     set_split(mp->L[g][mu], ksplit, ksplit > 1 ? mp->part_ws : nullptr);
@@ -2295,10 +2835,18 @@ int mixed_plan_tuning(const MixedPlan *mp, int g, int mu, int *ksplit, int64_t *
 {
     if (!mp || g < 0 || g > 2 || mu < 0 || mu >= mp->d) return -1;
     const ModeLaunch &L = mp->L[g][mu];
-    *ksplit = L.args.ksplit;
+    *ksplit = L.args.sk ? 0 : L.args.ksplit;
     *tiles = L.base_tiles;
     *tile_n = L.bn;
     for (int k = 0; k < 16; ++k) times[k] = mp->tune_ms[g][mu][k];
+    return 0;
+}
+
+int mixed_plan_streamk_times(const MixedPlan *mp, int g, int mu, float *times)
+{
+    if (!mp || g < 0 || g > 2 || mu < 0 || mu >= mp->d) return -1;
+    times[0] = mp->tune_ms[g][mu][16];
+    times[1] = mp->tune_ms[g][mu][17];
     return 0;
 }
 
@@ -2314,6 +2862,8 @@ void mixed_plan_destroy(MixedPlan *mp)
     cudaFree(mp->incD);
     cudaFree(mp->bands);
     cudaFree(mp->part_ws);
+    cudaFree(mp->sk_ws);
+    cudaFree(mp->sk_cnt);
     delete mp;
 }
 

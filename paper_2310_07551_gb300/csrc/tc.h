@@ -17,6 +17,8 @@ void mixed_plan_destroy(MixedPlan *mp);
 // autotuner record of launch (group g, mode mu): chosen split, output tiles,
 // candidate times in ms (0 = not tried); -1 on bad indices
 int mixed_plan_tuning(const MixedPlan *mp, int g, int mu, int *ksplit, int64_t *tiles, int *tile_n, float *times);
+// the stream-K candidates' times (ms; [0] 256-, [1] 128-column tiles; 0 = not tried)
+int mixed_plan_streamk_times(const MixedPlan *mp, int g, int mu, float *times);
 int mixed_plan_fusion(const MixedPlan *mp, int g, int *fused, float *ms_fused, float *ms_separate);
 int mixed_plan_set_fusion(MixedPlan *mp, int g, int fused);
 int mixed_plan_set_tiles(MixedPlan *mp, int g, int mu, int tile_n, int ksplit);

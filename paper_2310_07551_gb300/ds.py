@@ -76,6 +76,7 @@ def lib() -> ctypes.CDLL:
             "ds_plan_tuning_ex": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                    ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int),
                                    ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
+            "ds_plan_streamk_times": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
             "ds_plan_fusion": ([_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float),
                                 ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
             "ds_plan_profile_read_ex": ([_vp, _dp, ctypes.POINTER(ctypes.c_int64), _dp, _dp], ctypes.c_int),
@@ -232,7 +233,8 @@ class Plan:
 
     def set_tiles(self, group: int, mode: int, tile_n: int, ksplit: int = 1):
         """Override the autotuner for the launch of group (0 F, 1 D2, 2 D3)
-        and mode (1-based): output tile width 256 or 128, split-K factor."""
+        and mode (1-based): output tile width 256 or 128, split-K factor
+        (0: stream-K)."""
         check(lib().ds_plan_set_tiles(self._h, int(group), int(mode) - 1, int(tile_n), int(ksplit)))
 
     def set_fusion(self, group: int, fused: bool):
@@ -243,7 +245,7 @@ class Plan:
 
     def tuning(self):
         """Autotuner record: [(group, mode, ksplit, tiles, tile_n, {"<tile_n>x<split>": ms})]
-        for split-BF16 plans."""
+        for split-BF16 plans; ksplit 0 and the keys "<tile_n>xsk" stand for stream-K."""
         out = []
         for g in range(3):
             for mu in range(len(self.dims)):
@@ -253,9 +255,11 @@ class Plan:
                 ms = (ctypes.c_float * 16)()
                 check(lib().ds_plan_tuning_ex(self._h, g, mu, ctypes.byref(k), ctypes.byref(t),
                                               ctypes.byref(tn), ms))
-                out.append((g, mu + 1, k.value, t.value, tn.value,
-                            {f"{256 if i < 8 else 128}x{i % 8 + 1}": round(ms[i], 4)
-                             for i in range(16) if ms[i] > 0}))
+                sk = (ctypes.c_float * 2)()
+                check(lib().ds_plan_streamk_times(self._h, g, mu, sk))
+                cand = {f"{256 if i < 8 else 128}x{i % 8 + 1}": round(ms[i], 4) for i in range(16) if ms[i] > 0}
+                cand.update({f"{(256, 128)[i]}xsk": round(sk[i], 4) for i in range(2) if sk[i] > 0})
+                out.append((g, mu + 1, k.value, t.value, tn.value, cand))
         return out
 
     def profile(self, enable: bool = True):

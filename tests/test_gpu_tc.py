@@ -173,3 +173,71 @@ def test_compensated_accumulation_removes_most_of_the_bias(ds):
     print("mean relative error bf16x6 %.3e bf16x6c %.3e" % (b6, b6c))
     assert b6 < -5e-7
     assert abs(b6c) < 0.3 * abs(b6)
+
+
+SK_CASES = [
+    ((40, 33, 70), "fhn", (0.1, 2.0, -0.1), -1.0, 1.0, (1.0, 42.1887), 1e-3),
+    ((136, 40), "schnakenberg", (1000.0, 0.1, 0.9), 0.0, 1.0, (1.0, 10.0), 1e-4),
+    ((24, 16, 12, 10), "fhn", (0.1, 2.0, -0.1), -1.0, 1.0, (1.0, 5.0), 1e-3),
+]
+
+
+def set_all_tiles(plan, dims, tn, ksplit):
+    for g in range(3):
+        for mode in range(1, len(dims) + 1):
+            plan.set_tiles(g, mode, tn, ksplit)
+    assert all(t[4] == tn and t[2] == ksplit for t in plan.tuning())
+
+
+def integrate_copy(plan, U0, m):
+    U = torch.from_numpy(U0.copy()).cuda()
+    plan.integrate(U, m)
+    plan.sync(U, check_state=True)
+    return U.cpu().numpy()
+
+
+@pytest.mark.parametrize("dims,model,p,lo,hi,delta,tau", SK_CASES)
+@pytest.mark.parametrize("precision", ["bf16x6", "bf16x6c"])
+def test_streamk_matches_oracle_and_tiled_launches(ds, dims, model, p, lo, hi, delta, tau, precision):
+    """Stream-K launches (every CTA an equal share of the (tile, K chunk)
+    iterations; tiles shared by CTAs summed from FP32 partials by the last
+    CTA to deliver one) on every mode product of the step: within the
+    oracle tolerance of the other tests, and as close to it as the tiled
+    launches (they differ only in where the K sums are cut).  On these small
+    grids each CTA gets about four K chunks, so most tiles are shared by
+    several CTAs."""
+    As = problem(dims, lo, hi, delta)
+    U0 = inputs.initial_state(model, dims, seed=5)
+    m = 3
+    ref = O.step(dims, As, O.phi_set(dims, As, tau), model, p, tau, U0, m)
+    ps = ds.PhiSet(dims, As, tau)
+    plan = ds.Plan(ps, model, p, precision)
+    tn = 128 if precision == "bf16x6c" else 256
+    set_all_tiles(plan, dims, tn, 1)
+    tiled = integrate_copy(plan, U0, m)
+    set_all_tiles(plan, dims, tn, 0)
+    sk = integrate_copy(plan, U0, m)
+    e_t, e_s = relmax(tiled, ref), relmax(sk, ref)
+    print("stream-K", dims, precision, "tiled", e_t, "stream-K", e_s)
+    assert e_s < 2e-5, e_s
+    assert e_s < 2.0 * e_t + 1e-7, (e_s, e_t)
+
+
+@pytest.mark.parametrize("dims,model,p,lo,hi,delta,tau", SK_CASES[:2])
+def test_streamk_fused_and_separate_agree_bitwise_and_repeat(ds, dims, model, p, lo, hi, delta, tau):
+    """Under stream-K the separate last-mode product takes the fused launch's
+    unit order, so both cut the K sums at the same places and the partials
+    are summed in CTA order whichever CTA finishes a tile: fused and separate
+    epilogues agree bit for bit, and so do repeated runs."""
+    As = problem(dims, lo, hi, delta)
+    U0 = inputs.initial_state(model, dims, seed=8)
+    ps = ds.PhiSet(dims, As, tau)
+    plan = ds.Plan(ps, model, p, "bf16x6")
+    set_all_tiles(plan, dims, 256, 0)
+    out = []
+    for fused in (True, False, True):
+        for g in range(3):
+            plan.set_fusion(g, fused)
+        out.append(integrate_copy(plan, U0, 3))
+    assert np.array_equal(out[0], out[1])
+    assert np.array_equal(out[0], out[2])
