@@ -499,8 +499,8 @@ def main():
     }
     if args.precision in ("bf16x6", "bf16x6c"):
         line["autotuner"] = [{"group": ["F", "D2", "D3"][g], "mode": mu, "split_k": k or None, "stream_k": k == 0,
-                              "tiles": t,
-                              "tile_n": tn, "candidates_ms": c} for g, mu, k, t, tn, c in plan.tuning()]
+                              "tiles": t, "tile_n": tn, "tile_order": c.pop("order", 0), "candidates_ms": c}
+                             for g, mu, k, t, tn, c in plan.tuning()]
         line["epilogue_fusion"] = [{"group": ["F", "D2", "D3"][g], "fused": fz,
                                     "ms_fused": round(a, 4), "ms_separate": round(b, 4)}
                                    for g, fz, a, b in plan.fusion()]

@@ -323,6 +323,20 @@ ds_status ds_plan_tuning_ex(const ds_plan *plan, int group, int mu, int *ksplit,
  * one, which then runs the tile's epilogue (no CTA waits for another). */
 ds_status ds_plan_streamk_times(const ds_plan *plan, int group, int mu, float *times_ms);
 
+/* ds_plan_tile_order -- the order in which the CTAs of a mode-1 launch (mu =
+ * 0) take its output tiles: 0 row tiles fastest, then the stacked
+ * phi-matrices, then column tiles, so that neighbouring CTAs share a tile of
+ * the data; 1 column tiles fastest, so that they share a stripe of a
+ * phi-matrix.  times_ms[2]: the tuner's time of each order with the chosen
+ * tile width and K decomposition (0 = not tried).  The order does not change
+ * any result. */
+ds_status ds_plan_tile_order(const ds_plan *plan, int group, int mu, int *order, float *times_ms);
+
+/* ds_plan_set_tile_order -- override that order (1 only for mode-1 launches;
+ * DS_ERR_INVALID_ARG otherwise).  Waits for the plan's stream and drops its
+ * captured graphs. */
+ds_status ds_plan_set_tile_order(ds_plan *plan, int group, int mu, int order);
+
 /* ds_plan_set_tiles -- override the autotuner for one launch: output tile
  * width tile_n (256 or 128) and split-K factor (1 .. the largest factor the
  * tuner considered for that width, or 0 for stream-K where the tuner offered

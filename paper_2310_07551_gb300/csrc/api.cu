@@ -1290,6 +1290,27 @@ ds_status ds_plan_tuning_ex(const ds_plan *p, int group, int mu, int *ksplit, in
     return DS_OK;
 }
 
+ds_status ds_plan_set_tile_order(ds_plan *p, int group, int mu, int order)
+{
+    if (!p) return fail(DS_ERR_INVALID_ARG, "NULL plan");
+    if (!p->mixed) return fail(DS_ERR_UNSUPPORTED, "only split-BF16 plans have tile orders");
+    if (p->st) cudaStreamSynchronize(p->st);
+    if (tc::mixed_plan_set_tile_order(p->mixed, group, mu, order) != 0)
+        return fail(DS_ERR_INVALID_ARG, "group, mode or order out of range");
+    for (auto &kv : p->graphs) cudaGraphExecDestroy(kv.second);
+    p->graphs.clear();
+    return DS_OK;
+}
+
+ds_status ds_plan_tile_order(const ds_plan *p, int group, int mu, int *order, float *times_ms)
+{
+    if (!p || !order || !times_ms) return fail(DS_ERR_INVALID_ARG, "NULL argument");
+    if (!p->mixed) return fail(DS_ERR_UNSUPPORTED, "only split-BF16 plans are tuned");
+    if (tc::mixed_plan_tile_order(p->mixed, group, mu, order, times_ms) != 0)
+        return fail(DS_ERR_INVALID_ARG, "group or mode out of range");
+    return DS_OK;
+}
+
 ds_status ds_plan_streamk_times(const ds_plan *p, int group, int mu, float *times_ms)
 {
     if (!p || !times_ms) return fail(DS_ERR_INVALID_ARG, "NULL argument");

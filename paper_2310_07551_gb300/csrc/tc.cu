@@ -78,6 +78,10 @@ struct alignas(128) TcArgs {
     CUtensorMap tmB;
     int S, T, xs_stride, xs_div, n;
     int mtiles, ntiles, kchunks, out_kind;
+    // tile order of mode-1 launches: 0 row tiles fastest, then stacks, then
+    // column tiles (consecutive CTAs share a data tile); 1 column tiles
+    // fastest, then row tiles, then stacks (they share a phi-matrix stripe)
+    int order;
     int64_t I, O, num_tiles;
     int64_t out_cs, out_ps;
     void *out;
@@ -390,10 +394,17 @@ __device__ __forceinline__ TileCoord decode(const TcArgs &a, int64_t t)
 {
     TileCoord c;
     if (MODE1) {
-        c.mt = (int)(t % a.mtiles);
-        t /= a.mtiles;
-        c.s = (int)(t % a.S);
-        c.nt = (int)(t / a.S);
+        if (a.order) {
+            c.nt = (int)(t % a.ntiles);
+            t /= a.ntiles;
+            c.mt = (int)(t % a.mtiles);
+            c.s = (int)(t / a.mtiles);
+        } else {
+            c.mt = (int)(t % a.mtiles);
+            t /= a.mtiles;
+            c.s = (int)(t % a.S);
+            c.nt = (int)(t / a.S);
+        }
         c.o = 0;
     } else {
         c.nt = (int)(t % a.ntiles);
@@ -2000,6 +2011,7 @@ static ds_status describe(ModeLaunch &L, int d, const int64_t *n, int mu, const 
     a.npair = 1;
     a.num_units = a.num_tiles;
     a.epi = 0;
+    a.order = 0;
     L.base_tiles = a.num_tiles;
     L.N = N;
     L.grid = (int)std::min<int64_t>(a.num_units, num_sms());
@@ -2363,10 +2375,12 @@ static float time_launch(const ModeLaunch &L, cudaStream_t st, cudaEvent_t e0, c
 // described with 256- / 128-column tiles (same operands).  Every (width,
 // split) pair within max_split, and stream-K at each width, is timed on the
 // launch's own buffers (U: a scratch FP64 state for fused epilogues); a
-// narrower tile, a larger split or stream-K has to win by 3 %.
-// times[w * 8 + k - 1] receives the split timings, times[16 + w] stream-K's
-// (0 = not tried).  Returns k | (w << 4) | (stream-K << 6); cached per shape
-// (and in DS_TUNE_CACHE).
+// narrower tile, a larger split or stream-K has to win by 3 %.  Mode-1
+// launches then time the other tile order with the chosen configuration
+// (it, too, has to win by 3 %).  times[w * 8 + k - 1] receives the split
+// timings, times[16 + w] stream-K's, times[18], [19] the two orders' (0 = not
+// tried).  Returns k | (w << 4) | (stream-K << 6) | (order << 7); cached per
+// shape (and in DS_TUNE_CACHE).
 static int autotune_launch(ModeLaunch *c, int ncand, float *ws, float *skws, int *skcnt, cudaStream_t st,
                            float *times, double *U)
 {
@@ -2380,8 +2394,9 @@ static int autotune_launch(ModeLaunch *c, int ncand, float *ws, float *skws, int
         auto it = g_tuned.find(key);
         if (it != g_tuned.end()) {
             const int w = ((it->second >> 4) & 1) && ncand > 1 ? 1 : 0;
-            if (((it->second >> 6) & 1) && skws && streamk_ok(c[w])) return 1 | (w << 4) | (1 << 6);
-            return std::max(1, std::min(it->second & 15, max_split(c[w]))) | (w << 4);
+            const int ord = L0.mode1 ? it->second & (1 << 7) : 0;
+            if (((it->second >> 6) & 1) && skws && streamk_ok(c[w])) return 1 | (w << 4) | (1 << 6) | ord;
+            return std::max(1, std::min(it->second & 15, max_split(c[w]))) | (w << 4) | ord;
         }
     }
     cudaEvent_t e0, e1;
@@ -2410,6 +2425,22 @@ static int autotune_launch(ModeLaunch *c, int ncand, float *ws, float *skws, int
             }
         }
         set_split(c[w], 1, nullptr);
+    }
+    // mode-1 launches: the other tile order (column tiles fastest) for the
+    // chosen width and K decomposition
+    if (L0.mode1) {
+        ModeLaunch &C = c[(best >> 4) & 1];
+        if ((best >> 6) & 1) set_streamk(C, skws, skcnt, C.args.npair);
+        else set_split(C, best & 15, (best & 15) > 1 ? ws : nullptr);
+        C.args.order = 1;
+        const float ms = time_launch(C, st, e0, e1, U);
+        if (times) {
+            times[18] = best_ms;
+            times[19] = ms;
+        }
+        if (ms < best_ms * 0.97f) best |= 1 << 7;
+        C.args.order = 0;
+        set_split(C, 1, nullptr);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -2454,7 +2485,7 @@ struct MixedPlan {
     float *sk_ws = nullptr;    // stream-K partial slots
     int *sk_cnt = nullptr;     // stream-K delivery counters (zero between launches)
     // autotuner: time of each (tile width, split) candidate, [16 + w] stream-K (0 = not tried)
-    float tune_ms[3][kMaxD][18];
+    float tune_ms[3][kMaxD][20];
     StencilF stf[2];
     // launches[group][mode], both components in one launch;
     // group 0 = F, 1 = D2 (slot 2), 2 = D3 (slot 4).  The last mode's launch
@@ -2768,6 +2799,7 @@ ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatu
                 L = mp->C[g][mu][w];
                 if (sk) set_streamk(L, mp->sk_ws, mp->sk_cnt, L.args.npair);
                 else set_split(L, k, k > 1 ? mp->part_ws : nullptr);
+                L.args.order = (code >> 7) & 1;
                 // the separate form of the last mode runs the same contraction
                 // with the same tiles and K decomposition, so both forms give
                 // identical values
@@ -2804,9 +2836,11 @@ int mixed_plan_set_tiles(MixedPlan *mp, int g, int mu, int tile_n, int ksplit)
     const int w = tile_n == 128 && !mp->compensated ? 1 : 0;
     ModeLaunch &C = mp->C[g][mu][w];
     // ksplit 0: stream-K; the split-K workspace was sized for the autotuner's range
+    const int order = mp->L[g][mu].args.order;   // the tuned tile order stays
     if (ksplit == 0) {
         if (!mp->sk_ws || !streamk_ok(C)) return -2;
         mp->L[g][mu] = C;
+        mp->L[g][mu].args.order = order;
         set_streamk(mp->L[g][mu], mp->sk_ws, mp->sk_cnt, C.args.npair);
         if (mu == mp->d - 1) {
             mp->Lsep[g] = mp->Csep[g][w];
@@ -2816,6 +2850,7 @@ int mixed_plan_set_tiles(MixedPlan *mp, int g, int mu, int tile_n, int ksplit)
     }
     if (ksplit < 1 || ksplit > max_split(C) || (ksplit > 1 && !mp->part_ws)) return -2;
     mp->L[g][mu] = C;
+    mp->L[g][mu].args.order = order;
     set_split(mp->L[g][mu], ksplit, ksplit > 1 ? mp->part_ws : nullptr);
     if (mu == mp->d - 1) {
         mp->Lsep[g] = mp->Csep[g][w];
@@ -2847,6 +2882,23 @@ int mixed_plan_streamk_times(const MixedPlan *mp, int g, int mu, float *times)
     if (!mp || g < 0 || g > 2 || mu < 0 || mu >= mp->d) return -1;
     times[0] = mp->tune_ms[g][mu][16];
     times[1] = mp->tune_ms[g][mu][17];
+    return 0;
+}
+
+int mixed_plan_set_tile_order(MixedPlan *mp, int g, int mu, int order)
+{
+    if (!mp || g < 0 || g > 2 || mu < 0 || mu >= mp->d || order < 0 || order > 1) return -1;
+    if (!mp->L[g][mu].mode1 && order) return -1;
+    mp->L[g][mu].args.order = order;
+    return 0;
+}
+
+int mixed_plan_tile_order(const MixedPlan *mp, int g, int mu, int *order, float *times)
+{
+    if (!mp || g < 0 || g > 2 || mu < 0 || mu >= mp->d) return -1;
+    *order = mp->L[g][mu].args.order;
+    times[0] = mp->tune_ms[g][mu][18];
+    times[1] = mp->tune_ms[g][mu][19];
     return 0;
 }
 

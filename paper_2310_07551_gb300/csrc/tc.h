@@ -19,6 +19,10 @@ void mixed_plan_destroy(MixedPlan *mp);
 int mixed_plan_tuning(const MixedPlan *mp, int g, int mu, int *ksplit, int64_t *tiles, int *tile_n, float *times);
 // the stream-K candidates' times (ms; [0] 256-, [1] 128-column tiles; 0 = not tried)
 int mixed_plan_streamk_times(const MixedPlan *mp, int g, int mu, float *times);
+// tile order of the launch (mode-1 launches; 0 row tiles fastest, 1 column tiles fastest)
+// and the tuner's time of each (ms; 0 = not tried)
+int mixed_plan_tile_order(const MixedPlan *mp, int g, int mu, int *order, float *times);
+int mixed_plan_set_tile_order(MixedPlan *mp, int g, int mu, int order);
 int mixed_plan_fusion(const MixedPlan *mp, int g, int *fused, float *ms_fused, float *ms_separate);
 int mixed_plan_set_fusion(MixedPlan *mp, int g, int fused);
 int mixed_plan_set_tiles(MixedPlan *mp, int g, int mu, int tile_n, int ksplit);

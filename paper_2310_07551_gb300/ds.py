@@ -76,6 +76,9 @@ def lib() -> ctypes.CDLL:
             "ds_plan_tuning_ex": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                    ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int),
                                    ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
+            "ds_plan_set_tile_order": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+            "ds_plan_tile_order": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
             "ds_plan_streamk_times": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
             "ds_plan_fusion": ([_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float),
                                 ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
@@ -237,6 +240,11 @@ class Plan:
         (0: stream-K)."""
         check(lib().ds_plan_set_tiles(self._h, int(group), int(mode) - 1, int(tile_n), int(ksplit)))
 
+    def set_tile_order(self, group: int, mode: int, order: int):
+        """Tile order of a mode-1 launch: 0 row tiles fastest, 1 column tiles
+        fastest (results are the same)."""
+        check(lib().ds_plan_set_tile_order(self._h, int(group), int(mode) - 1, int(order)))
+
     def set_fusion(self, group: int, fused: bool):
         check(lib().ds_plan_set_fusion(self._h, int(group), int(bool(fused))))
 
@@ -245,7 +253,9 @@ class Plan:
 
     def tuning(self):
         """Autotuner record: [(group, mode, ksplit, tiles, tile_n, {"<tile_n>x<split>": ms})]
-        for split-BF16 plans; ksplit 0 and the keys "<tile_n>xsk" stand for stream-K."""
+        for split-BF16 plans; ksplit 0 and the keys "<tile_n>xsk" stand for stream-K,
+        "order0" / "order1" are the two tile orders' times of a mode-1 launch and
+        "order": 1 marks the column-fastest order."""
         out = []
         for g in range(3):
             for mu in range(len(self.dims)):
@@ -259,6 +269,12 @@ class Plan:
                 check(lib().ds_plan_streamk_times(self._h, g, mu, sk))
                 cand = {f"{256 if i < 8 else 128}x{i % 8 + 1}": round(ms[i], 4) for i in range(16) if ms[i] > 0}
                 cand.update({f"{(256, 128)[i]}xsk": round(sk[i], 4) for i in range(2) if sk[i] > 0})
+                od = ctypes.c_int()
+                ot = (ctypes.c_float * 2)()
+                check(lib().ds_plan_tile_order(self._h, g, mu, ctypes.byref(od), ot))
+                cand.update({f"order{i}": round(ot[i], 4) for i in range(2) if ot[i] > 0})
+                if od.value:
+                    cand["order"] = 1
                 out.append((g, mu + 1, k.value, t.value, tn.value, cand))
         return out
 
