@@ -323,18 +323,19 @@ ds_status ds_plan_tuning_ex(const ds_plan *plan, int group, int mu, int *ksplit,
  * one, which then runs the tile's epilogue (no CTA waits for another). */
 ds_status ds_plan_streamk_times(const ds_plan *plan, int group, int mu, float *times_ms);
 
-/* ds_plan_tile_order -- the order in which the CTAs of a mode-1 launch (mu =
- * 0) take its output tiles: 0 row tiles fastest, then the stacked
- * phi-matrices, then column tiles, so that neighbouring CTAs share a tile of
- * the data; 1 column tiles fastest, so that they share a stripe of a
- * phi-matrix.  times_ms[2]: the tuner's time of each order with the chosen
- * tile width and K decomposition (0 = not tried).  The order does not change
- * any result. */
+/* ds_plan_tile_order -- the order in which the CTAs of a launch take its
+ * output tiles.  Mode-1 launches (mu = 0): 0 row tiles fastest, then the
+ * stacked phi-matrices, then column tiles, so that neighbouring CTAs share a
+ * tile of the data; 1 column tiles fastest, so that they share a stripe of a
+ * phi-matrix.  Other modes: 0 column tiles fastest (neighbouring CTAs share
+ * a data tile), 1 row tiles fastest (they share a phi-matrix column block).
+ * times_ms[2]: the tuner's time of each order with the chosen tile width and
+ * K decomposition (0 = not tried).  Without stream-K the order changes no
+ * result; with it, it moves where K sums are cut. */
 ds_status ds_plan_tile_order(const ds_plan *plan, int group, int mu, int *order, float *times_ms);
 
-/* ds_plan_set_tile_order -- override that order (1 only for mode-1 launches;
- * DS_ERR_INVALID_ARG otherwise).  Waits for the plan's stream and drops its
- * captured graphs. */
+/* ds_plan_set_tile_order -- override that order (0 or 1; DS_ERR_INVALID_ARG
+ * otherwise).  Waits for the plan's stream and drops its captured graphs. */
 ds_status ds_plan_set_tile_order(ds_plan *plan, int group, int mu, int order);
 
 /* ds_plan_set_tiles -- override the autotuner for one launch: output tile

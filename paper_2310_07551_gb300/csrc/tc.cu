@@ -78,9 +78,12 @@ struct alignas(128) TcArgs {
     CUtensorMap tmB;
     int S, T, xs_stride, xs_div, n;
     int mtiles, ntiles, kchunks, out_kind;
-    // tile order of mode-1 launches: 0 row tiles fastest, then stacks, then
+    // tile order.  Mode-1 launches: 0 row tiles fastest, then stacks, then
     // column tiles (consecutive CTAs share a data tile); 1 column tiles
-    // fastest, then row tiles, then stacks (they share a phi-matrix stripe)
+    // fastest, then row tiles, then stacks (they share a phi-matrix stripe).
+    // Other modes: 0 column tiles fastest, then row tiles (consecutive CTAs
+    // share a data tile); 1 row tiles fastest, then column tiles (they share
+    // a phi-matrix column block); then the outer index and the stack.
     int order;
     int64_t I, O, num_tiles;
     int64_t out_cs, out_ps;
@@ -407,10 +410,17 @@ __device__ __forceinline__ TileCoord decode(const TcArgs &a, int64_t t)
         }
         c.o = 0;
     } else {
-        c.nt = (int)(t % a.ntiles);
-        t /= a.ntiles;
-        c.mt = (int)(t % a.mtiles);
-        t /= a.mtiles;
+        if (a.order) {
+            c.mt = (int)(t % a.mtiles);
+            t /= a.mtiles;
+            c.nt = (int)(t % a.ntiles);
+            t /= a.ntiles;
+        } else {
+            c.nt = (int)(t % a.ntiles);
+            t /= a.ntiles;
+            c.mt = (int)(t % a.mtiles);
+            t /= a.mtiles;
+        }
         c.o = t % a.O;
         c.s = (int)(t / a.O);
     }
@@ -564,10 +574,17 @@ __device__ __forceinline__ TileCoord work_item(const TcArgs &a, int64_t unit, in
     int64_t t = unit / a.ksplit;
     if (a.npair == 1) return decode<MODE1>(a, t);
     TileCoord c;
-    c.nt = (int)(t % a.ntiles);
-    t /= a.ntiles;
-    c.mt = (int)(t % a.mtiles);
-    t /= a.mtiles;
+    if (a.order) {
+        c.mt = (int)(t % a.mtiles);
+        t /= a.mtiles;
+        c.nt = (int)(t % a.ntiles);
+        t /= a.ntiles;
+    } else {
+        c.nt = (int)(t % a.ntiles);
+        t /= a.ntiles;
+        c.mt = (int)(t % a.mtiles);
+        t /= a.mtiles;
+    }
     c.o = t % a.O;
     c.s = (int)(t / a.O) + h * (a.S / 2);
     return c;
@@ -2375,9 +2392,9 @@ static float time_launch(const ModeLaunch &L, cudaStream_t st, cudaEvent_t e0, c
 // described with 256- / 128-column tiles (same operands).  Every (width,
 // split) pair within max_split, and stream-K at each width, is timed on the
 // launch's own buffers (U: a scratch FP64 state for fused epilogues); a
-// narrower tile, a larger split or stream-K has to win by 3 %.  Mode-1
-// launches then time the other tile order with the chosen configuration
-// (it, too, has to win by 3 %).  times[w * 8 + k - 1] receives the split
+// narrower tile, a larger split or stream-K has to win by 3 %.  Then the
+// other tile order is timed with the chosen configuration (it, too, has to
+// win by 3 %).  times[w * 8 + k - 1] receives the split
 // timings, times[16 + w] stream-K's, times[18], [19] the two orders' (0 = not
 // tried).  Returns k | (w << 4) | (stream-K << 6) | (order << 7); cached per
 // shape (and in DS_TUNE_CACHE).
@@ -2394,7 +2411,7 @@ static int autotune_launch(ModeLaunch *c, int ncand, float *ws, float *skws, int
         auto it = g_tuned.find(key);
         if (it != g_tuned.end()) {
             const int w = ((it->second >> 4) & 1) && ncand > 1 ? 1 : 0;
-            const int ord = L0.mode1 ? it->second & (1 << 7) : 0;
+            const int ord = it->second & (1 << 7);
             if (((it->second >> 6) & 1) && skws && streamk_ok(c[w])) return 1 | (w << 4) | (1 << 6) | ord;
             return std::max(1, std::min(it->second & 15, max_split(c[w]))) | (w << 4) | ord;
         }
@@ -2426,9 +2443,8 @@ static int autotune_launch(ModeLaunch *c, int ncand, float *ws, float *skws, int
         }
         set_split(c[w], 1, nullptr);
     }
-    // mode-1 launches: the other tile order (column tiles fastest) for the
-    // chosen width and K decomposition
-    if (L0.mode1) {
+    // the other tile order for the chosen width and K decomposition
+    {
         ModeLaunch &C = c[(best >> 4) & 1];
         if ((best >> 6) & 1) set_streamk(C, skws, skcnt, C.args.npair);
         else set_split(C, best & 15, (best & 15) > 1 ? ws : nullptr);
@@ -2807,6 +2823,7 @@ ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatu
                     mp->Lsep[g] = mp->Csep[g][w];
                     if (sk) set_streamk(mp->Lsep[g], mp->sk_ws, mp->sk_cnt, L.args.npair);
                     else set_split(mp->Lsep[g], k, k > 1 ? mp->part_ws : nullptr);
+                    mp->Lsep[g].args.order = L.args.order;
                 }
             }
         }
@@ -2845,6 +2862,7 @@ int mixed_plan_set_tiles(MixedPlan *mp, int g, int mu, int tile_n, int ksplit)
         if (mu == mp->d - 1) {
             mp->Lsep[g] = mp->Csep[g][w];
             set_streamk(mp->Lsep[g], mp->sk_ws, mp->sk_cnt, C.args.npair);
+            mp->Lsep[g].args.order = order;
         }
         return 0;
     }
@@ -2855,6 +2873,7 @@ int mixed_plan_set_tiles(MixedPlan *mp, int g, int mu, int tile_n, int ksplit)
     if (mu == mp->d - 1) {
         mp->Lsep[g] = mp->Csep[g][w];
         set_split(mp->Lsep[g], ksplit, ksplit > 1 ? mp->part_ws : nullptr);
+        mp->Lsep[g].args.order = order;
     }
     return 0;
 }
@@ -2888,8 +2907,8 @@ int mixed_plan_streamk_times(const MixedPlan *mp, int g, int mu, float *times)
 int mixed_plan_set_tile_order(MixedPlan *mp, int g, int mu, int order)
 {
     if (!mp || g < 0 || g > 2 || mu < 0 || mu >= mp->d || order < 0 || order > 1) return -1;
-    if (!mp->L[g][mu].mode1 && order) return -1;
     mp->L[g][mu].args.order = order;
+    if (mu == mp->d - 1) mp->Lsep[g].args.order = order;
     return 0;
 }
 

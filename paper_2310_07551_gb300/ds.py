@@ -241,8 +241,8 @@ class Plan:
         check(lib().ds_plan_set_tiles(self._h, int(group), int(mode) - 1, int(tile_n), int(ksplit)))
 
     def set_tile_order(self, group: int, mode: int, order: int):
-        """Tile order of a mode-1 launch: 0 row tiles fastest, 1 column tiles
-        fastest (results are the same)."""
+        """Tile order of a launch (0 or 1; see ds_plan_tile_order).  Without
+        stream-K the results are the same."""
         check(lib().ds_plan_set_tile_order(self._h, int(group), int(mode) - 1, int(order)))
 
     def set_fusion(self, group: int, fused: bool):
@@ -254,8 +254,8 @@ class Plan:
     def tuning(self):
         """Autotuner record: [(group, mode, ksplit, tiles, tile_n, {"<tile_n>x<split>": ms})]
         for split-BF16 plans; ksplit 0 and the keys "<tile_n>xsk" stand for stream-K,
-        "order0" / "order1" are the two tile orders' times of a mode-1 launch and
-        "order": 1 marks the column-fastest order."""
+        "order0" / "order1" are the two tile orders' times and "order": 1 marks the
+        second order."""
         out = []
         for g in range(3):
             for mu in range(len(self.dims)):

@@ -131,9 +131,8 @@ def test_fused_epilogues_match_separate_kernels_bitwise(ds, dims, model, p, lo, 
     ((24, 16, 12, 10), "fhn", (0.1, 2.0, -0.1), -1.0, 1.0, (1.0, 5.0), 1e-3),
 ])
 def test_tile_widths_agree_bitwise(ds, dims, model, p, lo, hi, delta, tau):
-    """128- and 256-column output tiles, and the two tile orders of mode-1
-    launches, change which CTA computes an element, not the order of its
-    sums: with split-K off, results agree bit for bit (and are within the
+    """128- and 256-column output tiles, and the two tile orders, change
+    which CTA computes an element, not the order of its sums: with split-K off, results agree bit for bit (and are within the
     oracle tolerance of the other tests)."""
     As = problem(dims, lo, hi, delta)
     U0 = inputs.initial_state(model, dims, seed=4)
@@ -152,16 +151,17 @@ def test_tile_widths_agree_bitwise(ds, dims, model, p, lo, hi, delta, tau):
     assert np.array_equal(out[0], out[1])
     with pytest.raises(ds.DsError):
         plan.set_tiles(0, 1, 192, 1)
-    # the mode-1 launches' other tile order: same values
+    # every launch in the other tile order: same values
     for g in range(3):
-        plan.set_tile_order(g, 1, 1)
-    assert all(t[5].get("order", 0) == 1 for t in plan.tuning() if t[1] == 1)
+        for mode in range(1, len(dims) + 1):
+            plan.set_tile_order(g, mode, 1)
+    assert all(t[5].get("order", 0) == 1 for t in plan.tuning())
     U = torch.from_numpy(U0.copy()).cuda()
     plan.integrate(U, 3)
     plan.sync(U, check_state=True)
     assert np.array_equal(out[0], U.cpu().numpy())
     with pytest.raises(ds.DsError):
-        plan.set_tile_order(0, 2, 1)
+        plan.set_tile_order(0, 1, 2)
 
 
 def test_compensated_accumulation_removes_most_of_the_bias(ds):
