@@ -255,10 +255,12 @@ def run_batch(args, rank, world):
     t = e0.elapsed_time(e1) / 1e3
     value = npts * args.steps / t
     # the timed graphs' fused-or-separate choices (ms 0: replayed from DS_TUNE_CACHE)
-    fusion = None
+    fusion = order = None
     if args.precision != "f64":
         fusion = {("F", "D2", "D3")[g]: {"fused": f, "ms_fused": a, "ms_separate": b}
                   for g, f, a, b in batch.fusion()}
+        order = {("F", "D2", "D3")[g]: {"order": o, "ms_order0": a, "ms_order1": b}
+                 for g, o, a, b in batch.tile_order()}
     useful = sum(40.0 * np.prod(i.dims) * sum(i.dims) for i in insts)   # flops per batch step
     err = None
     if args.precision != "f64" and args.err_steps != 0:
@@ -293,6 +295,7 @@ def run_batch(args, rank, world):
     }
     if fusion is not None:
         line["config"]["epilogue_fusion"] = fusion
+        line["config"]["mode1_tile_order"] = order
     print(json.dumps(line), flush=True)
     batch.close()
 

@@ -400,6 +400,14 @@ int64_t ds_batch_kernels_per_step(const ds_batch *batch);
  * first ds_batch_integrate or for other precisions. */
 ds_status ds_batch_fusion(const ds_batch *batch, int group, int *fused, float *ms_fused, float *ms_separate);
 
+/* ds_batch_tile_order -- the tile order (as ds_plan_tile_order) of the
+ * grouped mode-1 product of group g in the most recently captured
+ * split-BF16 batch graph; building the first graph of a batch shape times
+ * both orders (times_ms, fastest of five; 0 when replayed) and keeps the
+ * faster.  DS_ERR_UNSUPPORTED before the first ds_batch_integrate or for
+ * other precisions. */
+ds_status ds_batch_tile_order(const ds_batch *batch, int group, int *order, float *times_ms);
+
 /* ds_batch_set_fusion -- fix that choice for group g in graphs built from now
  * on: fused = 1 fused epilogue, 0 separate stage kernel, -1 timed (default).
  * Waits for the batch's stream and drops its captured graphs. */

@@ -1182,6 +1182,26 @@ ds_status ds_batch_fusion(const ds_batch *b, int group, int *fused, float *ms_fu
     return DS_OK;
 }
 
+ds_status ds_batch_tile_order(const ds_batch *b, int group, int *order, float *times_ms)
+{
+    if (!b || !order || !times_ms) return fail(DS_ERR_INVALID_ARG, "NULL argument");
+    if (group < 0 || group > 2) return fail(DS_ERR_INVALID_ARG, "group out of range");
+    bool any = false;
+    times_ms[0] = times_ms[1] = 0.f;
+    for (const auto &g : b->graphs) {
+        if (!g.group) continue;
+        float t[2];
+        tc::mixed_group_tile_order(g.group, group, order, t);
+        if (t[0] > 0.f) {
+            times_ms[0] = t[0];
+            times_ms[1] = t[1];
+        }
+        any = true;
+    }
+    if (!any) return fail(DS_ERR_UNSUPPORTED, "no grouped launches built (split-BF16 batches, after an integrate)");
+    return DS_OK;
+}
+
 ds_status ds_batch_set_fusion(ds_batch *b, int group, int fused)
 {
     if (!b) return fail(DS_ERR_INVALID_ARG, "NULL batch");

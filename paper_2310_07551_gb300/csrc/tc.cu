@@ -2999,6 +2999,9 @@ struct MixedGroup {
         int64_t *sprefix = nullptr;
         int64_t points = 0;
         float ms[2] = {};          // {fused, separate} at creation (0 = replayed)
+        // mode-1 slots: the problems' tile order and its two timings
+        int order = 0;
+        float oms[2] = {};
     };
     std::vector<Slot> slots;       // [g * d + mu]
     // every problem's F = K U + g(U) in one launch (all problems tiled)
@@ -3136,6 +3139,45 @@ ds_status mixed_group_create(const std::vector<MixedPlan *> &mps, const std::vec
                 r = fail(DS_ERR_OOM, "grouped launch tables");
                 break;
             }
+            if (mu == 0 && units > 0) {
+                // the grouped mode-1 product in both tile orders (cache key
+                // epi = 40; value order + 1)
+                const ShapeKey key{true, ninst, g, d, Ntot, units, 40 + (sl.dual ? 32 : 0)};
+                int cached = 0;
+                {
+                    std::lock_guard<std::mutex> lk(g_tune_mu);
+                    tune_cache_load();
+                    auto it = g_tuned.find(key);
+                    if (it != g_tuned.end()) cached = it->second;
+                }
+                if (cached) {
+                    sl.order = cached - 1;
+                } else {
+                    for (int ord = 0; ord < 2; ++ord) {
+                        for (auto &t : tab_s) t.order = ord;
+                        cudaMemcpy(sl.tab, tab_s.data(), sizeof(TcArgs) * ninst, cudaMemcpyHostToDevice);
+                        launch_group_slot(sl, false, 0);
+                        launch_group_slot(sl, false, 0);
+                        float best = 1e30f;
+                        for (int rep = 0; rep < 5; ++rep) {
+                            cudaEventRecord(e0, 0);
+                            launch_group_slot(sl, false, 0);
+                            cudaEventRecord(e1, 0);
+                            cudaEventSynchronize(e1);
+                            float ms = 0.f;
+                            cudaEventElapsedTime(&ms, e0, e1);
+                            best = std::min(best, ms);
+                        }
+                        sl.oms[ord] = best;
+                    }
+                    sl.order = sl.oms[1] < 0.97f * sl.oms[0] ? 1 : 0;
+                    std::lock_guard<std::mutex> lk(g_tune_mu);
+                    g_tuned[key] = sl.order + 1;
+                    tune_cache_append(key, sl.order + 1);
+                }
+                for (auto &t : tab) t.order = sl.order;
+                sl.a0.order = sl.order;
+            }
             if (last && units > 0) {
                 const ShapeKey key{false, ninst, g, d, Ntot, units, 20 + (sl.dual ? 32 : 0)};
                 int cached = 0;
@@ -3234,6 +3276,16 @@ int mixed_group_enqueue(const MixedGroup *G, cudaStream_t st, Prof *prof)
         L += sl.sep ? 2 : 1;
     }
     return L;
+}
+
+int mixed_group_tile_order(const MixedGroup *G, int g, int *order, float *times)
+{
+    if (!G || g < 0 || g > 2) return -1;
+    const MixedGroup::Slot &sl = G->slots[g * G->d];
+    *order = sl.order;
+    times[0] = sl.oms[0];
+    times[1] = sl.oms[1];
+    return 0;
 }
 
 int mixed_group_fusion(const MixedGroup *G, int g, int *fused, float *ms_fused, float *ms_separate)

@@ -45,6 +45,7 @@ int mixed_group_enqueue(const MixedGroup *G, cudaStream_t st, Prof *prof);
 // problem's grid has no tiled stencil kernel
 int mixed_group_enqueue_rhs(const MixedGroup *G, cudaStream_t st);
 int mixed_group_fusion(const MixedGroup *G, int g, int *fused, float *ms_fused, float *ms_separate);
+int mixed_group_tile_order(const MixedGroup *G, int g, int *order, float *times);
 // FP32 CUDA-core path pointwise kernels (two components, N points each)
 void launch_rhs_f32(const Stencil *sten, const Model &m, int64_t N, const double *U, float *F,
                     cudaStream_t st);

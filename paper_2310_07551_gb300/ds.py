@@ -93,6 +93,8 @@ def lib() -> ctypes.CDLL:
             "ds_batch_fusion": ([_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float),
                                  ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
             "ds_batch_set_fusion": ([_vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+            "ds_batch_tile_order": ([_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)],
+                                    ctypes.c_int),
             "ds_last_error": ([], ctypes.c_char_p),
             "ds_version": ([], ctypes.c_char_p),
         }
@@ -378,6 +380,17 @@ class Batch:
             b = ctypes.c_float()
             check(lib().ds_batch_fusion(self._h, g, ctypes.byref(fz), ctypes.byref(a), ctypes.byref(b)))
             out.append((g, bool(fz.value), float(a.value), float(b.value)))
+        return out
+
+    def tile_order(self):
+        """[(group, order, ms_order0, ms_order1)] of the grouped mode-1 products
+        of the last captured split-BF16 graph."""
+        out = []
+        for g in range(3):
+            od = ctypes.c_int()
+            t = (ctypes.c_float * 2)()
+            check(lib().ds_batch_tile_order(self._h, g, ctypes.byref(od), t))
+            out.append((g, od.value, float(t[0]), float(t[1])))
         return out
 
     def set_fusion(self, group: int, fused):

@@ -63,6 +63,7 @@ def test_batch_matches_individual_plans_and_oracle(ds, precision, fusion):
             assert batch.kernels_per_step == 1 + 6 + (0 if fusion else 3)
         else:
             assert all(a > 0 and b > 0 for _, _, a, b in fz) or all(a == 0 for _, _, a, _ in fz)
+        assert all(o in (0, 1) for _, o, _, _ in batch.tile_order())
     for k, inst in enumerate(insts):
         ps = ds.PhiSet(inst.dims, As[k], inst.tau)
         plan = ds.Plan(ps, "schnakenberg", inst.params, precision)
