@@ -2341,8 +2341,10 @@ static void tune_cache_load()
     if (!f) return;
     int m1, n, S, T, epi, k;
     long long I, O;
+    // values: split factor 1..8 in the low bits, then the tile-width (16),
+    // stream-K (64) and tile-order (128) flags
     while (fscanf(f, "%d %d %d %d %lld %lld %d %d", &m1, &n, &S, &T, &I, &O, &epi, &k) == 8)
-        if ((k & 15) >= 1 && (k & 15) <= 8 && (k >> 4) <= 1)
+        if ((k & 15) >= 1 && (k & 15) <= 8 && (k & ~(15 | 16 | 64 | 128)) == 0)
             g_tuned[ShapeKey{m1 != 0, n, S, T, (int64_t)I, (int64_t)O, epi}] = k;
     fclose(f);
 }
