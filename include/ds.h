@@ -46,7 +46,7 @@ extern "C" {
 typedef enum {
     DS_OK = 0,
     DS_ERR_INVALID_ARG = 1,   /* bad pointer, size, tau, model, ... */
-    DS_ERR_UNSUPPORTED = 2,   /* valid request this build cannot serve */
+    DS_ERR_UNSUPPORTED = 2,   /* valid request outside the library's shapes/precisions */
     DS_ERR_OOM = 3,           /* device allocation failed */
     DS_ERR_CUDA = 4,          /* a CUDA runtime call failed */
     DS_ERR_NONFINITE = 5,     /* NaN/Inf found in the state */
