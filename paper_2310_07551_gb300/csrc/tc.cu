@@ -986,6 +986,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else {
         // ---------------- epilogue (warps 2..9) ----------------
+        // Two forms of the same per-chunk output code: the stream-K
+        // instantiations call it as epi_chunk (shared with the finishing of
+        // shared tiles); the others keep it inline, where it compiles to the
+        // register allocation of the kernel without stream-K (the shared form
+        // spilled there and cost 5-14 % per launch).
         if constexpr (SK && !GROUPED) {
             // TMEM lane quarter = warp % 4; the two warps of a quarter split the
             // 256 accumulator columns into halves.
