@@ -468,6 +468,9 @@ def main():
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak,
                 "traffic": NCU_TRAFFIC.get(f"{_source_hash()}:{w.name}"),
+                "traffic_source": (f"profiles/launches_{w.name}.md (ncu, this kernel source)"
+                                   if f"{_source_hash()}:{w.name}" in NCU_TRAFFIC else
+                                   "no ncu capture of this kernel source in this workload's tuned configuration"),
                 "alg_bytes_per_launch": tc_by / tc_n if tc_n else None,
                 "launches_per_step": tc_n // kprof,
                 "kernel": "k_mode_tc (tcgen05 split-BF16 mode product)",
