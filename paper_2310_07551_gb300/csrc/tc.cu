@@ -1045,12 +1045,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                     // stream-K share of a unit that other CTAs share: the FP32
                     // partial to this CTA's slot (coalesced over the rows m)
                     float *ws = a.sk_ws + (int64_t)itr.slot * (BM * BN) + (half * (BN / 2)) * BM + m;
-    #pragma unroll 1
+#pragma unroll 1
                     for (int c = 0; c < BN / 64; ++c) {
                         if (t.cbase + c * 32 >= t.col_lim) break;
                         uint32_t v[32];
                         load_acc<DUAL, BN>(tbase + (uint32_t)(c * 32), v, true);
-    #pragma unroll
+#pragma unroll
                         for (int j = 0; j < 32; ++j) __stcg(ws + (c * 32 + j) * BM, __uint_as_float(v[j]));
                     }
                     tc_fence_before();
@@ -1079,7 +1079,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (*sk_flag) fin[fin[0] < 0 ? 0 : 1] = itr.lu;
                     continue;
                 }
-    #pragma unroll 1
+#pragma unroll 1
                 for (int c = 0; c < BN / 64; ++c) {
                     // warp-uniform exit (depends on the tile and c only), taken before
                     // the collective load so that every lane issues the same loads
@@ -1137,7 +1137,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int64_t cbase = (int64_t)tc.nt * BN + half * (BN / 2);
                 // element offset of column cbase in this row
                 const int64_t rbase = (int64_t)tc.s * out_cs + row_index + cbase * (int64_t)col_stride;
-    #pragma unroll 1
+#pragma unroll 1
                 for (int c = 0; c < BN / 64; ++c) {
                     // warp-uniform exit (depends on the tile and c only), taken before
                     // the collective load so that every lane issues the same loads
@@ -1150,7 +1150,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (DUAL) {
                         uint32_t w[32];
                         tmem_ld32(taddr + BN, w);
-    #pragma unroll
+#pragma unroll
                         for (int j = 0; j < 32; ++j)
                             v[j] = __float_as_uint(__uint_as_float(v[j]) + __uint_as_float(w[j]));
                     }
@@ -1171,7 +1171,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         // exchange.
                         const int odd = lane & 1;
                         const int64_t eb = e0 - odd;
-    #pragma unroll
+#pragma unroll
                         for (int j = 0; j < 32; j += 2) {
                             const float a0 = __uint_as_float(v[j]) * a.alpha;
                             const float a1 = __uint_as_float(v[j + 1]) * a.alpha;
@@ -1197,7 +1197,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (!row_ok) continue;
                     if (readback) {
                         float *o = (float *)out_ptr + e0;
-    #pragma unroll
+#pragma unroll
                         for (int j = 0; j < 32; ++j)
                             if (j < jmax) o[(uint32_t)j * col_stride] = __uint_as_float(v[j]) * a.alpha;
                     } else if (a.epi == 2) {
@@ -1207,11 +1207,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const int64_t pb = e0 - (int64_t)tc.s * out_cs;
                         double *Us = a.U + (int64_t)tc.s * a.out_ps + pb;
                         const float *ex = a.extra + (int64_t)tc.s * a.extra_cs + pb;
-    #pragma unroll
+#pragma unroll
                         for (int jb = 0; jb < 32; jb += 8) {
                             double u[8];
                             float e[8];
-    #pragma unroll
+#pragma unroll
                             for (int j = 0; j < 8; ++j) {
                                 if (jb + j < jmax) {
                                     const uint32_t off = (uint32_t)(jb + j) * col_stride;
@@ -1219,7 +1219,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                                     e[j] = ex[off];
                                 }
                             }
-    #pragma unroll
+#pragma unroll
                             for (int j = 0; j < 8; ++j)
                                 if (jb + j < jmax)
                                     Us[(uint32_t)(jb + j) * col_stride] =
@@ -1236,11 +1236,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const double *Uu = a.U + pb, *Uv = a.U + N + pb;
                         const float *exu = a.extra ? a.extra + pb : nullptr;
                         const float *exv = a.extra ? a.extra + a.extra_cs + pb : nullptr;
-    #pragma unroll
+#pragma unroll
                         for (int jb = 0; jb < 32; jb += 4) {
                             float du[4], dv[4];
                             double uu[4], uv[4];
-    #pragma unroll
+#pragma unroll
                             for (int j = 0; j < 4; ++j) {
                                 if (jb + j < jmax) {
                                     const uint32_t off = (uint32_t)(jb + j) * col_stride;
@@ -1254,7 +1254,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                                     }
                                 }
                             }
-    #pragma unroll
+#pragma unroll
                             for (int j = 0; j < 4; ++j) {
                                 if (jb + j < jmax) {
                                     const int64_t p = pb + (int64_t)(jb + j) * col_stride;
