@@ -29,7 +29,9 @@ double *g_scratch_ptr[kMaxDevices] = {};
 
 // Device address of g_static_scratch on the current device.  In host code
 // the array's name is only a host-side stand-in, so the address is looked up
-// once per device with that device current, and cached.
+// once per device with that device current, and cached for the life of the
+// process.  The address belongs to the device's context: a cudaDeviceReset
+// ends that context, and the cached address with it.
 ds_status scratch_address(double **out)
 {
     int dev = -1;
@@ -67,8 +69,10 @@ extern "C" ds_status ds_tucker_static(const ds_grid *grid, const double *X, doub
                             "grid has more than 1048576 points, the size of the static scratch of "
                             "ds_tucker_static; use ds_tucker");
     }
+    ds_status r = ds::check_device();
+    if (r != DS_OK) return r;
     double *scratch = nullptr;
-    ds_status r = scratch_address(&scratch);
+    r = scratch_address(&scratch);
     if (r != DS_OK) return r;
     cudaStream_t st = (cudaStream_t)stream;
     // every mode product writes all of its output (beta = 0), so nothing in

@@ -1,10 +1,12 @@
 """ds_tucker_static: the Tucker entry point for callers that cannot allocate
 device memory (allocator callbacks, hosts that forbid allocation after
-start-up, plugins whose framework owns the device heap).  It must give the
-result of the allocating entry point ds_tucker, call after call, while its
-intermediates live in the library's fixed device array.
+start-up, plugins whose framework owns the device heap).  It runs the same
+kernels as the allocating entry point ds_tucker on the same data, so the two
+must agree bit for bit, call after call, while its intermediates live in the
+library's fixed device array.
 
 Kept in a file of its own that collects last."""
+import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
@@ -25,8 +27,33 @@ def test_static_tucker_matches_ds_tucker_on_two_calls_in_a_row():
             ref = ds.tucker(X, Ls, transpose=transpose)
             got = ds.tucker_static(X, Ls, transpose=transpose)
             torch.cuda.synchronize()
-            rel = float((got - ref).abs().max() / ref.abs().max())
-            assert rel < 1e-13, (call, transpose, rel)
+            assert torch.equal(got, ref), (call, transpose)
+
+
+def test_static_tucker_matches_the_oracle():
+    from oracle import oracle as O
+    from paper_2310_07551_gb300 import ds, inputs
+    dims = (40, 24, 18)
+    X = inputs.random_tensor(dims, seed=36)
+    Ls = [inputs.random_matrix(n, seed=37, stream=q) for q, n in enumerate(dims)]
+    ref = O.tucker(X, Ls)
+    got = ds.tucker_static(torch.from_numpy(X).cuda(), [torch.from_numpy(L).cuda() for L in Ls]).cpu().numpy()
+    rel = float(np.abs(got - ref).max() / np.abs(ref).max())
+    assert rel < 1e-13, rel
+
+
+def test_static_tucker_flat_grid_at_the_launch_limits():
+    """(2, 2, 256, 512): the mode-2 product has 131,072 outer slices, more
+    than one launch's 65,535 grid rows, and 524,288 points fit the static
+    scratch; the result must still be the allocating entry point's."""
+    from paper_2310_07551_gb300 import ds, inputs
+    dims = (2, 2, 256, 512)
+    X = torch.from_numpy(inputs.random_tensor(dims, seed=38)).cuda()
+    Ls = [torch.from_numpy(inputs.random_matrix(n, seed=39, stream=q)).cuda() for q, n in enumerate(dims)]
+    ref = ds.tucker(X, Ls)
+    got = ds.tucker_static(X, Ls)
+    torch.cuda.synchronize()
+    assert torch.equal(got, ref)
 
 
 def test_static_tucker_rejects_grids_beyond_its_scratch():
