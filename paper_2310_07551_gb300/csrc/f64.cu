@@ -101,55 +101,69 @@ void launch_sgemm(const SGemm &g, cudaStream_t st)
     k_gemm<float, SGemm><<<grid, 256, 0, st>>>(g);
 }
 
-void launch_mode_product_f32(int d, const int64_t *n, const float *X, int mu, const float *L,
-                             int transpose, float *Y, double alpha, double beta, cudaStream_t st)
+namespace {
+// A mode product's GEMM with 64-bit sizes, launched as chunks that each fit
+// the launch limits: at most 65535 batch entries (gridDim.z), 65535 row
+// tiles of 64 (gridDim.y) and 2^30 columns (int indexing inside k_gemm).
+// Each chunk is an independent GEMM on offset pointers, so the result is the
+// same as one launch would give.
+constexpr int64_t kMaxBatch = 65535, kMaxRows = 65535 * (int64_t)BM, kMaxCols = (int64_t)1 << 30;
+
+template <typename G, typename T>
+void launch_chunked(int64_t M, int64_t N, int64_t K, int64_t batch, const T *A, int64_t sAm, int64_t sAk,
+                    int64_t sAb, const T *B, int64_t sBk, int64_t sBn, int64_t sBb, T *C, int64_t sCm,
+                    int64_t sCn, int64_t sCb, double alpha, double beta, void (*launch)(const G &, cudaStream_t),
+                    cudaStream_t st)
+{
+    for (int64_t b0 = 0; b0 < batch; b0 += kMaxBatch)
+        for (int64_t m0 = 0; m0 < M; m0 += kMaxRows)
+            for (int64_t n0 = 0; n0 < N; n0 += kMaxCols) {
+                G g{};
+                g.M = (int)std::min(kMaxRows, M - m0);
+                g.N = (int)std::min(kMaxCols, N - n0);
+                g.K = (int)K;
+                g.batch = (int)std::min(kMaxBatch, batch - b0);
+                g.A = A + b0 * sAb + m0 * sAm;
+                g.sAm = sAm; g.sAk = sAk; g.sAb = sAb;
+                g.B = B + b0 * sBb + n0 * sBn;
+                g.sBk = sBk; g.sBn = sBn; g.sBb = sBb;
+                g.C = C + b0 * sCb + m0 * sCm + n0 * sCn;
+                g.sCm = sCm; g.sCn = sCn; g.sCb = sCb;
+                g.alpha = alpha;
+                g.beta = beta;
+                launch(g, st);
+            }
+}
+
+// Y = X x_mu L (+ beta Y) as a GEMM; L(i, j) = L[i + m j], transposed L[j + m i]
+template <typename G, typename T>
+void mode_product(int d, const int64_t *n, const T *X, int mu, const T *L, int transpose, T *Y, double alpha,
+                  double beta, void (*launch)(const G &, cudaStream_t), cudaStream_t st)
 {
     int64_t I = 1, O = 1, m = n[mu];
     for (int q = 0; q < mu; ++q) I *= n[q];
     for (int q = mu + 1; q < d; ++q) O *= n[q];
     const int64_t sLi = transpose ? m : 1, sLj = transpose ? 1 : m;
-    SGemm g{};
-    g.alpha = alpha;
-    g.beta = beta;
-    if (mu == 0) {
-        g.M = (int)O; g.N = (int)m; g.K = (int)m; g.batch = 1;
-        g.A = X; g.sAm = m; g.sAk = 1; g.sAb = 0;
-        g.B = L; g.sBk = sLj; g.sBn = sLi; g.sBb = 0;
-        g.C = Y; g.sCm = m; g.sCn = 1; g.sCb = 0;
-    } else {
-        g.M = (int)m; g.N = (int)I; g.K = (int)m; g.batch = (int)O;
-        g.A = L; g.sAm = sLi; g.sAk = sLj; g.sAb = 0;
-        g.B = X; g.sBk = I; g.sBn = 1; g.sBb = I * m;
-        g.C = Y; g.sCm = I; g.sCn = 1; g.sCb = I * m;
-    }
-    launch_sgemm(g, st);
+    if (mu == 0)
+        // Y[r][i] = sum_j X[r][j] L(i, j): M = fibres r, N = i, K = j
+        launch_chunked<G, T>(O, m, m, 1, X, m, 1, 0, L, sLj, sLi, 0, Y, m, 1, 0, alpha, beta, launch, st);
+    else
+        // per outer index o: Y[o][i][x] = sum_j L(i, j) X[o][j][x]
+        launch_chunked<G, T>(m, I, m, O, L, sLi, sLj, 0, X, I, 1, I * m, Y, I, 1, I * m, alpha, beta, launch,
+                             st);
+}
+}  // namespace
+
+void launch_mode_product_f32(int d, const int64_t *n, const float *X, int mu, const float *L,
+                             int transpose, float *Y, double alpha, double beta, cudaStream_t st)
+{
+    mode_product<SGemm, float>(d, n, X, mu, L, transpose, Y, alpha, beta, launch_sgemm, st);
 }
 
 void launch_mode_product_f64(int d, const int64_t *n, const double *X, int mu, const double *L,
                              int transpose, double *Y, double alpha, double beta, cudaStream_t st)
 {
-    int64_t I = 1, O = 1, m = n[mu];
-    for (int q = 0; q < mu; ++q) I *= n[q];
-    for (int q = mu + 1; q < d; ++q) O *= n[q];
-    // L(i, j) = L[i + m j]; transposed: L[j + m i]
-    const int64_t sLi = transpose ? m : 1, sLj = transpose ? 1 : m;
-    DGemm g{};
-    g.alpha = alpha;
-    g.beta = beta;
-    if (mu == 0) {
-        // Y[r][i] = sum_j X[r][j] L(i, j): M = fibres r, N = i, K = j
-        g.M = (int)O; g.N = (int)m; g.K = (int)m; g.batch = 1;
-        g.A = X; g.sAm = m; g.sAk = 1; g.sAb = 0;
-        g.B = L; g.sBk = sLj; g.sBn = sLi; g.sBb = 0;
-        g.C = Y; g.sCm = m; g.sCn = 1; g.sCb = 0;
-    } else {
-        // per outer index o: Y[o][i][x] = sum_j L(i, j) X[o][j][x]
-        g.M = (int)m; g.N = (int)I; g.K = (int)m; g.batch = (int)O;
-        g.A = L; g.sAm = sLi; g.sAk = sLj; g.sAb = 0;
-        g.B = X; g.sBk = I; g.sBn = 1; g.sBb = I * m;
-        g.C = Y; g.sCm = I; g.sCn = 1; g.sCb = I * m;
-    }
-    launch_dgemm(g, st);
+    mode_product<DGemm, double>(d, n, X, mu, L, transpose, Y, alpha, beta, launch_dgemm, st);
 }
 
 // ---------------------------------------------------------------------------
