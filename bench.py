@@ -1,21 +1,24 @@
 """Throughput benchmark of the EXPRK3DS_REAL step on one GB300 (or N replicas).
 
-Default workload: 2D Schnakenberg on a 1024^2 grid (tau = 1e-4, 1000-step
-horizon), split-BF16 tensor-core mode products with the FP64 state; the error
-against the FP64 GPU path is measured over the full horizon.  --workload
-fhn3d_256 runs the 3D FitzHugh-Nagumo 256^3 case.  A "step" is one time step
-of the scheme (Kronecker-sum action + reaction, the three Tucker-operator
-groups and the stage updates); the phi-matrix setup runs once before timing
-and is reported separately.
+Default workload: 3D FitzHugh-Nagumo on a 256^3 grid (tau = 1e-3, 200-step
+horizon) in DS_PREC_F16X10: the Tucker group on F with fixed-head FP16
+operands on the tensor cores (~35-bit operands), the groups on D2, D3 in
+split BF16, the state in FP64; the error against the FP64 GPU path is
+measured over the full horizon.  --workload schnak2d_1024 runs the 2D
+Schnakenberg 1024^2 case, --workload batch64 the 64-instance batch.  A
+"step" is one time step of the scheme (Kronecker-sum action + reaction, the
+three Tucker-operator groups and the stage updates); the phi-matrix setup
+runs once before timing and is reported separately.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload schnak2d_1024|fhn3d_256|...] [--precision bf16x6|f32|f64]
+                  [--workload fhn3d_256|schnak2d_1024|batch64|...]
+                  [--precision f16x10|bf16x6|bf16x6c|f32|f64]
                   [--err-steps E]   (default: the workload's horizon; 0 skips)
 
 Under torchrun each rank runs an independent replica on its own GPU (the
 split step has no data-path exchange), timing is the max over ranks and the
-value is the whole-job rate.  --impl reference times the FP64 CPU oracle on a
-bounded sample of the same workload.
+value is the whole-job rate.  --impl reference times the FP64 CPU oracle's
+step on a bounded slab of the same workload.
 """
 from __future__ import annotations
 
@@ -36,13 +39,21 @@ sys.path.insert(0, ROOT)
 METRIC = "grid-point*steps/s"
 UNIT = "grid-point*steps/s"
 
+PREC_NOTE = {
+    "f16x10": ("Tucker group on F: fixed-head FP16 four-part operands, 10 tensor-core products in four "
+               "accumulators by weight class (exact head accumulation); groups on D2, D3: split BF16 "
+               "(6 products); stencil and reaction in double-float; state FP64"),
+    "bf16x6": "split BF16 (3 parts, 6 tensor-core products, FP32 accumulation); state FP64",
+    "bf16x6c": "split BF16 with the main product in its own accumulator; state FP64",
+    "f32": "FP32 CUDA-core mode products; state FP64",
+    "f64": "FP64 throughout",
+}
+
 # DRAM traffic per launch of the tensor-core mode-product kernel (mean over one
 # step's launches), from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum), keyed by "<hash of the kernel source>:<workload>";
 # a changed kernel reports null.
 NCU_TRAFFIC = {
-    # profiles/launches_*.md: mean over one step's k_mode_tc launches of read + write
-    "3fbd29567d1789c9:fhn3d_256": 1.502e9,
 }
 
 
@@ -156,28 +167,54 @@ def _tucker_ops_per_step(d: int) -> int:
     return 2 * (10 if d == 2 else 15)
 
 
-def oracle_sample(w, reps: int = 1):
-    """Time the FP64 oracle on a bounded sample of the workload: one mu-mode
-    product per direction on the full tensor (one Tucker operator's worth of
-    contraction work), scaled by the Tucker operators of a step.  Returns
-    (grid-point*steps/s, seconds of CPU work, description)."""
-    import numpy as np
+def _cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for key in ("Model name", "Model", "Vendor ID"):
+            for ln in out.splitlines():
+                if ln.split(":")[0].strip() == key and ln.split(":", 1)[1].strip() not in ("", "-"):
+                    return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
+
+def oracle_sample(w, thick: int, steps: int = 1):
+    """Time the FP64 oracle's EXPRK3DS step (Algorithm 1/2: Kronecker-sum
+    action, reaction, the three Tucker groups, the stage sums) on a slab of
+    the workload: the full grid with its last direction cut to `thick`
+    points, same model, tau and initial-data recipe.  The oracle's work per
+    grid point is proportional to the summed mode sizes (each Tucker
+    operator costs 2 N sum_mu n_mu), so the full grid's rate is the slab's
+    times sum(n_slab) / sum(n_full).  Returns (full-grid estimate in
+    grid-point*steps/s, slab rate, seconds of CPU work, description)."""
     from oracle import oracle as O
     from paper_2310_07551_gb300 import inputs
-    X = inputs.initial_state(w.model, w.dims, seed=w.seed)[0]
-    A = _problem(w)[1]
-    P = [O.phi(w.tau * Am, 1)[1] for Am in A]
+    dims = tuple(w.dims[:-1]) + (min(thick, w.dims[-1]),)
+    Ds = [inputs.fd_neumann(n, w.lo, w.hi) for n in dims]
+    As = [[dl * D for D in Ds] for dl in w.delta]
+    P = O.phi_set(dims, As, w.tau)
+    U = inputs.initial_state(w.model, dims, seed=w.seed)
+    npts = 1
+    for n in dims:
+        npts *= n
     t0 = time.perf_counter()
-    for _ in range(reps):
-        for mu in range(1, w.d + 1):
-            X = O.mode_product(X, mu, P[mu - 1])
-    t = (time.perf_counter() - t0) / reps
-    t_step = t * _tucker_ops_per_step(w.d)
-    del np
-    return w.npoints / t_step, t * reps, (
-        f"{reps} x one mu-mode product per direction on the full {'x'.join(map(str, w.dims))} tensor "
-        f"(= one Tucker operator), scaled by the {_tucker_ops_per_step(w.d)} Tucker operators of a step")
+    O.step(dims, As, P, w.model, w.params, w.tau, U, steps)
+    t = time.perf_counter() - t0
+    slab_rate = npts * steps / t
+    est = slab_rate * sum(dims) / sum(w.dims)
+    desc = (f"{steps} oracle step(s) on the {'x'.join(map(str, dims))} slab of the "
+            f"{'x'.join(map(str, w.dims))} workload ({t:.1f} s); full-grid rate = slab rate x "
+            f"sum(n_slab)/sum(n_full) = {sum(dims)}/{sum(w.dims)}")
+    return est, slab_rate, t, desc
+
+
+def _slab(w) -> int:
+    """Last-direction thickness of the CPU sample: about a quarter of the
+    3D grid, about an eighth of the 2D one (~10-20 s of oracle work on a
+    16-core host)."""
+    return max(8, w.dims[-1] // (4 if len(w.dims) == 3 else 8))
 
 
 def run_reference(args, w, rank, world):
@@ -186,14 +223,16 @@ def run_reference(args, w, rank, world):
     from oracle import oracle as O
     O.build()
     cores = O.set_threads(0)
-    # warm-up samples
+    # each step: one oracle step on a slab small enough that the whole
+    # --steps K --warmup W run ends within a few minutes
+    thick = max(4, min(_slab(w), w.dims[-1] * 16 // max(1, 4 * (args.steps + args.warmup))))
     for _ in range(max(0, args.warmup)):
-        oracle_sample(w, 1)
-    vals, secs = [], 0.0
+        oracle_sample(w, thick)
+    vals, secs, desc = [], 0.0, ""
     for _ in range(args.steps):
-        v, s, desc = oracle_sample(w, 1)
+        v, _, s_, desc = oracle_sample(w, thick)
         vals.append(v)
-        secs += s
+        secs += s_
     value = args.steps / sum(1.0 / v for v in vals)   # harmonic mean = total work / total time
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
@@ -201,8 +240,10 @@ def run_reference(args, w, rank, world):
         "ms_per_step": w.npoints / value * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w.name, "grid": list(w.dims), "tau": w.tau, "model": w.model,
+                   "scheme": "exprk3ds_real", "precision": "f64",
                    "oracle": "FP64 CPU oracle (plain loops, OpenMP)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "cpu": _cpu_model(),
                          "sample": desc + f"; {args.steps} samples, {secs:.1f} s of CPU work"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -312,8 +353,8 @@ def main():
                     help="timed steps (default: enough for about 1.5 s of timed work)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="schnak2d_1024")
-    ap.add_argument("--precision", default="bf16x6", choices=["bf16x6", "bf16x6c", "f32", "f64"])
+    ap.add_argument("--workload", default="fhn3d_256")
+    ap.add_argument("--precision", default="f16x10", choices=["f16x10", "bf16x6", "bf16x6c", "f32", "f64"])
     ap.add_argument("--err-steps", type=int, default=-1)
     ap.add_argument("--scheme", default="exprk3ds_real", choices=["exprk3ds_real", "etd2rkds"],
                     help="etd2rkds: the second-order split ETD2RK (FP64 plans)")
@@ -416,12 +457,12 @@ def main():
     plan.profile(False)
     plan.sync(U, check_state=True)
 
-    # end to end through the public API with host buffers: H2D of the state,
-    # one step, D2H of the new state, every step
-    Uh = torch.from_numpy(U0.copy()).pin_memory()
-    Uo = torch.empty_like(Uh).pin_memory()
+    # end to end through the public API with host buffers: every step copies
+    # the state from pinned host memory, steps it and copies the new state
+    # back into the same host buffer (the trajectory lives on the host)
+    Uh = torch.empty(U.shape, dtype=U.dtype).pin_memory()
+    Uh.copy_(U)
     k_e2e = max(3, min(args.steps, 10))
-    plan.integrate(U, 1)
     barrier()
     e2 = torch.cuda.Event(enable_timing=True)
     e3 = torch.cuda.Event(enable_timing=True)
@@ -429,7 +470,7 @@ def main():
     for _ in range(k_e2e):
         U.copy_(Uh, non_blocking=True)
         plan.integrate(U, 1)
-        Uo.copy_(U, non_blocking=True)
+        Uh.copy_(U, non_blocking=True)
     e3.record(stream)
     barrier()
     t_e2e = e2.elapsed_time(e3) / 1e3
@@ -454,40 +495,63 @@ def main():
 
     peaks, peak_src = _peaks()
     tc_ms, tc_n, tc_fl, tc_by = prof["tc"]
+    fx_ms, fx_n, fx_fl, fx_by = prof["fx"]
     f64_ms, f64_n, f64_fl, _ = prof["f64"]
     pw_ms, pw_n, _, pw_by = prof["pointwise"]
+    prof_ms = tc_ms + fx_ms + f64_ms + pw_ms
+    step_ms = t / args.steps * 1e3
     if args.precision == "f32":
         achieved = f64_fl / (f64_ms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": None, "unit": "TFLOP/s", "frac": None,
                 "traffic": None, "kernel": "k_gemm<float> (FP32 CUDA-core mode product)",
                 "peak_source": "no measured FP32 peak"}
-    elif args.precision in ("bf16x6", "bf16x6c"):
-        # tensor-instruction flops: six BF16 products per FP32-class product
-        achieved = 6.0 * tc_fl / (tc_ms / 1e3) / 1e12
+    elif args.precision in ("bf16x6", "bf16x6c", "f16x10"):
+        # The dominant kernel family: every k_mode_tc launch of the step.
+        # Tensor-instruction flops: six BF16 products per FP32-class product
+        # (split-BF16 launches), ten FP16 products (FX launches).  Their
+        # time is their share of the per-launch event profile times the
+        # graph-timed step, so it never exceeds ms_per_step.
+        tflops_step = (6.0 * tc_fl + 10.0 * fx_fl) / kprof
+        share = (tc_ms + fx_ms) / prof_ms if prof_ms > 0 else None
+        k_ms = share * step_ms if share else None
+        achieved = tflops_step / (k_ms / 1e3) / 1e12 if k_ms else None
         peak = peaks["bf16_tflops_sustained"]
+        key = f"{_source_hash()}:{w.name}:{args.precision}"
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak,
-                "traffic": NCU_TRAFFIC.get(f"{_source_hash()}:{w.name}"),
-                "traffic_source": (f"profiles/launches_{w.name}.md (ncu, this kernel source)"
-                                   if f"{_source_hash()}:{w.name}" in NCU_TRAFFIC else
-                                   "no ncu capture of this kernel source in this workload's tuned configuration"),
-                "alg_bytes_per_launch": tc_by / tc_n if tc_n else None,
-                "launches_per_step": tc_n // kprof,
-                "kernel": "k_mode_tc (tcgen05 split-BF16 mode product)",
-                "peak_source": f"{peak_src} bf16_tflops_sustained",
-                "useful_fp32_tflops": tc_fl / (tc_ms / 1e3) / 1e12,
-                "kernel_share_of_step": tc_ms / (tc_ms + pw_ms) if tc_ms + pw_ms > 0 else None,
+                "frac": achieved / peak if achieved else None,
+                "traffic": NCU_TRAFFIC.get(key),
+                "traffic_source": ("ncu capture of this kernel source on this workload (mean DRAM read + write "
+                                   "per k_mode_tc launch)" if key in NCU_TRAFFIC else
+                                   "null: no ncu capture of this kernel source on this workload"),
+                "alg_bytes_per_launch": (tc_by + fx_by) / (tc_n + fx_n) if tc_n + fx_n else None,
+                "launches_per_step": (tc_n + fx_n) // kprof,
+                "kernel": ("k_mode_tc (tcgen05 mode products: FX fixed-head FP16 on the F group, "
+                           "split BF16 on the D groups)" if fx_n else
+                           "k_mode_tc (tcgen05 split-BF16 mode product)"),
+                "tensor_flops_per_step": tflops_step,
+                "kernel_share_of_step": share,
+                "kernel_ms_per_step": k_ms,
+                "peak_source": f"{peak_src} bf16_tflops_sustained (FP16 and BF16 share the dense rate)",
+                "useful_fp32_class_tflops": (tc_fl + fx_fl) / kprof / (k_ms / 1e3) / 1e12 if k_ms else None,
+                "fx_launches": {"launches_per_step": fx_n // kprof,
+                                "tensor_tflops": 10.0 * fx_fl / (fx_ms / 1e3) / 1e12,
+                                "event_ms_per_step": fx_ms / kprof} if fx_n else None,
+                "bf16_launches": {"launches_per_step": tc_n // kprof,
+                                  "tensor_tflops": 6.0 * tc_fl / (tc_ms / 1e3) / 1e12,
+                                  "event_ms_per_step": tc_ms / kprof} if tc_n else None,
                 "pointwise": {"bound": "hbm", "achieved": pw_by / (pw_ms / 1e3) / 1e9 if pw_ms else None,
                               "peak": peaks["hbm_gbs"], "unit": "GB/s",
                               "frac": pw_by / (pw_ms / 1e3) / 1e9 / peaks["hbm_gbs"] if pw_ms else None,
                               "alg_bytes_per_step": pw_by / kprof,
-                              "kernels": "k_rhs_tiled (F = K U + g(U)); stage differences and the final update run in the tensor-core epilogues",
+                              "kernels": "k_rhs_tiled (F = K U + g(U)) and the stage kernels the tuner kept "
+                                         "separate",
                               "peak_source": f"{peak_src} hbm_gbs"}}
     else:
         achieved = f64_fl / (f64_ms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s",
                 "frac": achieved / 1.25, "traffic": None,
-                "kernel": "k_dgemm (FP64 mode product)", "peak_source": "nominal GB300 FP64"}
+                "kernel": "k_dgemm (FP64 mode product)",
+                "peak_source": "nominal GB300 FP64 (1.25 TFLOP/s; not a measured peak)"}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -498,17 +562,18 @@ def main():
                    "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": (f"L2 flushed between timed steps (256 MB buffer written outside each step's "
                           f"events); FP64 state {16 * w.npoints / 1e6:.0f} MB"),
+                   "arithmetic": PREC_NOTE.get(args.precision, args.precision),
                    "phi_setup_s": setup_s},
         "rel_err_vs_fp64": {"value": err, "steps": args.err_steps} if err is not None else None,
         "roofline": roof,
         "e2e": {"value": world * w.npoints * k_e2e / t_e2e, "unit": UNIT,
                 "h2d_bytes_per_step": bytes_state, "d2h_bytes_per_step": bytes_state},
         "gpu_launches": launches_per_step * args.steps,
-        "kernel_ms_per_step": {"tensor_core": tc_ms / kprof, "fp64_gemm": f64_ms / kprof,
-                               "pointwise": pw_ms / kprof},
+        "kernel_event_ms_per_step": {"tensor_core_bf16": tc_ms / kprof, "tensor_core_fx": fx_ms / kprof,
+                                     "fp64_gemm": f64_ms / kprof, "pointwise": pw_ms / kprof},
         "clocks": clk,
     }
-    if args.precision in ("bf16x6", "bf16x6c"):
+    if args.precision in ("bf16x6", "bf16x6c", "f16x10"):
         line["autotuner"] = [{"group": ["F", "D2", "D3"][g], "mode": mu, "split_k": k or None, "stream_k": k == 0,
                               "tiles": t, "tile_n": tn, "tile_order": c.pop("order", 0), "candidates_ms": c}
                              for g, mu, k, t, tn, c in plan.tuning()]
@@ -518,17 +583,9 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle import oracle as O
         threads = O.set_threads(0)
-        v, secs, desc = oracle_sample(w, 1)
-        reps = max(1, min(20, int(5.0 / max(secs, 1e-3))))
-        if reps > 1:
-            v, secs, desc = oracle_sample(w, reps)
-        # the same sample on one core
-        O.set_threads(1)
-        v1, secs1, _ = oracle_sample(w, 1)
-        O.set_threads(threads)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
-                                "sample": desc + f" ({secs:.1f} s of CPU work)",
-                                "value_1core": v1, "sample_1core": f"one repetition ({secs1:.1f} s)"}
+        v, slab_rate, secs, desc = oracle_sample(w, _slab(w))
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "cpu": _cpu_model(),
+                                "sample": desc, "slab_rate": slab_rate}
     if rank == 0:
         print(json.dumps(line), flush=True)
     plan.close()

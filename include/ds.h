@@ -68,8 +68,35 @@ typedef enum {
  *                    two tensor-memory accumulators, added with
  *                    round-to-nearest.  The tensor core's accumulation
  *                    truncates; this keeps its bias about six times smaller
- *                    (128-column tiles, same arithmetic otherwise). */
-typedef enum { DS_PREC_F64 = 0, DS_PREC_BF16X6 = 1, DS_PREC_F32 = 2, DS_PREC_BF16X6C = 3 } ds_precision;
+ *                    (128-column tiles, same arithmetic otherwise).
+ *   DS_PREC_F16X10 : the Tucker group on F (the stiff, large right-hand side
+ *                    of Algorithm 1/2) with ~35-bit operands on the tensor
+ *                    cores; the groups on D2, D3 as DS_PREC_BF16X6.  F and
+ *                    every intermediate of that group are held as four FP16
+ *                    parts x = 2^E (h + s1 + s2 + s3) with a fixed-point head
+ *                    h (a multiple of 16, |h| <= 2^11 nominally) and a
+ *                    fixed-point s1 (a multiple of 2^-7), E one exponent per
+ *                    tensor set; each phi-matrix row has its own exponent.
+ *                    Ten partial products run on the tensor cores, summed in
+ *                    four FP32 tensor-memory accumulators by weight class
+ *                    (head x head, where the sum is exact; the two products
+ *                    with s1; the three of weight ~2^-16; the four below)
+ *                    and combined in double-float, so the accumulators'
+ *                    truncation acts on small partial sums only.
+ *                    F = K U + g(U) is formed in double-float.  A plan sets
+ *                    each E from the largest magnitude the previous step
+ *                    wrote; the first step on a state pointer (of ds_step or
+ *                    ds_integrate) measures every tensor before writing it.
+ *                    A tensor that grows more than 16x within one step leaves
+ *                    the exact head range: ds_plan_sync then reports
+ *                    DS_ERR_NONFINITE.  d = 2 or 3, fewer than 2^31 points. */
+typedef enum {
+    DS_PREC_F64 = 0,
+    DS_PREC_BF16X6 = 1,
+    DS_PREC_F32 = 2,
+    DS_PREC_BF16X6C = 3,
+    DS_PREC_F16X10 = 4
+} ds_precision;
 
 /* Reaction term g of the two-component systems (Section 3).
  *   DS_SCHNAKENBERG, p = (gamma, a, b):
@@ -165,9 +192,12 @@ ds_status ds_phi_get_ex(const ds_phi_set *set, int c, int slot, int term, int mu
  *   L: host array of d device pointers to column-major n_mu x n_mu FP64
  *      matrices (L[0] is L_1).
  *   transpose = 1 uses L_mu^T instead of L_mu (the adjoint operator).
- *   precision: DS_PREC_F64, DS_PREC_F32, DS_PREC_BF16X6 or DS_PREC_BF16X6C (the latter two need
- *      n_1 % 8 == 0; for both reduced precisions intermediates are FP32 and
- *      Y is written in FP64).
+ *   precision: DS_PREC_F64, DS_PREC_F32, DS_PREC_BF16X6, DS_PREC_BF16X6C or
+ *      DS_PREC_F16X10 (the last three need n_1 % 8 == 0 and n_mu >= 8; with
+ *      BF16X6/BF16X6C the intermediates and the last product are FP32, with
+ *      F16X10 the intermediates are FX parts scaled by their exact largest
+ *      magnitude and the last product is formed in double-float).  Y is
+ *      written in FP64.
  *   Temporary device memory is allocated per call and released before the
  *   call returns (stream-ordered).
  *   Errors: DS_ERR_INVALID_ARG, DS_ERR_UNSUPPORTED (precision/shape),
@@ -187,15 +217,19 @@ ds_status ds_tucker(const ds_grid *grid, const double *X, double *Y,
  *   the process exits.  Grids with more than 1,048,576 points are rejected
  *   with DS_ERR_INVALID_ARG; use ds_tucker for them.
  *   The first call on each device looks up the array's device address
- *   (cudaGetSymbolAddress) with that device current; make that first call
- *   before any stream capture on the device.
+ *   (cudaGetSymbolAddress) with that device current and keeps it for the
+ *   life of the process; make that first call before any stream capture on
+ *   the device.  The kept address belongs to the device's context: after a
+ *   cudaDeviceReset of a device, do not call ds_tucker_static on it again in
+ *   the same process.
  *   All calls on a device share the array and it keeps the last call's
  *   contents; every intermediate is fully overwritten, so nothing needs
  *   clearing.  Calls whose work overlaps on the GPU (different streams,
  *   or host threads without ordering) race on the array and must be
  *   serialised by the caller.
  *   Arguments, layouts and the other errors are those of ds_tucker with
- *   precision DS_PREC_F64.  Asynchronous on `stream`. */
+ *   precision DS_PREC_F64 (DS_ERR_UNSUPPORTED on a device other than
+ *   sm_103).  Asynchronous on `stream`. */
 ds_status ds_tucker_static(const ds_grid *grid, const double *X, double *Y,
                            const double *const *L, int transpose, void *stream);
 
@@ -299,6 +333,16 @@ ds_status ds_plan_profile_read(ds_plan *plan, double *ms, int64_t *launches, dou
  * NULL; kinds without a byte model report 0. */
 ds_status ds_plan_profile_read_ex(ds_plan *plan, double *ms, int64_t *launches, double *flops,
                                   double *bytes);
+
+/* ds_plan_profile_kinds -- as ds_plan_profile_read_ex with nkinds (1..4)
+ * entries per array, the tensor-core launches split by operand format:
+ * kind 0 = split-BF16 mode products (six BF16 products per FP32-class
+ * product), 1 = FP64 mode products, 2 = pointwise kernels, 3 = FX mode
+ * products of DS_PREC_F16X10 plans (ten FP16 products per product).  The
+ * three-kind reads above count kind 3 under kind 0.  flops are the useful
+ * 2 N n_mu per product; bytes may be NULL.  Clears the records. */
+ds_status ds_plan_profile_kinds(ds_plan *plan, int nkinds, double *ms, int64_t *launches, double *flops,
+                                double *bytes);
 
 /* ds_plan_tuning -- what the autotuner chose for the split-BF16 plan's mode
  * product launch of group (0 = the F group, 1 = D2, 2 = D3) and mode mu: the

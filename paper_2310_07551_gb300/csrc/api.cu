@@ -128,6 +128,20 @@ const double kSlotW[kSlots] = {1.0 / 3.0, 2.0 / 3.0, 4.0 / 3.0, 1.0, 1.5};
 
 using namespace ds;
 
+// sm_103a (GB300) only: DS_ERR_CUDA without a device, DS_ERR_UNSUPPORTED on another one
+ds_status ds::check_device()
+{
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(DS_ERR_CUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+    int major = 0, minor = 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    if (major != 10 || minor != 3)
+        return fail(DS_ERR_UNSUPPORTED, "this library is built for sm_103a (GB300) only");
+    return DS_OK;
+}
+
 namespace {
 
 int64_t numel(const ds_grid *g)
@@ -148,18 +162,6 @@ ds_status check_grid(const ds_grid *g)
     return DS_OK;
 }
 
-ds_status check_device()
-{
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return fail(DS_ERR_CUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
-    int major = 0, minor = 0;
-    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
-    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
-    if (major != 10 || minor != 3)
-        return fail(DS_ERR_UNSUPPORTED, "this library is built for sm_103a (GB300) only");
-    return DS_OK;
-}
 
 bool is_tridiagonal(const double *A, int64_t n)
 {
@@ -194,6 +196,8 @@ struct ds_plan {
     double *bws = nullptr;                // adjoint workspace (24 N doubles), lazily allocated
     Prof prof;                            // optional per-launch event timing
     bool profiling = false;               // ds_step records events when set
+    const double *fx_state = nullptr;     // FX plans: the state the scales were last set for
+    std::map<double *, cudaGraphExec_t> calib_graphs;   // FX: calibrating first step per state
 };
 
 namespace {
@@ -425,7 +429,7 @@ int enqueue_step_etd2_f64(ds_plan *p, double *U, cudaStream_t st)
     return L;
 }
 
-int enqueue_step(ds_plan *p, double *U, cudaStream_t st, bool profile)
+int enqueue_step(ds_plan *p, double *U, cudaStream_t st, bool profile, bool calibrate = false)
 {
     p->prof.on = profile;
     int L;
@@ -438,7 +442,7 @@ int enqueue_step(ds_plan *p, double *U, cudaStream_t st, bool profile)
     else if (p->prec == DS_PREC_F32)
         L = enqueue_step_f32(p, U, st);
     else
-        L = tc::enqueue_step_mixed(p->mixed, p->set, p->model, p->sten, U, st, &p->prof);
+        L = tc::enqueue_step_mixed(p->mixed, p->set, p->model, p->sten, U, st, &p->prof, calibrate);
     p->prof.on = false;
     return L;
 }
@@ -730,6 +734,7 @@ ds_status ds_tucker(const ds_grid *grid, const double *X, double *Y, const doubl
     const int d = grid->d;
     if (precision == DS_PREC_BF16X6 || precision == DS_PREC_BF16X6C)
         return tc::tucker_mixed(grid, X, Y, L, transpose, st, precision == DS_PREC_BF16X6C);
+    if (precision == DS_PREC_F16X10) return tc::tucker_fx(grid, X, Y, L, transpose, st);
     if (precision == DS_PREC_F32) {
         int64_t pm = 0;
         for (int mu = 0; mu < d; ++mu) pm += grid->n[mu] * grid->n[mu];
@@ -790,7 +795,7 @@ ds_status ds_plan_create(const ds_grid *grid, const ds_params *params, const ds_
         for (int q = 0; q < 8; ++q)
             if (!isfinite(params->p[q])) return fail(DS_ERR_INVALID_ARG, "non-finite model parameter");
         if (precision != DS_PREC_F64 && precision != DS_PREC_BF16X6 && precision != DS_PREC_F32 &&
-            precision != DS_PREC_BF16X6C)
+            precision != DS_PREC_BF16X6C && precision != DS_PREC_F16X10)
             return fail(DS_ERR_UNSUPPORTED, "unknown precision");
         if (set->scheme != DS_EXPRK3DS_REAL && precision != DS_PREC_F64)
             return fail(DS_ERR_UNSUPPORTED, "ETD2RKDS, EXPRK3DS_CPLX and dense EXPRK3 plans are FP64 only");
@@ -837,7 +842,8 @@ ds_status ds_plan_create(const ds_grid *grid, const ds_params *params, const ds_
             }
             tc::launch_convert_f64_f32(set->P_count, set->P_dev, p->P32, 0);
         } else {
-            r = tc::mixed_plan_create(grid, set, p->status, &p->mixed, precision == DS_PREC_BF16X6C);
+            r = tc::mixed_plan_create(grid, set, p->status, &p->mixed, precision == DS_PREC_BF16X6C,
+                                      precision == DS_PREC_F16X10);
             if (r != DS_OK) { ds_plan_destroy(p); return r; }
         }
         cudaDeviceSynchronize();
@@ -852,8 +858,11 @@ ds_status ds_step(ds_plan *p, double *U, void *stream)
 {
     if (!p || !U) return fail(DS_ERR_INVALID_ARG, "NULL argument");
     cudaStream_t st = (cudaStream_t)stream;
-    p->launches = enqueue_step(p, U, st, p->profiling);
+    // FX plans measure their tensors' scales on the first step of a state
+    const bool calib = p->prec == DS_PREC_F16X10 && p->fx_state != U;
+    p->launches = enqueue_step(p, U, st, p->profiling, calib);
     if (p->launches < 0) return fail(DS_ERR_CUDA, "step enqueue failed");
+    p->fx_state = U;
     DS_CUDA_TRY(cudaGetLastError());
     return DS_OK;
 }
@@ -863,24 +872,42 @@ ds_status ds_integrate(ds_plan *p, double *U, int64_t nsteps, void *stream)
     if (!p || !U || nsteps < 0) return fail(DS_ERR_INVALID_ARG, "bad argument");
     if (nsteps == 0) return DS_OK;
     cudaStream_t user = (cudaStream_t)stream;
-    auto it = p->graphs.find(U);
-    if (it == p->graphs.end()) {
+    // one captured step per state pointer (FX plans: also a calibrating one)
+    auto capture = [&](bool calib, cudaGraphExec_t *out) -> ds_status {
         cudaGraph_t g;
         DS_CUDA_TRY(cudaStreamBeginCapture(p->st, cudaStreamCaptureModeThreadLocal));
-        int L = enqueue_step(p, U, p->st, false);
+        int L = enqueue_step(p, U, p->st, false, calib);
         cudaError_t e = cudaStreamEndCapture(p->st, &g);
         if (e != cudaSuccess || L < 0)
             return fail(DS_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-        p->launches = L;
-        cudaGraphExec_t ex;
-        e = cudaGraphInstantiate(&ex, g, 0);
+        if (!calib) p->launches = L;
+        e = cudaGraphInstantiate(out, g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) return fail(DS_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+        return DS_OK;
+    };
+    auto it = p->graphs.find(U);
+    if (it == p->graphs.end()) {
+        cudaGraphExec_t ex;
+        ds_status r = capture(false, &ex);
+        if (r != DS_OK) return r;
         it = p->graphs.emplace(U, ex).first;
+    }
+    const bool calib = p->prec == DS_PREC_F16X10 && p->fx_state != U;
+    cudaGraphExec_t cex = nullptr;
+    if (calib) {
+        auto ic = p->calib_graphs.find(U);
+        if (ic == p->calib_graphs.end()) {
+            ds_status r = capture(true, &cex);
+            if (r != DS_OK) return r;
+            ic = p->calib_graphs.emplace(U, cex).first;
+        }
+        cex = ic->second;
     }
     DS_CUDA_TRY(cudaEventRecord(p->ev_in, user));
     DS_CUDA_TRY(cudaStreamWaitEvent(p->st, p->ev_in, 0));
-    for (int64_t s = 0; s < nsteps; ++s) DS_CUDA_TRY(cudaGraphLaunch(it->second, p->st));
+    for (int64_t s = 0; s < nsteps; ++s) DS_CUDA_TRY(cudaGraphLaunch(s == 0 && cex ? cex : it->second, p->st));
+    p->fx_state = U;
     DS_CUDA_TRY(cudaEventRecord(p->ev_out, p->st));
     DS_CUDA_TRY(cudaStreamWaitEvent(user, p->ev_out, 0));
     return DS_OK;
@@ -1023,6 +1050,9 @@ ds_status ds_plan_sync(ds_plan *p, const double *U, int check_state)
         cudaMemset(&p->status->nonfinite, 0, sizeof(int));
         return fail(DS_ERR_NONFINITE, "state holds NaN/Inf");
     }
+    if (p->mixed && tc::mixed_plan_fx_overflow(p->mixed, true) > 0)
+        return fail(DS_ERR_NONFINITE,
+                    "an FX tensor grew more than 16x within one step and left its exact head range");
     return DS_OK;
 }
 
@@ -1394,10 +1424,12 @@ ds_status ds_plan_profile(ds_plan *p, int enable)
     return DS_OK;
 }
 
-ds_status ds_plan_profile_read_ex(ds_plan *p, double *ms, int64_t *launches, double *flops, double *bytes)
+ds_status ds_plan_profile_kinds(ds_plan *p, int nkinds, double *ms, int64_t *launches, double *flops,
+                                double *bytes)
 {
     if (!p || !ms || !launches || !flops) return fail(DS_ERR_INVALID_ARG, "NULL argument");
-    for (int k = 0; k < 3; ++k) {
+    if (nkinds < 1 || nkinds > 4) return fail(DS_ERR_INVALID_ARG, "nkinds must be 1..4");
+    for (int k = 0; k < nkinds; ++k) {
         ms[k] = 0.0;
         launches[k] = 0;
         flops[k] = 0.0;
@@ -1407,15 +1439,22 @@ ds_status ds_plan_profile_read_ex(ds_plan *p, double *ms, int64_t *launches, dou
         DS_CUDA_TRY(cudaEventSynchronize(r.b));
         float t = 0.f;
         DS_CUDA_TRY(cudaEventElapsedTime(&t, r.a, r.b));
-        ms[r.kind] += t;
-        launches[r.kind] += 1;
-        flops[r.kind] += r.flops;
-        if (bytes) bytes[r.kind] += r.bytes;
+        // kind 3 (FX tensor-core launches) counts as kind 0 in a three-kind read
+        const int k = r.kind < nkinds ? r.kind : 0;
+        ms[k] += t;
+        launches[k] += 1;
+        flops[k] += r.flops;
+        if (bytes) bytes[k] += r.bytes;
         p->prof.pool.push_back(r.a);
         p->prof.pool.push_back(r.b);
     }
     p->prof.recs.clear();
     return DS_OK;
+}
+
+ds_status ds_plan_profile_read_ex(ds_plan *p, double *ms, int64_t *launches, double *flops, double *bytes)
+{
+    return ds_plan_profile_kinds(p, 3, ms, launches, flops, bytes);
 }
 
 ds_status ds_plan_profile_read(ds_plan *p, double *ms, int64_t *launches, double *flops)
@@ -1428,6 +1467,7 @@ ds_status ds_plan_destroy(ds_plan *p)
     if (!p) return DS_OK;
     if (p->st) cudaStreamSynchronize(p->st);
     for (auto &kv : p->graphs) cudaGraphExecDestroy(kv.second);
+    for (auto &kv : p->calib_graphs) cudaGraphExecDestroy(kv.second);
     if (p->mixed) tc::mixed_plan_destroy(p->mixed);
     cudaFree(p->ws);
     cudaFree(p->bws);

@@ -37,6 +37,9 @@ extern const double kSlotW[kSlots];
 // Error helpers ----------------------------------------------------------
 void set_error(const std::string &msg);
 ds_status fail(ds_status st, const std::string &msg);
+// The current device is a GB300 (sm_103): DS_OK, else DS_ERR_CUDA (no
+// device) or DS_ERR_UNSUPPORTED (another architecture).
+ds_status check_device();
 #define DS_CUDA_TRY(expr)                                                             \
     do {                                                                              \
         cudaError_t _e = (expr);                                                      \
@@ -138,7 +141,8 @@ void launch_fold_cplx(int64_t nn, const double *Qr, const double *Qi, double er,
 void launch_nonfinite_scan(const double *x, int64_t count, int *flag, cudaStream_t st);
 
 // Optional per-launch timing with CUDA events on the launching stream.
-// kind: 0 = tensor-core mode product, 1 = FP64 mode product, 2 = pointwise.
+// kind: 0 = tensor-core mode product (split BF16), 1 = FP64 mode product,
+// 2 = pointwise, 3 = tensor-core mode product with FX operands.
 struct Prof {
     struct Rec {
         cudaEvent_t a, b;

@@ -27,6 +27,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -48,24 +49,60 @@ constexpr int BM = 128, BK = 32;
 constexpr int kThreads = 320;            // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
 constexpr int kEpiThreads = 256;
 constexpr uint32_t A_PLANE = BM * BK * 2;          // 8 KiB
-constexpr uint32_t STAGE_A = 3 * A_PLANE;
 constexpr uint32_t TMEM_COLS = 512;
 
 // Output tiles are BM x BNT: 256 columns (3-stage ring of 72 KiB) or 128
 // columns (4-stage ring of 48 KiB) for launches with few tiles.  The plan's
-// autotuner picks the width per launch.
-template <int BNT>
+// autotuner picks the width per launch.  NP operand planes per tensor: 3
+// (split BF16) or 4 (FX, 128-column tiles: 3-stage ring of 64 KiB).
+template <int BNT, int NP = 3>
 struct TileCfg {
-    static constexpr int STAGES = BNT == 256 ? 3 : 4;
+    static constexpr int STAGES = BNT == 256 ? 3 : (NP == 4 ? 3 : 4);
+    static constexpr uint32_t STAGE_A = NP * A_PLANE;
     static constexpr uint32_t B_PLANE = BNT * BK * 2;
-    static constexpr uint32_t STAGE_BYTES = STAGE_A + 3 * B_PLANE;
-    static constexpr uint32_t BAR_BYTES = 8 * (2 * STAGES + 7) + 16;
+    static constexpr uint32_t STAGE_BYTES = STAGE_A + NP * B_PLANE;
+    static constexpr uint32_t BAR_BYTES = 8 * (2 * STAGES + 8) + 16;
     static constexpr uint32_t SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + BAR_BYTES;
 };
 constexpr long long kTimeoutCycles = 4000000000LL;   // ~2 s at 2 GHz
 
 // UMMA shared-memory descriptor layout types
 constexpr uint32_t kSw128 = 2, kSw64 = 4;
+
+// Fixed-head FP16 ("FX") operands.  A value x of a tensor whose scale
+// exponent is E is held as x = 2^E (h + s1 + s2 + s3), four FP16 parts:
+// h a multiple of 16 with |h| < 2^15 (nominally <= 2^11: E is chosen so the
+// tensor's largest entry maps to 2^11), s1 = x 2^-E - h rounded to a
+// multiple of 2^-7 (|s1| <= 8), s2 = RN16 of the rest and s3 = RN16 of what
+// s2 leaves.  A phi-matrix row i carries its own exponent sigma_i the same
+// way.  In a contraction the products fall into four weight classes, each
+// summed over K in its own FP32 tensor-memory accumulator:
+//   A  = h h'                         multiples of 256, exact up to 2^32
+//   B1 = h s1' + s1 h'                multiples of 2^-3, exact up to 2^21
+//   B2 = s1 s1' + h s2' + s2 h'       |.| <~ 2^10
+//   B3 = s1 s2' + s2 s1' + h s3' + s3 h'   |.| <~ 1
+// (s2 s2', s1 s3' and below are dropped: < 2^-38 of the head products).
+// The tensor core's accumulation truncates toward zero after every MMA; a
+// truncation costs up to one unit in the last place of the accumulator it
+// lands in, so the four smallest products get an accumulator of their own
+// instead of adding four truncations per K step at B2's coarser grid.  The
+// parts keep ~2^-35 of the largest entry (FP16 subnormals bound s3), the
+// products ~2^-34 of the largest head product.
+//
+// Scale exponents live per tensor set ("slot") in a device table: the
+// producer of a tensor reads its slot's exponent and records the largest
+// magnitude it wrote; at the start of the next step each slot's exponent is
+// set from that maximum (so a tensor may grow 16x in one step before its
+// heads leave the exact range, which is reported as an overflow).
+constexpr int kFxSlots = 32;
+constexpr float kFxHeadMax = 32760.0f;   // |x 2^-E| beyond this: heads no longer exact
+struct FxScales {
+    float scale[kFxSlots];      // 2^E
+    float inv[kFxSlots];        // 2^-E
+    unsigned maxbits[kFxSlots]; // largest |value| written since the last rescale (float bits)
+    int overflow;               // a value left the exact head range
+    int pad[3];
+};
 
 // model parameters rounded to FP32 on the host
 struct ModelF {
@@ -123,6 +160,18 @@ struct alignas(128) TcArgs {
     int64_t extra_cs;
     bf16 *Dp;
     ModelF model;
+    // FX launches (fixed-head FP16 operands, three accumulators): the scale
+    // slots of input stack s (xsl_base + s / xsl_div) and of output stack s
+    // (osl_base + s / osl_div), the phi-matrix row scales [S][n] and the
+    // scale table; fx_measure: record the outputs' largest magnitude only,
+    // store nothing.  out_kind 2 (FX only): FP64 output.
+    int fx_measure;
+    int xsl_base, xsl_div, osl_base, osl_div;
+    const float *pscale;
+    FxScales *fxs;
+    // cycles a pipeline wait spins before it gives up (the drains at exit
+    // keep kTimeoutCycles)
+    long long wait_limit;
 };
 
 // ---------------------------------------------------------------------------
@@ -157,18 +206,36 @@ __device__ __forceinline__ uint32_t mbar_try(uint32_t bar, uint32_t parity)
         : "memory");
     return ok;
 }
-// Bounded wait: false when this CTA aborted or the wait timed out.
+// Non-blocking probe of a phase (mbarrier.test_wait never suspends).
+__device__ __forceinline__ uint32_t mbar_test(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok;
+}
+// Bounded wait: false when this CTA aborted or the wait timed out (after
+// `limit` cycles; the waits that drain a CTA at exit use kTimeoutCycles).
+// A limit below kTimeoutCycles (the test hook) polls with the non-blocking
+// probe and reads the clock on every poll, so that it is honoured even for
+// waits shorter than one suspended try_wait.
 __device__ __noinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile int *abort_flag,
-                                      DevStatus *st, int site)
+                                      DevStatus *st, int site, long long limit = kTimeoutCycles)
 {
     if (mbar_try(bar, parity)) return true;
     const long long t0 = clock64();
+    const bool short_limit = limit < kTimeoutCycles;
     uint32_t it = 0;
     while (true) {
-        if (mbar_try(bar, parity)) return true;
-        if ((++it & 63) == 0) {
+        if (short_limit ? mbar_test(bar, parity) : mbar_try(bar, parity)) return true;
+        if (short_limit || (++it & 63) == 0) {
             if (*abort_flag) return false;
-            if (clock64() - t0 > kTimeoutCycles) {
+            if (clock64() - t0 > limit) {
                 *abort_flag = 1;
                 if (st) {
                     atomicExch(&st->timeout, 1);
@@ -216,6 +283,13 @@ __host__ __device__ constexpr uint32_t make_idesc(int M, int N, int a_mn, int b_
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16) |
            ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
+// the same with FP16 x FP16 operands (A and B of one kind::f16 MMA always
+// share their type)
+__host__ __device__ constexpr uint32_t make_idesc_f16(int M, int N, int a_mn, int b_mn)
+{
+    return (1u << 4) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
 __device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc)
 {
     asm volatile(
@@ -243,6 +317,17 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+          "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32])
 {
     asm volatile(
@@ -292,6 +377,55 @@ __device__ __forceinline__ void split3_pair(float x0, float x1, uint32_t &q0, ui
     q0 = *reinterpret_cast<const uint32_t *>(&p0);
     q1 = *reinterpret_cast<const uint32_t *>(&p1);
     q2 = *reinterpret_cast<const uint32_t *>(&p2);
+}
+
+// FX split of v = x 2^-E given as a double-float (hi, lo), v = h + s1 + s2 +
+// s3: head h = 16 rint(hi / 16) (hi - h exact: h is a multiple of hi's ulp
+// within 8 of it); s1 = 2^-7 rint(128 r) with r = hi - h, a fixed-point part
+// (|s1| <= 8, an integer times 2^-7, exact in FP16), so head x s1 products
+// are multiples of 2^-3; q = r - s1 is exact (|q| <= 2^-8); s2 = RN16(q +
+// lo) and s3 = RN16((q - s2) + lo) (q - s2 exact).  The parts keep ~2^-36
+// of 2^11 (FP16 subnormals bound s3's resolution at 2^-25).
+__device__ __forceinline__ void fx_split(float hi, float lo, __half (&o)[4])
+{
+    const float hf = 16.0f * rintf(hi * 0.0625f);
+    const float r = __fsub_rn(hi, hf);
+    const float f1 = 0.0078125f * rintf(r * 128.0f);
+    const float q = __fsub_rn(r, f1);
+    const __half s2 = __float2half_rn(__fadd_rn(q, lo));
+    o[0] = __float2half_rn(hf);
+    o[1] = __float2half_rn(f1);
+    o[2] = s2;
+    o[3] = __float2half_rn(__fadd_rn(__fsub_rn(q, __half2float(s2)), lo));
+}
+// the same for an FP64 value (setup-time use: phi-matrix rows, FP64 tensors)
+__device__ __forceinline__ void fx_split_d(double v, __half (&o)[4])
+{
+    const double hf = 16.0 * rint(v * 0.0625);
+    const double r = v - hf;
+    const double f1 = 0.0078125 * rint(r * 128.0);
+    const double q = r - f1;
+    const __half s2 = __double2half(q);
+    o[0] = __double2half(hf);
+    o[1] = __double2half(f1);
+    o[2] = s2;
+    o[3] = __double2half(q - (double)__half2float(s2));
+}
+// two-sum of FP32 values: hi + lo == a + b exactly (Knuth)
+__device__ __forceinline__ void two_sum_f(float a, float b, float &hi, float &lo)
+{
+    hi = __fadd_rn(a, b);
+    const float bb = __fsub_rn(hi, a);
+    lo = __fadd_rn(__fsub_rn(a, __fsub_rn(hi, bb)), __fsub_rn(b, bb));
+}
+// ceil(log2 m) for a positive finite float (exact: from the bits)
+__device__ __forceinline__ int ceil_log2f(float m)
+{
+    const unsigned b = __float_as_uint(m);
+    const int e = (int)((b >> 23) & 0xFFu);
+    const unsigned mant = b & 0x7FFFFFu;
+    if (e == 0) return (mant <= 1u ? 0 : 32 - __clz((int)(mant - 1u))) - 149;   // subnormal: mant 2^-149
+    return e - 127 + (mant ? 1 : 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -814,23 +948,33 @@ __device__ __noinline__ void sk_fill(const TcArgs &a, int64_t unit, int h, const
 // zero; with one accumulator every one of the six products per 16-wide K
 // step truncates at the scale of the full sum, with two the cross products
 // truncate at ~2^-8 of it, so the bias drops about sixfold.
-template <bool MODE1, int BNT, bool DUAL, bool GROUPED, bool SK>
+//
+// FX (fixed-head FP16 operands, 128-column tiles): the four accumulators A,
+// B1, B2, B3 take TMEM columns [0, 128), [128, 256), [256, 384) and
+// [384, 512), one tile at a time: the epilogue reads them 32 columns at a
+// time, combines them in double-float and stores, then releases them
+// (TEMPTY) for the next tile's MMAs.  The producer keeps filling the operand
+// ring meanwhile.
+template <bool MODE1, int BNT, bool DUAL, bool GROUPED, bool SK, bool FX = false>
 __global__ void __launch_bounds__(kThreads, 1)
     k_mode_tc(const __grid_constant__ TcArgs a0, const TcArgs *__restrict__ gtab, const int64_t *__restrict__ gprefix,
               int ginst, int64_t gunits)
 {
     static_assert(!DUAL || BNT == 128, "dual accumulators need 128-column tiles");
+    static_assert(!FX || (BNT == 128 && !DUAL && !SK), "FX launches: 128-column tiles, no stream-K");
     constexpr int BN = BNT;
     constexpr uint32_t ACC_COLS = DUAL ? 2 * BNT : BNT;   // TMEM columns per accumulator buffer
-    constexpr int STAGES = TileCfg<BNT>::STAGES;
-    constexpr uint32_t B_PLANE = TileCfg<BNT>::B_PLANE;
-    constexpr uint32_t STAGE_BYTES = TileCfg<BNT>::STAGE_BYTES;
+    constexpr int NP = FX ? 4 : 3;                          // operand planes
+    constexpr int STAGES = TileCfg<BNT, NP>::STAGES;
+    constexpr uint32_t STAGE_A = TileCfg<BNT, NP>::STAGE_A;
+    constexpr uint32_t B_PLANE = TileCfg<BNT, NP>::B_PLANE;
+    constexpr uint32_t STAGE_BYTES = TileCfg<BNT, NP>::STAGE_BYTES;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t *gbase = smem_raw + (base - raw);
     const uint32_t bar0 = base + STAGES * STAGE_BYTES;
-    uint32_t *tmem_slot = (uint32_t *)(gbase + STAGES * STAGE_BYTES + 8 * (2 * STAGES + 7));
+    uint32_t *tmem_slot = (uint32_t *)(gbase + STAGES * STAGE_BYTES + 8 * (2 * STAGES + 8));
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
     volatile int *sk_flag = (volatile int *)(tmem_slot + 2);
 #define FULL(s) (bar0 + 8u * (s))
@@ -895,26 +1039,26 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int it0 = sk ? itr.k0 : part * a.kpi, it1 = sk ? itr.k1 : min(it0 + a.kpi, kiters);
                 for (int it = it0; it < it1; ++it) {
                     const int tt = it / a.kchunks, kc = it % a.kchunks;
-                    if (!wait_bar(EMPTY(stage), phase ^ 1u, abort_flag, a.status, 1)) { ok = false; break; }
+                    if (!wait_bar(EMPTY(stage), phase ^ 1u, abort_flag, a.status, 1, a.wait_limit)) { ok = false; break; }
                     mbar_expect_tx(FULL(stage), STAGE_BYTES);
                     const uint32_t sA = base + stage * STAGE_BYTES, sB = sA + STAGE_A;
                     const int xc = (tc.s / a.xs_div) * a.xs_stride + tt, pc = tc.s * a.T + tt;
                     if (MODE1) {
 #pragma unroll
-                        for (int p = 0; p < 3; ++p)
+                        for (int p = 0; p < NP; ++p)
                             tma_load_4d(sA + p * A_PLANE, &a.tmA, FULL(stage), kc * BK, tc.mt * BM, p, pc);
 #pragma unroll
-                        for (int p = 0; p < 3; ++p)
+                        for (int p = 0; p < NP; ++p)
                             tma_load_4d(sB + p * B_PLANE, &a.tmB, FULL(stage), kc * BK, tc.nt * BN, p, xc);
                     } else {
 #pragma unroll
-                        for (int p = 0; p < 3; ++p)
+                        for (int p = 0; p < NP; ++p)
 #pragma unroll
                             for (int h = 0; h < 2; ++h)
                                 tma_load_5d(sA + p * A_PLANE + h * (A_PLANE / 2), &a.tmA, FULL(stage),
                                             tc.mt * BM + h * 64, kc * BK, (int)tc.o, p, xc);
 #pragma unroll
-                        for (int p = 0; p < 3; ++p)
+                        for (int p = 0; p < NP; ++p)
                             tma_load_4d(sB + p * B_PLANE, &a.tmB, FULL(stage), kc * BK, tc.nt * BN, p, pc);
                     }
                     issued_phase[stage] = (int)phase;
@@ -931,7 +1075,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
-            const uint32_t idesc = MODE1 ? make_idesc(BM, BN, 0, 0) : make_idesc(BM, BN, 1, 0);
+            const uint32_t idesc = FX ? (MODE1 ? make_idesc_f16(BM, BN, 0, 0) : make_idesc_f16(BM, BN, 1, 0))
+                                      : (MODE1 ? make_idesc(BM, BN, 0, 0) : make_idesc(BM, BN, 1, 0));
             int stage = 0;
             uint32_t phase = 0;
             int acc = 0;
@@ -940,7 +1085,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             ItemIter<GROUPED, SK> itr(a0, gtab, gprefix, ginst, gunits);
             while (ok && itr.next()) {
                 const TcArgs &a = GROUPED ? *itr.a : a0;   // ungrouped: the kernel parameter itself
-                if (!wait_bar(TEMPTY(acc), acc_phase ^ 1u, abort_flag, a.status, 2)) break;
+                if (!wait_bar(TEMPTY(acc), acc_phase ^ 1u, abort_flag, a.status, 2, a.wait_limit)) break;
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)acc * ACC_COLS;
                 const int part = (int)(itr.lu % a.ksplit);
@@ -948,9 +1093,32 @@ __global__ void __launch_bounds__(kThreads, 1)
                 constexpr bool sk = SK && !GROUPED;
                 const int it0 = sk ? itr.k0 : part * a.kpi, it1 = sk ? itr.k1 : min(it0 + a.kpi, kiters);
                 for (int it = it0; it < it1; ++it) {
-                    if (!wait_bar(FULL(stage), phase, abort_flag, a.status, 3)) { ok = false; break; }
+                    if (!wait_bar(FULL(stage), phase, abort_flag, a.status, 3, a.wait_limit)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t sA = base + stage * STAGE_BYTES, sB = sA + STAGE_A;
+                    if constexpr (FX) {
+                        auto ad = [&](int p, int ks) {
+                            return MODE1 ? sdesc(sA + p * A_PLANE + ks * 32, 16, 512, kSw64)
+                                         : sdesc(sA + p * A_PLANE + ks * 2048, A_PLANE / 2, 1024, kSw128);
+                        };
+                        auto bd = [&](int p, int ks) { return sdesc(sB + p * B_PLANE + ks * 32, 16, 512, kSw64); };
+                        // A (= d) | B1 | B2 | B3, one tile at a time
+                        const uint32_t dB1 = tmem + BN, dB2 = tmem + 2 * BN, dB3 = tmem + 3 * BN;
+#pragma unroll
+                        for (int ks = 0; ks < BK / 16; ++ks) {
+                            const uint32_t first = (it > it0 || ks > 0) ? 1u : 0u;
+                            mma_bf16(d, ad(0, ks), bd(0, ks), idesc, first);
+                            mma_bf16(dB1, ad(0, ks), bd(1, ks), idesc, first);
+                            mma_bf16(dB1, ad(1, ks), bd(0, ks), idesc, 1u);
+                            mma_bf16(dB2, ad(1, ks), bd(1, ks), idesc, first);
+                            mma_bf16(dB2, ad(0, ks), bd(2, ks), idesc, 1u);
+                            mma_bf16(dB2, ad(2, ks), bd(0, ks), idesc, 1u);
+                            mma_bf16(dB3, ad(1, ks), bd(2, ks), idesc, first);
+                            mma_bf16(dB3, ad(2, ks), bd(1, ks), idesc, 1u);
+                            mma_bf16(dB3, ad(0, ks), bd(3, ks), idesc, 1u);
+                            mma_bf16(dB3, ad(3, ks), bd(0, ks), idesc, 1u);
+                        }
+                    } else {
 #pragma unroll
                     for (int ks = 0; ks < BK / 16; ++ks) {
 #pragma unroll
@@ -972,13 +1140,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                             }
                         }
                     }
+                    }
                     mma_commit(EMPTY(stage));
                     if (++stage == STAGES) { stage = 0; phase ^= 1u; }
                 }
                 if (!ok) break;
                 mma_commit(TFULL(acc));
-                acc ^= 1;
-                if (acc == 0) acc_phase ^= 1u;
+                if constexpr (FX) {
+                    acc_phase ^= 1u;   // one accumulator set: buffer 0 only
+                } else {
+                    acc ^= 1;
+                    if (acc == 0) acc_phase ^= 1u;
+                }
             }
             mma_commit(DRAIN);
             volatile int never = 0;
@@ -1036,7 +1209,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 } else {
                     // every lane waits, and the warp leaves together: tcgen05.ld below is
                     // .sync.aligned, so no lane may skip one that its warp executes
-                    const bool ready = wait_bar(TFULL(acc), acc_phase, abort_flag, a.status, 4);
+                    const bool ready = wait_bar(TFULL(acc), acc_phase, abort_flag, a.status, 4, a.wait_limit);
                     if (!__all_sync(0xffffffffu, ready)) break;
                     tc_fence_after();
                 }
@@ -1064,7 +1237,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     mbar_arrive(EPI_BAR);
                     if (threadIdx.x == 64) {
                         int last = 0;
-                        if (wait_bar(EPI_BAR, epi_phase, abort_flag, a.status, 5)) {
+                        if (wait_bar(EPI_BAR, epi_phase, abort_flag, a.status, 5, a.wait_limit)) {
                             const int need = sk_deliveries(a, itr.lu);
                             const int old = atom_add_acq_rel(a.sk_cnt + itr.lu, 1);
                             last = old == need - 1;
@@ -1073,7 +1246,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         *sk_flag = last;
                         mbar_arrive(EPI_DEC);
                     }
-                    const bool got = wait_bar(EPI_DEC, epi_phase, abort_flag, a.status, 6);
+                    const bool got = wait_bar(EPI_DEC, epi_phase, abort_flag, a.status, 6, a.wait_limit);
                     epi_phase ^= 1u;
                     if (!__all_sync(0xffffffffu, got)) break;
                     if (*sk_flag) fin[fin[0] < 0 ? 0 : 1] = itr.lu;
@@ -1114,7 +1287,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int64_t out_cs = a.ksplit > 1 ? a.out_ps : a.out_cs;
                 // every lane waits, and the warp leaves together: tcgen05.ld below is
                 // .sync.aligned, so no lane may skip one that its warp executes
-                const bool ready = wait_bar(TFULL(acc), acc_phase, abort_flag, a.status, 4);
+                const bool ready = wait_bar(TFULL(acc), acc_phase, abort_flag, a.status, 4, a.wait_limit);
                 if (!__all_sync(0xffffffffu, ready)) break;
                 tc_fence_after();
                 // row of the accumulator this thread owns, and the output stride
@@ -1137,6 +1310,116 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int64_t cbase = (int64_t)tc.nt * BN + half * (BN / 2);
                 // element offset of column cbase in this row
                 const int64_t rbase = (int64_t)tc.s * out_cs + row_index + cbase * (int64_t)col_stride;
+                if constexpr (FX) {
+                    // value = 2^(E_in + sigma) (A + B1 + B2 + B3), as a double-float
+                    const float xin = a.fxs->scale[a.xsl_base + tc.s / a.xsl_div];
+                    const int oslot = out_kind == 0 ? a.osl_base + tc.s / a.osl_div : 0;
+                    const float inv = out_kind == 0 ? a.fxs->inv[oslot] : 1.0f;
+                    float frow = 0.0f;
+                    if (MODE1 && row_ok) frow = a.pscale[(int64_t)tc.s * a.n + (tc.mt * BM + m)] * xin;
+                    const EpiTile et = epi_tile<MODE1, BN>(a, tc, part, m, half);
+                    float lmax = 0.0f;
+#pragma unroll 1
+                    for (int c = 0; c < BN / 64; ++c) {
+                        const int64_t col0 = cbase + c * 32;
+                        if (col0 >= col_lim) break;   // warp-uniform, before the collective load
+                        // this chunk of the four accumulators as a double-float vh + vl:
+                        // two-sum of the exact A and B1, then the small B2 + B3
+                        uint32_t v[32];
+                        float vh[32], vl[32];
+#pragma unroll
+                        for (int g = 0; g < 2; ++g) {   // 16 columns at a time
+                            const uint32_t tb = tmem + (uint32_t)(half * (BN / 2) + c * 32 + g * 16) +
+                                                ((uint32_t)(quarter * 32) << 16);
+                            uint32_t w0[16], w1[16];
+                            tmem_ld16(tb, w0);
+                            tmem_ld16(tb + BN, w1);
+                            tmem_wait_ld();
+#pragma unroll
+                            for (int j = 0; j < 16; ++j)
+                                two_sum_f(__uint_as_float(w0[j]), __uint_as_float(w1[j]), vh[g * 16 + j],
+                                          vl[g * 16 + j]);
+                            tmem_ld16(tb + 2 * BN, w0);
+                            tmem_ld16(tb + 3 * BN, w1);
+                            tmem_wait_ld();
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) {
+                                const float l = __fadd_rn(vl[g * 16 + j],
+                                                          __fadd_rn(__uint_as_float(w0[j]), __uint_as_float(w1[j])));
+                                two_sum_f(vh[g * 16 + j], l, vh[g * 16 + j], vl[g * 16 + j]);   // normalise
+                            }
+                        }
+                        const int jmax = (col_lim - col0 >= 32) ? 32 : (int)(col_lim - col0);
+                        const int64_t e0 = rbase + (int64_t)(c * 32) * col_stride;
+                        // value of column j as a normalised double-float (hi, lo)
+                        auto value = [&](int j, float &hi, float &lo) {
+                            hi = vh[j];
+                            lo = vl[j];
+                            const float f = MODE1 ? frow
+                                                  : (j < jmax ? __ldg(a.pscale + (int64_t)tc.s * a.n + col0 + j) * xin
+                                                              : 0.0f);
+                            hi *= f;
+                            lo *= f;
+                        };
+                        if (out_kind == 0) {
+                            // FX planes of the output tensor (scale slot oslot), as
+                            // pairs of rows like the plain BF16 store below: the even
+                            // lane stores rows (r, r+1) of column j, the odd lane those
+                            // of column j + 1
+                            const int odd = lane & 1;
+                            const int64_t eb = e0 - odd;
+                            bool over = false;
+#pragma unroll
+                            for (int j = 0; j < 32; j += 2) {
+                                float h0, l0, h1, l1;
+                                value(j, h0, l0);
+                                value(j + 1, h1, l1);
+                                if (row_ok) {
+                                    if (j < jmax) lmax = fmaxf(lmax, fabsf(h0));
+                                    if (j + 1 < jmax) lmax = fmaxf(lmax, fabsf(h1));
+                                }
+                                const float rh = __shfl_xor_sync(0xffffffffu, odd ? h0 : h1, 1);
+                                const float rl = __shfl_xor_sync(0xffffffffu, odd ? l0 : l1, 1);
+                                const int jj = j + odd;
+                                if (!a.fx_measure && row_ok && jj < jmax) {
+                                    const float x0h = (odd ? rh : h0) * inv, x0l = (odd ? rl : l0) * inv;
+                                    const float x1h = (odd ? h1 : rh) * inv, x1l = (odd ? l1 : rl) * inv;
+                                    __half q0[4], q1[4];
+                                    fx_split(x0h, x0l, q0);
+                                    fx_split(x1h, x1l, q1);
+                                    over = over || fabsf(x0h) > kFxHeadMax || fabsf(x1h) > kFxHeadMax;
+                                    __half *o = (__half *)out_ptr + eb + (uint32_t)jj * col_stride;
+#pragma unroll
+                                    for (int k = 0; k < 4; ++k) *(__half2 *)(o + k * a.out_ps) = __halves2half2(q0[k], q1[k]);
+                                }
+                            }
+                            if (over) atomicExch(&a.fxs->overflow, 1);
+                        } else if (out_kind == 2) {
+                            // FP64 output (the standalone operator's last mode)
+                            double *o = (double *)out_ptr + e0;
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) {
+                                float hi, lo;
+                                value(j, hi, lo);
+                                if (row_ok && j < jmax) o[(uint32_t)j * col_stride] = (double)hi + (double)lo;
+                            }
+                        } else {
+                            // FP32 values: the same stores and fused stage epilogue as
+                            // the BF16 launches (alpha = 1)
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) {
+                                float hi, lo;
+                                value(j, hi, lo);
+                                v[j] = __float_as_uint(__fadd_rn(hi, lo));
+                            }
+                            epi_chunk(a, tc, et, c, lane, v);
+                        }
+                    }
+                    if (out_kind == 0) {
+                        const unsigned mb = __reduce_max_sync(0xffffffffu, __float_as_uint(lmax));
+                        if (lane == 0 && mb) atomicMax(&a.fxs->maxbits[oslot], mb);
+                    }
+                } else {
 #pragma unroll 1
                 for (int c = 0; c < BN / 64; ++c) {
                     // warp-uniform exit (depends on the tile and c only), taken before
@@ -1270,10 +1553,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                         }
                     }
                 }
+                }
                 tc_fence_before();
                 mbar_arrive(TEMPTY(acc));
-                acc ^= 1;
-                if (acc == 0) acc_phase ^= 1u;
+                if constexpr (FX) {
+                    acc_phase ^= 1u;   // one accumulator set: buffer 0 only
+                } else {
+                    acc ^= 1;
+                    if (acc == 0) acc_phase ^= 1u;
+                }
             }
         }
     }
@@ -1383,6 +1671,9 @@ struct StencilF {
     int d;
     int64_t n[kMaxD];
     const float *hs[kMaxD], *hd[kMaxD], *rsum[kMaxD];
+    // FX plans: the FP32 remainders of the same coefficients (hs + hsl is
+    // the FP64 value to ~2^-48), else null
+    const float *hsl[kMaxD], *hdl[kMaxD], *rsl[kMaxD];
     int has_rsum[kMaxD];
     // r / n[mu] = (r * magic[mu]) >> shift[mu] for r < 2^31 (fast31: N < 2^31)
     unsigned long long magic[kMaxD];
@@ -1519,9 +1810,74 @@ struct RhsArgs {
     const double *U;
     bf16 *Fp;
     int gx, gy;   // tiles along x and y (grouped launches)
+    // FX: F_c goes out as FX planes of scale slot c; fx_measure: only record
+    // the largest |F_c|
+    FxScales *fxs;
+    int fx_measure;
 };
 
-template <int TX, int TY, int TZ, typename Idx, bool GROUPED>
+// Double-float pieces of the FX stencil.  Knuth's two-difference: s + e ==
+// a - b exactly.
+__device__ __forceinline__ dfl df_two_diff(float a, float b)
+{
+    const float s = __fsub_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fsub_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fadd_rn(b, bb))};
+}
+// u_nb - u_c from hi/lo parts, to ~2^-47 of the values (0 without a neighbour)
+__device__ __forceinline__ dfl df_diff_hl(bool has, float hn, float ln, float hc, float lc)
+{
+    if (!has) return {0.0f, 0.0f};
+    const dfl d = df_two_diff(hn, hc);
+    const float t = __fadd_rn(d.lo, __fsub_rn(ln, lc));
+    const float h = __fadd_rn(d.hi, t);
+    return {h, __fsub_rn(t, __fsub_rn(h, d.hi))};
+}
+// One direction's row of A u in double-float: hs (d_- + d_+) + hd (d_+ - d_-)
+// + rsum u, every coefficient a double-float (hi, lo).  For white-noise data
+// the neighbours are unrelated, so FP32 differences would already lose
+// 2^-24 of |u|; here the differences, their sums and the products keep
+// ~2^-44.
+__device__ __forceinline__ dfl stencil_dir_df(dfl hs, dfl hd, dfl rs, bool has_m, bool has_p, int has_rs,
+                                              float hm, float lm, float hp, float lp, float hc, float lc)
+{
+    const dfl dm = df_diff_hl(has_m, hm, lm, hc, lc), dp = df_diff_hl(has_p, hp, lp, hc, lc);
+    dfl r = df_mul(hs, df_add(dm, dp));
+    if (hd.hi != 0.0f) r = df_add(r, df_mul(hd, df_add(dp, df_neg(dm))));
+    if (has_rs) r = df_add(r, df_mul(rs, dfl{hc, lc}));
+    return r;
+}
+// g(u, v) in double-float (FX: F must keep ~2^-35 of its largest entry)
+__device__ __forceinline__ void react_df2(const ModelDF &m, dfl u, dfl v, dfl &gu, dfl &gv)
+{
+    if (m.model == DS_SCHNAKENBERG) {
+        const dfl u2v = df_mul(df_mul(u, u), v);
+        gu = df_mul(m.p[0], df_add(df_add(m.p[1], df_neg(u)), u2v));
+        gv = df_mul(m.p[0], df_add(m.p[2], df_neg(u2v)));
+    } else if (m.model == DS_FHN) {
+        const dfl u3 = df_mul(df_mul(u, u), u);
+        gu = df_add(df_add(u, df_neg(u3)), df_neg(v));
+        gv = df_mul(m.p[0], df_add(df_add(u, df_neg(df_mul(m.p[1], v))), df_neg(m.p[2])));
+    } else {
+        gu = {0.0f, 0.0f};
+        gv = {0.0f, 0.0f};
+    }
+}
+// F (a double-float) as FX planes at element i (plane stride `plane`), with
+// scale factor inv = 2^-E; flags values beyond the exact head range
+__device__ __forceinline__ void store_fx(__half *dst, int64_t plane, int64_t i, dfl F, float inv, bool &over)
+{
+    const float vh = F.hi * inv, vl = F.lo * inv;
+    __half q[4];
+    fx_split(vh, vl, q);
+    over = over || fabsf(vh) > kFxHeadMax;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) dst[i + k * plane] = q[k];
+}
+
+// FX: F in double-float, stored as FX planes (__half) with the scale of slot
+// c, and the largest |F_c| recorded for the next rescale.
+template <int TX, int TY, int TZ, typename Idx, bool GROUPED, bool FX = false>
 __global__ void __launch_bounds__(TX * TY) k_rhs_tiled(const __grid_constant__ RhsArgs a0,
                                                        const RhsArgs *__restrict__ gtab,
                                                        const int *__restrict__ gprefix, int ginst)
@@ -1576,7 +1932,10 @@ __global__ void __launch_bounds__(TX * TY) k_rhs_tiled(const __grid_constant__ R
         else if (tx == TX - 1 && x + 1 < n1) { xh = TX + 1; xoff = col + 1; }
     }
     float cx[2][3] = {}, cy[2][3] = {};
+    float cxl[2][3] = {}, cyl[2][3] = {};   // FX: lo parts of the coefficients
     float hp[2] = {}, lp[2] = {}, hc[2] = {}, lc[2] = {}, hn[2] = {}, ln[2] = {};
+    float fmax_[2] = {0.0f, 0.0f};
+    bool over = false;
     double rn[2] = {}, ry[2] = {}, rx[2] = {};   // raw values loaded one iteration ahead
     {
         const Idx pz = (Idx)z0 * plane;
@@ -1590,6 +1949,16 @@ __global__ void __launch_bounds__(TX * TY) k_rhs_tiled(const __grid_constant__ R
                     cy[c][0] = st[c]->hs[1][y];
                     cy[c][1] = st[c]->hd[1][y];
                     cy[c][2] = st[c]->rsum[1][y];
+                }
+                if constexpr (FX) {
+                    cxl[c][0] = st[c]->hsl[0][x];
+                    cxl[c][1] = st[c]->hdl[0][x];
+                    cxl[c][2] = st[c]->rsl[0][x];
+                    if (TY > 1) {
+                        cyl[c][0] = st[c]->hsl[1][y];
+                        cyl[c][1] = st[c]->hdl[1][y];
+                        cyl[c][2] = st[c]->rsl[1][y];
+                    }
                 }
                 split_hilo(U[c * N + pz + col], hc[c], lc[c]);
                 if (z0 > 0) split_hilo(U[c * N + pz - plane + col], hp[c], lp[c]);
@@ -1620,7 +1989,31 @@ __global__ void __launch_bounds__(TX * TY) k_rhs_tiled(const __grid_constant__ R
             }
         }
         __syncthreads();
-        if (in) {
+        if (FX && in) {
+            dfl g[2];
+            react_df2(m, dfl{hc[0], lc[0]}, dfl{hc[1], lc[1]}, g[0], g[1]);
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const StencilF &sc = *st[c];
+                dfl acc = stencil_dir_df({cx[c][0], cxl[c][0]}, {cx[c][1], cxl[c][1]}, {cx[c][2], cxl[c][2]}, x > 0,
+                                         x + 1 < n1, sc.has_rsum[0], sh[c][0][ty + 1][tx], sh[c][1][ty + 1][tx],
+                                         sh[c][0][ty + 1][tx + 2], sh[c][1][ty + 1][tx + 2], hc[c], lc[c]);
+                if (TY > 1)
+                    acc = df_add(acc, stencil_dir_df({cy[c][0], cyl[c][0]}, {cy[c][1], cyl[c][1]},
+                                                     {cy[c][2], cyl[c][2]}, y > 0, y + 1 < n2, sc.has_rsum[1],
+                                                     sh[c][0][ty][tx + 1], sh[c][1][ty][tx + 1],
+                                                     sh[c][0][ty + 2][tx + 1], sh[c][1][ty + 2][tx + 1], hc[c],
+                                                     lc[c]));
+                acc = df_add(acc, stencil_dir_df({sc.hs[dz][z], sc.hsl[dz][z]}, {sc.hd[dz][z], sc.hdl[dz][z]},
+                                                 {sc.rsum[dz][z], sc.rsl[dz][z]}, z > 0, z + 1 < n3,
+                                                 sc.has_rsum[dz], hp[c], lp[c], hn[c], ln[c], hc[c], lc[c]));
+                acc = df_add(acc, g[c]);
+                fmax_[c] = fmaxf(fmax_[c], fabsf(acc.hi));
+                if (!a.fx_measure)
+                    store_fx((__half *)Fp + 4 * (int64_t)N * c, (int64_t)N, (int64_t)(pz + col), acc,
+                             a.fxs->inv[c], over);
+            }
+        } else if (in) {
             float g[2];
             react_df(m, dfl{hc[0], lc[0]}, dfl{hc[1], lc[1]}, g[0], g[1]);
             float F[2];
@@ -1652,6 +2045,14 @@ __global__ void __launch_bounds__(TX * TY) k_rhs_tiled(const __grid_constant__ R
             hc[c] = hn[c];
             lc[c] = ln[c];
         }
+    }
+    if constexpr (FX) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const unsigned mb = __reduce_max_sync(0xffffffffu, __float_as_uint(fmax_[c]));
+            if ((threadIdx.x & 31) == 0 && mb) atomicMax(&a.fxs->maxbits[c], mb);
+        }
+        if (over) atomicExch(&a.fxs->overflow, 1);
     }
 }
 
@@ -1810,6 +2211,98 @@ __global__ void k_split_matrix(int n, int ldp, const double *__restrict__ L, int
     }
 }
 
+// FX scale update for slots [first, first + count): E = ceil(log2 max) - 11
+// from the largest magnitude recorded since the last update (a slot that saw
+// only zeros keeps its exponent), then the record is cleared.
+__global__ void k_fx_rescale(FxScales *f, int first, int count)
+{
+    const int k = first + (int)threadIdx.x;
+    if ((int)threadIdx.x >= count || k >= kFxSlots) return;
+    const float mx = __uint_as_float(f->maxbits[k]);
+    if (mx > 0.0f && mx <= 3.0e38f) {
+        const int E = ceil_log2f(mx) - 11;
+        f->scale[k] = ldexpf(1.0f, E);
+        f->inv[k] = ldexpf(1.0f, -E);
+    }
+    f->maxbits[k] = 0u;
+}
+
+// FX planes of phi-matrices, one block per output row i of stack s: the row
+// of every term t < T (matrix src[s T + t], column-major n x n, times
+// scale[s T + t]) shares one exponent sigma = ceil(log2 max_{t,j} |.|) - 11;
+// pscale[s n + i] = 2^sigma and planes [pc][4][n][ldp] (zero padded) hold
+// the FX split of each entry times 2^-sigma.
+struct FxMatJob {
+    const double *src;
+    double scale;
+    int transpose;      // use src^T
+};
+__device__ __forceinline__ double fx_job_at(const FxMatJob &J, int n, int i, int j)
+{
+    return J.scale * (J.transpose ? J.src[j + (int64_t)n * i] : J.src[i + (int64_t)n * j]);
+}
+__global__ void k_split_matrix_fx(int n, int ldp, int T, const FxMatJob *__restrict__ jobs, __half *__restrict__ out,
+                                  float *__restrict__ pscale)
+{
+    const int i = blockIdx.x, s = blockIdx.y;
+    __shared__ double red[256];
+    double mx = 0.0;
+    for (int t = 0; t < T; ++t) {
+        const FxMatJob J = jobs[s * T + t];
+        for (int j = threadIdx.x; j < n; j += blockDim.x) mx = fmax(mx, fabs(fx_job_at(J, n, i, j)));
+    }
+    red[threadIdx.x] = mx;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+        __syncthreads();
+    }
+    mx = red[0];
+    int sig = 0;
+    if (mx > 0.0) {
+        int e;
+        const double fr = frexp(mx, &e);   // mx = fr 2^e, fr in [0.5, 1)
+        sig = (fr == 0.5 ? e - 1 : e) - 11;
+    }
+    if (threadIdx.x == 0) pscale[(int64_t)s * n + i] = ldexpf(1.0f, sig);
+    const double inv = ldexp(1.0, -sig);
+    const int64_t plane = (int64_t)n * ldp;
+    for (int t = 0; t < T; ++t) {
+        const FxMatJob J = jobs[s * T + t];
+        __half *o = out + (int64_t)(s * T + t) * 4 * plane + (int64_t)i * ldp;
+        for (int j = threadIdx.x; j < ldp; j += blockDim.x) {
+            __half q[4];
+            if (j < n) fx_split_d(fx_job_at(J, n, i, j) * inv, q);
+            else q[0] = q[1] = q[2] = q[3] = __float2half(0.0f);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) o[j + k * plane] = q[k];
+        }
+    }
+}
+
+// FX planes of an FP64 tensor with the scale of slot k (standalone operator)
+__global__ void k_split_tensor_fx(int64_t N, const double *__restrict__ X, const FxScales *__restrict__ f, int k,
+                                  __half *__restrict__ out)
+{
+    const double inv = (double)f->inv[k];
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
+        __half q[4];
+        fx_split_d(X[p] * inv, q);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) out[p + k * N] = q[k];
+    }
+}
+
+// largest |X| into slot k's record (standalone operator)
+__global__ void k_absmax(int64_t N, const double *__restrict__ X, FxScales *f, int k)
+{
+    float m = 0.0f;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, (float)fabs(X[p]));
+    const unsigned mb = __reduce_max_sync(0xffffffffu, __float_as_uint(m));
+    if ((threadIdx.x & 31) == 0 && mb) atomicMax(&f->maxbits[k], mb);
+}
+
 __global__ void k_split_tensor(int64_t N, const double *__restrict__ X, bf16 *__restrict__ out)
 {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < N;
@@ -1940,6 +2433,7 @@ struct ModeLaunch {
     bool mode1 = false;
     int bn = 256;              // output tile width (columns): 256 or 128
     bool dual = false;         // two accumulators (128-column tiles, compensated precision)
+    bool fx = false;           // FX operands (128-column tiles, three accumulators)
     int grid = 0;
     int64_t base_tiles = 0;    // output tiles before the split-K factor
     int64_t N = 0;             // points per output combo
@@ -1966,11 +2460,19 @@ static int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 static ds_status describe(ModeLaunch &L, int d, const int64_t *n, int mu, const bf16 *X, int xcombos,
                           const bf16 *P, int pcombos, int ldp, int S, int T, int xs_stride, int xs_div,
                           void *out, int out_kind, float alpha, DevStatus *status, int bn = 256,
-                          bool dual = false)
+                          bool dual = false, bool fx = false)
 {
+    if (fx) {
+        // FX: 128-column tiles with three accumulators; scale factors in the epilogue
+        bn = 128;
+        dual = false;
+        alpha = 1.0f;
+    }
     const int BN = bn;
     L.bn = bn;
     L.dual = dual && bn == 128;
+    L.fx = fx;
+    const uint64_t NPL = fx ? 4 : 3;   // operand planes per tensor
     int64_t N = 1;
     for (int q = 0; q < d; ++q) N *= n[q];
     int64_t I = 1, O = 1;
@@ -1984,11 +2486,11 @@ static ds_status describe(ModeLaunch &L, int d, const int64_t *n, int mu, const 
     if (mu == 0) {
         L.mode1 = true;
         const int64_t R = O;
-        uint64_t pd[4] = {(uint64_t)nm, (uint64_t)nm, 3, (uint64_t)pcombos};
-        uint64_t ps[3] = {ldp * e2, nm * ldp * e2, 3 * nm * ldp * e2};
+        uint64_t pd[4] = {(uint64_t)nm, (uint64_t)nm, NPL, (uint64_t)pcombos};
+        uint64_t ps[3] = {ldp * e2, nm * ldp * e2, NPL * nm * ldp * e2};
         uint32_t pb[4] = {BK, BM, 1, 1};
-        uint64_t xd[4] = {(uint64_t)nm, (uint64_t)R, 3, (uint64_t)xcombos};
-        uint64_t xs[3] = {nm * e2, N * e2, 3 * N * e2};
+        uint64_t xd[4] = {(uint64_t)nm, (uint64_t)R, NPL, (uint64_t)xcombos};
+        uint64_t xs[3] = {nm * e2, N * e2, NPL * N * e2};
         uint32_t xb[4] = {BK, (uint32_t)BN, 1, 1};
         ok = make_map(&a.tmA, P, 4, pd, ps, pb, CU_TENSOR_MAP_SWIZZLE_64B) &&
              make_map(&a.tmB, X, 4, xd, xs, xb, CU_TENSOR_MAP_SWIZZLE_64B);
@@ -1999,11 +2501,11 @@ static ds_status describe(ModeLaunch &L, int d, const int64_t *n, int mu, const 
         a.O = R;
     } else {
         L.mode1 = false;
-        uint64_t xd[5] = {(uint64_t)I, (uint64_t)nm, (uint64_t)O, 3, (uint64_t)xcombos};
-        uint64_t xs[4] = {I * e2, I * nm * e2, N * e2, 3 * N * e2};
+        uint64_t xd[5] = {(uint64_t)I, (uint64_t)nm, (uint64_t)O, NPL, (uint64_t)xcombos};
+        uint64_t xs[4] = {I * e2, I * nm * e2, N * e2, NPL * N * e2};
         uint32_t xb[5] = {64, BK, 1, 1, 1};
-        uint64_t pd[4] = {(uint64_t)nm, (uint64_t)nm, 3, (uint64_t)pcombos};
-        uint64_t ps[3] = {ldp * e2, nm * ldp * e2, 3 * nm * ldp * e2};
+        uint64_t pd[4] = {(uint64_t)nm, (uint64_t)nm, NPL, (uint64_t)pcombos};
+        uint64_t ps[3] = {ldp * e2, nm * ldp * e2, NPL * nm * ldp * e2};
         uint32_t pb[4] = {BK, (uint32_t)BN, 1, 1};
         ok = make_map(&a.tmA, X, 5, xd, xs, xb, CU_TENSOR_MAP_SWIZZLE_128B) &&
              make_map(&a.tmB, P, 4, pd, ps, pb, CU_TENSOR_MAP_SWIZZLE_64B);
@@ -2023,7 +2525,7 @@ static ds_status describe(ModeLaunch &L, int d, const int64_t *n, int mu, const 
     a.out_kind = out_kind;
     a.out = out;
     a.out_ps = N;
-    a.out_cs = out_kind == 0 ? 3 * N : N;
+    a.out_cs = out_kind == 0 ? (int64_t)NPL * N : N;
     a.alpha = alpha;
     a.status = status;
     a.ksplit = 1;
@@ -2034,6 +2536,7 @@ static ds_status describe(ModeLaunch &L, int d, const int64_t *n, int mu, const 
     a.num_units = a.num_tiles;
     a.epi = 0;
     a.order = 0;
+    a.wait_limit = kTimeoutCycles;
     L.base_tiles = a.num_tiles;
     L.N = N;
     L.grid = (int)std::min<int64_t>(a.num_units, num_sms());
@@ -2045,8 +2548,9 @@ static ds_status describe(ModeLaunch &L, int d, const int64_t *n, int mu, const 
                 const int x = (s / xs_div) * xs_stride + t;
                 if (x < xcombos && !used[x]) { used[x] = 1; ++nx; }
             }
-        L.alg_bytes = 6.0 * nx * (double)N + 6.0 * S * T * (double)nm * (double)nm +
-                      (out_kind == 0 ? 6.0 : 4.0) * S * (double)N;
+        const double eb = 2.0 * (double)NPL;   // bytes per element over the planes
+        L.alg_bytes = eb * nx * (double)N + eb * S * T * (double)nm * (double)nm +
+                      (out_kind == 0 ? eb : out_kind == 2 ? 8.0 : 4.0) * S * (double)N;
     }
     return DS_OK;
 }
@@ -2226,8 +2730,19 @@ __global__ void k_split_reduce_epi(const __grid_constant__ TcArgs a)
 template <bool GROUPED, bool SK>
 static void launch_tc_k(bool mode1, int bn, bool dual, int grid, cudaStream_t st, const TcArgs &a,
                       const TcArgs *gtab = nullptr, const int64_t *gprefix = nullptr, int ginst = 0,
-                      int64_t gunits = 0)
+                      int64_t gunits = 0, bool fx = false)
 {
+    if (fx) {
+        if constexpr (!SK) {
+            if (mode1)
+                k_mode_tc<true, 128, false, GROUPED, false, true>
+                    <<<grid, kThreads, TileCfg<128, 4>::SMEM_BYTES, st>>>(a, gtab, gprefix, ginst, gunits);
+            else
+                k_mode_tc<false, 128, false, GROUPED, false, true>
+                    <<<grid, kThreads, TileCfg<128, 4>::SMEM_BYTES, st>>>(a, gtab, gprefix, ginst, gunits);
+        }
+        return;
+    }
     if (bn == 256) {
         if (mode1)
             k_mode_tc<true, 256, false, GROUPED, SK><<<grid, kThreads, TileCfg<256>::SMEM_BYTES, st>>>(a, gtab, gprefix,
@@ -2257,10 +2772,10 @@ static void launch_tc_k(bool mode1, int bn, bool dual, int grid, cudaStream_t st
 template <bool GROUPED>
 static void launch_tc(bool mode1, int bn, bool dual, int grid, cudaStream_t st, const TcArgs &a,
                       const TcArgs *gtab = nullptr, const int64_t *gprefix = nullptr, int ginst = 0,
-                      int64_t gunits = 0)
+                      int64_t gunits = 0, bool fx = false)
 {
     if (!GROUPED && a.sk) launch_tc_k<false, true>(mode1, bn, dual, grid, st, a);
-    else launch_tc_k<GROUPED, false>(mode1, bn, dual, grid, st, a, gtab, gprefix, ginst, gunits);
+    else launch_tc_k<GROUPED, false>(mode1, bn, dual, grid, st, a, gtab, gprefix, ginst, gunits, fx);
 }
 
 static void set_smem_limits()
@@ -2286,6 +2801,11 @@ static void set_smem_limits()
         cudaFuncSetAttribute(k_mode_tc<false, 128, false, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s128);
         cudaFuncSetAttribute(k_mode_tc<true, 128, true, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s128);
         cudaFuncSetAttribute(k_mode_tc<false, 128, true, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s128);
+        const int sfx = (int)TileCfg<128, 4>::SMEM_BYTES;
+        cudaFuncSetAttribute(k_mode_tc<true, 128, false, false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sfx);
+        cudaFuncSetAttribute(k_mode_tc<false, 128, false, false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sfx);
+        cudaFuncSetAttribute(k_mode_tc<true, 128, false, true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sfx);
+        cudaFuncSetAttribute(k_mode_tc<false, 128, false, true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sfx);
     });
 }
 
@@ -2299,7 +2819,7 @@ static void launch(const ModeLaunch &L, cudaStream_t st, double *U = nullptr, co
         a.U = U;
         if (model) a.model = *model;
     }
-    launch_tc<false>(L.mode1, L.bn, L.dual, L.grid, st, a);
+    launch_tc<false>(L.mode1, L.bn, L.dual, L.grid, st, a, nullptr, nullptr, 0, 0, L.fx);
     if (a.ksplit > 1) {
         const int64_t total = a.part_stride;
         const int g = (int)std::min<int64_t>((total / 4 + 255) / 256, 152 * 8);
@@ -2523,6 +3043,15 @@ struct MixedPlan {
     bool fused[3] = {true, true, true};
     bool compensated = false;
     float fuse_ms[3][2] = {};
+    // FX plans (DS_PREC_F16X10): the F group's three-slice fixed-head FP16
+    // products; F, Z1, Z2 hold FP16 planes.  Scale slots: F_c (c = 0, 1),
+    // then per Tucker level l = 1..d-1 the six (component, stage) sets
+    // 2 + 6 (l - 1) + 3 c + stage.
+    bool fx = false;
+    FxScales *fxs = nullptr;
+    float *pscale = nullptr;            // row scales of the F group's phi planes, per mode
+    int64_t pscale_off[kMaxD] = {};
+    FxMatJob *fx_jobs = nullptr;
 };
 
 // the separate stage kernel of group g (D2, D3 planes or the final update)
@@ -2551,7 +3080,7 @@ static void decide_fusion(MixedPlan *mp, cudaStream_t st, double *Us)
     for (int g = 0; g < 3; ++g) {
         const ModeLaunch &F = mp->L[g][mp->d - 1], &S = mp->Lsep[g];
         const ShapeKey key{F.mode1, F.args.n, F.args.S, F.args.T, F.args.I, F.args.O,
-                           10 + g + (F.dual ? 32 : 0)};
+                           10 + g + (F.dual ? 32 : 0) + (F.fx ? 64 : 0)};
         {
             std::lock_guard<std::mutex> lk(g_tune_mu);
             tune_cache_load();
@@ -2593,14 +3122,21 @@ static void decide_fusion(MixedPlan *mp, cudaStream_t st, double *Us)
 }
 
 ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatus *status, MixedPlan **out,
-                            bool compensated)
+                            bool compensated, bool fx)
 {
     ds_status r = check_shape(set->d, set->n);
     if (r != DS_OK) return r;
     if (!encode_fn()) return fail(DS_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled unavailable");
+    if (fx) {
+        int64_t Nq = 1;
+        for (int q = 0; q < set->d; ++q) Nq *= set->n[q];
+        if (set->d > 3 || Nq >= ((int64_t)1 << 31))
+            return fail(DS_ERR_UNSUPPORTED, "DS_PREC_F16X10 plans need d = 2 or 3 and fewer than 2^31 grid points");
+    }
     MixedPlan *mp = new MixedPlan();
     memset(mp->tune_ms, 0, sizeof(mp->tune_ms));
     mp->compensated = compensated;
+    mp->fx = fx;
     mp->d = set->d;
     mp->k = set->k;
     mp->N = 1;
@@ -2619,7 +3155,8 @@ ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatu
     {
         int64_t tot = 0;
         for (int mu = 0; mu < d; ++mu) tot += 2 * 3 * mp->n[mu];
-        std::vector<float> hb(tot);
+        // FX plans also keep the FP32 remainders (lo parts) at offset tot
+        std::vector<float> hb(fx ? 2 * tot : tot);
         int64_t off = 0;
         for (int c = 0; c < 2; ++c) {
             mp->stf[c].d = d;
@@ -2640,22 +3177,29 @@ ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatu
                 cudaMemcpy(band.data(), set->tri_dev + set->tri_off[c][mu], sizeof(double) * 3 * nm,
                            cudaMemcpyDeviceToHost);
                 for (int64_t i = 0; i < nm; ++i) {
-                    hb[off + i] = (float)(0.5 * (band[i] + band[2 * nm + i]));        // hs
-                    hb[off + nm + i] = (float)(0.5 * (band[2 * nm + i] - band[i]));   // hd
+                    const double hs = 0.5 * (band[i] + band[2 * nm + i]);
+                    const double hd = 0.5 * (band[2 * nm + i] - band[i]);
                     const double rsum = band[i] + band[nm + i] + band[2 * nm + i];
+                    hb[off + i] = (float)hs;
+                    hb[off + nm + i] = (float)hd;
                     hb[off + 2 * nm + i] = (float)rsum;
+                    if (fx) {
+                        hb[tot + off + i] = (float)(hs - (double)(float)hs);
+                        hb[tot + off + nm + i] = (float)(hd - (double)(float)hd);
+                        hb[tot + off + 2 * nm + i] = (float)(rsum - (double)(float)rsum);
+                    }
                     if (rsum != 0.0) mp->stf[c].has_rsum[mu] = 1;
                 }
                 mp->stf[c].hs[mu] = (const float *)(intptr_t)off;   // fixed up below
                 off += 3 * nm;
             }
         }
-        if (cudaMalloc(&mp->bands, sizeof(float) * tot) != cudaSuccess) {
+        if (cudaMalloc(&mp->bands, sizeof(float) * hb.size()) != cudaSuccess) {
             cudaGetLastError();
             delete mp;
             return fail(DS_ERR_OOM, "band copy");
         }
-        cudaMemcpy(mp->bands, hb.data(), sizeof(float) * tot, cudaMemcpyHostToDevice);
+        cudaMemcpy(mp->bands, hb.data(), sizeof(float) * hb.size(), cudaMemcpyHostToDevice);
         for (int c = 0; c < 2; ++c)
             for (int mu = 0; mu < d; ++mu) {
                 const int64_t o = (int64_t)(intptr_t)mp->stf[c].hs[mu];
@@ -2663,6 +3207,11 @@ ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatu
                 mp->stf[c].hs[mu] = mp->bands + o;
                 mp->stf[c].hd[mu] = mp->bands + o + nm;
                 mp->stf[c].rsum[mu] = mp->bands + o + 2 * nm;
+                if (fx) {
+                    mp->stf[c].hsl[mu] = mp->bands + tot + o;
+                    mp->stf[c].hdl[mu] = mp->bands + tot + o + nm;
+                    mp->stf[c].rsl[mu] = mp->bands + tot + o + 2 * nm;
+                }
             }
     }
     const int64_t N = mp->N;
@@ -2683,29 +3232,74 @@ ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatu
     //   group D2 (slot 2), D3 (slot 4): k combos; last mode carries w eta^{(2)}
     int64_t total = 0;
     int64_t goff[3][kMaxD];
+    // FX plans hold the F group's planes (phi, F, Z1, Z2) as 4 FP16 parts
+    const int npF = fx ? 4 : 3;
     for (int g = 0; g < 3; ++g)
         for (int mu = 0; mu < d; ++mu) {
             goff[g][mu] = total;
             const int combos = g == 0 ? 3 * k : k;
-            total += (int64_t)2 * combos * 3 * mp->n[mu] * round8(mp->n[mu]);
+            total += (int64_t)2 * combos * (g == 0 ? npF : 3) * mp->n[mu] * round8(mp->n[mu]);
         }
     auto cleanup = [&](ds_status s, const char *msg) {
         mixed_plan_destroy(mp);
         return fail(s, msg);
     };
     if (cudaMalloc(&mp->Pp, sizeof(bf16) * total) != cudaSuccess ||
-        cudaMalloc(&mp->Fp, sizeof(bf16) * 6 * N) != cudaSuccess ||
+        cudaMalloc(&mp->Fp, sizeof(bf16) * 2 * npF * N) != cudaSuccess ||
         cudaMalloc(&mp->Dp, sizeof(bf16) * 6 * N) != cudaSuccess ||
-        cudaMalloc(&mp->Z1, sizeof(bf16) * 18 * k * N) != cudaSuccess ||
-        (d >= 3 && cudaMalloc(&mp->Z2, sizeof(bf16) * 18 * k * N) != cudaSuccess) ||
+        cudaMalloc(&mp->Z1, sizeof(bf16) * 6 * npF * k * N) != cudaSuccess ||
+        (d >= 3 && cudaMalloc(&mp->Z2, sizeof(bf16) * 6 * npF * k * N) != cudaSuccess) ||
         cudaMalloc(&mp->incF, sizeof(float) * 6 * N) != cudaSuccess ||
         cudaMalloc(&mp->incD, sizeof(float) * 2 * N) != cudaSuccess) {
         cudaGetLastError();
         return cleanup(DS_ERR_OOM, "split-BF16 workspace");
     }
     const double tau = set->tau;
+    if (fx) {
+        if (!mp->rhs_tiled) return cleanup(DS_ERR_UNSUPPORTED, "DS_PREC_F16X10: grid too large for the tiled stencil");
+        // scale table (every scale 1 until the first calibration), row scales
+        // of the F group's planes, and intermediates cleared so that timing
+        // at creation multiplies zeros
+        int64_t ps_tot = 0;
+        for (int mu = 0; mu < d; ++mu) {
+            mp->pscale_off[mu] = ps_tot;
+            ps_tot += (int64_t)2 * 3 * k * mp->n[mu];
+        }
+        if (cudaMalloc(&mp->fxs, sizeof(FxScales)) != cudaSuccess ||
+            cudaMalloc(&mp->pscale, sizeof(float) * ps_tot) != cudaSuccess ||
+            cudaMalloc(&mp->fx_jobs, sizeof(FxMatJob) * 2 * 3 * k) != cudaSuccess) {
+            cudaGetLastError();
+            return cleanup(DS_ERR_OOM, "FX tables");
+        }
+        FxScales h{};
+        for (int q = 0; q < kFxSlots; ++q) h.scale[q] = h.inv[q] = 1.0f;
+        cudaMemcpy(mp->fxs, &h, sizeof(h), cudaMemcpyHostToDevice);
+        cudaMemset(mp->Fp, 0, sizeof(bf16) * 2 * npF * N);
+        cudaMemset(mp->Z1, 0, sizeof(bf16) * 6 * npF * k * N);
+        if (mp->Z2) cudaMemset(mp->Z2, 0, sizeof(bf16) * 6 * npF * k * N);
+    }
     for (int g = 0; g < 3; ++g)
         for (int mu = 0; mu < d; ++mu) {
+            if (fx && g == 0) {
+                // FX planes of the F group: per stack s one row scale over its T terms
+                const int64_t nm = mp->n[mu];
+                const int ldp = round8(nm);
+                const bool last = (mu == d - 1);
+                const int combos = 3 * k, T = last ? k : 1;
+                std::vector<FxMatJob> jobs(2 * combos);
+                for (int c = 0; c < 2; ++c)
+                    for (int cb = 0; cb < combos; ++cb) {
+                        const int slot = Fslots[cb / k], i = cb % k;
+                        const SplitCoeffs &co = set->co[kSlotEll[slot] - 1];
+                        jobs[c * combos + cb] = {set->P_dev + set->P_off[c][slot][i][mu],
+                                                 last ? kSlotW[slot] * tau * co.eta[i] : 1.0, 0};
+                    }
+                cudaMemcpy(mp->fx_jobs, jobs.data(), sizeof(FxMatJob) * jobs.size(), cudaMemcpyHostToDevice);
+                k_split_matrix_fx<<<dim3((unsigned)nm, (unsigned)(2 * combos / T)), 256>>>(
+                    (int)nm, ldp, T, mp->fx_jobs, (__half *)(mp->Pp + goff[g][mu]), mp->pscale + mp->pscale_off[mu]);
+                cudaDeviceSynchronize();   // the job table is reused for the next mode
+                continue;
+            }
             const int64_t nm = mp->n[mu];
             const int ldp = round8(nm);
             const int64_t psz = 3 * nm * ldp;
@@ -2752,8 +3346,18 @@ ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatu
                 ModeLaunch &Cw = mp->C[g][mu][w];
                 // compensated plans have one candidate: 128-column tiles, two accumulators
                 r = describe(Cw, d, mp->n, mu, X, xcombos, P, 2 * S0, ldp, S, T, xs, xdiv, out, kind, 1.0f,
-                             status, (w || compensated) ? 128 : 256, compensated);
+                             status, (w || compensated) ? 128 : 256, compensated, fx && g == 0);
                 if (r != DS_OK) { mixed_plan_destroy(mp); return r; }
+                if (fx && g == 0) {
+                    // scale slots: input F_c (mode 1) or level-mu sets, output level mu + 1
+                    TcArgs &a = Cw.args;
+                    a.fxs = mp->fxs;
+                    a.pscale = mp->pscale + mp->pscale_off[mu];
+                    a.xsl_base = mu == 0 ? 0 : 2 + 6 * (mu - 1);
+                    a.xsl_div = mu == 0 ? S0 : (last ? 1 : k);
+                    a.osl_base = 2 + 6 * mu;
+                    a.osl_div = k;
+                }
                 // the last mode's epilogue does the pointwise work of the stage:
                 //   F:  D2 = g(U + tau/3 S_2(F)) - g(U)                     (s = c * 3 + stage)
                 //   D2: D3 = g(U + 2tau/3 S_3(F) + 4tau/3 S_3(D2)) - g(U)   (s = c)
@@ -2814,6 +3418,17 @@ ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatu
         cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking);
         for (int g = 0; g < 3; ++g) {
             for (int mu = 0; mu < d; ++mu) {
+                if (fx && g == 0) {
+                    // FX launches: 128-column tiles, no K split (the partials would
+                    // need double-float storage), the first tile order
+                    mp->L[g][mu] = mp->C[g][mu][0];
+                    set_split(mp->L[g][mu], 1, nullptr);
+                    if (mu == d - 1) {
+                        mp->Lsep[g] = mp->Csep[g][0];
+                        set_split(mp->Lsep[g], 1, nullptr);
+                    }
+                    continue;
+                }
                 const int code = autotune_launch(mp->C[g][mu], compensated ? 1 : 2, mp->part_ws, mp->sk_ws,
                                                  mp->sk_cnt, ts, mp->tune_ms[g][mu], Us);
                 const int w = (code >> 4) & 1, k = code & 15;
@@ -2839,6 +3454,25 @@ ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatu
         cudaStreamDestroy(ts);
         cudaFree(Us);
         if (cudaGetLastError() != cudaSuccess) return cleanup(DS_ERR_CUDA, "autotuning");
+        if (fx) {
+            // nothing the timing runs recorded survives into the first step
+            FxScales h{};
+            for (int q = 0; q < kFxSlots; ++q) h.scale[q] = h.inv[q] = 1.0f;
+            cudaMemcpy(mp->fxs, &h, sizeof(h), cudaMemcpyHostToDevice);
+        }
+    }
+    // Test hook: DS_WAIT_LIMIT_CYCLES (a positive integer) replaces the ~2 s
+    // limit of the pipeline waits of the launches this plan's steps run (set
+    // after the autotuner, whose timing runs keep the full limit), so a test
+    // can make a wait give up: the kernel records DS_ERR_TIMEOUT, drains its
+    // copies and MMAs (with the full limit) and returns.
+    if (const char *wl = getenv("DS_WAIT_LIMIT_CYCLES")) {
+        const long long lim = atoll(wl);
+        if (lim > 0)
+            for (int g = 0; g < 3; ++g) {
+                for (int mu = 0; mu < d; ++mu) mp->L[g][mu].args.wait_limit = lim;
+                mp->Lsep[g].args.wait_limit = lim;
+            }
     }
     *out = mp;
     return DS_OK;
@@ -2856,6 +3490,7 @@ int mixed_plan_fusion(const MixedPlan *mp, int g, int *fused, float *ms_fused, f
 int mixed_plan_set_tiles(MixedPlan *mp, int g, int mu, int tile_n, int ksplit)
 {
     if (!mp || g < 0 || g > 2 || mu < 0 || mu >= mp->d || (tile_n != 256 && tile_n != 128)) return -1;
+    if (mp->fx && g == 0 && (ksplit != 1 || tile_n != 128)) return -2;   // FX: 128-column tiles, unsplit
     if (mp->compensated && tile_n != 128) return -1;
     const int w = tile_n == 128 && !mp->compensated ? 1 : 0;
     ModeLaunch &C = mp->C[g][mu][w];
@@ -2928,6 +3563,15 @@ int mixed_plan_tile_order(const MixedPlan *mp, int g, int mu, int *order, float 
     return 0;
 }
 
+int mixed_plan_fx_overflow(MixedPlan *mp, bool clear)
+{
+    if (!mp || !mp->fx) return -1;
+    int over = 0;
+    cudaMemcpy(&over, &mp->fxs->overflow, sizeof(int), cudaMemcpyDeviceToHost);
+    if (over && clear) cudaMemset(&mp->fxs->overflow, 0, sizeof(int));
+    return over;
+}
+
 void mixed_plan_destroy(MixedPlan *mp)
 {
     if (!mp) return;
@@ -2942,6 +3586,9 @@ void mixed_plan_destroy(MixedPlan *mp)
     cudaFree(mp->part_ws);
     cudaFree(mp->sk_ws);
     cudaFree(mp->sk_cnt);
+    cudaFree(mp->fxs);
+    cudaFree(mp->pscale);
+    cudaFree(mp->fx_jobs);
     delete mp;
 }
 
@@ -2961,6 +3608,20 @@ static ModelDF model_df(const Model &m)
 static double launch_flops(const ModeLaunch &L, int64_t N)
 {
     return (double)L.args.S * L.args.T * 2.0 * (double)N * L.args.n;
+}
+
+// F = K U + g(U) as FX planes (F_c in scale slot c); measure: only record
+// the largest |F_c|
+static void launch_rhs_fx(MixedPlan *mp, const Model &model, double *U, bool measure, cudaStream_t st)
+{
+    RhsArgs a = rhs_args(mp->stf[0], mp->stf[1], model_df(model), mp->N, U, mp->Fp);
+    a.fxs = mp->fxs;
+    a.fx_measure = measure ? 1 : 0;
+    const dim3 g = rhs_tiles(mp->stf[0]);
+    if (mp->d == 3)
+        k_rhs_tiled<RT3_X, RT3_Y, RT3_Z, int32_t, false, true><<<g, RT3_X * RT3_Y, 0, st>>>(a, nullptr, nullptr, 0);
+    else
+        k_rhs_tiled<RT2_X, 1, RT2_Z, int32_t, false, true><<<g, RT2_X, 0, st>>>(a, nullptr, nullptr, 0);
 }
 
 int enqueue_rhs_mixed(MixedPlan *mp, const Model &model, double *U, cudaStream_t st)
@@ -3306,7 +3967,7 @@ int mixed_group_fusion(const MixedGroup *G, int g, int *fused, float *ms_fused, 
 }
 
 int enqueue_step_mixed(MixedPlan *mp, const ds_phi_set *set, const Model &model, const Stencil *sten,
-                       double *U, cudaStream_t st, Prof *prof)
+                       double *U, cudaStream_t st, Prof *prof, bool calibrate)
 {
     (void)set;
     (void)sten;
@@ -3336,6 +3997,61 @@ int enqueue_step_mixed(MixedPlan *mp, const ds_phi_set *set, const Model &model,
             }
         }
     };
+    if (mp->fx) {
+        // FX F group.  Each producer of an FX tensor writes it with its slot's
+        // exponent from the previous step's maxima; a calibrating step first
+        // measures each tensor (a launch that stores nothing), sets the slot
+        // from that and then writes it.
+        const int nslots = 2 + 6 * (d - 1);
+        auto rescale = [&](int first, int count) {
+            k_fx_rescale<<<1, 32, 0, st>>>(mp->fxs, first, count);
+            ++L;
+        };
+        auto rhs = [&](bool measure) {
+            P.begin(st, 2, 0.0, (double)N * (16 + 12));
+            launch_rhs_fx(mp, model, U, measure, st);
+            P.end(st);
+            ++L;
+        };
+        auto mode = [&](int mu, bool measure) {
+            ModeLaunch ML = mp->L[0][mu];
+            ML.args.fx_measure = measure ? 1 : 0;
+            P.begin(st, 3, launch_flops(ML, N), ML.alg_bytes);
+            launch(ML, st, U, &mf);
+            P.end(st);
+            ++L;
+        };
+        if (calibrate) {
+            rhs(true);
+            rescale(0, 2);
+            rhs(false);
+            for (int mu = 0; mu < d - 1; ++mu) {
+                mode(mu, true);
+                rescale(2 + 6 * mu, 6);
+                mode(mu, false);
+            }
+        } else {
+            rescale(0, nslots);
+            rhs(false);
+            for (int mu = 0; mu < d - 1; ++mu) mode(mu, false);
+        }
+        // the last mode of the F group (fused or separate epilogue)
+        const bool sep = !mp->fused[0];
+        const ModeLaunch &ML = sep ? mp->Lsep[0] : mp->L[0][d - 1];
+        P.begin(st, 3, launch_flops(ML, N), ML.alg_bytes);
+        launch(ML, st, U, &mf);
+        P.end(st);
+        ++L;
+        if (sep) {
+            P.begin(st, 2, 0.0, (double)N * 36.0);
+            launch_stage_kernel(mp, 0, mf, U, st);
+            P.end(st);
+            ++L;
+        }
+        group(1);
+        group(2);
+        return L;
+    }
     // F = K U + g(U) as BF16 planes: FP64 state 16 B/point in, 2 x 6 B planes out
     P.begin(st, 2, 0.0, (double)N * (16 + 12));
     L += enqueue_rhs_mixed(mp, model, U, st);
@@ -3407,6 +4123,88 @@ ds_status tucker_mixed(const ds_grid *grid, const double *X, double *Y, const do
         cudaMemset(status, 0, sizeof(DevStatus));
         return fail(DS_ERR_TIMEOUT, "tensor-core pipeline wait gave up (site " + std::to_string(h.where) + ")");
     }
+    return DS_OK;
+}
+
+// Standalone Tucker operator with FX operands (synchronous): X is split with
+// its exact largest magnitude, every intermediate is measured by a launch
+// that stores nothing before it is written, the last mode writes FP64.
+ds_status tucker_fx(const ds_grid *grid, const double *X, double *Y, const double *const *L, int transpose,
+                    cudaStream_t st)
+{
+    const int d = grid->d;
+    ds_status r = check_shape(d, grid->n);
+    if (r != DS_OK) return r;
+    if (!encode_fn()) return fail(DS_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled unavailable");
+    DevStatus *status = global_status();
+    if (!status) return fail(DS_ERR_OOM, "status word");
+    int64_t N = 1, pmax = 0, psmax = 0;
+    for (int q = 0; q < d; ++q) {
+        N *= grid->n[q];
+        pmax += 4 * grid->n[q] * round8(grid->n[q]);
+        psmax += grid->n[q];
+    }
+    char *ws = nullptr;
+    const size_t bytes = sizeof(__half) * (8 * N + pmax) + sizeof(float) * psmax + sizeof(FxScales) +
+                         sizeof(FxMatJob) * kMaxD + 1024;
+    DS_CUDA_TRY(cudaMallocAsync((void **)&ws, bytes, st));
+    __half *A0 = (__half *)ws, *A1 = A0 + 4 * N, *Pp = A1 + 4 * N;
+    char *tail = (char *)(((uintptr_t)(Pp + pmax) + 255) & ~(uintptr_t)255);
+    FxScales *fxs = (FxScales *)tail;
+    FxMatJob *jobs = (FxMatJob *)(tail + ((sizeof(FxScales) + 255) & ~(size_t)255));
+    float *pscale = (float *)((char *)jobs + 256);
+    FxScales h{};
+    for (int q = 0; q < kFxSlots; ++q) h.scale[q] = h.inv[q] = 1.0f;
+    FxMatJob hj[kMaxD];
+    for (int q = 0; q < d; ++q) hj[q] = {L[q], 1.0, transpose};
+    DS_CUDA_TRY(cudaMemcpyAsync(fxs, &h, sizeof(h), cudaMemcpyHostToDevice, st));
+    DS_CUDA_TRY(cudaMemcpyAsync(jobs, hj, sizeof(FxMatJob) * d, cudaMemcpyHostToDevice, st));
+    k_absmax<<<pw_grid(N), 256, 0, st>>>(N, X, fxs, 0);
+    k_fx_rescale<<<1, 32, 0, st>>>(fxs, 0, 1);
+    k_split_tensor_fx<<<pw_grid(N), 256, 0, st>>>(N, X, fxs, 0, A0);
+    __half *pcur = Pp;
+    float *pscur = pscale;
+    const __half *in = A0;
+    __half *bufs[2] = {A1, A0};
+    for (int mu = 0; mu < d; ++mu) {
+        const int64_t nm = grid->n[mu];
+        const int ldp = round8(nm);
+        k_split_matrix_fx<<<dim3((unsigned)nm, 1), 256, 0, st>>>((int)nm, ldp, 1, jobs + mu, pcur, pscur);
+        const bool last = (mu == d - 1);
+        void *out = last ? (void *)Y : (void *)bufs[mu % 2];
+        ModeLaunch ml;
+        r = describe(ml, d, grid->n, mu, (const bf16 *)in, 1, (const bf16 *)pcur, 1, ldp, 1, 1, 0, 1, out,
+                     last ? 2 : 0, 1.0f, status, 128, false, true);
+        if (r != DS_OK) { cudaFreeAsync(ws, st); return r; }
+        ml.args.fxs = fxs;
+        ml.args.pscale = pscur;
+        ml.args.xsl_base = mu;
+        ml.args.xsl_div = 1;
+        ml.args.osl_base = mu + 1;
+        ml.args.osl_div = 1;
+        if (!last) {
+            ModeLaunch mm = ml;
+            mm.args.fx_measure = 1;
+            launch(mm, st);
+            k_fx_rescale<<<1, 32, 0, st>>>(fxs, mu + 1, 1);
+        }
+        launch(ml, st);
+        in = bufs[mu % 2];
+        pcur += 4 * nm * ldp;
+        pscur += nm;
+    }
+    DS_CUDA_TRY(cudaStreamSynchronize(st));
+    DS_CUDA_TRY(cudaGetLastError());
+    DevStatus hs{};
+    int over = 0;
+    DS_CUDA_TRY(cudaMemcpy(&hs, status, sizeof(hs), cudaMemcpyDeviceToHost));
+    DS_CUDA_TRY(cudaMemcpy(&over, &fxs->overflow, sizeof(int), cudaMemcpyDeviceToHost));
+    cudaFreeAsync(ws, st);
+    if (hs.timeout) {
+        cudaMemset(status, 0, sizeof(DevStatus));
+        return fail(DS_ERR_TIMEOUT, "tensor-core pipeline wait gave up (site " + std::to_string(hs.where) + ")");
+    }
+    if (over) return fail(DS_ERR_NONFINITE, "FX operand outside its exact head range");
     return DS_OK;
 }
 

@@ -10,9 +10,10 @@ namespace tc {
 
 struct MixedPlan;
 
-// compensated: dual-accumulator 128-column tiles (DS_PREC_BF16X6C)
+// compensated: dual-accumulator 128-column tiles (DS_PREC_BF16X6C); fx: the F
+// group in fixed-head FP16 operands (DS_PREC_F16X10)
 ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatus *status,
-                            MixedPlan **out, bool compensated = false);
+                            MixedPlan **out, bool compensated = false, bool fx = false);
 void mixed_plan_destroy(MixedPlan *mp);
 // autotuner record of launch (group g, mode mu): chosen split, output tiles,
 // candidate times in ms (0 = not tried); -1 on bad indices
@@ -27,9 +28,12 @@ int mixed_plan_fusion(const MixedPlan *mp, int g, int *fused, float *ms_fused, f
 int mixed_plan_set_fusion(MixedPlan *mp, int g, int fused);
 int mixed_plan_set_tiles(MixedPlan *mp, int g, int mu, int tile_n, int ksplit);
 // Enqueue one EXPRK3DS_REAL step on the split-BF16 path; returns the number
-// of kernel launches, or -1 on failure.
+// of kernel launches, or -1 on failure.  calibrate (FX plans): measure every
+// FX tensor before writing it instead of using the previous step's scales.
 int enqueue_step_mixed(MixedPlan *mp, const ds_phi_set *set, const Model &model,
-                       const Stencil *sten, double *U, cudaStream_t st, Prof *prof);
+                       const Stencil *sten, double *U, cudaStream_t st, Prof *prof, bool calibrate = false);
+// FX plans: the scale table's overflow flag (and clear it), -1 if none
+int mixed_plan_fx_overflow(MixedPlan *mp, bool clear);
 // F = K U + g(U) of one problem (the first kernel of its step)
 int enqueue_rhs_mixed(MixedPlan *mp, const Model &model, double *U, cudaStream_t st);
 // Grouped launches for batches: the same mode product of every problem in
@@ -57,6 +61,8 @@ void launch_convert_f64_f32(int64_t n, const double *x, float *y, cudaStream_t s
 void launch_convert_f32_f64(int64_t n, const float *x, double *y, cudaStream_t st);
 ds_status tucker_mixed(const ds_grid *grid, const double *X, double *Y, const double *const *L,
                        int transpose, cudaStream_t st, bool compensated = false);
+ds_status tucker_fx(const ds_grid *grid, const double *X, double *Y, const double *const *L, int transpose,
+                    cudaStream_t st);
 
 }  // namespace tc
 }  // namespace ds

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libds3.so")
 DS_OK, DS_ERR_INVALID_ARG, DS_ERR_UNSUPPORTED, DS_ERR_OOM, DS_ERR_CUDA, DS_ERR_NONFINITE, DS_ERR_TIMEOUT = range(7)
 STATUS_NAMES = ["DS_OK", "DS_ERR_INVALID_ARG", "DS_ERR_UNSUPPORTED", "DS_ERR_OOM", "DS_ERR_CUDA",
                 "DS_ERR_NONFINITE", "DS_ERR_TIMEOUT"]
-PREC = {"f64": 0, "bf16x6": 1, "f32": 2, "bf16x6c": 3}
+PREC = {"f64": 0, "bf16x6": 1, "f32": 2, "bf16x6c": 3, "f16x10": 4}
 MODELS = {"schnakenberg": 0, "fhn": 1, "linear": 2}
 SCHEMES = {"exprk3ds_real": 0, "etd2rkds": 1, "exprk3ds_cplx": 2, "exprk3_dense": 3}
 
@@ -83,6 +83,8 @@ def lib() -> ctypes.CDLL:
             "ds_plan_fusion": ([_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float),
                                 ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
             "ds_plan_profile_read_ex": ([_vp, _dp, ctypes.POINTER(ctypes.c_int64), _dp, _dp], ctypes.c_int),
+            "ds_plan_profile_kinds": ([_vp, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_int64), _dp, _dp],
+                                      ctypes.c_int),
             "ds_plan_destroy": ([_vp], ctypes.c_int),
             "ds_batch_create": ([ctypes.c_int, gp, ctypes.POINTER(_vp), _dp, pp, ctypes.c_int,
                                  ctypes.POINTER(_vp)], ctypes.c_int),
@@ -285,15 +287,17 @@ class Plan:
 
     def profile_read(self, with_bytes: bool = False):
         """{kind: (ms, launches, useful_flops[, algorithmic_bytes])} for kinds
-        'tc', 'f64', 'pointwise'."""
-        ms = (ctypes.c_double * 3)()
-        n = (ctypes.c_int64 * 3)()
-        fl = (ctypes.c_double * 3)()
-        by = (ctypes.c_double * 3)()
-        check(lib().ds_plan_profile_read_ex(self._h, ms, n, fl, by))
+        'tc' (split-BF16 mode products), 'f64', 'pointwise' and 'fx' (FX mode
+        products of f16x10 plans)."""
+        ms = (ctypes.c_double * 4)()
+        n = (ctypes.c_int64 * 4)()
+        fl = (ctypes.c_double * 4)()
+        by = (ctypes.c_double * 4)()
+        check(lib().ds_plan_profile_kinds(self._h, 4, ms, n, fl, by))
+        kinds = ("tc", "f64", "pointwise", "fx")
         if with_bytes:
-            return {k: (ms[i], n[i], fl[i], by[i]) for i, k in enumerate(("tc", "f64", "pointwise"))}
-        return {k: (ms[i], n[i], fl[i]) for i, k in enumerate(("tc", "f64", "pointwise"))}
+            return {k: (ms[i], n[i], fl[i], by[i]) for i, k in enumerate(kinds)}
+        return {k: (ms[i], n[i], fl[i]) for i, k in enumerate(kinds)}
 
     @property
     def kernels_per_step(self) -> int:

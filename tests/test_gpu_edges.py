@@ -65,8 +65,13 @@ def test_homogeneous_steady_state_stays_fixed(ds, precision, tol):
 
 
 @pytest.mark.parametrize("dims", [(8, 8), (8, 8, 8), (8, 8, 8, 8)])
-@pytest.mark.parametrize("precision", ["bf16x6", "bf16x6c"])
+@pytest.mark.parametrize("precision", ["bf16x6", "bf16x6c", "f16x10"])
 def test_smallest_tensor_core_grids(ds, dims, precision):
+    """One tile, mostly padding.  Bounds: 2e-5, the FP32-class per-config
+    bound of the split-BF16 precisions on white-noise FHN data (not the
+    workloads' 1e-6 target); 2e-7 for f16x10 (d <= 3)."""
+    if precision == "f16x10" and len(dims) > 3:
+        pytest.skip("DS_PREC_F16X10 plans take d = 2 or 3")
     As = problem(dims, -1.0, 1.0, (1.0, 5.0))
     U0 = inputs.initial_state("fhn", dims, seed=2)
     tau, m = 1e-3, 3
@@ -75,7 +80,7 @@ def test_smallest_tensor_core_grids(ds, dims, precision):
     U = torch.from_numpy(U0.copy()).cuda()
     plan.integrate(U, m)
     plan.sync(U, check_state=True)
-    assert relmax(U.cpu().numpy(), ref) < 2e-5
+    assert relmax(U.cpu().numpy(), ref) < (2e-7 if precision == "f16x10" else 2e-5)
 
 
 def test_long_narrow_problem(ds):
