@@ -156,6 +156,35 @@ def job_rate(t_local: float, points_per_rank: int, steps: int, dist=None, device
     return world * points_per_rank * steps / t, t
 
 
+def partition_instances(sizes, world: int):
+    """Split independent problems over `world` ranks with no exchange: largest
+    first, each to the rank with the least work so far (ties: lowest rank).
+    Returns one sorted index list per rank."""
+    order = sorted(range(len(sizes)), key=lambda i: (-sizes[i], i))
+    load = [0] * world
+    parts = [[] for _ in range(world)]
+    for i in order:
+        r = min(range(world), key=lambda q: (load[q], q))
+        parts[r].append(i)
+        load[r] += sizes[i]
+    return [sorted(p) for p in parts]
+
+
+def job_rate_sum(t_local: float, work_local: float, dist=None, device=None):
+    """Whole-job rate of ranks with unequal shares of independent problems:
+    the job time is the max over ranks, the work the sum over ranks.
+    Returns (value, t_max, work_total)."""
+    import torch
+    t, work = t_local, work_local
+    if dist is not None and dist.is_initialized():
+        tt = torch.tensor([t_local], dtype=torch.float64, device=device)
+        ww = torch.tensor([work_local], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        dist.all_reduce(ww, op=dist.ReduceOp.SUM)
+        t, work = float(tt.item()), float(ww.item())
+    return work / t, t, work
+
+
 def _problem(w):
     from paper_2310_07551_gb300 import inputs
     Ds = [inputs.fd_neumann(n, w.lo, w.hi) for n in w.dims]
@@ -252,8 +281,11 @@ def run_reference(args, w, rank, world):
 
 def run_batch(args, rank, world):
     """64 independent Schnakenberg instances with uneven grids, stepped
-    together by one CUDA graph per 10 steps (one captured stream per
-    instance).  value = sum of the instances' grid points x steps / time."""
+    together by CUDA graphs of 10 steps (grouped launches over all of a
+    rank's instances).  Under torchrun the instances are partitioned over the
+    ranks (largest first, to the least-loaded rank; no data-path exchange).
+    value = sum over ranks of the instances' grid points x steps / the
+    slowest rank's time."""
     import numpy as np
     import torch
 
@@ -261,7 +293,19 @@ def run_batch(args, rank, world):
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    insts = configs.batch_instances()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    every = configs.batch_instances()
+    mine = partition_instances([int(np.prod(i.dims)) for i in every], world)[rank]
+    insts = [every[k] for k in mine]
     As = []
     for inst in insts:
         Ds = [inputs.fd_neumann(n, 0.0, 1.0) for n in inst.dims]
@@ -271,7 +315,7 @@ def run_batch(args, rank, world):
                      [i.params for i in insts], args.precision)
     setup_s = time.perf_counter() - t0
     U0 = [inputs.initial_state("schnakenberg", i.dims, seed=7 + k, a=i.params[1], b=i.params[2])
-          for k, i in enumerate(insts)]
+          for k, i in zip(mine, insts)]
     Us = [torch.from_numpy(u.copy()).cuda() for u in U0]
     npts = sum(int(np.prod(i.dims)) for i in insts)
     batch.integrate(Us, args.warmup)
@@ -279,27 +323,31 @@ def run_batch(args, rank, world):
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if args.steps <= 0:
-        torch.cuda.synchronize()
+        barrier()
         e0.record(stream)
         batch.integrate(Us, 10)
         e1.record(stream)
-        torch.cuda.synchronize()
+        barrier()
         per = e0.elapsed_time(e1) / 1e4
-        args.steps = max(30, int(1.5 / max(per, 1e-6)) // 10 * 10)
+        steps = torch.tensor([max(30, int(1.5 / max(per, 1e-6)) // 10 * 10)], device="cuda")
+        if dist is not None:
+            dist.all_reduce(steps, op=dist.ReduceOp.MIN)
+        args.steps = int(steps.item())
     clocks = ClockSampler(local)
-    torch.cuda.synchronize()
+    barrier()
     clocks.start()
     time.sleep(0.3)
+    barrier()
     t_wall0 = time.time()
     e0.record(stream)
     batch.integrate(Us, args.steps)
     e1.record(stream)
-    torch.cuda.synchronize()
+    barrier()
     t_wall1 = time.time()
     clk = clocks.stop(t_wall0, t_wall1)
     batch.sync()
-    t = e0.elapsed_time(e1) / 1e3
-    value = npts * args.steps / t
+    t_local = e0.elapsed_time(e1) / 1e3
+    value, t, work = job_rate_sum(t_local, float(npts) * args.steps, dist, "cuda")
     # the timed graphs' fused-or-separate choices (ms 0: replayed from DS_TUNE_CACHE)
     fusion = order = None
     if args.precision != "f64":
@@ -307,7 +355,9 @@ def run_batch(args, rank, world):
                   for g, f, a, b in batch.fusion()}
         order = {("F", "D2", "D3")[g]: {"order": o, "ms_order0": a, "ms_order1": b}
                  for g, o, a, b in batch.tile_order()}
-    useful = sum(40.0 * np.prod(i.dims) * sum(i.dims) for i in insts)   # flops per batch step
+    # useful flops per batch step: 20 Tucker operators (2D: F group 6 per
+    # component, D2 and D3 2 each) of 2 N (n_1 + n_2) flops
+    useful = sum(40.0 * np.prod(i.dims) * sum(i.dims) for i in insts)
     err = None
     if args.precision != "f64" and args.err_steps != 0:
         m = configs.BATCH_STEPS if args.err_steps < 0 else args.err_steps
@@ -319,22 +369,35 @@ def run_batch(args, rank, world):
         b64.integrate(Ub, m)
         batch.sync()
         b64.sync()
-        err = max(float((a[c] - b[c]).abs().max() / b[c].abs().max()) for a, b in zip(Ua, Ub) for c in range(2))
+        per_inst = [max(float((a[c] - b[c]).abs().max() / b[c].abs().max()) for c in range(2))
+                    for a, b in zip(Ua, Ub)]
         b64.close()
-        err = {"value": err, "steps": m, "reduction": "max over instances and components"}
+        e = torch.tensor([max(per_inst)], dtype=torch.float64, device="cuda")
+        if dist is not None:
+            dist.all_reduce(e, op=dist.ReduceOp.MAX)
+        err = {"value": float(e.item()), "steps": m, "reduction": "max over instances and components",
+               "median_over_instances_this_rank": float(np.median(per_inst)),
+               "instances_above_1e-6_this_rank": int(sum(x > 1e-6 for x in per_inst))}
     peaks, peak_src = _peaks()
-    tensor_tf = 6.0 * useful * args.steps / t / 1e12 if args.precision in ("bf16x6", "bf16x6c") else None
+    # tensor instructions per useful product: 6 BF16 (split BF16); in f16x10
+    # the F group (6 of 10 operators per component) takes 10 FP16 products
+    per_prod = {"bf16x6": 6.0, "bf16x6c": 6.0, "f16x10": 0.6 * 10.0 + 0.4 * 6.0}.get(args.precision)
+    tensor_tf = per_prod * useful * args.steps / t_local / 1e12 if per_prod else None
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
-        "config": {"workload": "batch64", "instances": len(insts), "grid_points": npts,
+        "scaling": "weak" if world == 1 else "strong", "vs_baseline": None, "dtype": args.precision,
+        "data": "synthetic",
+        "config": {"workload": "batch64", "instances": len(every), "instances_this_rank": len(insts),
+                   "grid_points": int(sum(np.prod(i.dims) for i in every)),
+                   "parallelism": f"instances partitioned over {world} ranks" if world > 1 else "single",
                    "precision": args.precision, "state": "fp64", "phi_setup_s": setup_s,
+                   "arithmetic": PREC_NOTE.get(args.precision, args.precision),
                    "l2": "L2 not flushed (batch state 2.3 GB of FP64 > L2)"},
         "rel_err_vs_fp64": err,
         "roofline": {"bound": "tensor", "achieved": tensor_tf, "peak": peaks["bf16_tflops_sustained"],
                      "unit": "TFLOP/s", "frac": tensor_tf / peaks["bf16_tflops_sustained"] if tensor_tf else None,
-                     "traffic": None, "kernel": "whole batch step (all instances' kernels)",
+                     "traffic": None, "kernel": "whole batch step of rank 0 (all its instances' kernels)",
                      "peak_source": f"{peak_src} bf16_tflops_sustained"},
         "gpu_launches": batch.kernels_per_step * args.steps,
         "clocks": clk,
@@ -342,8 +405,11 @@ def run_batch(args, rank, world):
     if fusion is not None:
         line["config"]["epilogue_fusion"] = fusion
         line["config"]["mode1_tile_order"] = order
-    print(json.dumps(line), flush=True)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     batch.close()
+    if dist is not None:
+        dist.destroy_process_group()
 
 
 def main():

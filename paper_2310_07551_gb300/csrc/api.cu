@@ -1121,6 +1121,7 @@ ds_status batch_graph(ds_batch *b, double *const *U, int steps, cudaGraphExec_t 
     bool bad = false;
     if (grouped) {
         for (int k = 0; k < steps; ++k) {
+            L += tc::mixed_group_enqueue_rescale(G, b->origin);   // FX batches
             const int lr = tc::mixed_group_enqueue_rhs(G, b->origin);
             L += lr;
             if (!lr) {
@@ -1299,6 +1300,26 @@ ds_status ds_batch_integrate(ds_batch *b, double *const *U, int64_t nsteps, void
     for (int i = 0; i < b->ninst; ++i)
         if (!U[i]) return fail(DS_ERR_INVALID_ARG, "U[i] is NULL");
     if (nsteps == 0) return DS_OK;
+    cudaStream_t user = (cudaStream_t)stream;
+    // FX batches: the first step on a set of states is a calibrating step of
+    // each instance (its own launches), which measures every FX tensor before
+    // writing it; the grouped graphs then use the previous step's maxima
+    bool calib = false;
+    for (int i = 0; i < b->ninst; ++i)
+        calib = calib || (b->plans[i]->prec == DS_PREC_F16X10 && b->plans[i]->fx_state != U[i]);
+    if (calib) {
+        DS_CUDA_TRY(cudaEventRecord(b->ev_in, user));
+        DS_CUDA_TRY(cudaStreamWaitEvent(b->origin, b->ev_in, 0));
+        for (int i = 0; i < b->ninst; ++i) {
+            if (enqueue_step(b->plans[i], U[i], b->origin, false, true) < 0)
+                return fail(DS_ERR_CUDA, "instance " + std::to_string(i) + ": calibrating step");
+            b->plans[i]->fx_state = U[i];
+        }
+        DS_CUDA_TRY(cudaGetLastError());
+        DS_CUDA_TRY(cudaEventRecord(b->ev_out, b->origin));
+        DS_CUDA_TRY(cudaStreamWaitEvent(user, b->ev_out, 0));
+        if (--nsteps == 0) return DS_OK;
+    }
     const int chunk = (int)std::min<int64_t>(nsteps, 10);
     cudaGraphExec_t g_chunk = nullptr, g_one = nullptr;
     ds_status r = batch_graph(b, U, chunk, &g_chunk);
@@ -1307,7 +1328,6 @@ ds_status ds_batch_integrate(ds_batch *b, double *const *U, int64_t nsteps, void
         r = batch_graph(b, U, 1, &g_one);
         if (r != DS_OK) return r;
     }
-    cudaStream_t user = (cudaStream_t)stream;
     DS_CUDA_TRY(cudaEventRecord(b->ev_in, user));
     DS_CUDA_TRY(cudaStreamWaitEvent(b->origin, b->ev_in, 0));
     for (int64_t k = 0; k < nsteps / chunk; ++k) DS_CUDA_TRY(cudaGraphLaunch(g_chunk, b->origin));

@@ -2098,8 +2098,17 @@ static void launch_rhs_tiled(const StencilF &s0, const StencilF &s1, const Model
 
 // every problem's F planes in one launch (problems of one d, each < 2^31
 // points, at most 2^31 tiles in all)
-static void launch_rhs_group(int d, const RhsArgs *tab, const int *prefix, int ninst, int blocks, cudaStream_t st)
+static void launch_rhs_group(int d, const RhsArgs *tab, const int *prefix, int ninst, int blocks, cudaStream_t st,
+                             bool fx = false)
 {
+    if (fx) {
+        if (d == 3)
+            k_rhs_tiled<RT3_X, RT3_Y, RT3_Z, int32_t, true, true>
+                <<<blocks, RT3_X * RT3_Y, 0, st>>>(RhsArgs{}, tab, prefix, ninst);
+        else
+            k_rhs_tiled<RT2_X, 1, RT2_Z, int32_t, true, true><<<blocks, RT2_X, 0, st>>>(RhsArgs{}, tab, prefix, ninst);
+        return;
+    }
     if (d == 3)
         k_rhs_tiled<RT3_X, RT3_Y, RT3_Z, int32_t, true><<<blocks, RT3_X * RT3_Y, 0, st>>>(RhsArgs{}, tab, prefix,
                                                                                          ninst);
@@ -2214,10 +2223,8 @@ __global__ void k_split_matrix(int n, int ldp, const double *__restrict__ L, int
 // FX scale update for slots [first, first + count): E = ceil(log2 max) - 11
 // from the largest magnitude recorded since the last update (a slot that saw
 // only zeros keeps its exponent), then the record is cleared.
-__global__ void k_fx_rescale(FxScales *f, int first, int count)
+__device__ __forceinline__ void fx_rescale_slot(FxScales *f, int k)
 {
-    const int k = first + (int)threadIdx.x;
-    if ((int)threadIdx.x >= count || k >= kFxSlots) return;
     const float mx = __uint_as_float(f->maxbits[k]);
     if (mx > 0.0f && mx <= 3.0e38f) {
         const int E = ceil_log2f(mx) - 11;
@@ -2225,6 +2232,18 @@ __global__ void k_fx_rescale(FxScales *f, int first, int count)
         f->inv[k] = ldexpf(1.0f, -E);
     }
     f->maxbits[k] = 0u;
+}
+__global__ void k_fx_rescale(FxScales *f, int first, int count)
+{
+    const int k = first + (int)threadIdx.x;
+    if ((int)threadIdx.x >= count || k >= kFxSlots) return;
+    fx_rescale_slot(f, k);
+}
+// the same for slots [0, count) of every problem of a batch (block i: tab[i])
+__global__ void k_fx_rescale_group(FxScales *const *__restrict__ tab, int count)
+{
+    if ((int)threadIdx.x >= count || (int)threadIdx.x >= kFxSlots) return;
+    fx_rescale_slot(tab[blockIdx.x], (int)threadIdx.x);
 }
 
 // FX planes of phi-matrices, one block per output row i of stack s: the row
@@ -3627,6 +3646,10 @@ static void launch_rhs_fx(MixedPlan *mp, const Model &model, double *U, bool mea
 int enqueue_rhs_mixed(MixedPlan *mp, const Model &model, double *U, cudaStream_t st)
 {
     const int64_t N = mp->N;
+    if (mp->fx) {
+        launch_rhs_fx(mp, model, U, false, st);   // FX planes with the current scales
+        return 1;
+    }
     if (mp->rhs_tiled)
         launch_rhs_tiled(mp->stf[0], mp->stf[1], model_df(model), N, U, mp->Fp, st);
     else
@@ -3642,10 +3665,17 @@ int enqueue_rhs_mixed(MixedPlan *mp, const Model &model, double *U, cudaStream_t
 // ---------------------------------------------------------------------------
 struct MixedGroup {
     int d = 0;
+    // FX batches (DS_PREC_F16X10 plans): every problem's scale table, rescaled
+    // for all problems by one launch at the start of each step
+    bool fx = false;
+    FxScales **fxtab = nullptr;    // device [ninst]
+    int nslots = 0;
+    int ninst = 0;
     struct Slot {
         bool mode1 = false;
         int bn = 256;
         bool dual = false;
+        bool fx = false;
         TcArgs *tab = nullptr;     // device [ninst]
         int64_t *prefix = nullptr; // device [ninst]
         int ninst = 0;
@@ -3692,6 +3722,7 @@ void mixed_group_destroy(MixedGroup *G)
     }
     cudaFree(G->rtab);
     cudaFree(G->rprefix);
+    cudaFree(G->fxtab);
     delete G;
 }
 
@@ -3699,9 +3730,9 @@ static void launch_group_slot(const MixedGroup::Slot &sl, bool sep, cudaStream_t
 {
     if (sep)
         launch_tc<true>(sl.mode1, sl.bn, sl.dual, sl.grid_sep, st, sl.a0_sep, sl.tab_sep, sl.prefix_sep, sl.ninst,
-                        sl.units_sep);
+                        sl.units_sep, sl.fx);
     else
-        launch_tc<true>(sl.mode1, sl.bn, sl.dual, sl.grid, st, sl.a0, sl.tab, sl.prefix, sl.ninst, sl.units);
+        launch_tc<true>(sl.mode1, sl.bn, sl.dual, sl.grid, st, sl.a0, sl.tab, sl.prefix, sl.ninst, sl.units, sl.fx);
     if (sep)
         k_stage_group<<<pw_grid(sl.points), 256, 0, st>>>(sl.stab, sl.sprefix, sl.ninst, sl.points, sl.kind);
 }
@@ -3714,10 +3745,18 @@ ds_status mixed_group_create(const std::vector<MixedPlan *> &mps, const std::vec
         return fail(DS_ERR_INVALID_ARG, "grouped launch: inconsistent problem lists");
     const int d = mps[0]->d;
     for (auto *mp : mps)
-        if (mp->d != d || mp->compensated != mps[0]->compensated)
+        if (mp->d != d || mp->compensated != mps[0]->compensated || mp->fx != mps[0]->fx)
             return fail(DS_ERR_UNSUPPORTED, "grouped launch: problems differ in dimension or precision");
     MixedGroup *G = new MixedGroup();
     G->d = d;
+    G->fx = mps[0]->fx;
+    G->ninst = ninst;
+    G->nslots = 2 + 6 * (d - 1);
+    // FX: the timing runs below write scale records; each problem's table is
+    // put back as it was afterwards
+    std::vector<FxScales> fx_saved(G->fx ? ninst : 0);
+    for (int i = 0; i < (int)fx_saved.size(); ++i)
+        cudaMemcpy(&fx_saved[i], mps[i]->fxs, sizeof(FxScales), cudaMemcpyDeviceToHost);
     G->slots.resize(3 * d);
     auto dev_copy = [&](auto **dst, const auto &v) {
         using T = typename std::decay_t<decltype(v)>::value_type;
@@ -3789,6 +3828,7 @@ ds_status mixed_group_create(const std::vector<MixedPlan *> &mps, const std::vec
                     sl.mode1 = L.mode1;
                     sl.bn = L.bn;
                     sl.dual = L.dual;
+                    sl.fx = L.fx;
                     sl.a0 = a;
                     if (last) sl.a0_sep = tab_sep[0];
                 }
@@ -3894,6 +3934,13 @@ ds_status mixed_group_create(const std::vector<MixedPlan *> &mps, const std::vec
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(Us);
+    for (int i = 0; i < (int)fx_saved.size(); ++i)
+        cudaMemcpy(mps[i]->fxs, &fx_saved[i], sizeof(FxScales), cudaMemcpyHostToDevice);
+    if (r == DS_OK && G->fx) {
+        std::vector<FxScales *> ft;
+        for (auto *mp : mps) ft.push_back(mp->fxs);
+        if (!dev_copy(&G->fxtab, ft)) r = fail(DS_ERR_OOM, "grouped FX scale tables");
+    }
     if (r == DS_OK) {
         bool tiled = d <= 3;
         int64_t blocks = 0;
@@ -3903,6 +3950,10 @@ ds_status mixed_group_create(const std::vector<MixedPlan *> &mps, const std::vec
             const MixedPlan *mp = mps[i];
             tiled = mp->rhs_tiled && mp->N < ((int64_t)1 << 31);
             rt.push_back(rhs_args(mp->stf[0], mp->stf[1], model_df(models[i]), mp->N, U[i], mp->Fp));
+            if (G->fx) {
+                rt.back().fxs = mp->fxs;
+                rt.back().fx_measure = 0;
+            }
             rp.push_back((int)blocks);
             const dim3 g = rhs_tiles(mp->stf[0]);
             blocks += (int64_t)g.x * g.y * g.z;
@@ -3921,10 +3972,17 @@ ds_status mixed_group_create(const std::vector<MixedPlan *> &mps, const std::vec
     return DS_OK;
 }
 
+int mixed_group_enqueue_rescale(const MixedGroup *G, cudaStream_t st)
+{
+    if (!G || !G->fx) return 0;
+    k_fx_rescale_group<<<G->ninst, 32, 0, st>>>(G->fxtab, G->nslots);
+    return 1;
+}
+
 int mixed_group_enqueue_rhs(const MixedGroup *G, cudaStream_t st)
 {
     if (!G || G->rblocks <= 0) return 0;
-    launch_rhs_group(G->d, G->rtab, G->rprefix, G->rinst, G->rblocks, st);
+    launch_rhs_group(G->d, G->rtab, G->rprefix, G->rinst, G->rblocks, st, G->fx);
     return 1;
 }
 

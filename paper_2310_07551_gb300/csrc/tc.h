@@ -34,7 +34,8 @@ int enqueue_step_mixed(MixedPlan *mp, const ds_phi_set *set, const Model &model,
                        const Stencil *sten, double *U, cudaStream_t st, Prof *prof, bool calibrate = false);
 // FX plans: the scale table's overflow flag (and clear it), -1 if none
 int mixed_plan_fx_overflow(MixedPlan *mp, bool clear);
-// F = K U + g(U) of one problem (the first kernel of its step)
+// F = K U + g(U) of one problem (the first kernel of its step; FX plans: FX
+// planes with the scales already set for the step)
 int enqueue_rhs_mixed(MixedPlan *mp, const Model &model, double *U, cudaStream_t st);
 // Grouped launches for batches: the same mode product of every problem in
 // one persistent launch (tables built for one set of state pointers).
@@ -48,6 +49,9 @@ int mixed_group_enqueue(const MixedGroup *G, cudaStream_t st, Prof *prof);
 // every problem's F planes in one launch; 0 (nothing launched) where some
 // problem's grid has no tiled stencil kernel
 int mixed_group_enqueue_rhs(const MixedGroup *G, cudaStream_t st);
+// FX batches: the start-of-step rescale of every problem's scale table (one
+// launch; 0 for other precisions).  Enqueue it before the F planes.
+int mixed_group_enqueue_rescale(const MixedGroup *G, cudaStream_t st);
 int mixed_group_fusion(const MixedGroup *G, int g, int *fused, float *ms_fused, float *ms_separate);
 int mixed_group_tile_order(const MixedGroup *G, int g, int *order, float *times);
 // FP32 CUDA-core path pointwise kernels (two components, N points each)

@@ -38,7 +38,8 @@ def problem(inst):
 
 
 @pytest.mark.parametrize("precision,fusion", [("f64", None), ("bf16x6", None), ("bf16x6", True),
-                                              ("bf16x6", False), ("bf16x6c", None)])
+                                              ("bf16x6", False), ("bf16x6c", None), ("f16x10", None),
+                                              ("f16x10", True), ("f16x10", False)])
 def test_batch_matches_individual_plans_and_oracle(ds, precision, fusion):
     insts = small_instances()
     As = [problem(i) for i in insts]
@@ -59,8 +60,9 @@ def test_batch_matches_individual_plans_and_oracle(ds, precision, fusion):
         fz = batch.fusion()
         if fusion is not None:
             assert all(f == fusion for _, f, _, _ in fz)
-            # one grouped stencil launch + 3 d grouped products (+ 3 stage kernels)
-            assert batch.kernels_per_step == 1 + 6 + (0 if fusion else 3)
+            # one grouped stencil launch + 3 d grouped products (+ 3 stage
+            # kernels; f16x10: + the grouped rescale of the scale tables)
+            assert batch.kernels_per_step == 1 + 6 + (0 if fusion else 3) + (precision == "f16x10")
         else:
             assert all(a > 0 and b > 0 for _, _, a, b in fz) or all(a == 0 for _, _, a, _ in fz)
         assert all(o in (0, 1) for _, o, _, _ in batch.tile_order())
@@ -81,3 +83,32 @@ def test_batch_matches_individual_plans_and_oracle(ds, precision, fusion):
                          inst.params, inst.tau, U0[k], m)
             got = Ub[k].cpu().numpy()
             assert np.abs(got - ref).max() / np.abs(ref).max() < 1e-12
+
+
+@pytest.mark.parametrize("precision,tol", [("f16x10", 1e-7), ("bf16x6", 2e-6)])
+def test_batch_of_workload_sized_instances_matches_the_oracle(ds, precision, tol):
+    """Four instances of the 64-instance workload itself (grids of 96 to 512
+    points per side, their own parameters and tau), five batch steps (the
+    calibrating first step of f16x10, then grouped launches), against the
+    oracle per instance.  f16x10: the 1e-8 class of its arithmetic;
+    bf16x6: the FP32-class per-config bound at these sizes (not the
+    workload's 1e-6 target over 500 steps)."""
+    every = configs.batch_instances()
+    pick = [8, 12, 21, 33]   # 512 x 96, 512 x 384, 96 x 96, 96 x 384
+    insts = [every[k] for k in pick]
+    As = [problem(i) for i in insts]
+    batch = ds.Batch([i.dims for i in insts], As, [i.tau for i in insts], "schnakenberg",
+                     [i.params for i in insts], precision)
+    U0 = [inputs.initial_state("schnakenberg", i.dims, seed=7 + k, a=i.params[1], b=i.params[2])
+          for k, i in zip(pick, insts)]
+    Ub = [torch.from_numpy(u.copy()).cuda() for u in U0]
+    m = 5
+    batch.integrate(Ub, m)
+    batch.sync()
+    for k, inst in enumerate(insts):
+        ref = O.step(inst.dims, As[k], O.phi_set(inst.dims, As[k], inst.tau), "schnakenberg",
+                     inst.params, inst.tau, U0[k], m)
+        got = Ub[k].cpu().numpy()
+        err = max(np.abs(got[c] - ref[c]).max() / np.abs(ref[c]).max() for c in range(2))
+        print("batch", precision, inst.dims, err)
+        assert err < tol, (inst.dims, err)
