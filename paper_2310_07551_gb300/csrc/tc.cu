@@ -62,7 +62,11 @@ struct TileCfg {
     static constexpr uint32_t B_PLANE = BNT * BK * 2;
     static constexpr uint32_t STAGE_BYTES = STAGE_A + NP * B_PLANE;
     static constexpr uint32_t BAR_BYTES = 8 * (2 * STAGES + 8) + 16;
-    static constexpr uint32_t SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + BAR_BYTES;
+    // FX: the drained low parts of the second 32-column chunk of every
+    // epilogue thread's half row (32 x 256 floats)
+    static constexpr uint32_t SPILL_OFF = (STAGES * STAGE_BYTES + BAR_BYTES + 127u) & ~127u;
+    static constexpr uint32_t SPILL_BYTES = NP == 4 ? 32u * 256u * 4u : 0u;
+    static constexpr uint32_t SMEM_BYTES = SPILL_OFF + SPILL_BYTES + 1024;
 };
 constexpr long long kTimeoutCycles = 4000000000LL;   // ~2 s at 2 GHz
 
@@ -397,6 +401,25 @@ __device__ __forceinline__ void fx_split(float hi, float lo, __half (&o)[4])
     o[1] = __float2half_rn(f1);
     o[2] = s2;
     o[3] = __float2half_rn(__fadd_rn(__fsub_rn(q, __half2float(s2)), lo));
+}
+// The same split for two values at once (rows r and r+1 of one column), each
+// part packed as a half2 (low half: the first value).  Rounding to a multiple
+// of 16 (of 2^-7) by adding and subtracting 1.5 * 2^27 (1.5 * 2^16): the sum
+// lands where the float spacing is 16 (2^-7), so the result is the
+// round-to-nearest-even multiple, as 16 rint(x / 16) gives (|x| < 2^26).
+__device__ __forceinline__ void fx_split2(float xh0, float xl0, float xh1, float xl1, __half2 (&o)[4])
+{
+    constexpr float M16 = 201326592.0f, M7 = 98304.0f;
+    const float h0 = __fsub_rn(__fadd_rn(xh0, M16), M16), h1 = __fsub_rn(__fadd_rn(xh1, M16), M16);
+    const float r0 = __fsub_rn(xh0, h0), r1 = __fsub_rn(xh1, h1);
+    const float a0 = __fsub_rn(__fadd_rn(r0, M7), M7), a1 = __fsub_rn(__fadd_rn(r1, M7), M7);
+    const float q0 = __fsub_rn(r0, a0), q1 = __fsub_rn(r1, a1);
+    const __half2 s2 = __floats2half2_rn(__fadd_rn(q0, xl0), __fadd_rn(q1, xl1));
+    const float2 s2f = __half22float2(s2);
+    o[0] = __floats2half2_rn(h0, h1);
+    o[1] = __floats2half2_rn(a0, a1);
+    o[2] = s2;
+    o[3] = __floats2half2_rn(__fadd_rn(__fsub_rn(q0, s2f.x), xl0), __fadd_rn(__fsub_rn(q1, s2f.y), xl1));
 }
 // the same for an FP64 value (setup-time use: phi-matrix rows, FP64 tensors)
 __device__ __forceinline__ void fx_split_d(double v, __half (&o)[4])
@@ -951,11 +974,11 @@ __device__ __noinline__ void sk_fill(const TcArgs &a, int64_t unit, int h, const
 //
 // FX (fixed-head FP16 operands, 128-column tiles): the four accumulators A,
 // B1, B2, B3 take TMEM columns [0, 128), [128, 256), [256, 384) and
-// [384, 512), one tile at a time: the epilogue reads them 32 columns at a
-// time, combines them in double-float and stores, then releases them
-// (TEMPTY) for the next tile's MMAs.  The producer keeps filling the operand
-// ring meanwhile.
-template <bool MODE1, int BNT, bool DUAL, bool GROUPED, bool SK, bool FX = false>
+// [384, 512), one tile at a time.  The epilogue first drains all four into a
+// double-float per element (registers, half of the low parts in shared
+// memory) and releases them (TEMPTY); its scaling, FX split and stores then
+// overlap the next tile's MMAs.
+template <bool MODE1, int BNT, bool DUAL, bool GROUPED, bool SK, int FX = 0>
 __global__ void __launch_bounds__(kThreads, 1)
     k_mode_tc(const __grid_constant__ TcArgs a0, const TcArgs *__restrict__ gtab, const int64_t *__restrict__ gprefix,
               int ginst, int64_t gunits)
@@ -1310,21 +1333,122 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int64_t cbase = (int64_t)tc.nt * BN + half * (BN / 2);
                 // element offset of column cbase in this row
                 const int64_t rbase = (int64_t)tc.s * out_cs + row_index + cbase * (int64_t)col_stride;
-                if constexpr (FX) {
-                    // value = 2^(E_in + sigma) (A + B1 + B2 + B3), as a double-float
+                if constexpr (FX == 1) {
+                    // (1) drain: the four accumulators of this thread's half row
+                    // as a normalised double-float vh + vl (two-sum of the exact A
+                    // and B1, then the small B2 + B3), chunk 0's low parts in
+                    // registers and chunk 1's in shared memory; then release the
+                    // accumulators, so the next tile's MMAs run while this tile's
+                    // values are scaled, split and stored
+                    float vh[BN / 2], vl0[32];
+                    float *const vls = (float *)(gbase + TileCfg<BNT, NP>::SPILL_OFF) + (threadIdx.x - 64);
+#pragma unroll
+                    for (int c = 0; c < BN / 64; ++c) {
+                        if (cbase + c * 32 < col_lim) {   // warp-uniform
+#pragma unroll
+                            for (int g = 0; g < 2; ++g) {   // 16 columns at a time
+                                const uint32_t tb = tmem + (uint32_t)(half * (BN / 2) + c * 32 + g * 16) +
+                                                    ((uint32_t)(quarter * 32) << 16);
+                                uint32_t w0[16], w1[16];
+                                float t[16];
+                                tmem_ld16(tb, w0);
+                                tmem_ld16(tb + BN, w1);
+                                tmem_wait_ld();
+#pragma unroll
+                                for (int j = 0; j < 16; ++j)
+                                    two_sum_f(__uint_as_float(w0[j]), __uint_as_float(w1[j]), vh[c * 32 + g * 16 + j],
+                                              t[j]);
+                                tmem_ld16(tb + 2 * BN, w0);
+                                tmem_ld16(tb + 3 * BN, w1);
+                                tmem_wait_ld();
+#pragma unroll
+                                for (int j = 0; j < 16; ++j) {
+                                    const float l = __fadd_rn(t[j], __fadd_rn(__uint_as_float(w0[j]),
+                                                                              __uint_as_float(w1[j])));
+                                    float lo;
+                                    two_sum_f(vh[c * 32 + g * 16 + j], l, vh[c * 32 + g * 16 + j], lo);
+                                    if (c == 0) vl0[g * 16 + j] = lo;
+                                    else vls[(g * 16 + j) * kEpiThreads] = lo;
+                                }
+                            }
+                        }
+                    }
+                    tc_fence_before();
+                    mbar_arrive(TEMPTY(acc));
+                    // (2) value = 2^(E_in + sigma) (vh + vl), further scaled by the
+                    // output slot's 2^-E (inv): all powers of two
                     const float xin = a.fxs->scale[a.xsl_base + tc.s / a.xsl_div];
-                    const int oslot = out_kind == 0 ? a.osl_base + tc.s / a.osl_div : 0;
-                    const float inv = out_kind == 0 ? a.fxs->inv[oslot] : 1.0f;
+                    const int oslot = a.osl_base + tc.s / a.osl_div;
+                    const float inv = a.fxs->inv[oslot];
+                    float grow = 0.0f;   // mode 1: one factor per accumulator row
+                    if (MODE1 && row_ok) grow = a.pscale[(int64_t)tc.s * a.n + (tc.mt * BM + m)] * xin * inv;
+                    float lmax = 0.0f;   // largest |value| written, in units of the output scale
+#pragma unroll
+                    for (int c = 0; c < BN / 64; ++c) {
+                        const int64_t col0 = cbase + c * 32;
+                        if (col0 >= col_lim) break;   // warp-uniform
+                        const int jmax = (col_lim - col0 >= 32) ? 32 : (int)(col_lim - col0);
+                        const int64_t e0 = rbase + (int64_t)(c * 32) * col_stride;
+                        // modes >= 2: one factor per column; lane j holds column col0 + j's
+                        const float gcol = MODE1 ? 0.0f
+                                                 : (lane < jmax ? __ldg(a.pscale + (int64_t)tc.s * a.n + col0 + lane) *
+                                                                      xin * inv
+                                                                : 0.0f);
+                        // value of column j as a double-float (hi, lo); every lane calls it
+                        // with the same j (the column factor is a warp shuffle)
+                        auto value = [&](int j, float &hi, float &lo) {
+                            const float g = MODE1 ? grow : __shfl_sync(0xffffffffu, gcol, j);
+                            hi = vh[c * 32 + j] * g;
+                            lo = (c == 0 ? vl0[j] : vls[j * kEpiThreads]) * g;
+                        };
+                        {
+                            // FX planes of the output tensor, as pairs of rows: the even
+                            // lane stores rows (r, r+1) of column j, the odd lane those of
+                            // column j + 1.  Values outside the tile's rows and columns are
+                            // exact zeros (zero-filled operands), so the maximum needs no mask.
+                            const int odd = lane & 1;
+                            const int64_t eb = e0 - odd;
+#pragma unroll
+                            for (int j = 0; j < 32; j += 2) {
+                                float h0, l0, h1, l1;
+                                value(j, h0, l0);
+                                value(j + 1, h1, l1);
+                                lmax = fmaxf(lmax, fmaxf(fabsf(h0), fabsf(h1)));
+                                const float rh = __shfl_xor_sync(0xffffffffu, odd ? h0 : h1, 1);
+                                const float rl = __shfl_xor_sync(0xffffffffu, odd ? l0 : l1, 1);
+                                const int jj = j + odd;
+                                __half2 q[4];
+                                fx_split2(odd ? rh : h0, odd ? rl : l0, odd ? h1 : rh, odd ? l1 : rl, q);
+                                if (!a.fx_measure && row_ok && jj < jmax) {
+                                    __half *o = (__half *)out_ptr + eb + (uint32_t)jj * col_stride;
+#pragma unroll
+                                    for (int k = 0; k < 4; ++k) *(__half2 *)(o + k * a.out_ps) = q[k];
+                                }
+                            }
+                        }
+                    }
+                    {
+                        // the heads stay exact below kFxHeadMax; the next rescale takes
+                        // the largest value in real units (times 2^E, exact)
+                        if (!a.fx_measure && lmax > kFxHeadMax) atomicExch(&a.fxs->overflow, 1);
+                        const unsigned mb =
+                            __reduce_max_sync(0xffffffffu, __float_as_uint(lmax * a.fxs->scale[oslot]));
+                        if (lane == 0 && mb) atomicMax(&a.fxs->maxbits[oslot], mb);
+                    }
+                } else if constexpr (FX == 2) {
+                    // last modes (FP32 increments with the stage epilogue, or FP64):
+                    // each 32-column chunk of the four accumulators is read, combined
+                    // in double-float and stored in place; the accumulators are
+                    // released after the tile (K = T n is long here, so the MMA time
+                    // per tile dwarfs this epilogue)
+                    const float xin = a.fxs->scale[a.xsl_base + tc.s / a.xsl_div];
                     float frow = 0.0f;
                     if (MODE1 && row_ok) frow = a.pscale[(int64_t)tc.s * a.n + (tc.mt * BM + m)] * xin;
                     const EpiTile et = epi_tile<MODE1, BN>(a, tc, part, m, half);
-                    float lmax = 0.0f;
 #pragma unroll 1
                     for (int c = 0; c < BN / 64; ++c) {
                         const int64_t col0 = cbase + c * 32;
                         if (col0 >= col_lim) break;   // warp-uniform, before the collective load
-                        // this chunk of the four accumulators as a double-float vh + vl:
-                        // two-sum of the exact A and B1, then the small B2 + B3
                         uint32_t v[32];
                         float vh[32], vl[32];
 #pragma unroll
@@ -1344,57 +1468,22 @@ __global__ void __launch_bounds__(kThreads, 1)
                             tmem_wait_ld();
 #pragma unroll
                             for (int j = 0; j < 16; ++j) {
-                                const float l = __fadd_rn(vl[g * 16 + j],
-                                                          __fadd_rn(__uint_as_float(w0[j]), __uint_as_float(w1[j])));
+                                const float l = __fadd_rn(vl[g * 16 + j], __fadd_rn(__uint_as_float(w0[j]),
+                                                                                    __uint_as_float(w1[j])));
                                 two_sum_f(vh[g * 16 + j], l, vh[g * 16 + j], vl[g * 16 + j]);   // normalise
                             }
                         }
                         const int jmax = (col_lim - col0 >= 32) ? 32 : (int)(col_lim - col0);
                         const int64_t e0 = rbase + (int64_t)(c * 32) * col_stride;
-                        // value of column j as a normalised double-float (hi, lo)
+                        // value = 2^(E_in + sigma) (vh + vl), as a double-float (hi, lo)
                         auto value = [&](int j, float &hi, float &lo) {
-                            hi = vh[j];
-                            lo = vl[j];
                             const float f = MODE1 ? frow
                                                   : (j < jmax ? __ldg(a.pscale + (int64_t)tc.s * a.n + col0 + j) * xin
                                                               : 0.0f);
-                            hi *= f;
-                            lo *= f;
+                            hi = vh[j] * f;
+                            lo = vl[j] * f;
                         };
-                        if (out_kind == 0) {
-                            // FX planes of the output tensor (scale slot oslot), as
-                            // pairs of rows like the plain BF16 store below: the even
-                            // lane stores rows (r, r+1) of column j, the odd lane those
-                            // of column j + 1
-                            const int odd = lane & 1;
-                            const int64_t eb = e0 - odd;
-                            bool over = false;
-#pragma unroll
-                            for (int j = 0; j < 32; j += 2) {
-                                float h0, l0, h1, l1;
-                                value(j, h0, l0);
-                                value(j + 1, h1, l1);
-                                if (row_ok) {
-                                    if (j < jmax) lmax = fmaxf(lmax, fabsf(h0));
-                                    if (j + 1 < jmax) lmax = fmaxf(lmax, fabsf(h1));
-                                }
-                                const float rh = __shfl_xor_sync(0xffffffffu, odd ? h0 : h1, 1);
-                                const float rl = __shfl_xor_sync(0xffffffffu, odd ? l0 : l1, 1);
-                                const int jj = j + odd;
-                                if (!a.fx_measure && row_ok && jj < jmax) {
-                                    const float x0h = (odd ? rh : h0) * inv, x0l = (odd ? rl : l0) * inv;
-                                    const float x1h = (odd ? h1 : rh) * inv, x1l = (odd ? l1 : rl) * inv;
-                                    __half q0[4], q1[4];
-                                    fx_split(x0h, x0l, q0);
-                                    fx_split(x1h, x1l, q1);
-                                    over = over || fabsf(x0h) > kFxHeadMax || fabsf(x1h) > kFxHeadMax;
-                                    __half *o = (__half *)out_ptr + eb + (uint32_t)jj * col_stride;
-#pragma unroll
-                                    for (int k = 0; k < 4; ++k) *(__half2 *)(o + k * a.out_ps) = __halves2half2(q0[k], q1[k]);
-                                }
-                            }
-                            if (over) atomicExch(&a.fxs->overflow, 1);
-                        } else if (out_kind == 2) {
+                        if (out_kind == 2) {
                             // FP64 output (the standalone operator's last mode)
                             double *o = (double *)out_ptr + e0;
 #pragma unroll
@@ -1414,10 +1503,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                             }
                             epi_chunk(a, tc, et, c, lane, v);
                         }
-                    }
-                    if (out_kind == 0) {
-                        const unsigned mb = __reduce_max_sync(0xffffffffu, __float_as_uint(lmax));
-                        if (lane == 0 && mb) atomicMax(&a.fxs->maxbits[oslot], mb);
                     }
                 } else {
 #pragma unroll 1
@@ -1554,11 +1639,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                 }
                 }
-                tc_fence_before();
-                mbar_arrive(TEMPTY(acc));
-                if constexpr (FX) {
-                    acc_phase ^= 1u;   // one accumulator set: buffer 0 only
+                if constexpr (FX == 1) {
+                    acc_phase ^= 1u;   // released after the drain; one accumulator set
+                } else if constexpr (FX == 2) {
+                    tc_fence_before();
+                    mbar_arrive(TEMPTY(acc));
+                    acc_phase ^= 1u;   // one accumulator set
                 } else {
+                    tc_fence_before();
+                    mbar_arrive(TEMPTY(acc));
                     acc ^= 1;
                     if (acc == 0) acc_phase ^= 1u;
                 }
@@ -2752,13 +2841,20 @@ static void launch_tc_k(bool mode1, int bn, bool dual, int grid, cudaStream_t st
                       int64_t gunits = 0, bool fx = false)
 {
     if (fx) {
+        // FX launches: intermediates (FX planes out) or last modes (FP32 / FP64 out)
         if constexpr (!SK) {
-            if (mode1)
-                k_mode_tc<true, 128, false, GROUPED, false, true>
-                    <<<grid, kThreads, TileCfg<128, 4>::SMEM_BYTES, st>>>(a, gtab, gprefix, ginst, gunits);
-            else
-                k_mode_tc<false, 128, false, GROUPED, false, true>
-                    <<<grid, kThreads, TileCfg<128, 4>::SMEM_BYTES, st>>>(a, gtab, gprefix, ginst, gunits);
+            constexpr uint32_t sm = TileCfg<128, 4>::SMEM_BYTES;
+            if (a.out_kind == 0) {
+                if (mode1)
+                    k_mode_tc<true, 128, false, GROUPED, false, 1><<<grid, kThreads, sm, st>>>(a, gtab, gprefix, ginst, gunits);
+                else
+                    k_mode_tc<false, 128, false, GROUPED, false, 1><<<grid, kThreads, sm, st>>>(a, gtab, gprefix, ginst, gunits);
+            } else {
+                if (mode1)
+                    k_mode_tc<true, 128, false, GROUPED, false, 2><<<grid, kThreads, sm, st>>>(a, gtab, gprefix, ginst, gunits);
+                else
+                    k_mode_tc<false, 128, false, GROUPED, false, 2><<<grid, kThreads, sm, st>>>(a, gtab, gprefix, ginst, gunits);
+            }
         }
         return;
     }
@@ -2821,10 +2917,14 @@ static void set_smem_limits()
         cudaFuncSetAttribute(k_mode_tc<true, 128, true, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s128);
         cudaFuncSetAttribute(k_mode_tc<false, 128, true, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s128);
         const int sfx = (int)TileCfg<128, 4>::SMEM_BYTES;
-        cudaFuncSetAttribute(k_mode_tc<true, 128, false, false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sfx);
-        cudaFuncSetAttribute(k_mode_tc<false, 128, false, false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sfx);
-        cudaFuncSetAttribute(k_mode_tc<true, 128, false, true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sfx);
-        cudaFuncSetAttribute(k_mode_tc<false, 128, false, true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sfx);
+        cudaFuncSetAttribute(k_mode_tc<true, 128, false, false, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sfx);
+        cudaFuncSetAttribute(k_mode_tc<false, 128, false, false, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sfx);
+        cudaFuncSetAttribute(k_mode_tc<true, 128, false, true, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sfx);
+        cudaFuncSetAttribute(k_mode_tc<false, 128, false, true, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sfx);
+        cudaFuncSetAttribute(k_mode_tc<true, 128, false, false, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sfx);
+        cudaFuncSetAttribute(k_mode_tc<false, 128, false, false, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sfx);
+        cudaFuncSetAttribute(k_mode_tc<true, 128, false, true, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sfx);
+        cudaFuncSetAttribute(k_mode_tc<false, 128, false, true, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sfx);
     });
 }
 
