@@ -85,11 +85,18 @@ typedef enum {
  *                    truncation acts on small partial sums only.
  *                    F = K U + g(U) is formed in double-float.  A plan sets
  *                    each E from the largest magnitude the previous step
- *                    wrote; the first step on a state pointer (of ds_step or
- *                    ds_integrate) measures every tensor before writing it.
- *                    A tensor that grows more than 16x within one step leaves
- *                    the exact head range: ds_plan_sync then reports
- *                    DS_ERR_NONFINITE.  d = 2 or 3, fewer than 2^31 points. */
+ *                    wrote, never more than 10 below the largest E since the
+ *                    state's calibrating step (a tensor that settles far
+ *                    below its early size keeps a precision floor instead of
+ *                    following it down); the first step on a state pointer
+ *                    (of ds_step, ds_integrate or a batch) is that
+ *                    calibrating step: it measures every tensor before
+ *                    writing it.  The parts stay exact up to 2^16 times 2^E,
+ *                    so a tensor may grow ~32x within one step (beyond 16x
+ *                    its head products lose their exact sum for that step);
+ *                    a value beyond the FP16 range of its parts makes
+ *                    ds_plan_sync report DS_ERR_NONFINITE.  d = 2 or 3,
+ *                    fewer than 2^31 points. */
 typedef enum {
     DS_PREC_F64 = 0,
     DS_PREC_BF16X6 = 1,

@@ -96,17 +96,38 @@ constexpr uint32_t kSw128 = 2, kSw64 = 4;
 // Scale exponents live per tensor set ("slot") in a device table: the
 // producer of a tensor reads its slot's exponent and records the largest
 // magnitude it wrote; at the start of the next step each slot's exponent is
-// set from that maximum (so a tensor may grow 16x in one step before its
-// heads leave the exact range, which is reported as an overflow).
+// set from that maximum, but never more than kFxFloorBits below the largest
+// exponent the slot had since the state's calibrating step.  A tensor that
+// shrinks far below its early size (a state settling to a steady pattern,
+// whose F then fluctuates from step to step) keeps a precision floor of
+// ~2^-45 of that size instead of following it down, so it can grow again by
+// large factors without leaving its range.  The parts stay exact while
+// |x 2^-E| < 2^16 (the head and s1 are rounded to FP16 before the rest is
+// formed), so a tensor may grow ~32x in one step from its scale; beyond 2^15
+// the head products lose their exact sum for that step only.  A value past
+// the FP16 range of its parts is reported as an overflow.
 constexpr int kFxSlots = 32;
-constexpr float kFxHeadMax = 32760.0f;   // |x 2^-E| beyond this: heads no longer exact
+constexpr float kFxRangeMax = 65472.0f;  // |x 2^-E| beyond this: the parts leave FP16's range
+constexpr int kFxFloorBits = 10;         // exponent floor below the slot's largest since calibration
+constexpr int kFxNoHist = -4096;         // no exponent set since the last calibration
 struct FxScales {
     float scale[kFxSlots];      // 2^E
     float inv[kFxSlots];        // 2^-E
     unsigned maxbits[kFxSlots]; // largest |value| written since the last rescale (float bits)
-    int overflow;               // a value left the exact head range
+    int ehist[kFxSlots];        // largest E since the state's calibrating step (kFxNoHist: none)
+    int overflow;               // a value left the FP16 range of its parts
     int pad[3];
 };
+// a fresh table: every scale 1, no history
+static inline FxScales fx_scales_init()
+{
+    FxScales h{};
+    for (int q = 0; q < kFxSlots; ++q) {
+        h.scale[q] = h.inv[q] = 1.0f;
+        h.ehist[q] = kFxNoHist;
+    }
+    return h;
+}
 
 // model parameters rounded to FP32 on the host
 struct ModelF {
@@ -384,21 +405,22 @@ __device__ __forceinline__ void split3_pair(float x0, float x1, uint32_t &q0, ui
 }
 
 // FX split of v = x 2^-E given as a double-float (hi, lo), v = h + s1 + s2 +
-// s3: head h = 16 rint(hi / 16) (hi - h exact: h is a multiple of hi's ulp
-// within 8 of it); s1 = 2^-7 rint(128 r) with r = hi - h, a fixed-point part
-// (|s1| <= 8, an integer times 2^-7, exact in FP16), so head x s1 products
-// are multiples of 2^-3; q = r - s1 is exact (|q| <= 2^-8); s2 = RN16(q +
-// lo) and s3 = RN16((q - s2) + lo) (q - s2 exact).  The parts keep ~2^-36
-// of 2^11 (FP16 subnormals bound s3's resolution at 2^-25).
+// s3: head h = RN16(16 rint(hi / 16)); r = hi - h (exact); s1 = RN16(2^-7
+// rint(128 r)); q = r - s1 (exact); s2 = RN16(q + lo) and s3 = RN16((q - s2)
+// + lo) (q - s2 exact).  Below |v| = 2^15 the two RN16 roundings are exact
+// (h a multiple of 16, |s1| <= 8 on the 2^-7 grid); up to FP16's range they
+// keep the parts summing to v, with |s1| and |q| a few times larger.  The
+// parts keep ~2^-36 of 2^11 (FP16 subnormals bound s3's resolution at
+// 2^-25).
 __device__ __forceinline__ void fx_split(float hi, float lo, __half (&o)[4])
 {
-    const float hf = 16.0f * rintf(hi * 0.0625f);
-    const float r = __fsub_rn(hi, hf);
-    const float f1 = 0.0078125f * rintf(r * 128.0f);
-    const float q = __fsub_rn(r, f1);
+    const __half h = __float2half_rn(16.0f * rintf(hi * 0.0625f));
+    const float r = __fsub_rn(hi, __half2float(h));
+    const __half a = __float2half_rn(0.0078125f * rintf(r * 128.0f));
+    const float q = __fsub_rn(r, __half2float(a));
     const __half s2 = __float2half_rn(__fadd_rn(q, lo));
-    o[0] = __float2half_rn(hf);
-    o[1] = __float2half_rn(f1);
+    o[0] = h;
+    o[1] = a;
     o[2] = s2;
     o[3] = __float2half_rn(__fadd_rn(__fsub_rn(q, __half2float(s2)), lo));
 }
@@ -410,27 +432,29 @@ __device__ __forceinline__ void fx_split(float hi, float lo, __half (&o)[4])
 __device__ __forceinline__ void fx_split2(float xh0, float xl0, float xh1, float xl1, __half2 (&o)[4])
 {
     constexpr float M16 = 201326592.0f, M7 = 98304.0f;
-    const float h0 = __fsub_rn(__fadd_rn(xh0, M16), M16), h1 = __fsub_rn(__fadd_rn(xh1, M16), M16);
-    const float r0 = __fsub_rn(xh0, h0), r1 = __fsub_rn(xh1, h1);
-    const float a0 = __fsub_rn(__fadd_rn(r0, M7), M7), a1 = __fsub_rn(__fadd_rn(r1, M7), M7);
-    const float q0 = __fsub_rn(r0, a0), q1 = __fsub_rn(r1, a1);
+    const __half2 h = __floats2half2_rn(__fsub_rn(__fadd_rn(xh0, M16), M16), __fsub_rn(__fadd_rn(xh1, M16), M16));
+    const float2 hf = __half22float2(h);
+    const float r0 = __fsub_rn(xh0, hf.x), r1 = __fsub_rn(xh1, hf.y);
+    const __half2 a = __floats2half2_rn(__fsub_rn(__fadd_rn(r0, M7), M7), __fsub_rn(__fadd_rn(r1, M7), M7));
+    const float2 af = __half22float2(a);
+    const float q0 = __fsub_rn(r0, af.x), q1 = __fsub_rn(r1, af.y);
     const __half2 s2 = __floats2half2_rn(__fadd_rn(q0, xl0), __fadd_rn(q1, xl1));
     const float2 s2f = __half22float2(s2);
-    o[0] = __floats2half2_rn(h0, h1);
-    o[1] = __floats2half2_rn(a0, a1);
+    o[0] = h;
+    o[1] = a;
     o[2] = s2;
     o[3] = __floats2half2_rn(__fadd_rn(__fsub_rn(q0, s2f.x), xl0), __fadd_rn(__fsub_rn(q1, s2f.y), xl1));
 }
 // the same for an FP64 value (setup-time use: phi-matrix rows, FP64 tensors)
 __device__ __forceinline__ void fx_split_d(double v, __half (&o)[4])
 {
-    const double hf = 16.0 * rint(v * 0.0625);
-    const double r = v - hf;
-    const double f1 = 0.0078125 * rint(r * 128.0);
-    const double q = r - f1;
+    const __half h = __double2half(16.0 * rint(v * 0.0625));
+    const double r = v - (double)__half2float(h);
+    const __half a = __double2half(0.0078125 * rint(r * 128.0));
+    const double q = r - (double)__half2float(a);
     const __half s2 = __double2half(q);
-    o[0] = __double2half(hf);
-    o[1] = __double2half(f1);
+    o[0] = h;
+    o[1] = a;
     o[2] = s2;
     o[3] = __double2half(q - (double)__half2float(s2));
 }
@@ -1428,28 +1452,81 @@ __global__ void __launch_bounds__(kThreads, 1)
                         }
                     }
                     {
-                        // the heads stay exact below kFxHeadMax; the next rescale takes
+                        // the parts stay within FP16's range below kFxRangeMax; the next rescale takes
                         // the largest value in real units (times 2^E, exact)
-                        if (!a.fx_measure && lmax > kFxHeadMax) atomicExch(&a.fxs->overflow, 1);
+                        if (!a.fx_measure && lmax > kFxRangeMax) atomicExch(&a.fxs->overflow, 1);
                         const unsigned mb =
                             __reduce_max_sync(0xffffffffu, __float_as_uint(lmax * a.fxs->scale[oslot]));
                         if (lane == 0 && mb) atomicMax(&a.fxs->maxbits[oslot], mb);
                     }
-                } else if constexpr (FX == 2) {
-                    // last modes (FP32 increments with the stage epilogue, or FP64):
-                    // each 32-column chunk of the four accumulators is read, combined
-                    // in double-float and stored in place; the accumulators are
-                    // released after the tile (K = T n is long here, so the MMA time
-                    // per tile dwarfs this epilogue)
+                } else if constexpr (FX >= 2) {
+                    // last modes: FP32 increments with the stage epilogue (FX == 2)
+                    // or FP64 (FX == 3, the standalone operator)
                     const float xin = a.fxs->scale[a.xsl_base + tc.s / a.xsl_div];
                     float frow = 0.0f;
                     if (MODE1 && row_ok) frow = a.pscale[(int64_t)tc.s * a.n + (tc.mt * BM + m)] * xin;
-                    const EpiTile et = epi_tile<MODE1, BN>(a, tc, part, m, half);
+                    if constexpr (FX == 2) {
+                        const EpiTile et = epi_tile<MODE1, BN>(a, tc, part, m, half);
+                        // FP32 out: each element is the double-float value rounded
+                        // once, times its power-of-two factor; the four accumulators
+                        // are drained to one float per element (chunk 0 in
+                        // registers, chunk 1 in shared memory) and released before
+                        // the stores and the stage epilogue
+                        float vs[32];
+                        float *const vss = (float *)(gbase + TileCfg<BNT, NP>::SPILL_OFF) + (threadIdx.x - 64);
+#pragma unroll
+                        for (int c = 0; c < BN / 64; ++c) {
+                            const int64_t col0 = cbase + c * 32;
+                            if (col0 >= col_lim) break;   // warp-uniform
+                            const int jmax = (col_lim - col0 >= 32) ? 32 : (int)(col_lim - col0);
+                            const float fcol =
+                                MODE1 ? 0.0f
+                                      : (lane < jmax ? __ldg(a.pscale + (int64_t)tc.s * a.n + col0 + lane) * xin : 0.0f);
+#pragma unroll
+                            for (int g = 0; g < 2; ++g) {   // 16 columns at a time
+                                const uint32_t tb = tmem + (uint32_t)(half * (BN / 2) + c * 32 + g * 16) +
+                                                    ((uint32_t)(quarter * 32) << 16);
+                                uint32_t w0[16], w1[16];
+                                float h[16], l[16];
+                                tmem_ld16(tb, w0);
+                                tmem_ld16(tb + BN, w1);
+                                tmem_wait_ld();
+#pragma unroll
+                                for (int j = 0; j < 16; ++j)
+                                    two_sum_f(__uint_as_float(w0[j]), __uint_as_float(w1[j]), h[j], l[j]);
+                                tmem_ld16(tb + 2 * BN, w0);
+                                tmem_ld16(tb + 3 * BN, w1);
+                                tmem_wait_ld();
+#pragma unroll
+                                for (int j = 0; j < 16; ++j) {
+                                    const float lo = __fadd_rn(l[j], __fadd_rn(__uint_as_float(w0[j]),
+                                                                               __uint_as_float(w1[j])));
+                                    const float f = MODE1 ? frow : __shfl_sync(0xffffffffu, fcol, g * 16 + j);
+                                    const float val = __fadd_rn(h[j], lo) * f;
+                                    if (c == 0) vs[g * 16 + j] = val;
+                                    else vss[(g * 16 + j) * kEpiThreads] = val;
+                                }
+                            }
+                        }
+                        tc_fence_before();
+                        mbar_arrive(TEMPTY(acc));
+#pragma unroll 1
+                        for (int c = 0; c < BN / 64; ++c) {
+                            if (cbase + c * 32 >= col_lim) break;   // warp-uniform
+                            uint32_t v[32];
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) v[j] = __float_as_uint(c == 0 ? vs[j] : vss[j * kEpiThreads]);
+                            epi_chunk(a, tc, et, c, lane, v);
+                        }
+                    } else {
+                    // FP64 out: each 32-column chunk of the four accumulators is
+                    // read, combined in double-float and stored in place; the
+                    // accumulators are released after the tile (the operator's
+                    // last launch only)
 #pragma unroll 1
                     for (int c = 0; c < BN / 64; ++c) {
                         const int64_t col0 = cbase + c * 32;
                         if (col0 >= col_lim) break;   // warp-uniform, before the collective load
-                        uint32_t v[32];
                         float vh[32], vl[32];
 #pragma unroll
                         for (int g = 0; g < 2; ++g) {   // 16 columns at a time
@@ -1475,34 +1552,25 @@ __global__ void __launch_bounds__(kThreads, 1)
                         }
                         const int jmax = (col_lim - col0 >= 32) ? 32 : (int)(col_lim - col0);
                         const int64_t e0 = rbase + (int64_t)(c * 32) * col_stride;
-                        // value = 2^(E_in + sigma) (vh + vl), as a double-float (hi, lo)
+                        // modes >= 2: one factor per column; lane j holds column col0 + j's
+                        const float fcol = MODE1 ? 0.0f
+                                                 : (lane < jmax ? __ldg(a.pscale + (int64_t)tc.s * a.n + col0 + lane) * xin
+                                                                : 0.0f);
+                        // value = 2^(E_in + sigma) (vh + vl), as a double-float (hi, lo);
+                        // every lane calls it with the same j (warp shuffle)
                         auto value = [&](int j, float &hi, float &lo) {
-                            const float f = MODE1 ? frow
-                                                  : (j < jmax ? __ldg(a.pscale + (int64_t)tc.s * a.n + col0 + j) * xin
-                                                              : 0.0f);
+                            const float f = MODE1 ? frow : __shfl_sync(0xffffffffu, fcol, j);
                             hi = vh[j] * f;
                             lo = vl[j] * f;
                         };
-                        if (out_kind == 2) {
-                            // FP64 output (the standalone operator's last mode)
-                            double *o = (double *)out_ptr + e0;
+                        double *o = (double *)out_ptr + e0;
 #pragma unroll
-                            for (int j = 0; j < 32; ++j) {
-                                float hi, lo;
-                                value(j, hi, lo);
-                                if (row_ok && j < jmax) o[(uint32_t)j * col_stride] = (double)hi + (double)lo;
-                            }
-                        } else {
-                            // FP32 values: the same stores and fused stage epilogue as
-                            // the BF16 launches (alpha = 1)
-#pragma unroll
-                            for (int j = 0; j < 32; ++j) {
-                                float hi, lo;
-                                value(j, hi, lo);
-                                v[j] = __float_as_uint(__fadd_rn(hi, lo));
-                            }
-                            epi_chunk(a, tc, et, c, lane, v);
+                        for (int j = 0; j < 32; ++j) {
+                            float hi, lo;
+                            value(j, hi, lo);
+                            if (row_ok && j < jmax) o[(uint32_t)j * col_stride] = (double)hi + (double)lo;
                         }
+                    }
                     }
                 } else {
 #pragma unroll 1
@@ -1642,6 +1710,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if constexpr (FX == 1) {
                     acc_phase ^= 1u;   // released after the drain; one accumulator set
                 } else if constexpr (FX == 2) {
+                    acc_phase ^= 1u;   // released after the drain; one accumulator set
+                } else if constexpr (FX == 3) {
                     tc_fence_before();
                     mbar_arrive(TEMPTY(acc));
                     acc_phase ^= 1u;   // one accumulator set
@@ -1959,7 +2029,7 @@ __device__ __forceinline__ void store_fx(__half *dst, int64_t plane, int64_t i, 
     const float vh = F.hi * inv, vl = F.lo * inv;
     __half q[4];
     fx_split(vh, vl, q);
-    over = over || fabsf(vh) > kFxHeadMax;
+    over = over || fabsf(vh) > kFxRangeMax;
 #pragma unroll
     for (int k = 0; k < 4; ++k) dst[i + k * plane] = q[k];
 }
@@ -2312,27 +2382,34 @@ __global__ void k_split_matrix(int n, int ldp, const double *__restrict__ L, int
 // FX scale update for slots [first, first + count): E = ceil(log2 max) - 11
 // from the largest magnitude recorded since the last update (a slot that saw
 // only zeros keeps its exponent), then the record is cleared.
-__device__ __forceinline__ void fx_rescale_slot(FxScales *f, int k)
+// E = ceil(log2 max) - 11 from the largest magnitude recorded since the
+// last update, floored at kFxFloorBits below the slot's history (reset:
+// a calibrating step, which starts the history); a slot that saw only zeros
+// keeps its exponent.  The record is cleared.
+__device__ __forceinline__ void fx_rescale_slot(FxScales *f, int k, bool reset)
 {
     const float mx = __uint_as_float(f->maxbits[k]);
+    if (reset) f->ehist[k] = kFxNoHist;
     if (mx > 0.0f && mx <= 3.0e38f) {
-        const int E = ceil_log2f(mx) - 11;
+        int E = ceil_log2f(mx) - 11;
+        if (f->ehist[k] != kFxNoHist) E = max(E, f->ehist[k] - kFxFloorBits);
+        f->ehist[k] = max(f->ehist[k], E);
         f->scale[k] = ldexpf(1.0f, E);
         f->inv[k] = ldexpf(1.0f, -E);
     }
     f->maxbits[k] = 0u;
 }
-__global__ void k_fx_rescale(FxScales *f, int first, int count)
+__global__ void k_fx_rescale(FxScales *f, int first, int count, int reset)
 {
     const int k = first + (int)threadIdx.x;
     if ((int)threadIdx.x >= count || k >= kFxSlots) return;
-    fx_rescale_slot(f, k);
+    fx_rescale_slot(f, k, reset != 0);
 }
 // the same for slots [0, count) of every problem of a batch (block i: tab[i])
 __global__ void k_fx_rescale_group(FxScales *const *__restrict__ tab, int count)
 {
     if ((int)threadIdx.x >= count || (int)threadIdx.x >= kFxSlots) return;
-    fx_rescale_slot(tab[blockIdx.x], (int)threadIdx.x);
+    fx_rescale_slot(tab[blockIdx.x], (int)threadIdx.x, false);
 }
 
 // FX planes of phi-matrices, one block per output row i of stack s: the row
@@ -2849,11 +2926,16 @@ static void launch_tc_k(bool mode1, int bn, bool dual, int grid, cudaStream_t st
                     k_mode_tc<true, 128, false, GROUPED, false, 1><<<grid, kThreads, sm, st>>>(a, gtab, gprefix, ginst, gunits);
                 else
                     k_mode_tc<false, 128, false, GROUPED, false, 1><<<grid, kThreads, sm, st>>>(a, gtab, gprefix, ginst, gunits);
-            } else {
+            } else if (a.out_kind == 1) {
                 if (mode1)
                     k_mode_tc<true, 128, false, GROUPED, false, 2><<<grid, kThreads, sm, st>>>(a, gtab, gprefix, ginst, gunits);
                 else
                     k_mode_tc<false, 128, false, GROUPED, false, 2><<<grid, kThreads, sm, st>>>(a, gtab, gprefix, ginst, gunits);
+            } else if constexpr (!GROUPED) {
+                if (mode1)
+                    k_mode_tc<true, 128, false, false, false, 3><<<grid, kThreads, sm, st>>>(a, gtab, gprefix, ginst, gunits);
+                else
+                    k_mode_tc<false, 128, false, false, false, 3><<<grid, kThreads, sm, st>>>(a, gtab, gprefix, ginst, gunits);
             }
         }
         return;
@@ -2925,6 +3007,8 @@ static void set_smem_limits()
         cudaFuncSetAttribute(k_mode_tc<false, 128, false, false, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sfx);
         cudaFuncSetAttribute(k_mode_tc<true, 128, false, true, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sfx);
         cudaFuncSetAttribute(k_mode_tc<false, 128, false, true, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sfx);
+        cudaFuncSetAttribute(k_mode_tc<true, 128, false, false, false, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sfx);
+        cudaFuncSetAttribute(k_mode_tc<false, 128, false, false, false, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, sfx);
     });
 }
 
@@ -3390,8 +3474,7 @@ ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatu
             cudaGetLastError();
             return cleanup(DS_ERR_OOM, "FX tables");
         }
-        FxScales h{};
-        for (int q = 0; q < kFxSlots; ++q) h.scale[q] = h.inv[q] = 1.0f;
+        const FxScales h = fx_scales_init();
         cudaMemcpy(mp->fxs, &h, sizeof(h), cudaMemcpyHostToDevice);
         cudaMemset(mp->Fp, 0, sizeof(bf16) * 2 * npF * N);
         cudaMemset(mp->Z1, 0, sizeof(bf16) * 6 * npF * k * N);
@@ -3575,8 +3658,7 @@ ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatu
         if (cudaGetLastError() != cudaSuccess) return cleanup(DS_ERR_CUDA, "autotuning");
         if (fx) {
             // nothing the timing runs recorded survives into the first step
-            FxScales h{};
-            for (int q = 0; q < kFxSlots; ++q) h.scale[q] = h.inv[q] = 1.0f;
+            const FxScales h = fx_scales_init();
             cudaMemcpy(mp->fxs, &h, sizeof(h), cudaMemcpyHostToDevice);
         }
     }
@@ -4161,8 +4243,9 @@ int enqueue_step_mixed(MixedPlan *mp, const ds_phi_set *set, const Model &model,
         // measures each tensor (a launch that stores nothing), sets the slot
         // from that and then writes it.
         const int nslots = 2 + 6 * (d - 1);
-        auto rescale = [&](int first, int count) {
-            k_fx_rescale<<<1, 32, 0, st>>>(mp->fxs, first, count);
+        // reset: the calibrating step starts each slot's exponent history
+        auto rescale = [&](int first, int count, bool reset) {
+            k_fx_rescale<<<1, 32, 0, st>>>(mp->fxs, first, count, reset ? 1 : 0);
             ++L;
         };
         auto rhs = [&](bool measure) {
@@ -4181,15 +4264,15 @@ int enqueue_step_mixed(MixedPlan *mp, const ds_phi_set *set, const Model &model,
         };
         if (calibrate) {
             rhs(true);
-            rescale(0, 2);
+            rescale(0, 2, true);
             rhs(false);
             for (int mu = 0; mu < d - 1; ++mu) {
                 mode(mu, true);
-                rescale(2 + 6 * mu, 6);
+                rescale(2 + 6 * mu, 6, true);
                 mode(mu, false);
             }
         } else {
-            rescale(0, nslots);
+            rescale(0, nslots, false);
             rhs(false);
             for (int mu = 0; mu < d - 1; ++mu) mode(mu, false);
         }
@@ -4311,14 +4394,13 @@ ds_status tucker_fx(const ds_grid *grid, const double *X, double *Y, const doubl
     FxScales *fxs = (FxScales *)tail;
     FxMatJob *jobs = (FxMatJob *)(tail + ((sizeof(FxScales) + 255) & ~(size_t)255));
     float *pscale = (float *)((char *)jobs + 256);
-    FxScales h{};
-    for (int q = 0; q < kFxSlots; ++q) h.scale[q] = h.inv[q] = 1.0f;
+    const FxScales h = fx_scales_init();
     FxMatJob hj[kMaxD];
     for (int q = 0; q < d; ++q) hj[q] = {L[q], 1.0, transpose};
     DS_CUDA_TRY(cudaMemcpyAsync(fxs, &h, sizeof(h), cudaMemcpyHostToDevice, st));
     DS_CUDA_TRY(cudaMemcpyAsync(jobs, hj, sizeof(FxMatJob) * d, cudaMemcpyHostToDevice, st));
     k_absmax<<<pw_grid(N), 256, 0, st>>>(N, X, fxs, 0);
-    k_fx_rescale<<<1, 32, 0, st>>>(fxs, 0, 1);
+    k_fx_rescale<<<1, 32, 0, st>>>(fxs, 0, 1, 1);
     k_split_tensor_fx<<<pw_grid(N), 256, 0, st>>>(N, X, fxs, 0, A0);
     __half *pcur = Pp;
     float *pscur = pscale;
@@ -4344,7 +4426,7 @@ ds_status tucker_fx(const ds_grid *grid, const double *X, double *Y, const doubl
             ModeLaunch mm = ml;
             mm.args.fx_measure = 1;
             launch(mm, st);
-            k_fx_rescale<<<1, 32, 0, st>>>(fxs, mu + 1, 1);
+            k_fx_rescale<<<1, 32, 0, st>>>(fxs, mu + 1, 1, 1);
         }
         launch(ml, st);
         in = bufs[mu % 2];
