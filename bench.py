@@ -43,6 +43,9 @@ PREC_NOTE = {
     "f16x10": ("Tucker group on F: fixed-head FP16 four-part operands, 10 tensor-core products in four "
                "accumulators by weight class (exact head accumulation); groups on D2, D3: split BF16 "
                "(6 products); stencil and reaction in double-float; state FP64"),
+    "f16x10a": ("all three Tucker groups: fixed-head FP16 four-part operands, 10 tensor-core products in four "
+                "accumulators by weight class; increments kept as double-floats, stage differences and the final "
+                "update in double-float; stencil and reaction in double-float; state FP64"),
     "bf16x6": "split BF16 (3 parts, 6 tensor-core products, FP32 accumulation); state FP64",
     "bf16x6c": "split BF16 with the main product in its own accumulator; state FP64",
     "f32": "FP32 CUDA-core mode products; state FP64",
@@ -381,7 +384,7 @@ def run_batch(args, rank, world):
     peaks, peak_src = _peaks()
     # tensor instructions per useful product: 6 BF16 (split BF16); in f16x10
     # the F group (6 of 10 operators per component) takes 10 FP16 products
-    per_prod = {"bf16x6": 6.0, "bf16x6c": 6.0, "f16x10": 0.6 * 10.0 + 0.4 * 6.0}.get(args.precision)
+    per_prod = {"bf16x6": 6.0, "bf16x6c": 6.0, "f16x10": 0.6 * 10.0 + 0.4 * 6.0, "f16x10a": 10.0}.get(args.precision)
     tensor_tf = per_prod * useful * args.steps / t_local / 1e12 if per_prod else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -420,13 +423,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="fhn3d_256")
-    ap.add_argument("--precision", default="f16x10", choices=["f16x10", "bf16x6", "bf16x6c", "f32", "f64"])
+    ap.add_argument("--precision", default=None, choices=["f16x10", "f16x10a", "bf16x6", "bf16x6c", "f32", "f64"],
+                    help="default: f16x10 (f16x10a for batch64)")
     ap.add_argument("--err-steps", type=int, default=-1)
     ap.add_argument("--scheme", default="exprk3ds_real", choices=["exprk3ds_real", "etd2rkds"],
                     help="etd2rkds: the second-order split ETD2RK (FP64 plans)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.precision is None:
+        args.precision = "f16x10a" if args.workload == "batch64" else "f16x10"
 
     from paper_2310_07551_gb300 import configs
     if args.workload == "batch64":
@@ -571,7 +577,7 @@ def main():
         roof = {"bound": "alu", "achieved": achieved, "peak": None, "unit": "TFLOP/s", "frac": None,
                 "traffic": None, "kernel": "k_gemm<float> (FP32 CUDA-core mode product)",
                 "peak_source": "no measured FP32 peak"}
-    elif args.precision in ("bf16x6", "bf16x6c", "f16x10"):
+    elif args.precision in ("bf16x6", "bf16x6c", "f16x10", "f16x10a"):
         # The dominant kernel family: every k_mode_tc launch of the step.
         # Tensor-instruction flops: six BF16 products per FP32-class product
         # (split-BF16 launches), ten FP16 products (FX launches).  Their
@@ -639,7 +645,7 @@ def main():
                                      "fp64_gemm": f64_ms / kprof, "pointwise": pw_ms / kprof},
         "clocks": clk,
     }
-    if args.precision in ("bf16x6", "bf16x6c", "f16x10"):
+    if args.precision in ("bf16x6", "bf16x6c", "f16x10", "f16x10a"):
         line["autotuner"] = [{"group": ["F", "D2", "D3"][g], "mode": mu, "split_k": k or None, "stream_k": k == 0,
                               "tiles": t, "tile_n": tn, "tile_order": c.pop("order", 0), "candidates_ms": c}
                              for g, mu, k, t, tn, c in plan.tuning()]

@@ -163,6 +163,9 @@ ds_status check_grid(const ds_grid *g)
 }
 
 
+// the precisions with FX operands (scales calibrated per state)
+bool is_fx(int prec) { return prec == DS_PREC_F16X10 || prec == DS_PREC_F16X10A; }
+
 bool is_tridiagonal(const double *A, int64_t n)
 {
     for (int64_t j = 0; j < n; ++j)
@@ -734,7 +737,7 @@ ds_status ds_tucker(const ds_grid *grid, const double *X, double *Y, const doubl
     const int d = grid->d;
     if (precision == DS_PREC_BF16X6 || precision == DS_PREC_BF16X6C)
         return tc::tucker_mixed(grid, X, Y, L, transpose, st, precision == DS_PREC_BF16X6C);
-    if (precision == DS_PREC_F16X10) return tc::tucker_fx(grid, X, Y, L, transpose, st);
+    if (precision == DS_PREC_F16X10 || precision == DS_PREC_F16X10A) return tc::tucker_fx(grid, X, Y, L, transpose, st);
     if (precision == DS_PREC_F32) {
         int64_t pm = 0;
         for (int mu = 0; mu < d; ++mu) pm += grid->n[mu] * grid->n[mu];
@@ -795,7 +798,7 @@ ds_status ds_plan_create(const ds_grid *grid, const ds_params *params, const ds_
         for (int q = 0; q < 8; ++q)
             if (!isfinite(params->p[q])) return fail(DS_ERR_INVALID_ARG, "non-finite model parameter");
         if (precision != DS_PREC_F64 && precision != DS_PREC_BF16X6 && precision != DS_PREC_F32 &&
-            precision != DS_PREC_BF16X6C && precision != DS_PREC_F16X10)
+            precision != DS_PREC_BF16X6C && precision != DS_PREC_F16X10 && precision != DS_PREC_F16X10A)
             return fail(DS_ERR_UNSUPPORTED, "unknown precision");
         if (set->scheme != DS_EXPRK3DS_REAL && precision != DS_PREC_F64)
             return fail(DS_ERR_UNSUPPORTED, "ETD2RKDS, EXPRK3DS_CPLX and dense EXPRK3 plans are FP64 only");
@@ -843,7 +846,7 @@ ds_status ds_plan_create(const ds_grid *grid, const ds_params *params, const ds_
             tc::launch_convert_f64_f32(set->P_count, set->P_dev, p->P32, 0);
         } else {
             r = tc::mixed_plan_create(grid, set, p->status, &p->mixed, precision == DS_PREC_BF16X6C,
-                                      precision == DS_PREC_F16X10);
+                                      precision == DS_PREC_F16X10, precision == DS_PREC_F16X10A);
             if (r != DS_OK) { ds_plan_destroy(p); return r; }
         }
         cudaDeviceSynchronize();
@@ -859,7 +862,7 @@ ds_status ds_step(ds_plan *p, double *U, void *stream)
     if (!p || !U) return fail(DS_ERR_INVALID_ARG, "NULL argument");
     cudaStream_t st = (cudaStream_t)stream;
     // FX plans measure their tensors' scales on the first step of a state
-    const bool calib = p->prec == DS_PREC_F16X10 && p->fx_state != U;
+    const bool calib = is_fx(p->prec) && p->fx_state != U;
     p->launches = enqueue_step(p, U, st, p->profiling, calib);
     if (p->launches < 0) return fail(DS_ERR_CUDA, "step enqueue failed");
     p->fx_state = U;
@@ -893,7 +896,7 @@ ds_status ds_integrate(ds_plan *p, double *U, int64_t nsteps, void *stream)
         if (r != DS_OK) return r;
         it = p->graphs.emplace(U, ex).first;
     }
-    const bool calib = p->prec == DS_PREC_F16X10 && p->fx_state != U;
+    const bool calib = is_fx(p->prec) && p->fx_state != U;
     cudaGraphExec_t cex = nullptr;
     if (calib) {
         auto ic = p->calib_graphs.find(U);
@@ -1306,7 +1309,7 @@ ds_status ds_batch_integrate(ds_batch *b, double *const *U, int64_t nsteps, void
     // writing it; the grouped graphs then use the previous step's maxima
     bool calib = false;
     for (int i = 0; i < b->ninst; ++i)
-        calib = calib || (b->plans[i]->prec == DS_PREC_F16X10 && b->plans[i]->fx_state != U[i]);
+        calib = calib || (is_fx(b->plans[i]->prec) && b->plans[i]->fx_state != U[i]);
     if (calib) {
         DS_CUDA_TRY(cudaEventRecord(b->ev_in, user));
         DS_CUDA_TRY(cudaStreamWaitEvent(b->origin, b->ev_in, 0));
@@ -1416,8 +1419,9 @@ ds_status ds_plan_set_fusion(ds_plan *p, int group, int fused)
     if (!p) return fail(DS_ERR_INVALID_ARG, "NULL plan");
     if (!p->mixed) return fail(DS_ERR_UNSUPPORTED, "only split-BF16 plans fuse epilogues");
     if (p->st) cudaStreamSynchronize(p->st);
-    if (tc::mixed_plan_set_fusion(p->mixed, group, fused) != 0)
-        return fail(DS_ERR_INVALID_ARG, "group out of range");
+    const int rc = tc::mixed_plan_set_fusion(p->mixed, group, fused);
+    if (rc == -2) return fail(DS_ERR_UNSUPPORTED, "DS_PREC_F16X10A plans run the separate stage kernels only");
+    if (rc != 0) return fail(DS_ERR_INVALID_ARG, "group out of range");
     // captured steps hold the previous launch sequence
     for (auto &kv : p->graphs) cudaGraphExecDestroy(kv.second);
     p->graphs.clear();

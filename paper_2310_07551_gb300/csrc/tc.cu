@@ -192,6 +192,9 @@ struct alignas(128) TcArgs {
     // store nothing.  out_kind 2 (FX only): FP64 output.
     int fx_measure;
     int xsl_base, xsl_div, osl_base, osl_div;
+    // FX launches with FP32 output: the rounding residual of each element
+    // (value = out + out_lo to ~2^-48), same layout as out; null: not kept
+    float *out_lo;
     const float *pscale;
     FxScales *fxs;
     // cycles a pipeline wait spins before it gives up (the drains at exit
@@ -1502,9 +1505,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                                     const float lo = __fadd_rn(l[j], __fadd_rn(__uint_as_float(w0[j]),
                                                                                __uint_as_float(w1[j])));
                                     const float f = MODE1 ? frow : __shfl_sync(0xffffffffu, fcol, g * 16 + j);
-                                    const float val = __fadd_rn(h[j], lo) * f;
+                                    float sh, se;
+                                    two_sum_f(h[j], lo, sh, se);
+                                    const float val = sh * f;
                                     if (c == 0) vs[g * 16 + j] = val;
                                     else vss[(g * 16 + j) * kEpiThreads] = val;
+                                    // the residual, where the caller keeps it (coalesced:
+                                    // the lanes of a warp own consecutive rows)
+                                    if (a.out_lo && row_ok && g * 16 + j < jmax)
+                                        a.out_lo[rbase + (int64_t)(c * 32 + g * 16 + j) * col_stride] = se * f;
                                 }
                             }
                         }
@@ -2037,7 +2046,7 @@ __device__ __forceinline__ void store_fx(__half *dst, int64_t plane, int64_t i, 
 // FX: F in double-float, stored as FX planes (__half) with the scale of slot
 // c, and the largest |F_c| recorded for the next rescale.
 template <int TX, int TY, int TZ, typename Idx, bool GROUPED, bool FX = false>
-__global__ void __launch_bounds__(TX * TY) k_rhs_tiled(const __grid_constant__ RhsArgs a0,
+__global__ void __launch_bounds__(TX * TY, FX ? 3 : 1) k_rhs_tiled(const __grid_constant__ RhsArgs a0,
                                                        const RhsArgs *__restrict__ gtab,
                                                        const int *__restrict__ gprefix, int ginst)
 {
@@ -2311,6 +2320,152 @@ __global__ void k_final_mixed(int64_t N, double *__restrict__ U, const float *__
          p += (int64_t)gridDim.x * blockDim.x) {
         U[p] += widen_f(a[p] + b[p]);
         U[N + p] += widen_f(a[cs_a + p] + b[cs_b + p]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Stage kernels of FX-all plans (DS_PREC_F16X10A): the increments arrive as
+// double-floats (the FP32 increment plus its rounding residual), the stage
+// differences are formed in double-float and written as FX planes, and the
+// final update adds the double-float sum.
+// ---------------------------------------------------------------------------
+// g(u + du, v + dv) - g(u, v) as a polynomial in the increments (no
+// cancellation), in double-float:
+//   Schnakenberg: q = du (2u + du) = (u+du)^2 - u^2, w = q (v + dv) + u^2 dv,
+//                 Du = gamma (w - du), Dv = -gamma w;
+//   FitzHugh-Nagumo: c = du (3u (u + du) + du^2) = (u+du)^3 - u^3,
+//                 Du = du - dv - c, Dv = eps (du - alpha1 dv).
+__device__ __forceinline__ void react_diff_df(const ModelDF &m, dfl u, dfl v, dfl du, dfl dv, dfl &Du, dfl &Dv)
+{
+    if (m.model == DS_SCHNAKENBERG) {
+        const dfl q = df_mul(du, df_add(df_add(u, u), du));
+        const dfl w = df_add(df_mul(q, df_add(v, dv)), df_mul(df_mul(u, u), dv));
+        Du = df_mul(m.p[0], df_add(w, df_neg(du)));
+        Dv = df_neg(df_mul(m.p[0], w));
+    } else if (m.model == DS_FHN) {
+        const dfl t = df_add(df_mul(df_mul(dfl{3.0f, 0.0f}, u), df_add(u, du)), df_mul(du, du));
+        Du = df_add(df_add(du, df_neg(dv)), df_neg(df_mul(du, t)));
+        Dv = df_mul(m.p[0], df_add(du, df_neg(df_mul(m.p[1], dv))));
+    } else {
+        Du = {0.0f, 0.0f};
+        Dv = {0.0f, 0.0f};
+    }
+}
+
+// One point of a stage: D_c = g(U + a (+ b)) - g(U) from double-float
+// increments, as FX planes of slot `slot + c` (measure: only the maxima).
+struct StageFx {
+    int64_t N;
+    double *U;
+    const float *ah, *al;      // first increment [c] with component stride cs_a
+    int64_t cs_a;
+    const float *bh, *bl;      // second increment (null: none)
+    int64_t cs_b;
+    __half *Dp;                // [c][4][N]
+    FxScales *fxs;
+    int slot;
+    int measure;
+    ModelDF model;
+};
+__device__ __forceinline__ void stage_fx_point(const StageFx &a, int64_t p, float (&mx)[2], bool &over)
+{
+    const int64_t N = a.N;
+    float hu, lu, hv, lv;
+    split_hilo(a.U[p], hu, lu);
+    split_hilo(a.U[N + p], hv, lv);
+    dfl du{a.ah[p], a.al[p]}, dv{a.ah[a.cs_a + p], a.al[a.cs_a + p]};
+    if (a.bh) {
+        du = df_add(du, dfl{a.bh[p], a.bl[p]});
+        dv = df_add(dv, dfl{a.bh[a.cs_b + p], a.bl[a.cs_b + p]});
+    }
+    dfl Du, Dv;
+    react_diff_df(a.model, dfl{hu, lu}, dfl{hv, lv}, du, dv, Du, Dv);
+    mx[0] = fmaxf(mx[0], fabsf(Du.hi));
+    mx[1] = fmaxf(mx[1], fabsf(Dv.hi));
+    if (!a.measure) {
+        store_fx(a.Dp, N, p, Du, a.fxs->inv[a.slot], over);
+        store_fx(a.Dp + 4 * N, N, p, Dv, a.fxs->inv[a.slot + 1], over);
+    }
+}
+__device__ __forceinline__ void stage_fx_record(FxScales *fxs, int slot, const float (&mx)[2], bool over)
+{
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const unsigned mb = __reduce_max_sync(0xffffffffu, __float_as_uint(mx[c]));
+        if ((threadIdx.x & 31) == 0 && mb) atomicMax(&fxs->maxbits[slot + c], mb);
+    }
+    if (over) atomicExch(&fxs->overflow, 1);
+}
+__global__ void k_stage_fx(const __grid_constant__ StageFx a)
+{
+    float mx[2] = {0.0f, 0.0f};
+    bool over = false;
+    // every lane of a warp runs the same number of iterations (the shuffle
+    // reduction below needs the whole warp)
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p0 = blockIdx.x * (int64_t)blockDim.x; p0 < a.N; p0 += stride) {
+        const int64_t p = p0 + threadIdx.x;
+        if (p < a.N) stage_fx_point(a, p, mx, over);
+    }
+    stage_fx_record(a.fxs, a.slot, mx, over);
+}
+
+// U_c += a_c + b_c for double-float increments: summed in double-float,
+// then added in FP64 (hi, then lo)
+__device__ __forceinline__ void final_fx_point(int64_t N, double *U, const float *ah, const float *al, int64_t cs_a,
+                                               const float *bh, const float *bl, int64_t cs_b, int64_t p)
+{
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const dfl s = df_add(dfl{ah[c * cs_a + p], al[c * cs_a + p]}, dfl{bh[c * cs_b + p], bl[c * cs_b + p]});
+        U[c * N + p] = (U[c * N + p] + widen_f(s.hi)) + widen_f(s.lo);
+    }
+}
+__global__ void k_final_fx(int64_t N, double *__restrict__ U, const float *__restrict__ ah,
+                           const float *__restrict__ al, int64_t cs_a, const float *__restrict__ bh,
+                           const float *__restrict__ bl, int64_t cs_b)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x)
+        final_fx_point(N, U, ah, al, cs_a, bh, bl, cs_b, p);
+}
+
+// The same over every problem of a batch: block b belongs to problem i with
+// bprefix[i] <= b < bprefix[i + 1] and covers kStageFxBlock of its points,
+// so a warp's maxima are one problem's.
+constexpr int kStageFxBlock = 2048;
+__device__ __forceinline__ int group_of_block(const int *__restrict__ bprefix, int ninst)
+{
+    int lo = 0, hi = ninst - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (bprefix[mid] <= (int)blockIdx.x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+__global__ void k_stage_fx_group(const StageFx *__restrict__ tab, const int *__restrict__ bprefix, int ninst)
+{
+    const int i = group_of_block(bprefix, ninst);
+    const StageFx &a = tab[i];
+    const int64_t b0 = (int64_t)((int)blockIdx.x - bprefix[i]) * kStageFxBlock;
+    float mx[2] = {0.0f, 0.0f};
+    bool over = false;
+#pragma unroll 1
+    for (int k = 0; k < kStageFxBlock; k += 256) {
+        const int64_t p = b0 + k + threadIdx.x;
+        if (p < a.N) stage_fx_point(a, p, mx, over);
+    }
+    stage_fx_record(a.fxs, a.slot, mx, over);
+}
+__global__ void k_final_fx_group(const StageFx *__restrict__ tab, const int *__restrict__ bprefix, int ninst)
+{
+    const int i = group_of_block(bprefix, ninst);
+    const StageFx &a = tab[i];
+    const int64_t b0 = (int64_t)((int)blockIdx.x - bprefix[i]) * kStageFxBlock;
+#pragma unroll 1
+    for (int k = 0; k < kStageFxBlock; k += 256) {
+        const int64_t p = b0 + k + threadIdx.x;
+        if (p < a.N) final_fx_point(a.N, a.U, a.ah, a.al, a.cs_a, a.bh, a.bl, a.cs_b, p);
     }
 }
 
@@ -3252,9 +3407,19 @@ struct MixedPlan {
     // 2 + 6 (l - 1) + 3 c + stage.
     bool fx = false;
     FxScales *fxs = nullptr;
-    float *pscale = nullptr;            // row scales of the F group's phi planes, per mode
-    int64_t pscale_off[kMaxD] = {};
+    float *pscale = nullptr;            // row scales of the FX groups' phi planes, per group and mode
+    int64_t pscale_off[3][kMaxD] = {};
     FxMatJob *fx_jobs = nullptr;
+    // FX-all plans (DS_PREC_F16X10A): the groups on D2 and D3 in FX operands
+    // too, D planes [c][4][N] FX, and the increments as double-floats (the
+    // FP32 values plus their rounding residuals incFlo [c][stage][N], incDlo
+    // [c][N]); the stage differences and the final update run in the
+    // separate double-float stage kernels.  Scale slots of the D groups:
+    // their inputs D_c at fx_base(g) + c, their level-mu intermediates at
+    // fx_base(g) + 2 + 2 (mu - 1) + c.
+    bool fx_all = false;
+    float *incFlo = nullptr, *incDlo = nullptr;
+    int fx_nslots = 0;
 };
 
 // the separate stage kernel of group g (D2, D3 planes or the final update)
@@ -3324,9 +3489,18 @@ static void decide_fusion(MixedPlan *mp, cudaStream_t st, double *Us)
     cudaEventDestroy(e1);
 }
 
-ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatus *status, MixedPlan **out,
-                            bool compensated, bool fx)
+// First scale slot of group g's FX tensors: F group 0 (F_c, then six sets
+// per level), D2 group after it, D3 group after that (two per level each).
+static int fx_base(int g, int d)
 {
+    const int b1 = 2 + 6 * (d - 1), b2 = b1 + 2 + 2 * (d - 1);
+    return g == 0 ? 0 : g == 1 ? b1 : b2;
+}
+
+ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatus *status, MixedPlan **out,
+                            bool compensated, bool fx, bool fx_all)
+{
+    fx = fx || fx_all;
     ds_status r = check_shape(set->d, set->n);
     if (r != DS_OK) return r;
     if (!encode_fn()) return fail(DS_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled unavailable");
@@ -3334,12 +3508,13 @@ ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatu
         int64_t Nq = 1;
         for (int q = 0; q < set->d; ++q) Nq *= set->n[q];
         if (set->d > 3 || Nq >= ((int64_t)1 << 31))
-            return fail(DS_ERR_UNSUPPORTED, "DS_PREC_F16X10 plans need d = 2 or 3 and fewer than 2^31 grid points");
+            return fail(DS_ERR_UNSUPPORTED, "DS_PREC_F16X10 / F16X10A plans need d = 2 or 3 and fewer than 2^31 grid points");
     }
     MixedPlan *mp = new MixedPlan();
     memset(mp->tune_ms, 0, sizeof(mp->tune_ms));
     mp->compensated = compensated;
     mp->fx = fx;
+    mp->fx_all = fx_all;
     mp->d = set->d;
     mp->k = set->k;
     mp->N = 1;
@@ -3435,13 +3610,15 @@ ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatu
     //   group D2 (slot 2), D3 (slot 4): k combos; last mode carries w eta^{(2)}
     int64_t total = 0;
     int64_t goff[3][kMaxD];
-    // FX plans hold the F group's planes (phi, F, Z1, Z2) as 4 FP16 parts
+    // FX plans hold the F group's planes (phi, F, Z1, Z2) as 4 FP16 parts;
+    // FX-all plans the D groups' too
     const int npF = fx ? 4 : 3;
+    auto fxg = [&](int g) { return fx && (g == 0 || fx_all); };
     for (int g = 0; g < 3; ++g)
         for (int mu = 0; mu < d; ++mu) {
             goff[g][mu] = total;
             const int combos = g == 0 ? 3 * k : k;
-            total += (int64_t)2 * combos * (g == 0 ? npF : 3) * mp->n[mu] * round8(mp->n[mu]);
+            total += (int64_t)2 * combos * (fxg(g) ? 4 : 3) * mp->n[mu] * round8(mp->n[mu]);
         }
     auto cleanup = [&](ds_status s, const char *msg) {
         mixed_plan_destroy(mp);
@@ -3449,25 +3626,29 @@ ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatu
     };
     if (cudaMalloc(&mp->Pp, sizeof(bf16) * total) != cudaSuccess ||
         cudaMalloc(&mp->Fp, sizeof(bf16) * 2 * npF * N) != cudaSuccess ||
-        cudaMalloc(&mp->Dp, sizeof(bf16) * 6 * N) != cudaSuccess ||
+        cudaMalloc(&mp->Dp, sizeof(bf16) * (fx_all ? 8 : 6) * N) != cudaSuccess ||
         cudaMalloc(&mp->Z1, sizeof(bf16) * 6 * npF * k * N) != cudaSuccess ||
         (d >= 3 && cudaMalloc(&mp->Z2, sizeof(bf16) * 6 * npF * k * N) != cudaSuccess) ||
         cudaMalloc(&mp->incF, sizeof(float) * 6 * N) != cudaSuccess ||
-        cudaMalloc(&mp->incD, sizeof(float) * 2 * N) != cudaSuccess) {
+        cudaMalloc(&mp->incD, sizeof(float) * 2 * N) != cudaSuccess ||
+        (fx_all && (cudaMalloc(&mp->incFlo, sizeof(float) * 6 * N) != cudaSuccess ||
+                    cudaMalloc(&mp->incDlo, sizeof(float) * 2 * N) != cudaSuccess))) {
         cudaGetLastError();
         return cleanup(DS_ERR_OOM, "split-BF16 workspace");
     }
     const double tau = set->tau;
     if (fx) {
-        if (!mp->rhs_tiled) return cleanup(DS_ERR_UNSUPPORTED, "DS_PREC_F16X10: grid too large for the tiled stencil");
+        if (!mp->rhs_tiled) return cleanup(DS_ERR_UNSUPPORTED, "DS_PREC_F16X10 / F16X10A: grid too large for the tiled stencil");
         // scale table (every scale 1 until the first calibration), row scales
         // of the F group's planes, and intermediates cleared so that timing
         // at creation multiplies zeros
         int64_t ps_tot = 0;
-        for (int mu = 0; mu < d; ++mu) {
-            mp->pscale_off[mu] = ps_tot;
-            ps_tot += (int64_t)2 * 3 * k * mp->n[mu];
-        }
+        for (int g = 0; g < 3; ++g)
+            for (int mu = 0; mu < d && fxg(g); ++mu) {
+                mp->pscale_off[g][mu] = ps_tot;
+                ps_tot += (int64_t)2 * (g == 0 ? 3 * k : k) * mp->n[mu];
+            }
+        mp->fx_nslots = fx_all ? fx_base(2, d) + 2 + 2 * (d - 1) : 2 + 6 * (d - 1);
         if (cudaMalloc(&mp->fxs, sizeof(FxScales)) != cudaSuccess ||
             cudaMalloc(&mp->pscale, sizeof(float) * ps_tot) != cudaSuccess ||
             cudaMalloc(&mp->fx_jobs, sizeof(FxMatJob) * 2 * 3 * k) != cudaSuccess) {
@@ -3477,28 +3658,29 @@ ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatu
         const FxScales h = fx_scales_init();
         cudaMemcpy(mp->fxs, &h, sizeof(h), cudaMemcpyHostToDevice);
         cudaMemset(mp->Fp, 0, sizeof(bf16) * 2 * npF * N);
+        if (fx_all) cudaMemset(mp->Dp, 0, sizeof(bf16) * 8 * N);
         cudaMemset(mp->Z1, 0, sizeof(bf16) * 6 * npF * k * N);
         if (mp->Z2) cudaMemset(mp->Z2, 0, sizeof(bf16) * 6 * npF * k * N);
     }
     for (int g = 0; g < 3; ++g)
         for (int mu = 0; mu < d; ++mu) {
-            if (fx && g == 0) {
-                // FX planes of the F group: per stack s one row scale over its T terms
+            if (fxg(g)) {
+                // FX planes of the group: per stack s one row scale over its T terms
                 const int64_t nm = mp->n[mu];
                 const int ldp = round8(nm);
                 const bool last = (mu == d - 1);
-                const int combos = 3 * k, T = last ? k : 1;
+                const int combos = g == 0 ? 3 * k : k, T = last ? k : 1;
                 std::vector<FxMatJob> jobs(2 * combos);
                 for (int c = 0; c < 2; ++c)
                     for (int cb = 0; cb < combos; ++cb) {
-                        const int slot = Fslots[cb / k], i = cb % k;
+                        const int slot = g == 0 ? Fslots[cb / k] : (g == 1 ? 2 : 4), i = cb % k;
                         const SplitCoeffs &co = set->co[kSlotEll[slot] - 1];
                         jobs[c * combos + cb] = {set->P_dev + set->P_off[c][slot][i][mu],
                                                  last ? kSlotW[slot] * tau * co.eta[i] : 1.0, 0};
                     }
                 cudaMemcpy(mp->fx_jobs, jobs.data(), sizeof(FxMatJob) * jobs.size(), cudaMemcpyHostToDevice);
                 k_split_matrix_fx<<<dim3((unsigned)nm, (unsigned)(2 * combos / T)), 256>>>(
-                    (int)nm, ldp, T, mp->fx_jobs, (__half *)(mp->Pp + goff[g][mu]), mp->pscale + mp->pscale_off[mu]);
+                    (int)nm, ldp, T, mp->fx_jobs, (__half *)(mp->Pp + goff[g][mu]), mp->pscale + mp->pscale_off[g][mu]);
                 cudaDeviceSynchronize();   // the job table is reused for the next mode
                 continue;
             }
@@ -3548,16 +3730,19 @@ ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatu
                 ModeLaunch &Cw = mp->C[g][mu][w];
                 // compensated plans have one candidate: 128-column tiles, two accumulators
                 r = describe(Cw, d, mp->n, mu, X, xcombos, P, 2 * S0, ldp, S, T, xs, xdiv, out, kind, 1.0f,
-                             status, (w || compensated) ? 128 : 256, compensated, fx && g == 0);
+                             status, (w || compensated) ? 128 : 256, compensated, fxg(g));
                 if (r != DS_OK) { mixed_plan_destroy(mp); return r; }
-                if (fx && g == 0) {
-                    // scale slots: input F_c (mode 1) or level-mu sets, output level mu + 1
+                if (fxg(g)) {
+                    // scale slots: input (F_c or D_c for mode 1, the level-mu sets
+                    // after), output level mu + 1.  F group: six sets (c, stage) per
+                    // level; D groups: two (c) per level, after the group's inputs.
                     TcArgs &a = Cw.args;
+                    const int base = fx_base(g, d), per = g == 0 ? 6 : 2;
                     a.fxs = mp->fxs;
-                    a.pscale = mp->pscale + mp->pscale_off[mu];
-                    a.xsl_base = mu == 0 ? 0 : 2 + 6 * (mu - 1);
+                    a.pscale = mp->pscale + mp->pscale_off[g][mu];
+                    a.xsl_base = mu == 0 ? base : base + 2 + per * (mu - 1);
                     a.xsl_div = mu == 0 ? S0 : (last ? 1 : k);
-                    a.osl_base = 2 + 6 * mu;
+                    a.osl_base = base + 2 + per * mu;
                     a.osl_div = k;
                 }
                 // the last mode's epilogue does the pointwise work of the stage:
@@ -3566,6 +3751,8 @@ ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatu
                 //   D3: U += tau S_f(F) + 3tau/2 S_f(D3)
                 if (last) {
                     mp->Csep[g][w] = Cw;
+                    // FX-all: the separate last mode keeps the increments' residuals
+                    if (fx_all) mp->Csep[g][w].args.out_lo = g == 0 ? mp->incFlo : mp->incDlo;
                     if (g == 0) set_fused(Cw, 1, nullptr, 0, mp->Dp);
                     else if (g == 1) set_fused(Cw, 1, mp->incF + N, 3 * N, mp->Dp);
                     else set_fused(Cw, 2, mp->incF + 2 * N, 3 * N, nullptr);
@@ -3620,7 +3807,7 @@ ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatu
         cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking);
         for (int g = 0; g < 3; ++g) {
             for (int mu = 0; mu < d; ++mu) {
-                if (fx && g == 0) {
+                if (fxg(g)) {
                     // FX launches: 128-column tiles, no K split (the partials would
                     // need double-float storage), the first tile order
                     mp->L[g][mu] = mp->C[g][mu][0];
@@ -3651,7 +3838,13 @@ ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatu
                 }
             }
         }
-        decide_fusion(mp, ts, Us);
+        if (fx_all) {
+            // FX-all plans: every group's last mode is the plain product followed
+            // by the double-float stage kernels
+            for (int g = 0; g < 3; ++g) mp->fused[g] = false;
+        } else {
+            decide_fusion(mp, ts, Us);
+        }
         cudaStreamSynchronize(ts);
         cudaStreamDestroy(ts);
         cudaFree(Us);
@@ -3724,6 +3917,7 @@ int mixed_plan_set_tiles(MixedPlan *mp, int g, int mu, int tile_n, int ksplit)
 int mixed_plan_set_fusion(MixedPlan *mp, int g, int fused)
 {
     if (!mp || g < 0 || g > 2) return -1;
+    if (mp->fx_all && fused) return -2;   // FX-all: double-float stage kernels only
     mp->fused[g] = fused != 0;
     return 0;
 }
@@ -3790,6 +3984,8 @@ void mixed_plan_destroy(MixedPlan *mp)
     cudaFree(mp->fxs);
     cudaFree(mp->pscale);
     cudaFree(mp->fx_jobs);
+    cudaFree(mp->incFlo);
+    cudaFree(mp->incDlo);
     delete mp;
 }
 
@@ -3876,6 +4072,12 @@ struct MixedGroup {
         int grid_sep = 0;
         TcArgs a0_sep;
         StageArgs *stab = nullptr; // device [ninst]
+        // FX-all batches: the double-float stage kernel of the group (kind 0:
+        // D2, 1: D3, 2: final update) over every problem, kStageFxBlock
+        // points per block
+        StageFx *ftab = nullptr;   // device [ninst]
+        int *fbprefix = nullptr;   // device [ninst], first block of each problem
+        int fblocks = 0;
         int64_t *sprefix = nullptr;
         int64_t points = 0;
         float ms[2] = {};          // {fused, separate} at creation (0 = replayed)
@@ -3901,6 +4103,8 @@ void mixed_group_destroy(MixedGroup *G)
         cudaFree(sl.prefix_sep);
         cudaFree(sl.stab);
         cudaFree(sl.sprefix);
+        cudaFree(sl.ftab);
+        cudaFree(sl.fbprefix);
     }
     cudaFree(G->rtab);
     cudaFree(G->rprefix);
@@ -3915,8 +4119,14 @@ static void launch_group_slot(const MixedGroup::Slot &sl, bool sep, cudaStream_t
                         sl.units_sep, sl.fx);
     else
         launch_tc<true>(sl.mode1, sl.bn, sl.dual, sl.grid, st, sl.a0, sl.tab, sl.prefix, sl.ninst, sl.units, sl.fx);
-    if (sep)
+    if (sep && sl.ftab) {
+        if (sl.kind == 2)
+            k_final_fx_group<<<sl.fblocks, 256, 0, st>>>(sl.ftab, sl.fbprefix, sl.ninst);
+        else
+            k_stage_fx_group<<<sl.fblocks, 256, 0, st>>>(sl.ftab, sl.fbprefix, sl.ninst);
+    } else if (sep) {
         k_stage_group<<<pw_grid(sl.points), 256, 0, st>>>(sl.stab, sl.sprefix, sl.ninst, sl.points, sl.kind);
+    }
 }
 
 ds_status mixed_group_create(const std::vector<MixedPlan *> &mps, const std::vector<double *> &U,
@@ -3927,13 +4137,15 @@ ds_status mixed_group_create(const std::vector<MixedPlan *> &mps, const std::vec
         return fail(DS_ERR_INVALID_ARG, "grouped launch: inconsistent problem lists");
     const int d = mps[0]->d;
     for (auto *mp : mps)
-        if (mp->d != d || mp->compensated != mps[0]->compensated || mp->fx != mps[0]->fx)
+        if (mp->d != d || mp->compensated != mps[0]->compensated || mp->fx != mps[0]->fx ||
+            mp->fx_all != mps[0]->fx_all)
             return fail(DS_ERR_UNSUPPORTED, "grouped launch: problems differ in dimension or precision");
     MixedGroup *G = new MixedGroup();
     G->d = d;
     G->fx = mps[0]->fx;
     G->ninst = ninst;
-    G->nslots = 2 + 6 * (d - 1);
+    G->nslots = mps[0]->fx ? mps[0]->fx_nslots : 0;
+    const bool fx_all = mps[0]->fx_all;
     // FX: the timing runs below write scale records; each problem's table is
     // put back as it was afterwards
     std::vector<FxScales> fx_saved(G->fx ? ninst : 0);
@@ -4068,7 +4280,40 @@ ds_status mixed_group_create(const std::vector<MixedPlan *> &mps, const std::vec
                 for (auto &t : tab) t.order = sl.order;
                 sl.a0.order = sl.order;
             }
-            if (last && units > 0) {
+            if (last && fx_all) {
+                // FX-all: the plain last mode, then the group's double-float stage
+                // kernel over every problem (no fused form, nothing to time)
+                std::vector<StageFx> ft(ninst);
+                std::vector<int> fb(ninst);
+                int blocks = 0;
+                for (int i = 0; i < ninst; ++i) {
+                    const MixedPlan *mp = mps[i];
+                    const int64_t Ni = mp->N;
+                    StageFx &a = ft[i];
+                    a = StageFx{};
+                    a.N = Ni;
+                    a.U = U[i];
+                    a.ah = mp->incF + (int64_t)g * Ni;
+                    a.al = mp->incFlo + (int64_t)g * Ni;
+                    a.cs_a = 3 * Ni;
+                    a.bh = g == 0 ? nullptr : mp->incD;
+                    a.bl = g == 0 ? nullptr : mp->incDlo;
+                    a.cs_b = Ni;
+                    a.Dp = (__half *)mp->Dp;
+                    a.fxs = mp->fxs;
+                    a.slot = g < 2 ? fx_base(g + 1, d) : 0;
+                    a.measure = 0;
+                    a.model = model_df(models[i]);
+                    fb[i] = blocks;
+                    blocks += (int)((Ni + kStageFxBlock - 1) / kStageFxBlock);
+                }
+                if (!dev_copy(&sl.ftab, ft) || !dev_copy(&sl.fbprefix, fb)) {
+                    r = fail(DS_ERR_OOM, "grouped FX stage tables");
+                    break;
+                }
+                sl.fblocks = blocks;
+                sl.sep = true;
+            } else if (last && units > 0) {
                 const ShapeKey key{false, ninst, g, d, Ntot, units, 20 + (sl.dual ? 32 : 0)};
                 int cached = 0;
                 {
@@ -4238,11 +4483,10 @@ int enqueue_step_mixed(MixedPlan *mp, const ds_phi_set *set, const Model &model,
         }
     };
     if (mp->fx) {
-        // FX F group.  Each producer of an FX tensor writes it with its slot's
+        // FX groups.  Each producer of an FX tensor writes it with its slot's
         // exponent from the previous step's maxima; a calibrating step first
         // measures each tensor (a launch that stores nothing), sets the slot
         // from that and then writes it.
-        const int nslots = 2 + 6 * (d - 1);
         // reset: the calibrating step starts each slot's exponent history
         auto rescale = [&](int first, int count, bool reset) {
             k_fx_rescale<<<1, 32, 0, st>>>(mp->fxs, first, count, reset ? 1 : 0);
@@ -4254,43 +4498,96 @@ int enqueue_step_mixed(MixedPlan *mp, const ds_phi_set *set, const Model &model,
             P.end(st);
             ++L;
         };
-        auto mode = [&](int mu, bool measure) {
-            ModeLaunch ML = mp->L[0][mu];
+        auto mode = [&](int g, int mu, bool measure) {
+            ModeLaunch ML = mp->L[g][mu];
             ML.args.fx_measure = measure ? 1 : 0;
             P.begin(st, 3, launch_flops(ML, N), ML.alg_bytes);
             launch(ML, st, U, &mf);
             P.end(st);
             ++L;
         };
+        // an FX group's modes before the last (calibrating: measure, set, write)
+        auto fx_modes = [&](int g) {
+            const int base = fx_base(g, d), per = g == 0 ? 6 : 2;
+            for (int mu = 0; mu < d - 1; ++mu) {
+                if (calibrate) {
+                    mode(g, mu, true);
+                    rescale(base + 2 + per * mu, per, true);
+                }
+                mode(g, mu, false);
+            }
+        };
         if (calibrate) {
             rhs(true);
             rescale(0, 2, true);
-            rhs(false);
-            for (int mu = 0; mu < d - 1; ++mu) {
-                mode(mu, true);
-                rescale(2 + 6 * mu, 6, true);
-                mode(mu, false);
-            }
         } else {
-            rescale(0, nslots, false);
-            rhs(false);
-            for (int mu = 0; mu < d - 1; ++mu) mode(mu, false);
+            rescale(0, mp->fx_nslots, false);
         }
-        // the last mode of the F group (fused or separate epilogue)
-        const bool sep = !mp->fused[0];
-        const ModeLaunch &ML = sep ? mp->Lsep[0] : mp->L[0][d - 1];
-        P.begin(st, 3, launch_flops(ML, N), ML.alg_bytes);
-        launch(ML, st, U, &mf);
-        P.end(st);
-        ++L;
-        if (sep) {
-            P.begin(st, 2, 0.0, (double)N * 36.0);
-            launch_stage_kernel(mp, 0, mf, U, st);
+        rhs(false);
+        fx_modes(0);
+        // the last mode of the F group (fused or separate epilogue; FX-all:
+        // always separate)
+        const bool sep = mp->fx_all || !mp->fused[0];
+        {
+            const ModeLaunch &ML = sep ? mp->Lsep[0] : mp->L[0][d - 1];
+            P.begin(st, 3, launch_flops(ML, N), ML.alg_bytes);
+            launch(ML, st, U, &mf);
             P.end(st);
             ++L;
         }
-        group(1);
-        group(2);
+        if (!mp->fx_all) {
+            if (sep) {
+                P.begin(st, 2, 0.0, (double)N * 36.0);
+                launch_stage_kernel(mp, 0, mf, U, st);
+                P.end(st);
+                ++L;
+            }
+            group(1);
+            group(2);
+            return L;
+        }
+        // FX-all: double-float stage kernels and FX groups on D2, D3
+        const ModelDF mdf = model_df(model);
+        auto stage = [&](int g, bool measure) {
+            // g = 1: D2 = g(U + inc_0) - g(U); g = 2: D3 = g(U + inc_1 + incD) - g(U)
+            StageFx sa{};
+            sa.N = N;
+            sa.U = U;
+            sa.ah = mp->incF + (g == 1 ? 0 : N);
+            sa.al = mp->incFlo + (g == 1 ? 0 : N);
+            sa.cs_a = 3 * N;
+            sa.bh = g == 1 ? nullptr : mp->incD;
+            sa.bl = g == 1 ? nullptr : mp->incDlo;
+            sa.cs_b = N;
+            sa.Dp = (__half *)mp->Dp;
+            sa.fxs = mp->fxs;
+            sa.slot = fx_base(g, d);
+            sa.measure = measure ? 1 : 0;
+            sa.model = mdf;
+            P.begin(st, 2, 0.0, (double)N * (g == 1 ? 48.0 : 64.0));
+            k_stage_fx<<<pw_grid(N), 256, 0, st>>>(sa);
+            P.end(st);
+            ++L;
+        };
+        for (int g = 1; g < 3; ++g) {
+            if (calibrate) {
+                stage(g, true);
+                rescale(fx_base(g, d), 2, true);
+            }
+            stage(g, false);
+            fx_modes(g);
+            const ModeLaunch &ML = mp->Lsep[g];
+            P.begin(st, 3, launch_flops(ML, N), ML.alg_bytes);
+            launch(ML, st, U, &mf);
+            P.end(st);
+            ++L;
+        }
+        // U += tau S_f(F) + 3tau/2 S_f(D3), both as double-floats
+        P.begin(st, 2, 0.0, (double)N * 64.0);
+        k_final_fx<<<pw_grid(N), 256, 0, st>>>(N, U, mp->incF + 2 * N, mp->incFlo + 2 * N, 3 * N, mp->incD,
+                                               mp->incDlo, N);
+        P.end(st);
+        ++L;
         return L;
     }
     // F = K U + g(U) as BF16 planes: FP64 state 16 B/point in, 2 x 6 B planes out
