@@ -43,7 +43,7 @@ PREC_NOTE = {
     "f16x10": ("Tucker group on F: fixed-head FP16 four-part operands, 10 tensor-core products in four "
                "accumulators by weight class (exact head accumulation); groups on D2, D3: split BF16 "
                "(6 products); stencil and reaction in double-float; state FP64"),
-    "f16x10a": ("all three Tucker groups: fixed-head FP16 four-part operands, 10 tensor-core products in four "
+    "f16x13": ("all three Tucker groups: fixed-head FP16 four-part operands, 13 tensor-core products in four "
                 "accumulators by weight class; increments kept as double-floats, stage differences and the final "
                 "update in double-float; stencil and reaction in double-float; state FP64"),
     "bf16x6": "split BF16 (3 parts, 6 tensor-core products, FP32 accumulation); state FP64",
@@ -57,6 +57,10 @@ PREC_NOTE = {
 # dram__bytes_write.sum), keyed by "<hash of the kernel source>:<workload>";
 # a changed kernel reports null.
 NCU_TRAFFIC = {
+    # FitzHugh-Nagumo, DS_PREC_F16X10: mean over one step's nine k_mode_tc
+    # launches, captured on the (256, 256, 128) half-size case (867 MB per
+    # launch; every tensor term scales with the points) and doubled
+    "6bba85c39f38dc24:fhn3d_256:f16x10": 1.735e9,
 }
 
 
@@ -384,7 +388,7 @@ def run_batch(args, rank, world):
     peaks, peak_src = _peaks()
     # tensor instructions per useful product: 6 BF16 (split BF16); in f16x10
     # the F group (6 of 10 operators per component) takes 10 FP16 products
-    per_prod = {"bf16x6": 6.0, "bf16x6c": 6.0, "f16x10": 0.6 * 10.0 + 0.4 * 6.0, "f16x10a": 10.0}.get(args.precision)
+    per_prod = {"bf16x6": 6.0, "bf16x6c": 6.0, "f16x10": 0.6 * 10.0 + 0.4 * 6.0, "f16x13": 13.0}.get(args.precision)
     tensor_tf = per_prod * useful * args.steps / t_local / 1e12 if per_prod else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -423,8 +427,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="fhn3d_256")
-    ap.add_argument("--precision", default=None, choices=["f16x10", "f16x10a", "bf16x6", "bf16x6c", "f32", "f64"],
-                    help="default: f16x10 (f16x10a for batch64)")
+    ap.add_argument("--precision", default=None, choices=["f16x10", "f16x13", "bf16x6", "bf16x6c", "f32", "f64"],
+                    help="default: f16x10 (f16x13 for batch64)")
     ap.add_argument("--err-steps", type=int, default=-1)
     ap.add_argument("--scheme", default="exprk3ds_real", choices=["exprk3ds_real", "etd2rkds"],
                     help="etd2rkds: the second-order split ETD2RK (FP64 plans)")
@@ -432,7 +436,7 @@ def main():
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.precision is None:
-        args.precision = "f16x10a" if args.workload == "batch64" else "f16x10"
+        args.precision = "f16x13" if args.workload == "batch64" else "f16x10"
 
     from paper_2310_07551_gb300 import configs
     if args.workload == "batch64":
@@ -577,13 +581,14 @@ def main():
         roof = {"bound": "alu", "achieved": achieved, "peak": None, "unit": "TFLOP/s", "frac": None,
                 "traffic": None, "kernel": "k_gemm<float> (FP32 CUDA-core mode product)",
                 "peak_source": "no measured FP32 peak"}
-    elif args.precision in ("bf16x6", "bf16x6c", "f16x10", "f16x10a"):
+    elif args.precision in ("bf16x6", "bf16x6c", "f16x10", "f16x13"):
         # The dominant kernel family: every k_mode_tc launch of the step.
         # Tensor-instruction flops: six BF16 products per FP32-class product
-        # (split-BF16 launches), ten FP16 products (FX launches).  Their
+        # (split-BF16 launches), ten FP16 products (FX launches; 13 in f16x13).  Their
         # time is their share of the per-launch event profile times the
         # graph-timed step, so it never exceeds ms_per_step.
-        tflops_step = (6.0 * tc_fl + 10.0 * fx_fl) / kprof
+        fx_prods = 13.0 if args.precision == "f16x13" else 10.0
+        tflops_step = (6.0 * tc_fl + fx_prods * fx_fl) / kprof
         share = (tc_ms + fx_ms) / prof_ms if prof_ms > 0 else None
         k_ms = share * step_ms if share else None
         achieved = tflops_step / (k_ms / 1e3) / 1e12 if k_ms else None
@@ -592,8 +597,9 @@ def main():
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak if achieved else None,
                 "traffic": NCU_TRAFFIC.get(key),
-                "traffic_source": ("ncu capture of this kernel source on this workload (mean DRAM read + write "
-                                   "per k_mode_tc launch)" if key in NCU_TRAFFIC else
+                "traffic_source": ("ncu capture of this kernel source (mean DRAM read + write per k_mode_tc "
+                                   "launch of one step, on the half-size case, scaled to the full grid)"
+                                   if key in NCU_TRAFFIC else
                                    "null: no ncu capture of this kernel source on this workload"),
                 "alg_bytes_per_launch": (tc_by + fx_by) / (tc_n + fx_n) if tc_n + fx_n else None,
                 "launches_per_step": (tc_n + fx_n) // kprof,
@@ -606,7 +612,7 @@ def main():
                 "peak_source": f"{peak_src} bf16_tflops_sustained (FP16 and BF16 share the dense rate)",
                 "useful_fp32_class_tflops": (tc_fl + fx_fl) / kprof / (k_ms / 1e3) / 1e12 if k_ms else None,
                 "fx_launches": {"launches_per_step": fx_n // kprof,
-                                "tensor_tflops": 10.0 * fx_fl / (fx_ms / 1e3) / 1e12,
+                                "tensor_tflops": fx_prods * fx_fl / (fx_ms / 1e3) / 1e12,
                                 "event_ms_per_step": fx_ms / kprof} if fx_n else None,
                 "bf16_launches": {"launches_per_step": tc_n // kprof,
                                   "tensor_tflops": 6.0 * tc_fl / (tc_ms / 1e3) / 1e12,
@@ -645,7 +651,7 @@ def main():
                                      "fp64_gemm": f64_ms / kprof, "pointwise": pw_ms / kprof},
         "clocks": clk,
     }
-    if args.precision in ("bf16x6", "bf16x6c", "f16x10", "f16x10a"):
+    if args.precision in ("bf16x6", "bf16x6c", "f16x10", "f16x13"):
         line["autotuner"] = [{"group": ["F", "D2", "D3"][g], "mode": mu, "split_k": k or None, "stream_k": k == 0,
                               "tiles": t, "tile_n": tn, "tile_order": c.pop("order", 0), "candidates_ms": c}
                              for g, mu, k, t, tn, c in plan.tuning()]

@@ -97,21 +97,24 @@ typedef enum {
  *                    a value beyond the FP16 range of its parts makes
  *                    ds_plan_sync report DS_ERR_NONFINITE.  d = 2 or 3,
  *                    fewer than 2^31 points.
- *   DS_PREC_F16X10A: DS_PREC_F16X10 for all three Tucker groups (F, D2, D3),
- *                    with every stage increment kept as a double-float (the
- *                    FP32 value plus its rounding residual) and the stage
- *                    differences g(U_s) - g(U) and the final update formed in
- *                    double-float (separate stage kernels; the D planes are
- *                    FX tensors with their own exponents).  For problems
- *                    whose dynamics amplify every rounding (Turing growth),
- *                    where the FP32-class parts of DS_PREC_F16X10 dominate. */
+ *   DS_PREC_F16X13 : the FX operands of DS_PREC_F16X10 for all three Tucker
+ *                    groups (F, D2, D3), with thirteen partial products (the
+ *                    ten above plus s1 s3', s3 s1' and s2 s2' in the fourth
+ *                    accumulator), every stage increment kept as a
+ *                    double-float (the FP32 value plus its rounding residual)
+ *                    and the stage differences g(U_s) - g(U) and the final
+ *                    update formed in double-float (separate stage kernels;
+ *                    the D planes are FX tensors with their own exponents).
+ *                    For problems whose dynamics amplify every rounding
+ *                    (Turing growth), where the FP32-class parts of
+ *                    DS_PREC_F16X10 dominate. */
 typedef enum {
     DS_PREC_F64 = 0,
     DS_PREC_BF16X6 = 1,
     DS_PREC_F32 = 2,
     DS_PREC_BF16X6C = 3,
     DS_PREC_F16X10 = 4,
-    DS_PREC_F16X10A = 5
+    DS_PREC_F16X13 = 5
 } ds_precision;
 
 /* Reaction term g of the two-component systems (Section 3).

@@ -164,7 +164,7 @@ ds_status check_grid(const ds_grid *g)
 
 
 // the precisions with FX operands (scales calibrated per state)
-bool is_fx(int prec) { return prec == DS_PREC_F16X10 || prec == DS_PREC_F16X10A; }
+bool is_fx(int prec) { return prec == DS_PREC_F16X10 || prec == DS_PREC_F16X13; }
 
 bool is_tridiagonal(const double *A, int64_t n)
 {
@@ -737,7 +737,7 @@ ds_status ds_tucker(const ds_grid *grid, const double *X, double *Y, const doubl
     const int d = grid->d;
     if (precision == DS_PREC_BF16X6 || precision == DS_PREC_BF16X6C)
         return tc::tucker_mixed(grid, X, Y, L, transpose, st, precision == DS_PREC_BF16X6C);
-    if (precision == DS_PREC_F16X10 || precision == DS_PREC_F16X10A) return tc::tucker_fx(grid, X, Y, L, transpose, st);
+    if (precision == DS_PREC_F16X10 || precision == DS_PREC_F16X13) return tc::tucker_fx(grid, X, Y, L, transpose, st);
     if (precision == DS_PREC_F32) {
         int64_t pm = 0;
         for (int mu = 0; mu < d; ++mu) pm += grid->n[mu] * grid->n[mu];
@@ -798,7 +798,7 @@ ds_status ds_plan_create(const ds_grid *grid, const ds_params *params, const ds_
         for (int q = 0; q < 8; ++q)
             if (!isfinite(params->p[q])) return fail(DS_ERR_INVALID_ARG, "non-finite model parameter");
         if (precision != DS_PREC_F64 && precision != DS_PREC_BF16X6 && precision != DS_PREC_F32 &&
-            precision != DS_PREC_BF16X6C && precision != DS_PREC_F16X10 && precision != DS_PREC_F16X10A)
+            precision != DS_PREC_BF16X6C && precision != DS_PREC_F16X10 && precision != DS_PREC_F16X13)
             return fail(DS_ERR_UNSUPPORTED, "unknown precision");
         if (set->scheme != DS_EXPRK3DS_REAL && precision != DS_PREC_F64)
             return fail(DS_ERR_UNSUPPORTED, "ETD2RKDS, EXPRK3DS_CPLX and dense EXPRK3 plans are FP64 only");
@@ -846,7 +846,7 @@ ds_status ds_plan_create(const ds_grid *grid, const ds_params *params, const ds_
             tc::launch_convert_f64_f32(set->P_count, set->P_dev, p->P32, 0);
         } else {
             r = tc::mixed_plan_create(grid, set, p->status, &p->mixed, precision == DS_PREC_BF16X6C,
-                                      precision == DS_PREC_F16X10, precision == DS_PREC_F16X10A);
+                                      precision == DS_PREC_F16X10, precision == DS_PREC_F16X13);
             if (r != DS_OK) { ds_plan_destroy(p); return r; }
         }
         cudaDeviceSynchronize();
@@ -1055,7 +1055,7 @@ ds_status ds_plan_sync(ds_plan *p, const double *U, int check_state)
     }
     if (p->mixed && tc::mixed_plan_fx_overflow(p->mixed, true) > 0)
         return fail(DS_ERR_NONFINITE,
-                    "an FX tensor grew more than 16x within one step and left its exact head range");
+                    "an FX tensor left the FP16 range of its parts (grew ~32x or more past its scale within one step)");
     return DS_OK;
 }
 
@@ -1420,7 +1420,7 @@ ds_status ds_plan_set_fusion(ds_plan *p, int group, int fused)
     if (!p->mixed) return fail(DS_ERR_UNSUPPORTED, "only split-BF16 plans fuse epilogues");
     if (p->st) cudaStreamSynchronize(p->st);
     const int rc = tc::mixed_plan_set_fusion(p->mixed, group, fused);
-    if (rc == -2) return fail(DS_ERR_UNSUPPORTED, "DS_PREC_F16X10A plans run the separate stage kernels only");
+    if (rc == -2) return fail(DS_ERR_UNSUPPORTED, "DS_PREC_F16X13 plans run the separate stage kernels only");
     if (rc != 0) return fail(DS_ERR_INVALID_ARG, "group out of range");
     // captured steps hold the previous launch sequence
     for (auto &kv : p->graphs) cudaGraphExecDestroy(kv.second);

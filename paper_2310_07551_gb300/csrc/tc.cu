@@ -85,7 +85,8 @@ constexpr uint32_t kSw128 = 2, kSw64 = 4;
 //   B1 = h s1' + s1 h'                multiples of 2^-3, exact up to 2^21
 //   B2 = s1 s1' + h s2' + s2 h'       |.| <~ 2^10
 //   B3 = s1 s2' + s2 s1' + h s3' + s3 h'   |.| <~ 1
-// (s2 s2', s1 s3' and below are dropped: < 2^-38 of the head products).
+// (s2 s2', s1 s3', s3 s1' and below are dropped, each < 2^-38 of the head
+// products; DS_PREC_F16X13 adds those three to B3: 13 products per K step).
 // The tensor core's accumulation truncates toward zero after every MMA; a
 // truncation costs up to one unit in the last place of the accumulator it
 // lands in, so the four smallest products get an accumulator of their own
@@ -195,6 +196,9 @@ struct alignas(128) TcArgs {
     // FX launches with FP32 output: the rounding residual of each element
     // (value = out + out_lo to ~2^-48), same layout as out; null: not kept
     float *out_lo;
+    // FX launches: also the three products s1 s3', s3 s1', s2 s2' (into B3),
+    // 13 per K step instead of 10 (DS_PREC_F16X13)
+    int fx_extra;
     const float *pscale;
     FxScales *fxs;
     // cycles a pipeline wait spins before it gives up (the drains at exit
@@ -1167,6 +1171,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                             mma_bf16(dB3, ad(2, ks), bd(1, ks), idesc, 1u);
                             mma_bf16(dB3, ad(0, ks), bd(3, ks), idesc, 1u);
                             mma_bf16(dB3, ad(3, ks), bd(0, ks), idesc, 1u);
+                            if (a.fx_extra) {
+                                mma_bf16(dB3, ad(1, ks), bd(3, ks), idesc, 1u);
+                                mma_bf16(dB3, ad(3, ks), bd(1, ks), idesc, 1u);
+                                mma_bf16(dB3, ad(2, ks), bd(2, ks), idesc, 1u);
+                            }
                         }
                     } else {
 #pragma unroll
@@ -2324,7 +2333,7 @@ __global__ void k_final_mixed(int64_t N, double *__restrict__ U, const float *__
 }
 
 // ---------------------------------------------------------------------------
-// Stage kernels of FX-all plans (DS_PREC_F16X10A): the increments arrive as
+// Stage kernels of FX-all plans (DS_PREC_F16X13): the increments arrive as
 // double-floats (the FP32 increment plus its rounding residual), the stage
 // differences are formed in double-float and written as FX planes, and the
 // final update adds the double-float sum.
@@ -3410,7 +3419,7 @@ struct MixedPlan {
     float *pscale = nullptr;            // row scales of the FX groups' phi planes, per group and mode
     int64_t pscale_off[3][kMaxD] = {};
     FxMatJob *fx_jobs = nullptr;
-    // FX-all plans (DS_PREC_F16X10A): the groups on D2 and D3 in FX operands
+    // FX-all plans (DS_PREC_F16X13): the groups on D2 and D3 in FX operands
     // too, D planes [c][4][N] FX, and the increments as double-floats (the
     // FP32 values plus their rounding residuals incFlo [c][stage][N], incDlo
     // [c][N]); the stage differences and the final update run in the
@@ -3508,7 +3517,7 @@ ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatu
         int64_t Nq = 1;
         for (int q = 0; q < set->d; ++q) Nq *= set->n[q];
         if (set->d > 3 || Nq >= ((int64_t)1 << 31))
-            return fail(DS_ERR_UNSUPPORTED, "DS_PREC_F16X10 / F16X10A plans need d = 2 or 3 and fewer than 2^31 grid points");
+            return fail(DS_ERR_UNSUPPORTED, "DS_PREC_F16X10 / F16X13 plans need d = 2 or 3 and fewer than 2^31 grid points");
     }
     MixedPlan *mp = new MixedPlan();
     memset(mp->tune_ms, 0, sizeof(mp->tune_ms));
@@ -3638,7 +3647,7 @@ ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatu
     }
     const double tau = set->tau;
     if (fx) {
-        if (!mp->rhs_tiled) return cleanup(DS_ERR_UNSUPPORTED, "DS_PREC_F16X10 / F16X10A: grid too large for the tiled stencil");
+        if (!mp->rhs_tiled) return cleanup(DS_ERR_UNSUPPORTED, "DS_PREC_F16X10 / F16X13: grid too large for the tiled stencil");
         // scale table (every scale 1 until the first calibration), row scales
         // of the F group's planes, and intermediates cleared so that timing
         // at creation multiplies zeros
@@ -3744,6 +3753,7 @@ ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatu
                     a.xsl_div = mu == 0 ? S0 : (last ? 1 : k);
                     a.osl_base = base + 2 + per * mu;
                     a.osl_div = k;
+                    a.fx_extra = fx_all ? 1 : 0;
                 }
                 // the last mode's epilogue does the pointwise work of the stage:
                 //   F:  D2 = g(U + tau/3 S_2(F)) - g(U)                     (s = c * 3 + stage)

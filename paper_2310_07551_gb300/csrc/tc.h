@@ -12,7 +12,7 @@ struct MixedPlan;
 
 // compensated: dual-accumulator 128-column tiles (DS_PREC_BF16X6C); fx: the F
 // group in fixed-head FP16 operands (DS_PREC_F16X10); fx_all: all three groups,
-// with double-float increments and stage kernels (DS_PREC_F16X10A)
+// with double-float increments and stage kernels (DS_PREC_F16X13)
 ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatus *status,
                             MixedPlan **out, bool compensated = false, bool fx = false, bool fx_all = false);
 void mixed_plan_destroy(MixedPlan *mp);

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libds3.so")
 DS_OK, DS_ERR_INVALID_ARG, DS_ERR_UNSUPPORTED, DS_ERR_OOM, DS_ERR_CUDA, DS_ERR_NONFINITE, DS_ERR_TIMEOUT = range(7)
 STATUS_NAMES = ["DS_OK", "DS_ERR_INVALID_ARG", "DS_ERR_UNSUPPORTED", "DS_ERR_OOM", "DS_ERR_CUDA",
                 "DS_ERR_NONFINITE", "DS_ERR_TIMEOUT"]
-PREC = {"f64": 0, "bf16x6": 1, "f32": 2, "bf16x6c": 3, "f16x10": 4, "f16x10a": 5}
+PREC = {"f64": 0, "bf16x6": 1, "f32": 2, "bf16x6c": 3, "f16x10": 4, "f16x13": 5}
 MODELS = {"schnakenberg": 0, "fhn": 1, "linear": 2}
 SCHEMES = {"exprk3ds_real": 0, "etd2rkds": 1, "exprk3ds_cplx": 2, "exprk3_dense": 3}
 

@@ -39,7 +39,7 @@ def problem(inst):
 
 @pytest.mark.parametrize("precision,fusion", [("f64", None), ("bf16x6", None), ("bf16x6", True),
                                               ("bf16x6", False), ("bf16x6c", None), ("f16x10", None),
-                                              ("f16x10", True), ("f16x10", False), ("f16x10a", None)])
+                                              ("f16x10", True), ("f16x10", False), ("f16x13", None)])
 def test_batch_matches_individual_plans_and_oracle(ds, precision, fusion):
     insts = small_instances()
     As = [problem(i) for i in insts]
@@ -71,7 +71,7 @@ def test_batch_matches_individual_plans_and_oracle(ds, precision, fusion):
         plan = ds.Plan(ps, "schnakenberg", inst.params, precision)
         if precision != "f64":
             for g in range(3):
-                if precision != "f16x10a":   # f16x10a: separate stage kernels only
+                if precision != "f16x13":   # f16x13: separate stage kernels only
                     plan.set_fusion(g, True)
                 for mode in range(1, len(inst.dims) + 1):
                     plan.set_tiles(g, mode, 128, 1)
@@ -86,7 +86,7 @@ def test_batch_matches_individual_plans_and_oracle(ds, precision, fusion):
             assert np.abs(got - ref).max() / np.abs(ref).max() < 1e-12
 
 
-@pytest.mark.parametrize("precision,tol", [("f16x10", 1e-7), ("f16x10a", 1e-7), ("bf16x6", 2e-6)])
+@pytest.mark.parametrize("precision,tol", [("f16x10", 1e-7), ("f16x13", 1e-7), ("bf16x6", 2e-6)])
 def test_batch_of_workload_sized_instances_matches_the_oracle(ds, precision, tol):
     """Four instances of the 64-instance workload itself (grids of 96 to 512
     points per side, their own parameters and tau), five batch steps (the

@@ -89,11 +89,11 @@ def run(ds, dims, lo, hi, delta, model, p, tau, U0, m, precision="f16x10"):
     return U.cpu().numpy(), ref
 
 
-@pytest.mark.parametrize("precision", ["f16x10", "f16x10a"])
+@pytest.mark.parametrize("precision", ["f16x10", "f16x13"])
 @pytest.mark.parametrize("dims,m", [((32, 24, 16), 5), ((40, 33, 70), 3), ((64, 48, 40), 3), ((96, 72, 20), 2)])
 def test_fhn_3d_f16x10_step_matches_oracle(ds, dims, m, precision):
     """White-noise FHN data (the stiff case where FP32-class contractions err
-    by ~1e-5): the FX F group brings the step to the 1e-8 class (f16x10a:
+    by ~1e-5): the FX F group brings the step to the 1e-8 class (f16x13:
     every group FX, double-float stages)."""
     U0 = inputs.initial_state("fhn", dims, seed=1)
     got, ref = run(ds, dims, -1.0, 1.0, FHN_DELTA, "fhn", FHN_P, 1e-3, U0, m, precision)
@@ -102,7 +102,7 @@ def test_fhn_3d_f16x10_step_matches_oracle(ds, dims, m, precision):
     assert err < 2e-7, err
 
 
-@pytest.mark.parametrize("precision", ["f16x10", "f16x10a"])
+@pytest.mark.parametrize("precision", ["f16x10", "f16x13"])
 @pytest.mark.parametrize("dims,m", [((64, 64), 20), ((136, 40), 10)])
 def test_schnakenberg_2d_f16x10_step_matches_oracle(ds, dims, m, precision):
     U0 = inputs.initial_state("schnakenberg", dims, seed=1)
