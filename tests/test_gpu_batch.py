@@ -113,3 +113,30 @@ def test_batch_of_workload_sized_instances_matches_the_oracle(ds, precision, tol
         err = max(np.abs(got[c] - ref[c]).max() / np.abs(ref[c]).max() for c in range(2))
         print("batch", precision, inst.dims, err)
         assert err < tol, (inst.dims, err)
+
+
+def test_batch_workload_f16x13_within_1e6_of_fp64_at_its_horizon(ds):
+    """The 64-instance workload's accuracy target: after its 500-step horizon
+    every instance of the f16x13 batch is within 1e-6 (relative, maximum norm
+    per component) of the FP64 batch, whose steps match the oracle (above).
+    Turing growth multiplies step errors ~10^4-fold here, which is why the
+    FP32-class precisions end 24-27 instances above the target."""
+    every = configs.batch_instances()
+    As = [problem(i) for i in every]
+    U0 = [inputs.initial_state("schnakenberg", i.dims, seed=7 + k, a=i.params[1], b=i.params[2])
+          for k, i in enumerate(every)]
+    args = ([i.dims for i in every], As, [i.tau for i in every], "schnakenberg", [i.params for i in every])
+    bx = ds.Batch(*args, "f16x13")
+    b64 = ds.Batch(*args, "f64")
+    Ua = [torch.from_numpy(u.copy()).cuda() for u in U0]
+    Ub = [torch.from_numpy(u.copy()).cuda() for u in U0]
+    bx.integrate(Ua, configs.BATCH_STEPS)
+    b64.integrate(Ub, configs.BATCH_STEPS)
+    bx.sync()
+    b64.sync()
+    errs = [max(float((a[c] - b[c]).abs().max() / b[c].abs().max()) for c in range(2)) for a, b in zip(Ua, Ub)]
+    worst = max(range(len(errs)), key=lambda k: errs[k])
+    print("batch64 f16x13 at step", configs.BATCH_STEPS, "worst", every[worst].dims, errs[worst])
+    assert errs[worst] <= 1e-6, (worst, errs[worst])
+    bx.close()
+    b64.close()
