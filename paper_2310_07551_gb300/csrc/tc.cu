@@ -431,27 +431,6 @@ __device__ __forceinline__ void fx_split(float hi, float lo, __half (&o)[4])
     o[2] = s2;
     o[3] = __float2half_rn(__fadd_rn(__fsub_rn(q, __half2float(s2)), lo));
 }
-// The same split for two values at once (rows r and r+1 of one column), each
-// part packed as a half2 (low half: the first value).  Rounding to a multiple
-// of 16 (of 2^-7) by adding and subtracting 1.5 * 2^27 (1.5 * 2^16): the sum
-// lands where the float spacing is 16 (2^-7), so the result is the
-// round-to-nearest-even multiple, as 16 rint(x / 16) gives (|x| < 2^26).
-__device__ __forceinline__ void fx_split2(float xh0, float xl0, float xh1, float xl1, __half2 (&o)[4])
-{
-    constexpr float M16 = 201326592.0f, M7 = 98304.0f;
-    const __half2 h = __floats2half2_rn(__fsub_rn(__fadd_rn(xh0, M16), M16), __fsub_rn(__fadd_rn(xh1, M16), M16));
-    const float2 hf = __half22float2(h);
-    const float r0 = __fsub_rn(xh0, hf.x), r1 = __fsub_rn(xh1, hf.y);
-    const __half2 a = __floats2half2_rn(__fsub_rn(__fadd_rn(r0, M7), M7), __fsub_rn(__fadd_rn(r1, M7), M7));
-    const float2 af = __half22float2(a);
-    const float q0 = __fsub_rn(r0, af.x), q1 = __fsub_rn(r1, af.y);
-    const __half2 s2 = __floats2half2_rn(__fadd_rn(q0, xl0), __fadd_rn(q1, xl1));
-    const float2 s2f = __half22float2(s2);
-    o[0] = h;
-    o[1] = a;
-    o[2] = s2;
-    o[3] = __floats2half2_rn(__fadd_rn(__fsub_rn(q0, s2f.x), xl0), __fadd_rn(__fsub_rn(q1, s2f.y), xl1));
-}
 // the same for an FP64 value (setup-time use: phi-matrix rows, FP64 tensors)
 __device__ __forceinline__ void fx_split_d(double v, __half (&o)[4])
 {
@@ -471,6 +450,45 @@ __device__ __forceinline__ void two_sum_f(float a, float b, float &hi, float &lo
     hi = __fadd_rn(a, b);
     const float bb = __fsub_rn(hi, a);
     lo = __fadd_rn(__fsub_rn(a, __fsub_rn(hi, bb)), __fsub_rn(b, bb));
+}
+// Packed FP32 pairs (add/mul/fma .f32x2: one instruction for both lanes,
+// each lane rounded as its scalar form)
+__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// a - b with one rounding: b (-1) + a is exact before it
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+__device__ __forceinline__ float2 f2neg(float2 a) { return make_float2(-a.x, -a.y); }
+// Knuth's two-sum in each lane: s + e == a + b exactly
+__device__ __forceinline__ void f2two_sum(float2 a, float2 b, float2 &s, float2 &e)
+{
+    s = f2add(a, b);
+    const float2 bb = f2sub(s, a);
+    e = f2add(f2sub(a, f2sub(s, bb)), f2sub(b, bb));
+}
+// lanes k, k + 1 of a TMEM load as a float2
+__device__ __forceinline__ float2 u2f2(const uint32_t (&w)[16], int k)
+{
+    return make_float2(__uint_as_float(w[k]), __uint_as_float(w[k + 1]));
+}
+// The same split for two values at once, each part packed as a half2 (low
+// half: the first value), the values as float2 lanes (heads xh, low parts
+// xl).  Rounding to a multiple of 16 (of 2^-7) by adding and subtracting
+// 1.5 * 2^27 (1.5 * 2^16): the sum lands where the float spacing is 16
+// (2^-7), so the result is the round-to-nearest-even multiple, as
+// 16 rint(x / 16) gives (|x| < 2^26).
+__device__ __forceinline__ void fx_split2v(float2 xh, float2 xl, __half2 (&o)[4])
+{
+    const float2 M16 = make_float2(201326592.0f, 201326592.0f), M7 = make_float2(98304.0f, 98304.0f);
+    const __half2 h = __float22half2_rn(f2sub(f2add(xh, M16), M16));
+    const float2 r = f2sub(xh, __half22float2(h));
+    const __half2 a = __float22half2_rn(f2sub(f2add(r, M7), M7));
+    const float2 q = f2sub(r, __half22float2(a));
+    const __half2 s2 = __float22half2_rn(f2add(q, xl));
+    o[0] = h;
+    o[1] = a;
+    o[2] = s2;
+    o[3] = __float22half2_rn(f2add(f2sub(q, __half22float2(s2)), xl));
 }
 // ceil(log2 m) for a positive finite float (exact: from the bits)
 __device__ __forceinline__ int ceil_log2f(float m)
@@ -1371,13 +1389,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int64_t rbase = (int64_t)tc.s * out_cs + row_index + cbase * (int64_t)col_stride;
                 if constexpr (FX == 1) {
                     // (1) drain: the four accumulators of this thread's half row
-                    // as a normalised double-float vh + vl (two-sum of the exact A
-                    // and B1, then the small B2 + B3), chunk 0's low parts in
-                    // registers and chunk 1's in shared memory; then release the
-                    // accumulators, so the next tile's MMAs run while this tile's
-                    // values are scaled, split and stored
-                    float vh[BN / 2], vl0[32];
-                    float *const vls = (float *)(gbase + TileCfg<BNT, NP>::SPILL_OFF) + (threadIdx.x - 64);
+                    // as a head vh = RN(A + B1) (two-sum of the exact A and B1) and
+                    // a rest vl = its error + (B2 + B3), in pairs of columns
+                    // (packed FP32), chunk 0's rests in registers and chunk 1's in
+                    // shared memory; then release the accumulators, so the next
+                    // tile's MMAs run while this tile's values are normalised,
+                    // scaled, split and stored
+                    float2 vh[BN / 4], vl0[16];   // [column / 2]
+                    float2 *const vls = (float2 *)(gbase + TileCfg<BNT, NP>::SPILL_OFF) + (threadIdx.x - 64);
 #pragma unroll
                     for (int c = 0; c < BN / 64; ++c) {
                         if (cbase + c * 32 < col_lim) {   // warp-uniform
@@ -1386,25 +1405,20 @@ __global__ void __launch_bounds__(kThreads, 1)
                                 const uint32_t tb = tmem + (uint32_t)(half * (BN / 2) + c * 32 + g * 16) +
                                                     ((uint32_t)(quarter * 32) << 16);
                                 uint32_t w0[16], w1[16];
-                                float t[16];
+                                float2 t[8];
                                 tmem_ld16(tb, w0);
                                 tmem_ld16(tb + BN, w1);
                                 tmem_wait_ld();
 #pragma unroll
-                                for (int j = 0; j < 16; ++j)
-                                    two_sum_f(__uint_as_float(w0[j]), __uint_as_float(w1[j]), vh[c * 32 + g * 16 + j],
-                                              t[j]);
+                                for (int i = 0; i < 8; ++i) f2two_sum(u2f2(w0, 2 * i), u2f2(w1, 2 * i), vh[c * 16 + g * 8 + i], t[i]);
                                 tmem_ld16(tb + 2 * BN, w0);
                                 tmem_ld16(tb + 3 * BN, w1);
                                 tmem_wait_ld();
 #pragma unroll
-                                for (int j = 0; j < 16; ++j) {
-                                    const float l = __fadd_rn(t[j], __fadd_rn(__uint_as_float(w0[j]),
-                                                                              __uint_as_float(w1[j])));
-                                    float lo;
-                                    two_sum_f(vh[c * 32 + g * 16 + j], l, vh[c * 32 + g * 16 + j], lo);
-                                    if (c == 0) vl0[g * 16 + j] = lo;
-                                    else vls[(g * 16 + j) * kEpiThreads] = lo;
+                                for (int i = 0; i < 8; ++i) {
+                                    const float2 l = f2add(t[i], f2add(u2f2(w0, 2 * i), u2f2(w1, 2 * i)));
+                                    if (c == 0) vl0[g * 8 + i] = l;
+                                    else vls[(g * 8 + i) * kEpiThreads] = l;
                                 }
                             }
                         }
@@ -1430,12 +1444,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                                                  : (lane < jmax ? __ldg(a.pscale + (int64_t)tc.s * a.n + col0 + lane) *
                                                                       xin * inv
                                                                 : 0.0f);
-                        // value of column j as a double-float (hi, lo); every lane calls it
-                        // with the same j (the column factor is a warp shuffle)
-                        auto value = [&](int j, float &hi, float &lo) {
-                            const float g = MODE1 ? grow : __shfl_sync(0xffffffffu, gcol, j);
-                            hi = vh[c * 32 + j] * g;
-                            lo = (c == 0 ? vl0[j] : vls[j * kEpiThreads]) * g;
+                        // values of columns j, j + 1 (j even) as normalised double-floats
+                        // (hi, lo); every lane calls it with the same j (the column
+                        // factors are warp shuffles)
+                        auto value = [&](int j, float2 &hi, float2 &lo) {
+                            const float2 g = MODE1 ? make_float2(grow, grow)
+                                                   : make_float2(__shfl_sync(0xffffffffu, gcol, j),
+                                                                 __shfl_sync(0xffffffffu, gcol, j + 1));
+                            f2two_sum(vh[c * 16 + j / 2], c == 0 ? vl0[j / 2] : vls[(j / 2) * kEpiThreads], hi, lo);
+                            hi = f2mul(hi, g);
+                            lo = f2mul(lo, g);
                         };
                         {
                             // FX planes of the output tensor, as pairs of rows: the even
@@ -1446,15 +1464,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                             const int64_t eb = e0 - odd;
 #pragma unroll
                             for (int j = 0; j < 32; j += 2) {
-                                float h0, l0, h1, l1;
-                                value(j, h0, l0);
-                                value(j + 1, h1, l1);
+                                float2 hv, lv;
+                                value(j, hv, lv);
+                                const float h0 = hv.x, l0 = lv.x, h1 = hv.y, l1 = lv.y;
                                 lmax = fmaxf(lmax, fmaxf(fabsf(h0), fabsf(h1)));
                                 const float rh = __shfl_xor_sync(0xffffffffu, odd ? h0 : h1, 1);
                                 const float rl = __shfl_xor_sync(0xffffffffu, odd ? l0 : l1, 1);
                                 const int jj = j + odd;
                                 __half2 q[4];
-                                fx_split2(odd ? rh : h0, odd ? rl : l0, odd ? h1 : rh, odd ? l1 : rl, q);
+                                fx_split2v(make_float2(odd ? rh : h0, odd ? h1 : rh), make_float2(odd ? rl : l0, odd ? l1 : rl), q);
                                 if (!a.fx_measure && row_ok && jj < jmax) {
                                     __half *o = (__half *)out_ptr + eb + (uint32_t)jj * col_stride;
 #pragma unroll
@@ -1481,11 +1499,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const EpiTile et = epi_tile<MODE1, BN>(a, tc, part, m, half);
                         // FP32 out: each element is the double-float value rounded
                         // once, times its power-of-two factor; the four accumulators
-                        // are drained to one float per element (chunk 0 in
-                        // registers, chunk 1 in shared memory) and released before
-                        // the stores and the stage epilogue
-                        float vs[32];
-                        float *const vss = (float *)(gbase + TileCfg<BNT, NP>::SPILL_OFF) + (threadIdx.x - 64);
+                        // are drained to one float per element, in pairs of columns
+                        // (packed FP32; chunk 0 in registers, chunk 1 in shared
+                        // memory) and released before the stores and the stage
+                        // epilogue
+                        float2 vs[16];
+                        float2 *const vss = (float2 *)(gbase + TileCfg<BNT, NP>::SPILL_OFF) + (threadIdx.x - 64);
 #pragma unroll
                         for (int c = 0; c < BN / 64; ++c) {
                             const int64_t col0 = cbase + c * 32;
@@ -1499,30 +1518,35 @@ __global__ void __launch_bounds__(kThreads, 1)
                                 const uint32_t tb = tmem + (uint32_t)(half * (BN / 2) + c * 32 + g * 16) +
                                                     ((uint32_t)(quarter * 32) << 16);
                                 uint32_t w0[16], w1[16];
-                                float h[16], l[16];
+                                float2 h[8], l[8];
                                 tmem_ld16(tb, w0);
                                 tmem_ld16(tb + BN, w1);
                                 tmem_wait_ld();
 #pragma unroll
-                                for (int j = 0; j < 16; ++j)
-                                    two_sum_f(__uint_as_float(w0[j]), __uint_as_float(w1[j]), h[j], l[j]);
+                                for (int i = 0; i < 8; ++i) f2two_sum(u2f2(w0, 2 * i), u2f2(w1, 2 * i), h[i], l[i]);
                                 tmem_ld16(tb + 2 * BN, w0);
                                 tmem_ld16(tb + 3 * BN, w1);
                                 tmem_wait_ld();
 #pragma unroll
-                                for (int j = 0; j < 16; ++j) {
-                                    const float lo = __fadd_rn(l[j], __fadd_rn(__uint_as_float(w0[j]),
-                                                                               __uint_as_float(w1[j])));
-                                    const float f = MODE1 ? frow : __shfl_sync(0xffffffffu, fcol, g * 16 + j);
-                                    float sh, se;
-                                    two_sum_f(h[j], lo, sh, se);
-                                    const float val = sh * f;
-                                    if (c == 0) vs[g * 16 + j] = val;
-                                    else vss[(g * 16 + j) * kEpiThreads] = val;
+                                for (int i = 0; i < 8; ++i) {
+                                    const int j = g * 16 + 2 * i;
+                                    const float2 lo = f2add(l[i], f2add(u2f2(w0, 2 * i), u2f2(w1, 2 * i)));
+                                    const float2 f = MODE1 ? make_float2(frow, frow)
+                                                           : make_float2(__shfl_sync(0xffffffffu, fcol, j),
+                                                                         __shfl_sync(0xffffffffu, fcol, j + 1));
+                                    float2 sh, se;
+                                    f2two_sum(h[i], lo, sh, se);
+                                    const float2 val = f2mul(sh, f);
+                                    if (c == 0) vs[j / 2] = val;
+                                    else vss[(j / 2) * kEpiThreads] = val;
                                     // the residual, where the caller keeps it (coalesced:
                                     // the lanes of a warp own consecutive rows)
-                                    if (a.out_lo && row_ok && g * 16 + j < jmax)
-                                        a.out_lo[rbase + (int64_t)(c * 32 + g * 16 + j) * col_stride] = se * f;
+                                    if (a.out_lo && row_ok) {
+                                        const float2 r = f2mul(se, f);
+                                        float *const ol = a.out_lo + rbase + (int64_t)(c * 32 + j) * col_stride;
+                                        if (j < jmax) ol[0] = r.x;
+                                        if (j + 1 < jmax) ol[col_stride] = r.y;
+                                    }
                                 }
                             }
                         }
@@ -1533,7 +1557,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                             if (cbase + c * 32 >= col_lim) break;   // warp-uniform
                             uint32_t v[32];
 #pragma unroll
-                            for (int j = 0; j < 32; ++j) v[j] = __float_as_uint(c == 0 ? vs[j] : vss[j * kEpiThreads]);
+                            for (int i = 0; i < 16; ++i) {
+                                const float2 p = c == 0 ? vs[i] : vss[i * kEpiThreads];
+                                v[2 * i] = __float_as_uint(p.x);
+                                v[2 * i + 1] = __float_as_uint(p.y);
+                            }
                             epi_chunk(a, tc, et, c, lane, v);
                         }
                     } else {
@@ -1848,9 +1876,6 @@ struct StencilF {
     int d;
     int64_t n[kMaxD];
     const float *hs[kMaxD], *hd[kMaxD], *rsum[kMaxD];
-    // FX plans: the FP32 remainders of the same coefficients (hs + hsl is
-    // the FP64 value to ~2^-48), else null
-    const float *hsl[kMaxD], *hdl[kMaxD], *rsl[kMaxD];
     int has_rsum[kMaxD];
     // r / n[mu] = (r * magic[mu]) >> shift[mu] for r < 2^31 (fast31: N < 2^31)
     unsigned long long magic[kMaxD];
@@ -1988,57 +2013,140 @@ struct RhsArgs {
     bf16 *Fp;
     int gx, gy;   // tiles along x and y (grouped launches)
     // FX: F_c goes out as FX planes of scale slot c; fx_measure: only record
-    // the largest |F_c|
+    // the largest |F_c|.  cf[mu]: direction mu's coefficients as [hs, hd,
+    // rs][n_mu] quadruples (head u, head v, low u, low v), head + low = the
+    // FP64 value to ~2^-48
     FxScales *fxs;
     int fx_measure;
+    const float4 *cf[kMaxD];
 };
 
-// Double-float pieces of the FX stencil.  Knuth's two-difference: s + e ==
-// a - b exactly.
-__device__ __forceinline__ dfl df_two_diff(float a, float b)
+// ---------------------------------------------------------------------------
+// FX stencil arithmetic.  Both components of a grid point travel together as
+// the two lanes of a float2 through the packed FP32 instructions
+// (add/mul/fma .f32x2, one instruction for both lanes, each lane rounded as
+// its scalar form).  Each term of F is a head and a rest: the second
+// differences from exact two-sums of the heads (the low parts and the sums'
+// errors in the rest), the products with the coefficients from FMA
+// two-products, and the running sum a double-float renormalised after each
+// term.  F keeps ~2^-47 of the state times the coefficients (the accuracy of
+// the head/low split of the FP64 state), where its FX planes need ~2^-35 of
+// its largest entry.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 f2hi(float4 q) { return make_float2(q.x, q.y); }
+__device__ __forceinline__ float2 f2lo(float4 q) { return make_float2(q.z, q.w); }
+// p + r = (ch + cl)(b + t) up to the cl t term (below 2^-47 of the product):
+// p = RN(ch b), and r gathers its FMA rounding error and the remainder
+__device__ __forceinline__ void f2prod(float2 ch, float2 cl, float2 b, float2 t, float2 &p, float2 &r)
 {
-    const float s = __fsub_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    return {s, __fsub_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fadd_rn(b, bb))};
+    p = f2mul(ch, b);
+    r = f2fma(ch, t, f2fma(cl, b, f2fma(ch, b, f2neg(p))));
 }
-// u_nb - u_c from hi/lo parts, to ~2^-47 of the values (0 without a neighbour)
-__device__ __forceinline__ dfl df_diff_hl(bool has, float hn, float ln, float hc, float lc)
+// (Sh, Sl) += p + r: the heads by a two-sum, then renormalised
+__device__ __forceinline__ void f2acc(float2 &Sh, float2 &Sl, float2 p, float2 r)
 {
-    if (!has) return {0.0f, 0.0f};
-    const dfl d = df_two_diff(hn, hc);
-    const float t = __fadd_rn(d.lo, __fsub_rn(ln, lc));
-    const float h = __fadd_rn(d.hi, t);
-    return {h, __fsub_rn(t, __fsub_rn(h, d.hi))};
+    float2 s, e;
+    f2two_sum(Sh, p, s, e);
+    const float2 t = f2add(f2add(Sl, r), e);
+    Sh = f2add(s, t);
+    Sl = f2sub(t, f2sub(Sh, s));
 }
-// One direction's row of A u in double-float: hs (d_- + d_+) + hd (d_+ - d_-)
-// + rsum u, every coefficient a double-float (hi, lo).  For white-noise data
-// the neighbours are unrelated, so FP32 differences would already lose
-// 2^-24 of |u|; here the differences, their sums and the products keep
-// ~2^-44.
-__device__ __forceinline__ dfl stencil_dir_df(dfl hs, dfl hd, dfl rs, bool has_m, bool has_p, int has_rs,
-                                              float hm, float lm, float hp, float lp, float hc, float lc)
+// b + t moved into b as far as it goes (b = 0 after an exact cancellation of
+// the heads leaves the whole value in t)
+__device__ __forceinline__ void f2norm(float2 &b, float2 &t)
 {
-    const dfl dm = df_diff_hl(has_m, hm, lm, hc, lc), dp = df_diff_hl(has_p, hp, lp, hc, lc);
-    dfl r = df_mul(hs, df_add(dm, dp));
-    if (hd.hi != 0.0f) r = df_add(r, df_mul(hd, df_add(dp, df_neg(dm))));
-    if (has_rs) r = df_add(r, df_mul(rs, dfl{hc, lc}));
-    return r;
+    const float2 s = f2add(b, t);
+    t = f2sub(t, f2sub(s, b));
+    b = s;
 }
-// g(u, v) in double-float (FX: F must keep ~2^-35 of its largest entry)
-__device__ __forceinline__ void react_df2(const ModelDF &m, dfl u, dfl v, dfl &gu, dfl &gv)
+// One direction's row of A_mu u, hs (d_- + d_+) + hd (d_+ - d_-) + rs u_c with
+// d_-+ = u_{i-+1} - u_c, for both components, added to (Sh, Sl).  cq: the
+// direction's (hs, hd, rs) quadruples, hs the one at row i.  Rows with hd =
+// rs = 0 and both neighbours (the interior rows of a uniform grid) take the
+// second difference u_m + u_p - 2 u_c: two exact two-sums of the heads (2 u_c's
+// head is exact), the low parts and the two-sum errors in the rest.  Other rows
+// form the two differences first.
+__device__ __forceinline__ void f2row(bool plain, float4 hs, const float4 *__restrict__ cq, int n, int i,
+                                      bool has_m, bool has_p, float4 qm, float4 qp, float2 Hc, float2 Lc,
+                                      float2 Hc2, float2 &Sh, float2 &Sl)
 {
-    if (m.model == DS_SCHNAKENBERG) {
-        const dfl u2v = df_mul(df_mul(u, u), v);
-        gu = df_mul(m.p[0], df_add(df_add(m.p[1], df_neg(u)), u2v));
-        gv = df_mul(m.p[0], df_add(m.p[2], df_neg(u2v)));
-    } else if (m.model == DS_FHN) {
-        const dfl u3 = df_mul(df_mul(u, u), u);
-        gu = df_add(df_add(u, df_neg(u3)), df_neg(v));
-        gv = df_mul(m.p[0], df_add(df_add(u, df_neg(df_mul(m.p[1], v))), df_neg(m.p[2])));
-    } else {
-        gu = {0.0f, 0.0f};
-        gv = {0.0f, 0.0f};
+    float2 p, r;
+    if (plain) {
+        float2 a, ea, b, eb;
+        f2two_sum(f2hi(qm), f2hi(qp), a, ea);
+        f2two_sum(a, Hc2, b, eb);
+        float2 t = f2add(f2add(ea, eb), f2fma(Lc, make_float2(-2.0f, -2.0f), f2add(f2lo(qm), f2lo(qp))));
+        f2norm(b, t);
+        f2prod(f2hi(hs), f2lo(hs), b, t, p, r);
+        f2acc(Sh, Sl, p, r);
+        return;
     }
+    const float4 hd = cq[n + i], rs = cq[2 * n + i];
+    const float2 z = make_float2(0.0f, 0.0f);
+    float2 dmh = z, dml = z, dph = z, dpl = z, e;
+    if (has_m) {
+        f2two_sum(f2hi(qm), f2neg(Hc), dmh, e);
+        dml = f2add(f2sub(f2lo(qm), Lc), e);
+    }
+    if (has_p) {
+        f2two_sum(f2hi(qp), f2neg(Hc), dph, e);
+        dpl = f2add(f2sub(f2lo(qp), Lc), e);
+    }
+    float2 s, t;
+    f2two_sum(dmh, dph, s, e);
+    t = f2add(e, f2add(dml, dpl));
+    f2norm(s, t);
+    f2prod(f2hi(hs), f2lo(hs), s, t, p, r);
+    f2acc(Sh, Sl, p, r);
+    f2two_sum(dph, f2neg(dmh), s, e);
+    t = f2add(e, f2sub(dpl, dml));
+    f2norm(s, t);
+    f2prod(f2hi(hd), f2lo(hd), s, t, p, r);
+    f2acc(Sh, Sl, p, r);
+    f2prod(f2hi(rs), f2lo(rs), Hc, Lc, p, r);
+    f2acc(Sh, Sl, p, r);
+}
+// g(u, v) of both components as p + r, from the head/low parts H, L of the
+// FP64 state (u in the x lanes, v in the y lanes).  Products are FMA
+// two-products; the low x low terms are below 2^-47 of the values.
+__device__ __forceinline__ void f2react(const ModelDF &m, float2 H, float2 L, float2 &p, float2 &r)
+{
+    const float uh = H.x, ul = L.x, vh = H.y, vl = L.y;
+    // u^2 = s + se
+    const float s = __fmul_rn(uh, uh);
+    const float se = __fmaf_rn(__fadd_rn(uh, uh), ul, __fmaf_rn(uh, uh, -s));
+    float xh, xl, yh, yl, e1, e2, x1;   // the two inner sums as head + rest
+    float2 ch, cl;                      // their outer factors
+    if (m.model == DS_SCHNAKENBERG) {
+        // g_u = gamma (a - u + u^2 v), g_v = gamma (b - u^2 v), w = u^2 v
+        const float w = __fmul_rn(s, vh);
+        const float we = __fmaf_rn(s, vl, __fmaf_rn(se, vh, __fmaf_rn(s, vh, -w)));
+        two_sum_f(m.p[1].hi, -uh, x1, e1);
+        two_sum_f(x1, w, xh, e2);
+        xl = __fadd_rn(__fadd_rn(__fsub_rn(m.p[1].lo, ul), we), __fadd_rn(e1, e2));
+        two_sum_f(m.p[2].hi, -w, yh, e1);
+        yl = __fadd_rn(__fsub_rn(m.p[2].lo, we), e1);
+        ch = make_float2(m.p[0].hi, m.p[0].hi);
+        cl = make_float2(m.p[0].lo, m.p[0].lo);
+    } else if (m.model == DS_FHN) {
+        // g_u = u - v - u^3, g_v = eps (u - alpha1 v - alpha0), u^3 = c + ce
+        const float c = __fmul_rn(s, uh);
+        const float ce = __fmaf_rn(se, uh, __fmaf_rn(s, ul, __fmaf_rn(s, uh, -c)));
+        two_sum_f(uh, -vh, x1, e1);
+        two_sum_f(x1, -c, xh, e2);
+        xl = __fadd_rn(__fsub_rn(__fsub_rn(ul, vl), ce), __fadd_rn(e1, e2));
+        const float q = __fmul_rn(m.p[1].hi, vh);
+        const float qe = __fmaf_rn(m.p[1].hi, vl, __fmaf_rn(m.p[1].lo, vh, __fmaf_rn(m.p[1].hi, vh, -q)));
+        two_sum_f(uh, -q, x1, e1);
+        two_sum_f(x1, -m.p[2].hi, yh, e2);
+        yl = __fadd_rn(__fsub_rn(__fsub_rn(ul, qe), m.p[2].lo), __fadd_rn(e1, e2));
+        ch = make_float2(1.0f, m.p[0].hi);
+        cl = make_float2(0.0f, m.p[0].lo);
+    } else {
+        p = r = make_float2(0.0f, 0.0f);
+        return;
+    }
+    f2prod(ch, cl, make_float2(xh, yh), make_float2(xl, yl), p, r);
 }
 // F (a double-float) as FX planes at element i (plane stride `plane`), with
 // scale factor inv = 2^-E; flags values beyond the exact head range
@@ -2052,12 +2160,10 @@ __device__ __forceinline__ void store_fx(__half *dst, int64_t plane, int64_t i, 
     for (int k = 0; k < 4; ++k) dst[i + k * plane] = q[k];
 }
 
-// FX: F in double-float, stored as FX planes (__half) with the scale of slot
-// c, and the largest |F_c| recorded for the next rescale.
-template <int TX, int TY, int TZ, typename Idx, bool GROUPED, bool FX = false>
-__global__ void __launch_bounds__(TX * TY, FX ? 3 : 1) k_rhs_tiled(const __grid_constant__ RhsArgs a0,
-                                                       const RhsArgs *__restrict__ gtab,
-                                                       const int *__restrict__ gprefix, int ginst)
+template <int TX, int TY, int TZ, typename Idx, bool GROUPED>
+__global__ void __launch_bounds__(TX * TY, 1) k_rhs_tiled(const __grid_constant__ RhsArgs a0,
+                                                          const RhsArgs *__restrict__ gtab,
+                                                          const int *__restrict__ gprefix, int ginst)
 {
     __shared__ float sh[2][2][TY + 2][TX + 2];   // [component][hi, lo][y][x], one-point halo
     int gi = 0, lb = 0;
@@ -2109,10 +2215,7 @@ __global__ void __launch_bounds__(TX * TY, FX ? 3 : 1) k_rhs_tiled(const __grid_
         else if (tx == TX - 1 && x + 1 < n1) { xh = TX + 1; xoff = col + 1; }
     }
     float cx[2][3] = {}, cy[2][3] = {};
-    float cxl[2][3] = {}, cyl[2][3] = {};   // FX: lo parts of the coefficients
     float hp[2] = {}, lp[2] = {}, hc[2] = {}, lc[2] = {}, hn[2] = {}, ln[2] = {};
-    float fmax_[2] = {0.0f, 0.0f};
-    bool over = false;
     double rn[2] = {}, ry[2] = {}, rx[2] = {};   // raw values loaded one iteration ahead
     {
         const Idx pz = (Idx)z0 * plane;
@@ -2126,16 +2229,6 @@ __global__ void __launch_bounds__(TX * TY, FX ? 3 : 1) k_rhs_tiled(const __grid_
                     cy[c][0] = st[c]->hs[1][y];
                     cy[c][1] = st[c]->hd[1][y];
                     cy[c][2] = st[c]->rsum[1][y];
-                }
-                if constexpr (FX) {
-                    cxl[c][0] = st[c]->hsl[0][x];
-                    cxl[c][1] = st[c]->hdl[0][x];
-                    cxl[c][2] = st[c]->rsl[0][x];
-                    if (TY > 1) {
-                        cyl[c][0] = st[c]->hsl[1][y];
-                        cyl[c][1] = st[c]->hdl[1][y];
-                        cyl[c][2] = st[c]->rsl[1][y];
-                    }
                 }
                 split_hilo(U[c * N + pz + col], hc[c], lc[c]);
                 if (z0 > 0) split_hilo(U[c * N + pz - plane + col], hp[c], lp[c]);
@@ -2166,31 +2259,7 @@ __global__ void __launch_bounds__(TX * TY, FX ? 3 : 1) k_rhs_tiled(const __grid_
             }
         }
         __syncthreads();
-        if (FX && in) {
-            dfl g[2];
-            react_df2(m, dfl{hc[0], lc[0]}, dfl{hc[1], lc[1]}, g[0], g[1]);
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                const StencilF &sc = *st[c];
-                dfl acc = stencil_dir_df({cx[c][0], cxl[c][0]}, {cx[c][1], cxl[c][1]}, {cx[c][2], cxl[c][2]}, x > 0,
-                                         x + 1 < n1, sc.has_rsum[0], sh[c][0][ty + 1][tx], sh[c][1][ty + 1][tx],
-                                         sh[c][0][ty + 1][tx + 2], sh[c][1][ty + 1][tx + 2], hc[c], lc[c]);
-                if (TY > 1)
-                    acc = df_add(acc, stencil_dir_df({cy[c][0], cyl[c][0]}, {cy[c][1], cyl[c][1]},
-                                                     {cy[c][2], cyl[c][2]}, y > 0, y + 1 < n2, sc.has_rsum[1],
-                                                     sh[c][0][ty][tx + 1], sh[c][1][ty][tx + 1],
-                                                     sh[c][0][ty + 2][tx + 1], sh[c][1][ty + 2][tx + 1], hc[c],
-                                                     lc[c]));
-                acc = df_add(acc, stencil_dir_df({sc.hs[dz][z], sc.hsl[dz][z]}, {sc.hd[dz][z], sc.hdl[dz][z]},
-                                                 {sc.rsum[dz][z], sc.rsl[dz][z]}, z > 0, z + 1 < n3,
-                                                 sc.has_rsum[dz], hp[c], lp[c], hn[c], ln[c], hc[c], lc[c]));
-                acc = df_add(acc, g[c]);
-                fmax_[c] = fmaxf(fmax_[c], fabsf(acc.hi));
-                if (!a.fx_measure)
-                    store_fx((__half *)Fp + 4 * (int64_t)N * c, (int64_t)N, (int64_t)(pz + col), acc,
-                             a.fxs->inv[c], over);
-            }
-        } else if (in) {
+        if (in) {
             float g[2];
             react_df(m, dfl{hc[0], lc[0]}, dfl{hc[1], lc[1]}, g[0], g[1]);
             float F[2];
@@ -2223,14 +2292,183 @@ __global__ void __launch_bounds__(TX * TY, FX ? 3 : 1) k_rhs_tiled(const __grid_
             lc[c] = ln[c];
         }
     }
-    if constexpr (FX) {
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            const unsigned mb = __reduce_max_sync(0xffffffffu, __float_as_uint(fmax_[c]));
-            if ((threadIdx.x & 31) == 0 && mb) atomicMax(&a.fxs->maxbits[c], mb);
+}
+
+// F = K U + g(U) of an FX plan (DS_PREC_F16X10 / F16X13): both components in
+// the packed double-float form above, written as FX planes of scale slots 0
+// and 1 ([c][4][N] halves), and the largest |F_c| recorded for the next
+// rescale (fx_measure: recorded only).  Tiles of TX x TY points march along
+// the last direction over TZ planes; the plane's head/low parts go to a
+// double-buffered shared tile with a one-point halo (one barrier per plane),
+// the halo loaded by the first 2 (TX + TY) threads.  One-dimensional grid,
+// tile b of a problem at (b % gx, b / gx % gy, b / (gx gy)); grouped launches
+// find their problem in the block prefix.  N < 2^31.
+template <int TX, int TY, int TZ, bool GROUPED>
+__global__ void __launch_bounds__(TX * TY, 3) k_rhs_fx(const __grid_constant__ RhsArgs a0,
+                                                       const RhsArgs *__restrict__ gtab,
+                                                       const int *__restrict__ gprefix, int ginst)
+{
+    constexpr int HX = TX + 2, HY = TY + 2;
+    constexpr int NHALO = TY > 1 ? 2 * (TX + TY) : 2;
+    static_assert(NHALO <= TX * TY, "one halo point per thread");
+    __shared__ float4 sh[2][HY][HX];   // [buffer][y][x]: (head u, head v, low u, low v)
+    int gi = 0, lb = (int)blockIdx.x;
+    if (GROUPED) {
+        int lo = 0, hi = ginst - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (gprefix[mid] <= (int)blockIdx.x) lo = mid;
+            else hi = mid - 1;
         }
-        if (over) atomicExch(&a.fxs->overflow, 1);
+        gi = lo;
+        lb = (int)blockIdx.x - gprefix[lo];
     }
+    const RhsArgs &a = GROUPED ? gtab[gi] : a0;
+    const int bx = lb % a.gx, by = (lb / a.gx) % a.gy, bz = lb / (a.gx * a.gy);
+    const double *__restrict__ U = a.U;
+    const int d = a.s0.d, dz = d - 1;
+    const int n1 = (int)a.s0.n[0], n2 = d == 3 ? (int)a.s0.n[1] : 1, n3 = (int)a.s0.n[dz];
+    const int N = (int)a.N;
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    const int x = bx * TX + tx, y = by * TY + ty;
+    const bool in = x < n1 && y < n2;
+    const int z0 = bz * TZ, z1 = min(z0 + TZ, n3);
+    const int plane = n1 * n2;
+    const int col = y * n1 + x;
+    // halo point of this thread: rows above and below the tile, then the
+    // columns left and right of it (2D: the two columns only)
+    int hy = 0, hx = 0, hoff = 0;
+    bool hv = false;
+    if ((int)threadIdx.x < NHALO) {
+        const int h = threadIdx.x;
+        int gx, gy;
+        if (TY > 1 && h < 2 * TX) {
+            const bool top = h < TX;
+            hx = (top ? h : h - TX) + 1;
+            hy = top ? 0 : TY + 1;
+            gx = bx * TX + hx - 1;
+            gy = top ? by * TY - 1 : by * TY + TY;
+        } else {
+            const int k = TY > 1 ? h - 2 * TX : h;
+            const bool left = k < TY;
+            hy = (left ? k : k - TY) + 1;
+            hx = left ? 0 : TX + 1;
+            gx = left ? bx * TX - 1 : bx * TX + TX;
+            gy = by * TY + hy - 1;
+        }
+        hv = gx >= 0 && gx < n1 && gy >= 0 && gy < n2;
+        hoff = hv ? gy * n1 + gx : 0;
+    }
+    // the x and y rows' coefficients; plain: the second-difference form applies
+    const float4 *__restrict__ cx = a.cf[0];
+    const float4 *__restrict__ cy = a.cf[TY > 1 ? 1 : 0];
+    const float4 *__restrict__ cz = a.cf[dz];
+    float4 hsx = {}, hsy = {};
+    bool plainx = false, plainy = false;
+    if (in) {
+        hsx = cx[x];
+        const float4 hd = cx[n1 + x], rs = cx[2 * n1 + x];
+        plainx = x > 0 && x + 1 < n1 && hd.x == 0.0f && hd.y == 0.0f && rs.x == 0.0f && rs.y == 0.0f;
+        if (TY > 1) {
+            hsy = cy[y];
+            const float4 hdy = cy[n2 + y], rsy = cy[2 * n2 + y];
+            plainy = y > 0 && y + 1 < n2 && hdy.x == 0.0f && hdy.y == 0.0f && rsy.x == 0.0f && rsy.y == 0.0f;
+        }
+    }
+    const float2 inv = make_float2(a.fxs->inv[0], a.fxs->inv[1]);
+    __half *const Fx = (__half *)a.Fp;
+    float2 Hc = {}, Lc = {}, Hp = {}, Lp = {}, Hn = {}, Ln = {};
+    float fm0 = 0.0f, fm1 = 0.0f;
+    bool over = false;
+    double rn0 = 0.0, rn1 = 0.0, rh0 = 0.0, rh1 = 0.0;   // raw values loaded one plane ahead
+    if (in) {
+        const int p = z0 * plane + col;
+        split_hilo(U[p], Hc.x, Lc.x);
+        split_hilo(U[N + p], Hc.y, Lc.y);
+        if (z0 > 0) {
+            split_hilo(U[p - plane], Hp.x, Lp.x);
+            split_hilo(U[N + p - plane], Hp.y, Lp.y);
+        }
+        if (z0 + 1 < n3) {
+            rn0 = U[p + plane];
+            rn1 = U[N + p + plane];
+        }
+    }
+    if (hv) {
+        rh0 = U[z0 * plane + hoff];
+        rh1 = U[N + z0 * plane + hoff];
+    }
+    for (int z = z0; z < z1; ++z) {
+        float4(*const buf)[HX] = sh[(z - z0) & 1];
+        const bool more = z + 1 < z1;
+        const int pz = z * plane;
+        if (in) {
+            if (z + 1 < n3) {
+                split_hilo(rn0, Hn.x, Ln.x);
+                split_hilo(rn1, Hn.y, Ln.y);
+            }
+            buf[ty + 1][tx + 1] = make_float4(Hc.x, Hc.y, Lc.x, Lc.y);
+            if (more && z + 2 < n3) {
+                rn0 = U[pz + 2 * plane + col];
+                rn1 = U[N + pz + 2 * plane + col];
+            }
+        }
+        if (hv) {
+            float4 q;
+            split_hilo(rh0, q.x, q.z);
+            split_hilo(rh1, q.y, q.w);
+            buf[hy][hx] = q;
+            if (more) {
+                rh0 = U[pz + plane + hoff];
+                rh1 = U[N + pz + plane + hoff];
+            }
+        }
+        // one barrier per plane: a thread writes this buffer again two planes on,
+        // after every thread has passed the next plane's barrier
+        __syncthreads();
+        if (in) {
+            float2 Sh, Sl;
+            f2react(a.m, Hc, Lc, Sh, Sl);
+            const float2 Hc2 = f2mul(Hc, make_float2(-2.0f, -2.0f));
+            f2row(plainx, hsx, cx, n1, x, x > 0, x + 1 < n1, buf[ty + 1][tx], buf[ty + 1][tx + 2], Hc, Lc, Hc2, Sh,
+                  Sl);
+            if (TY > 1)
+                f2row(plainy, hsy, cy, n2, y, y > 0, y + 1 < n2, buf[ty][tx + 1], buf[ty + 2][tx + 1], Hc, Lc, Hc2,
+                      Sh, Sl);
+            {
+                const float4 hsz = __ldg(cz + z), hdz = __ldg(cz + n3 + z), rsz = __ldg(cz + 2 * n3 + z);
+                const bool plainz =
+                    z > 0 && z + 1 < n3 && hdz.x == 0.0f && hdz.y == 0.0f && rsz.x == 0.0f && rsz.y == 0.0f;
+                f2row(plainz, hsz, cz, n3, z, z > 0, z + 1 < n3, make_float4(Hp.x, Hp.y, Lp.x, Lp.y),
+                      make_float4(Hn.x, Hn.y, Ln.x, Ln.y), Hc, Lc, Hc2, Sh, Sl);
+            }
+            fm0 = fmaxf(fm0, fabsf(Sh.x));
+            fm1 = fmaxf(fm1, fabsf(Sh.y));
+            if (!a.fx_measure) {
+                const float2 vh = f2mul(Sh, inv), vl = f2mul(Sl, inv);
+                over = over || fmaxf(fabsf(vh.x), fabsf(vh.y)) > kFxRangeMax;
+                __half2 q[4];
+                fx_split2v(vh, vl, q);
+                __half *const o = Fx + pz + col;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    o[k * N] = __low2half(q[k]);
+                    o[(4 + k) * N] = __high2half(q[k]);
+                }
+            }
+        }
+        Hp = Hc;
+        Lp = Lc;
+        Hc = Hn;
+        Lc = Ln;
+    }
+    const unsigned m0 = __reduce_max_sync(0xffffffffu, __float_as_uint(fm0));
+    const unsigned m1 = __reduce_max_sync(0xffffffffu, __float_as_uint(fm1));
+    if ((threadIdx.x & 31) == 0) {
+        if (m0) atomicMax(&a.fxs->maxbits[0], m0);
+        if (m1) atomicMax(&a.fxs->maxbits[1], m1);
+    }
+    if (over) atomicExch(&a.fxs->overflow, 1);
 }
 
 // tile shapes: 3D 32 x 8 (x, y) tiles over 32 planes; 2D 128-wide x tiles over 8 rows
@@ -2280,10 +2518,9 @@ static void launch_rhs_group(int d, const RhsArgs *tab, const int *prefix, int n
 {
     if (fx) {
         if (d == 3)
-            k_rhs_tiled<RT3_X, RT3_Y, RT3_Z, int32_t, true, true>
-                <<<blocks, RT3_X * RT3_Y, 0, st>>>(RhsArgs{}, tab, prefix, ninst);
+            k_rhs_fx<RT3_X, RT3_Y, RT3_Z, true><<<blocks, RT3_X * RT3_Y, 0, st>>>(RhsArgs{}, tab, prefix, ninst);
         else
-            k_rhs_tiled<RT2_X, 1, RT2_Z, int32_t, true, true><<<blocks, RT2_X, 0, st>>>(RhsArgs{}, tab, prefix, ninst);
+            k_rhs_fx<RT2_X, 1, RT2_Z, true><<<blocks, RT2_X, 0, st>>>(RhsArgs{}, tab, prefix, ninst);
         return;
     }
     if (d == 3)
@@ -3389,7 +3626,8 @@ struct MixedPlan {
     bf16 *Z2 = nullptr;        // [3k][3][N] (d >= 3)
     float *incF = nullptr;     // [2][3][N]
     float *incD = nullptr;     // [2][N]
-    float *bands = nullptr;    // FP32 bands [c][mu][lo, up, rowsum][n_mu]
+    float *bands = nullptr;    // FP32 bands [c][mu][hs, hd, rowsum][n_mu]
+    float4 *cf4 = nullptr;     // FX: [mu][hs, hd, rowsum][n_mu] as (head u, head v, low u, low v)
     bool rhs_tiled = false;    // k_rhs_tiled (d <= 3) instead of k_rhs_planes
     float *part_ws = nullptr;  // split-K partials
     float *sk_ws = nullptr;    // stream-K partial slots
@@ -3542,8 +3780,10 @@ ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatu
     {
         int64_t tot = 0;
         for (int mu = 0; mu < d; ++mu) tot += 2 * 3 * mp->n[mu];
-        // FX plans also keep the FP32 remainders (lo parts) at offset tot
-        std::vector<float> hb(fx ? 2 * tot : tot);
+        std::vector<float> hb(tot);
+        // FX plans: the same coefficients as head + low quadruples of both
+        // components, [mu][hs, hd, rowsum][n_mu]
+        std::vector<float4> cq(fx ? tot / 2 : 0);
         int64_t off = 0;
         for (int c = 0; c < 2; ++c) {
             mp->stf[c].d = d;
@@ -3558,6 +3798,7 @@ ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatu
                 mp->stf[c].shift[mu] = 31 + l;
                 mp->stf[c].magic[mu] = (unsigned long long)(((unsigned __int128)1 << (31 + l)) / (unsigned)nm) + 1ull;
             }
+            int64_t oq = 0;
             for (int mu = 0; mu < d; ++mu) {
                 const int64_t nm = mp->n[mu];
                 std::vector<double> band(3 * nm);
@@ -3571,22 +3812,30 @@ ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatu
                     hb[off + nm + i] = (float)hd;
                     hb[off + 2 * nm + i] = (float)rsum;
                     if (fx) {
-                        hb[tot + off + i] = (float)(hs - (double)(float)hs);
-                        hb[tot + off + nm + i] = (float)(hd - (double)(float)hd);
-                        hb[tot + off + 2 * nm + i] = (float)(rsum - (double)(float)rsum);
+                        const double v3[3] = {hs, hd, rsum};
+                        for (int k = 0; k < 3; ++k) {
+                            float4 &q = cq[oq + k * nm + i];
+                            const float h = (float)v3[k], l = (float)(v3[k] - (double)h);
+                            (c == 0 ? q.x : q.y) = h;
+                            (c == 0 ? q.z : q.w) = l;
+                        }
                     }
                     if (rsum != 0.0) mp->stf[c].has_rsum[mu] = 1;
                 }
                 mp->stf[c].hs[mu] = (const float *)(intptr_t)off;   // fixed up below
                 off += 3 * nm;
+                oq += 3 * nm;
             }
         }
-        if (cudaMalloc(&mp->bands, sizeof(float) * hb.size()) != cudaSuccess) {
+        if (cudaMalloc(&mp->bands, sizeof(float) * hb.size()) != cudaSuccess ||
+            (fx && cudaMalloc(&mp->cf4, sizeof(float4) * cq.size()) != cudaSuccess)) {
             cudaGetLastError();
+            cudaFree(mp->bands);
             delete mp;
             return fail(DS_ERR_OOM, "band copy");
         }
         cudaMemcpy(mp->bands, hb.data(), sizeof(float) * hb.size(), cudaMemcpyHostToDevice);
+        if (fx) cudaMemcpy(mp->cf4, cq.data(), sizeof(float4) * cq.size(), cudaMemcpyHostToDevice);
         for (int c = 0; c < 2; ++c)
             for (int mu = 0; mu < d; ++mu) {
                 const int64_t o = (int64_t)(intptr_t)mp->stf[c].hs[mu];
@@ -3594,11 +3843,6 @@ ds_status mixed_plan_create(const ds_grid *grid, const ds_phi_set *set, DevStatu
                 mp->stf[c].hs[mu] = mp->bands + o;
                 mp->stf[c].hd[mu] = mp->bands + o + nm;
                 mp->stf[c].rsum[mu] = mp->bands + o + 2 * nm;
-                if (fx) {
-                    mp->stf[c].hsl[mu] = mp->bands + tot + o;
-                    mp->stf[c].hdl[mu] = mp->bands + tot + o + nm;
-                    mp->stf[c].rsl[mu] = mp->bands + tot + o + 2 * nm;
-                }
             }
     }
     const int64_t N = mp->N;
@@ -3988,6 +4232,7 @@ void mixed_plan_destroy(MixedPlan *mp)
     cudaFree(mp->incF);
     cudaFree(mp->incD);
     cudaFree(mp->bands);
+    cudaFree(mp->cf4);
     cudaFree(mp->part_ws);
     cudaFree(mp->sk_ws);
     cudaFree(mp->sk_cnt);
@@ -4019,16 +4264,29 @@ static double launch_flops(const ModeLaunch &L, int64_t N)
 
 // F = K U + g(U) as FX planes (F_c in scale slot c); measure: only record
 // the largest |F_c|
-static void launch_rhs_fx(MixedPlan *mp, const Model &model, double *U, bool measure, cudaStream_t st)
+static RhsArgs rhs_args_fx(const MixedPlan *mp, const Model &model, const double *U, bool measure)
 {
     RhsArgs a = rhs_args(mp->stf[0], mp->stf[1], model_df(model), mp->N, U, mp->Fp);
     a.fxs = mp->fxs;
     a.fx_measure = measure ? 1 : 0;
+    int64_t o = 0;
+    for (int mu = 0; mu < mp->d; ++mu) {
+        a.cf[mu] = mp->cf4 + o;
+        o += 3 * mp->n[mu];
+    }
+    return a;
+}
+
+// one-dimensional grid of the tiles (FX plans have fewer than 2^31 points)
+static void launch_rhs_fx(MixedPlan *mp, const Model &model, double *U, bool measure, cudaStream_t st)
+{
+    const RhsArgs a = rhs_args_fx(mp, model, U, measure);
     const dim3 g = rhs_tiles(mp->stf[0]);
+    const unsigned blocks = g.x * g.y * g.z;
     if (mp->d == 3)
-        k_rhs_tiled<RT3_X, RT3_Y, RT3_Z, int32_t, false, true><<<g, RT3_X * RT3_Y, 0, st>>>(a, nullptr, nullptr, 0);
+        k_rhs_fx<RT3_X, RT3_Y, RT3_Z, false><<<blocks, RT3_X * RT3_Y, 0, st>>>(a, nullptr, nullptr, 0);
     else
-        k_rhs_tiled<RT2_X, 1, RT2_Z, int32_t, false, true><<<g, RT2_X, 0, st>>>(a, nullptr, nullptr, 0);
+        k_rhs_fx<RT2_X, 1, RT2_Z, false><<<blocks, RT2_X, 0, st>>>(a, nullptr, nullptr, 0);
 }
 
 int enqueue_rhs_mixed(MixedPlan *mp, const Model &model, double *U, cudaStream_t st)
@@ -4386,11 +4644,8 @@ ds_status mixed_group_create(const std::vector<MixedPlan *> &mps, const std::vec
         for (int i = 0; i < ninst && tiled; ++i) {
             const MixedPlan *mp = mps[i];
             tiled = mp->rhs_tiled && mp->N < ((int64_t)1 << 31);
-            rt.push_back(rhs_args(mp->stf[0], mp->stf[1], model_df(models[i]), mp->N, U[i], mp->Fp));
-            if (G->fx) {
-                rt.back().fxs = mp->fxs;
-                rt.back().fx_measure = 0;
-            }
+            rt.push_back(G->fx ? rhs_args_fx(mp, models[i], U[i], false)
+                               : rhs_args(mp->stf[0], mp->stf[1], model_df(models[i]), mp->N, U[i], mp->Fp));
             rp.push_back((int)blocks);
             const dim3 g = rhs_tiles(mp->stf[0]);
             blocks += (int64_t)g.x * g.y * g.z;
