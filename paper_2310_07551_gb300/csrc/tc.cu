@@ -330,6 +330,29 @@ __device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t ad, uint64_t bd, u
         "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
         : "memory");
 }
+// The same MMA with the A operand kept in the tensor core's collector buffer
+// across consecutive MMAs that share it: C = 1 reads A from shared memory and
+// keeps it, 2 reuses it, 3 reuses it for the last time.
+template <int C>
+__device__ __forceinline__ void mma_f16_coll(uint32_t d, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc)
+{
+    static_assert(C >= 1 && C <= 3, "collector usage: fill, use, lastuse");
+    if constexpr (C == 1)
+        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                     "tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+                     "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                     : "memory");
+    else if constexpr (C == 2)
+        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                     "tcgen05.mma.cta_group::1.kind::f16.collector::a::use [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+                     "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                     : "memory");
+    else
+        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                     "tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+                     "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                     : "memory");
+}
 __device__ __forceinline__ void mma_commit(uint32_t bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
@@ -1174,25 +1197,35 @@ __global__ void __launch_bounds__(kThreads, 1)
                                          : sdesc(sA + p * A_PLANE + ks * 2048, A_PLANE / 2, 1024, kSw128);
                         };
                         auto bd = [&](int p, int ks) { return sdesc(sB + p * B_PLANE + ks * 32, 16, 512, kSw64); };
-                        // A (= d) | B1 | B2 | B3, one tile at a time
+                        // A (= d) | B1 | B2 | B3, one tile at a time.  The products are
+                        // grouped by their A part, which the collector buffer holds
+                        // across its group (A read from shared memory 4 times per K
+                        // step instead of 10); each accumulator's first product is
+                        // in the h group.
                         const uint32_t dB1 = tmem + BN, dB2 = tmem + 2 * BN, dB3 = tmem + 3 * BN;
 #pragma unroll
                         for (int ks = 0; ks < BK / 16; ++ks) {
                             const uint32_t first = (it > it0 || ks > 0) ? 1u : 0u;
-                            mma_bf16(d, ad(0, ks), bd(0, ks), idesc, first);
-                            mma_bf16(dB1, ad(0, ks), bd(1, ks), idesc, first);
-                            mma_bf16(dB1, ad(1, ks), bd(0, ks), idesc, 1u);
-                            mma_bf16(dB2, ad(1, ks), bd(1, ks), idesc, first);
-                            mma_bf16(dB2, ad(0, ks), bd(2, ks), idesc, 1u);
-                            mma_bf16(dB2, ad(2, ks), bd(0, ks), idesc, 1u);
-                            mma_bf16(dB3, ad(1, ks), bd(2, ks), idesc, first);
-                            mma_bf16(dB3, ad(2, ks), bd(1, ks), idesc, 1u);
-                            mma_bf16(dB3, ad(0, ks), bd(3, ks), idesc, 1u);
-                            mma_bf16(dB3, ad(3, ks), bd(0, ks), idesc, 1u);
+                            const uint64_t a0 = ad(0, ks), a1 = ad(1, ks), a2 = ad(2, ks), a3 = ad(3, ks);
+                            mma_f16_coll<1>(d, a0, bd(0, ks), idesc, first);     // h h'
+                            mma_f16_coll<2>(dB1, a0, bd(1, ks), idesc, first);   // h s1'
+                            mma_f16_coll<2>(dB2, a0, bd(2, ks), idesc, first);   // h s2'
+                            mma_f16_coll<3>(dB3, a0, bd(3, ks), idesc, first);   // h s3'
+                            mma_f16_coll<1>(dB1, a1, bd(0, ks), idesc, 1u);      // s1 h'
+                            mma_f16_coll<2>(dB2, a1, bd(1, ks), idesc, 1u);      // s1 s1'
                             if (a.fx_extra) {
-                                mma_bf16(dB3, ad(1, ks), bd(3, ks), idesc, 1u);
-                                mma_bf16(dB3, ad(3, ks), bd(1, ks), idesc, 1u);
-                                mma_bf16(dB3, ad(2, ks), bd(2, ks), idesc, 1u);
+                                mma_f16_coll<2>(dB3, a1, bd(2, ks), idesc, 1u);  // s1 s2'
+                                mma_f16_coll<3>(dB3, a1, bd(3, ks), idesc, 1u);  // s1 s3'
+                                mma_f16_coll<1>(dB2, a2, bd(0, ks), idesc, 1u);  // s2 h'
+                                mma_f16_coll<2>(dB3, a2, bd(1, ks), idesc, 1u);  // s2 s1'
+                                mma_f16_coll<3>(dB3, a2, bd(2, ks), idesc, 1u);  // s2 s2'
+                                mma_f16_coll<1>(dB3, a3, bd(0, ks), idesc, 1u);  // s3 h'
+                                mma_f16_coll<3>(dB3, a3, bd(1, ks), idesc, 1u);  // s3 s1'
+                            } else {
+                                mma_f16_coll<3>(dB3, a1, bd(2, ks), idesc, 1u);  // s1 s2'
+                                mma_f16_coll<1>(dB2, a2, bd(0, ks), idesc, 1u);  // s2 h'
+                                mma_f16_coll<3>(dB3, a2, bd(1, ks), idesc, 1u);  // s2 s1'
+                                mma_bf16(dB3, a3, bd(0, ks), idesc, 1u);         // s3 h'
                             }
                         }
                     } else {
