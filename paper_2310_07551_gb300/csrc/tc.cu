@@ -2358,10 +2358,12 @@ __global__ void __launch_bounds__(TX * TY, 3) k_rhs_fx(const __grid_constant__ R
     }
     const RhsArgs &a = GROUPED ? gtab[gi] : a0;
     const int bx = lb % a.gx, by = (lb / a.gx) % a.gy, bz = lb / (a.gx * a.gy);
+    // the two components' state (offsets within one plane set stay below 2^31)
     const double *__restrict__ U = a.U;
+    const double *__restrict__ U1 = a.U + a.N;
     const int d = a.s0.d, dz = d - 1;
     const int n1 = (int)a.s0.n[0], n2 = d == 3 ? (int)a.s0.n[1] : 1, n3 = (int)a.s0.n[dz];
-    const int N = (int)a.N;
+    const int64_t N = a.N;
     const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
     const int x = bx * TX + tx, y = by * TY + ty;
     const bool in = x < n1 && y < n2;
@@ -2417,19 +2419,19 @@ __global__ void __launch_bounds__(TX * TY, 3) k_rhs_fx(const __grid_constant__ R
     if (in) {
         const int p = z0 * plane + col;
         split_hilo(U[p], Hc.x, Lc.x);
-        split_hilo(U[N + p], Hc.y, Lc.y);
+        split_hilo(U1[p], Hc.y, Lc.y);
         if (z0 > 0) {
             split_hilo(U[p - plane], Hp.x, Lp.x);
-            split_hilo(U[N + p - plane], Hp.y, Lp.y);
+            split_hilo(U1[p - plane], Hp.y, Lp.y);
         }
         if (z0 + 1 < n3) {
             rn0 = U[p + plane];
-            rn1 = U[N + p + plane];
+            rn1 = U1[p + plane];
         }
     }
     if (hv) {
         rh0 = U[z0 * plane + hoff];
-        rh1 = U[N + z0 * plane + hoff];
+        rh1 = U1[z0 * plane + hoff];
     }
     for (int z = z0; z < z1; ++z) {
         float4(*const buf)[HX] = sh[(z - z0) & 1];
@@ -2443,7 +2445,7 @@ __global__ void __launch_bounds__(TX * TY, 3) k_rhs_fx(const __grid_constant__ R
             buf[ty + 1][tx + 1] = make_float4(Hc.x, Hc.y, Lc.x, Lc.y);
             if (more && z + 2 < n3) {
                 rn0 = U[pz + 2 * plane + col];
-                rn1 = U[N + pz + 2 * plane + col];
+                rn1 = U1[pz + 2 * plane + col];
             }
         }
         if (hv) {
@@ -2453,7 +2455,7 @@ __global__ void __launch_bounds__(TX * TY, 3) k_rhs_fx(const __grid_constant__ R
             buf[hy][hx] = q;
             if (more) {
                 rh0 = U[pz + plane + hoff];
-                rh1 = U[N + pz + plane + hoff];
+                rh1 = U1[pz + plane + hoff];
             }
         }
         // one barrier per plane: a thread writes this buffer again two planes on,
@@ -2485,7 +2487,7 @@ __global__ void __launch_bounds__(TX * TY, 3) k_rhs_fx(const __grid_constant__ R
                 __half *const o = Fx + pz + col;
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    o[k * N] = __low2half(q[k]);
+                    o[k * N] = __low2half(q[k]);   // 64-bit plane offsets: 7 N may pass 2^31
                     o[(4 + k) * N] = __high2half(q[k]);
                 }
             }
